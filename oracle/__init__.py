@@ -1,0 +1,201 @@
+"""FP64 CPU oracle for the DG right-hand side (Tonicello & Ihme, arXiv 2306.05002).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` are the only users of this package; the product
+path (``paper_2306_05002_gb300``) never imports it, and this package imports
+nothing from the product.  The arithmetic lives in ``dg_oracle.c`` (plain C,
+FP64, compiled with FMA contraction disabled); this module only marshals numpy
+arrays through ctypes.
+
+Parity status of each function is pinned by ``tests/test_oracle_*.py`` against
+closed forms, invariants of the paper's scheme (Sec. 3: interface equilibrium,
+conservation, free stream), the symmetry of the SIP bilinear form, textbook
+limits of the stiffened-gas closure and convergence rates.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dg_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+BC = {"periodic": 0, "noslip": 1, "slip": 2}
+NV = 7
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (gcc, FP64, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "dg_oracle.h"))
+    ):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC", "-shared",
+             "-o", tmp, _SRC, "-lm"]
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("p", ctypes.c_int),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("bc", ctypes.c_int * 4),
+        ("gamma", ctypes.c_double * 2), ("pinf", ctypes.c_double * 2),
+        ("rho0", ctypes.c_double * 2), ("mu", ctypes.c_double * 2),
+        ("sigma", ctypes.c_double), ("g", ctypes.c_double * 2),
+        ("Gamma", ctypes.c_double), ("eps", ctypes.c_double), ("c_ip", ctypes.c_double),
+        ("viscous", ctypes.c_int), ("gravity", ctypes.c_int), ("surface_tension", ctypes.c_int),
+    ]
+
+
+@dataclass
+class Problem:
+    """Plain description of one DG problem (mesh, order, closure, model constants)."""
+    dim: int = 2
+    nx: int = 4
+    ny: int = 4
+    p: int = 3
+    x0: float = 0.0
+    x1: float = 1.0
+    y0: float = 0.0
+    y1: float = 1.0
+    bc: tuple = ("periodic",) * 4
+    gamma: tuple = (1.4, 4.4)
+    pinf: tuple = (0.0, 6e8)
+    rho0: tuple = (1.0, 1000.0)
+    mu: tuple = (0.0, 0.0)
+    sigma: float = 0.0
+    g: tuple = (0.0, 0.0)
+    Gamma: float = 1.0
+    eps: float = 0.01
+    c_ip: float = 1.0
+    viscous: bool = False
+    gravity: bool = False
+    surface_tension: bool = False
+
+    @property
+    def Np(self) -> int:
+        return (self.p + 1) ** self.dim
+
+    @property
+    def N(self) -> int:
+        return self.nx * self.ny * self.Np
+
+    def _c(self) -> _Problem:
+        s = _Problem()
+        s.dim, s.nx, s.ny, s.p = self.dim, self.nx, self.ny, self.p
+        s.x0, s.x1, s.y0, s.y1 = self.x0, self.x1, self.y0, self.y1
+        for i, b in enumerate(self.bc):
+            s.bc[i] = BC[b] if isinstance(b, str) else int(b)
+        for i in range(2):
+            s.gamma[i], s.pinf[i] = self.gamma[i], self.pinf[i]
+            s.rho0[i], s.mu[i], s.g[i] = self.rho0[i], self.mu[i], self.g[i]
+        s.sigma, s.Gamma, s.eps, s.c_ip = self.sigma, self.Gamma, self.eps, self.c_ip
+        s.viscous, s.gravity, s.surface_tension = int(self.viscous), int(self.gravity), int(self.surface_tension)
+        return s
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        pp = ctypes.POINTER(_Problem)
+        _lib.orc_gll.argtypes = [ctypes.c_int, dp, dp]
+        _lib.orc_lagrange_deriv.argtypes = [ctypes.c_int, dp, dp]
+        _lib.orc_num_nodes.argtypes = [pp]
+        _lib.orc_num_nodes.restype = ctypes.c_long
+        _lib.orc_nodes.argtypes = [pp, dp, dp]
+        _lib.orc_primitives.argtypes = [pp, dp, dp]
+        _lib.orc_rhs.argtypes = [pp, dp, dp, dp, dp]
+        _lib.orc_rk3.argtypes = [pp, dp, ctypes.c_double, ctypes.c_int]
+        _lib.orc_diag.argtypes = [pp, dp, dp]
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with status {rc}")
+
+
+def gll(p: int):
+    """GLL nodes and weights on [-1, 1]."""
+    xi = np.zeros(p + 1)
+    wt = np.zeros(p + 1)
+    _check(lib().orc_gll(p, _ptr(xi), _ptr(wt)), "gll")
+    return xi, wt
+
+
+def lagrange_deriv(p: int, xi):
+    """D[a, b] = l_b'(xi_a)."""
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    D = np.zeros((p + 1, p + 1))
+    _check(lib().orc_lagrange_deriv(p, _ptr(xi), _ptr(D)), "lagrange_deriv")
+    return D
+
+
+def nodes(pb: Problem):
+    x = np.zeros(pb.N)
+    y = np.zeros(pb.N)
+    s = pb._c()
+    _check(lib().orc_nodes(ctypes.byref(s), _ptr(x), _ptr(y)), "nodes")
+    return x, y
+
+
+def primitives(pb: Problem, w):
+    """rho, u, v, P, c, B at every node, shape (6, N)."""
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(NV, pb.N)
+    out = np.zeros((6, pb.N))
+    s = pb._c()
+    _check(lib().orc_primitives(ctypes.byref(s), _ptr(w), _ptr(out)), "primitives")
+    return out
+
+
+def rhs(pb: Problem, w, want_scale: bool = False, want_parts: bool = False):
+    """L = M^-1 R(w), shape (7, N); optionally the rounding scale S and the parts."""
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(NV, pb.N)
+    L = np.zeros((NV, pb.N))
+    S = np.zeros((NV, pb.N)) if want_scale else None
+    parts = np.zeros((3, NV, pb.N)) if want_parts else None
+    s = pb._c()
+    _check(lib().orc_rhs(ctypes.byref(s), _ptr(w), _ptr(L), _ptr(S), _ptr(parts)), "rhs")
+    out = [L]
+    if want_scale:
+        out.append(S)
+    if want_parts:
+        out.append(parts)
+    return out[0] if len(out) == 1 else tuple(out)
+
+
+def rk3(pb: Problem, w, dt: float, nsteps: int):
+    """Return w after nsteps SSP-RK3 steps (input left untouched)."""
+    w = np.array(w, dtype=np.float64).reshape(NV, pb.N).copy()
+    s = pb._c()
+    _check(lib().orc_rk3(ctypes.byref(s), _ptr(w), float(dt), int(nsteps)), "rk3")
+    return w
+
+
+def diag(pb: Problem, w):
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(NV, pb.N)
+    out = np.zeros(16)
+    s = pb._c()
+    _check(lib().orc_diag(ctypes.byref(s), _ptr(w), _ptr(out)), "diag")
+    return out

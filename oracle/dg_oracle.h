@@ -1,0 +1,72 @@
+/*
+ * dg_oracle.h -- plain FP64 CPU oracle for the DG right-hand side of the
+ * quasi-conservative five-equation two-phase model coupled to the Allen-Cahn
+ * phase field and an advected level set (Tonicello & Ihme, arXiv 2306.05002).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code exists to check the GPU library
+ * against the paper.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load it; the product path never does.
+ * It shares no code, header, table or constant generator with the CUDA path.
+ *
+ * State layout (shared with the library only as a documented convention):
+ *   w[v * N + e * Np + a],  v = 0..6 = [phi, psi, m1, m2, rho_u, rho_v, rho_E]
+ *   N  = E * Np,  E = nx * ny elements, e = ex + nx * ey,
+ *   Np = (p+1)^dim,  a = i + (p+1) * j with (i, j) the GLL node indices.
+ *   phi = phi_1 (volume fraction of phase 1), m_l = rho_l phi_l.
+ */
+#ifndef DG_ORACLE_H
+#define DG_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_NV 7
+enum { ORC_PHI = 0, ORC_PSI = 1, ORC_M1 = 2, ORC_M2 = 3, ORC_RU = 4, ORC_RV = 5, ORC_RE = 6 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_NOSLIP = 1, ORC_BC_SLIP = 2 };
+
+typedef struct {
+  int dim;            /* 1 or 2 */
+  int nx, ny;         /* elements per direction (ny = 1 when dim = 1) */
+  int p;              /* polynomial order, 1..8 */
+  double x0, x1, y0, y1;
+  int bc[4];          /* west, east, south, north */
+  double gamma[2], pinf[2], rho0[2], mu[2];   /* phase 1, phase 2 */
+  double sigma;       /* surface tension coefficient */
+  double g[2];        /* gravitational acceleration */
+  double Gamma, eps;  /* Allen-Cahn velocity scale and interface thickness */
+  double c_ip;        /* interior-penalty constant: eta = c_ip (p+1)^2 / h */
+  int viscous, gravity, surface_tension;
+} orc_problem;
+
+/* GLL nodes xi[0..p] (ascending) and weights wt[0..p] on [-1, 1]. */
+int orc_gll(int p, double *xi, double *wt);
+/* D[a*(p+1)+b] = l_b'(xi_a), derivative of the b-th Lagrange polynomial. */
+int orc_lagrange_deriv(int p, const double *xi, double *D);
+/* Total number of nodes E * Np. */
+long orc_num_nodes(const orc_problem *pr);
+/* Physical coordinates of every node (y may be NULL for dim = 1). */
+int orc_nodes(const orc_problem *pr, double *x, double *y);
+/* Primitive variables at every node: prim[q * N + n], q = rho, u, v, P, c, B. */
+int orc_primitives(const orc_problem *pr, const double *w, double *prim);
+/*
+ * L = M^-1 R(w).  S (nullable) receives the sum of absolute values of every
+ * contribution to R, also scaled by M^-1, which sets the rounding scale for
+ * parity checks.  parts (nullable, 3 * 7 * N) receives the volume (including
+ * the non-conservative transport), surface (including the symmetric interior
+ * penalty term) and source parts of L separately.
+ */
+int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double *parts);
+/* nsteps of three-stage SSP Runge-Kutta (Shu-Osher form), in place. */
+int orc_rk3(const orc_problem *pr, double *w, double dt, int nsteps);
+/*
+ * Diagnostics: out[0..6] = integrals of the 7 variables, out[7..8] = min/max
+ * phi, out[9..10] = min/max P, out[11..12] = min/max u, out[13..14] =
+ * min/max v, out[15] = number of non-finite state entries.
+ */
+int orc_diag(const orc_problem *pr, const double *w, double *out16);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

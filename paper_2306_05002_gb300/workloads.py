@@ -1,0 +1,241 @@
+"""Seeded synthetic workloads shaped like the paper's test cases (Sec. 4).
+
+This module is shared by the tests and the benchmark; it holds none of the
+DG method's arithmetic.  It only
+
+* places analytic initial conditions at Gauss-Lobatto-Legendre points (found
+  with ``numpy.polynomial.legendre``), in the state layout of the library,
+* writes them in conserved form by solving the stiffened-gas relation of
+  Sec. 2 for the internal energy, rho e = P sum phi_l/(gamma_l-1) +
+  sum phi_l gamma_l Pinf_l/(gamma_l-1), and
+* picks a time step from the pure-phase sound speeds and a CFL number.
+
+Phase 1 is the outer (or upper) phase and phi = phi_1 its volume fraction.
+The interface profile is phi = (1 + tanh(s / (2 eps))) / 2 with s a signed
+distance that grows into phase 1, and the level set is psi = s (Sec. 4.1;
+the sign of psi is chosen so that n = grad psi/|grad psi| points into phase 1,
+which makes the hyperbolic-tangent profile an equilibrium of a_1).
+
+Nothing here is drawn from a dataset: every field is analytic, and every
+random number comes from ``numpy.random.default_rng(seed)``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+from typing import Optional
+
+import numpy as np
+
+AIR = dict(gamma=1.4, pinf=0.0, rho0=1.0)
+WATER = dict(gamma=4.4, pinf=6e8, rho0=1000.0)
+
+
+@dataclass
+class Workload:
+    """A DG problem plus its initial state, time step and step count."""
+    name: str
+    dim: int
+    nx: int
+    ny: int
+    p: int
+    x0: float = 0.0
+    x1: float = 1.0
+    y0: float = 0.0
+    y1: float = 1.0
+    bc: tuple = ("periodic",) * 4
+    gamma: tuple = (1.4, 4.4)
+    pinf: tuple = (0.0, 6e8)
+    rho0: tuple = (1.0, 1000.0)
+    mu: tuple = (0.0, 0.0)
+    sigma: float = 0.0
+    g: tuple = (0.0, 0.0)
+    Gamma: float = 1.0
+    eps: float = 0.01
+    c_ip: float = 1.0
+    viscous: bool = False
+    gravity: bool = False
+    surface_tension: bool = False
+    w: Optional[np.ndarray] = None   # (7, N) float64
+    dt: float = 0.0
+    nsteps: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def Np(self) -> int:
+        return (self.p + 1) ** self.dim
+
+    @property
+    def E(self) -> int:
+        return self.nx * self.ny
+
+    @property
+    def N(self) -> int:
+        return self.E * self.Np
+
+    @property
+    def hx(self) -> float:
+        return (self.x1 - self.x0) / self.nx
+
+    @property
+    def hy(self) -> float:
+        return (self.y1 - self.y0) / self.ny if self.dim == 2 else self.hx
+
+    def problem_kwargs(self) -> dict:
+        """Fields shared by the oracle's and the library's problem descriptions."""
+        keys = ["dim", "nx", "ny", "p", "x0", "x1", "y0", "y1", "bc", "gamma", "pinf", "rho0", "mu",
+                "sigma", "g", "Gamma", "eps", "c_ip", "viscous", "gravity", "surface_tension"]
+        return {k: getattr(self, k) for k in keys}
+
+
+# ---------------------------------------------------------------------------
+# Geometry
+# ---------------------------------------------------------------------------
+
+def gll_points(p: int) -> np.ndarray:
+    """Gauss-Lobatto-Legendre points on [-1, 1]: the end points and the roots of P_p'."""
+    inner = np.polynomial.legendre.Legendre.basis(p).deriv().roots()
+    return np.concatenate([[-1.0], np.sort(inner.real), [1.0]])
+
+
+def node_coords(wl: Workload):
+    """x, y of every node in the state layout: node n = e * Np + i + (p+1) j, e = ex + nx ey."""
+    xi = gll_points(wl.p)
+    P1 = wl.p + 1
+    ex = np.arange(wl.nx)
+    if wl.dim == 1:
+        x = wl.x0 + wl.hx * (ex[:, None] + 0.5 * (xi[None, :] + 1.0))
+        return x.reshape(-1), np.zeros(wl.N)
+    ey = np.arange(wl.ny)
+    # shape (ny, nx, P1[j], P1[i])
+    x = wl.x0 + wl.hx * (ex[None, :, None, None] + 0.5 * (xi[None, None, None, :] + 1.0))
+    y = wl.y0 + wl.hy * (ey[:, None, None, None] + 0.5 * (xi[None, None, :, None] + 1.0))
+    x = np.broadcast_to(x, (wl.ny, wl.nx, P1, P1))
+    y = np.broadcast_to(y, (wl.ny, wl.nx, P1, P1))
+    return np.ascontiguousarray(x).reshape(-1), np.ascontiguousarray(y).reshape(-1)
+
+
+# ---------------------------------------------------------------------------
+# Conserved state from primitive fields
+# ---------------------------------------------------------------------------
+
+def conserved(wl: Workload, phi, psi, P, u, v, rho1=None, rho2=None) -> np.ndarray:
+    """Pack phi, psi, m1, m2, rho u, rho v, rho E (rho_l defaults to the reference densities)."""
+    g1, g2 = wl.gamma
+    pi1, pi2 = wl.pinf
+    rho1 = wl.rho0[0] if rho1 is None else rho1
+    rho2 = wl.rho0[1] if rho2 is None else rho2
+    phi2 = 1.0 - phi
+    m1 = rho1 * phi
+    m2 = rho2 * phi2
+    rho = m1 + m2
+    rhoe = P * (phi / (g1 - 1.0) + phi2 / (g2 - 1.0)) + (phi * g1 * pi1 / (g1 - 1.0) + phi2 * g2 * pi2 / (g2 - 1.0))
+    rhoE = rhoe + 0.5 * rho * (u * u + v * v)
+    w = np.stack([phi, psi, m1, m2, rho * u, rho * v, rhoE]).astype(np.float64)
+    return np.ascontiguousarray(np.broadcast_to(w, (7, wl.N)))
+
+
+def tanh_profile(s, eps):
+    return 0.5 * (1.0 + np.tanh(s / (2.0 * eps)))
+
+
+def stable_dt(wl: Workload, umax: float, P0: float, cfl: float = 0.5) -> float:
+    """CFL time step from the pure-phase sound speeds c_l = sqrt(gamma_l (P + Pinf_l)/rho_l)."""
+    c = max(np.sqrt(wl.gamma[l] * (P0 + wl.pinf[l]) / wl.rho0[l]) for l in range(2))
+    h = min(wl.hx, wl.hy)
+    q = 2 * wl.p + 1
+    dt = cfl * h / (q * (umax + c))
+    # the interior-penalty diffusion operators need a tighter, parabolic limit
+    if wl.Gamma * wl.eps > 0:
+        dt = min(dt, 0.1 * h * h / (q * q * wl.Gamma * wl.eps))
+    if wl.viscous and max(wl.mu) > 0:
+        nu = max(wl.mu) / min(wl.rho0)
+        dt = min(dt, 0.1 * h * h / (q * q * nu))
+    return dt
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+
+def slab_1d(nx: int = 100, p: int = 3, nsteps: int = 1000, u: float = 1.0, P0: float = 1e5) -> Workload:
+    """1D periodic advection of a water slab |x - 0.5| < 0.25 in air, eps = one element width."""
+    wl = Workload(name=f"slab1d_{nx}p{p}", dim=1, nx=nx, ny=1, p=p, bc=("periodic",) * 4,
+                  gamma=(AIR["gamma"], WATER["gamma"]), pinf=(AIR["pinf"], WATER["pinf"]),
+                  rho0=(AIR["rho0"], WATER["rho0"]), nsteps=nsteps)
+    wl.eps = wl.hx
+    wl.Gamma = abs(u)
+    x, _ = node_coords(wl)
+    s = np.abs(x - 0.5) - 0.25          # grows into the air (phase 1)
+    phi = tanh_profile(s, wl.eps)
+    wl.w = conserved(wl, phi, s, P0, u, 0.0)
+    wl.dt = stable_dt(wl, abs(u), P0)
+    wl.meta = dict(P0=P0, u=u, v=0.0)
+    return wl
+
+
+def periodic_distance(x, y, cx, cy):
+    dx = x - cx
+    dy = y - cy
+    dx -= np.round(dx)
+    dy -= np.round(dy)
+    return np.sqrt(dx * dx + dy * dy)
+
+
+def drop_2d(n: int = 64, p: int = 3, seed: int = 2, R: float = 0.15, u: float = 1.0, v: float = 0.5,
+            P0: float = 1e5, eps_h: float = 0.75, nsteps: int = 500, center=None,
+            water_inside: bool = True) -> Workload:
+    """Periodic unit square, water drop (or air bubble) of radius R at a seeded random centre."""
+    rng = np.random.default_rng(seed)
+    cx, cy = rng.uniform(0.0, 1.0, size=2) if center is None else center
+    wl = Workload(name=f"drop2d_{n}x{n}p{p}", dim=2, nx=n, ny=n, p=p, bc=("periodic",) * 4,
+                  gamma=(AIR["gamma"], WATER["gamma"]), pinf=(AIR["pinf"], WATER["pinf"]),
+                  rho0=(AIR["rho0"], WATER["rho0"]), nsteps=nsteps)
+    if not water_inside:  # air bubble in water: phase 1 (outer) is water
+        wl.gamma, wl.pinf, wl.rho0 = wl.gamma[::-1], wl.pinf[::-1], wl.rho0[::-1]
+    wl.eps = eps_h * wl.hx
+    wl.Gamma = float(np.hypot(u, v))
+    x, y = node_coords(wl)
+    s = periodic_distance(x, y, cx, cy) - R
+    phi = tanh_profile(s, wl.eps)
+    wl.w = conserved(wl, phi, s, P0, u, v)
+    wl.dt = stable_dt(wl, float(np.hypot(u, v)), P0)
+    wl.meta = dict(P0=P0, u=u, v=v, cx=float(cx), cy=float(cy), R=R, seed=seed)
+    return wl
+
+
+def rayleigh_taylor(n: int = 256, p: int = 4, seed: int = 3, nsteps: int = 2000, P_top: float = 1e5,
+                    eps_h: float = 0.75, Gamma: float = 2.21, amp: float = 0.01, modes: int = 8) -> Workload:
+    """Viscous Rayleigh-Taylor set-up: heavy phase 1 on top, density ratio 3, no-slip walls,
+    gravity -9.81, surface tension 0.07, hydrostatic pressure, seeded 8-mode interface."""
+    rng = np.random.default_rng(seed)
+    a = rng.normal(size=modes)
+    a /= np.abs(a).sum()
+    theta = rng.uniform(0.0, 2.0 * np.pi, size=modes)
+    g = 9.81
+    rho1, rho2 = 3000.0, 1000.0
+    mu = rho1 * np.sqrt(g) / 3000.0
+    wl = Workload(name=f"rt2d_{n}x{n}p{p}", dim=2, nx=n, ny=n, p=p, bc=("noslip",) * 4,
+                  gamma=(4.4, 4.4), pinf=(6e8, 6e8), rho0=(rho1, rho2), mu=(mu, mu), sigma=0.07,
+                  g=(0.0, -g), Gamma=Gamma, viscous=True, gravity=True, surface_tension=True,
+                  nsteps=nsteps)
+    wl.eps = eps_h * wl.hx
+    x, y = node_coords(wl)
+    k = np.arange(1, modes + 1)
+    eta = 0.5 + amp * np.sum(a[None, :] * np.cos(2 * np.pi * k[None, :] * x[:, None] + theta[None, :]), axis=1)
+    s = y - eta                          # grows into the heavy upper phase 1
+    phi = tanh_profile(s, wl.eps)
+    # hydrostatic pressure P(y) = P_top + g int_y^1 rho(y') dy' with rho = rho2 + (rho1-rho2) phi
+    def F(yy):  # antiderivative of phi along y: y/2 + eps log cosh((y - eta)/(2 eps))
+        z = (yy - eta) / (2.0 * wl.eps)
+        az = np.abs(z)
+        return 0.5 * yy + wl.eps * (az + np.log1p(np.exp(-2.0 * az)) - np.log(2.0))
+    P = P_top + g * (rho2 * (1.0 - y) + (rho1 - rho2) * (F(1.0) - F(y)))
+    wl.w = conserved(wl, phi, s, P, 0.0, 0.0)
+    wl.dt = stable_dt(wl, 0.0, P_top)
+    wl.meta = dict(P_top=P_top, a=a.tolist(), theta=theta.tolist(), seed=seed)
+    return wl
+
+
+def resized(wl_fn, **kw) -> Workload:
+    """Convenience: build a workload with overridden sizes (used for small parity cases)."""
+    return wl_fn(**kw)
