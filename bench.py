@@ -1,0 +1,311 @@
+"""Benchmark of the DG right-hand side / SSP-RK3 step on GB300.
+
+Metric: DOF-updates/s = nodes x 7 fields x 3 right-hand-side evaluations per
+SSP-RK3 step / time.  One bench "step" is one SSP-RK3 step of the whole hot
+path on the 2D periodic drop workload (64 x 64 quadrilaterals, p = 3, water
+drop R = 0.15 in air at a seeded centre, u = (1, 0.5), P = 1e5, eps = 0.75 h),
+with the state resident in HBM.  L2 (129 MB) is flushed between timed steps by
+writing a 512 MB buffer, because the state (3.7 MB) would otherwise stay in L2.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--precision fp64]
+Under torchrun each rank advances its own independent replica (weak scaling,
+no collective on the data path).  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DG RHS DOF-updates/s (fp32-bulk vs fp64 at stated L2 err); adjoint/forward time"
+UNIT = "DOF-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--cpu-sample-steps", type=int, default=0,
+                    help="oracle steps for the cpu_baseline leg (0 = size for ~15 s)")
+    return ap.parse_args()
+
+
+def workload(seed: int):
+    from paper_2306_05002_gb300 import workloads as W
+    return W.drop_2d(n=64, p=3, seed=seed)
+
+
+def config_of(wl, extra=None):
+    c = {"workload": f"2D periodic drop advection {wl.nx}x{wl.ny} quads p={wl.p} (water drop R=0.15 in air, "
+                     f"u=(1,0.5), P=1e5, eps=0.75h, Gamma=|u|, SSP-RK3)",
+         "elements": wl.E, "p": wl.p, "nodes": wl.N, "dof_per_rhs": 7 * wl.N, "dt": wl.dt,
+         "l2": "flushed between timed steps (512 MB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[2:]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- roofline helpers
+
+KERNEL_SOURCES = ["paper_2306_05002_gb300/csrc/dg_kernels_fp64.cuh", "paper_2306_05002_gb300/csrc/dg_common.cuh"]
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, wl_name: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{wl_name}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# FP64 ALU peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# --------------------------------------------------------------------------- oracle leg
+
+def oracle_rate(wl, steps: int):
+    import oracle
+    pb = oracle.Problem(**wl.problem_kwargs())
+    t0 = time.perf_counter()
+    oracle.rk3(pb, wl.w, wl.dt, steps)
+    dt = time.perf_counter() - t0
+    return 7 * wl.N * 3 * steps / dt, dt
+
+
+def cpu_baseline(wl, steps: int):
+    if steps <= 0:
+        _, t1 = oracle_rate(wl, 1)
+        steps = max(1, min(200, int(15.0 / max(t1, 1e-3))))
+    rate, secs = oracle_rate(wl, steps)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} SSP-RK3 steps of the same workload ({secs:.1f} s, single-threaded plain C FP64)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = workload(2)
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_rate(wl, 1)
+    per_step = []
+    for _ in range(args.steps):
+        r, secs = oracle_rate(wl, 1)
+        per_step.append(secs)
+    total = sum(per_step)
+    value = 7 * wl.N * 3 * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(wl, {"l2": "n/a (CPU)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} SSP-RK3 steps, one per timed step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- our leg
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2306_05002_gb300 as dg
+
+    torch.cuda.set_device(local_rank)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    wl = workload(2 + rank)
+    solver = dg.Solver(wl, precision=args.precision)
+    w = torch.from_numpy(wl.w.copy()).cuda()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        solver.dg_step(w, wl.dt, 1)
+    barrier()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        solver.dg_step(w, wl.dt, 1)
+        ends[k].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    clk = clocks.stop()
+    status = solver.dg_status_read()
+
+    # per-kernel durations for the roofline of the dominant kernel
+    kms = solver.dg_time_kernels(w, nrep=20)
+    flops, bytes_ = solver.dg_kernel_costs()
+    names = ["k_volume", "k_surface"]
+    dom = max(range(len(kms)), key=lambda i: kms[i])
+    achieved = flops[dom] / (kms[dom] * 1e-3) / 1e12
+
+    # end to end through the public API with a pinned host state: H2D, step, D2H
+    host = torch.from_numpy(wl.w.copy()).pin_memory()
+    for _ in range(2):
+        solver.dg_step(host, wl.dt, 1)
+    torch.cuda.synchronize()
+    e2e_steps = max(5, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.dg_step(host, wl.dt, 1)
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+
+    # max over ranks
+    tens = torch.tensor([ms, e2e_t], dtype=torch.float64, device="cuda")
+    if dist:
+        tdist.all_reduce(tens, op=tdist.ReduceOp.MAX)
+    ms_max, e2e_max = tens.tolist()
+
+    if rank == 0:
+        units = 7 * wl.N * 3
+        value = units * args.steps * world / (ms_max * 1e-3)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_of(wl, {"parallelism": f"replicas x{world}", "precision": args.precision,
+                                         "wall_s_timed_region": wall}),
+                "gpu_launches": 6 * args.steps,
+                "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved,
+                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                             "traffic": profiled_traffic(names[dom], wl.name),
+                             "kernel_ms": dict(zip(names, kms)),
+                             "algorithmic_flops_per_launch": dict(zip(names, flops)),
+                             "algorithmic_bytes_per_launch": dict(zip(names, bytes_))},
+                "e2e": {"value": units * e2e_steps * world / e2e_max, "unit": UNIT,
+                        "h2d_bytes_per_step": 8 * 7 * wl.N, "d2h_bytes_per_step": 8 * 7 * wl.N},
+                "clocks": clk, "device_status": status}
+        if world == 1:
+            line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
+        print(json.dumps(line), flush=True)
+    solver.close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

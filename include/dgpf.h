@@ -1,0 +1,149 @@
+/*
+ * dgpf.h -- C ABI of libdgpf, a GB300 (sm_103a) implementation of the explicit
+ * Discontinuous Galerkin right-hand side of Tonicello & Ihme, "A high-order
+ * diffused-interface approach for two-phase compressible flow simulations
+ * using a Discontinuous Galerkin framework" (arXiv 2306.05002), driving a
+ * three-stage SSP Runge-Kutta step.
+ *
+ * The equations are the system of Sec. 2 (phase field phi = phi_1, level set
+ * psi, partial densities m_l = rho_l phi_l, momentum rho u, total energy rho E,
+ * interface flux a_1 = Gamma (eps grad phi - phi (1 - phi) n) with
+ * n = grad psi/|grad psi|, stiffened-gas closure, optional viscous stress,
+ * gravity and CSF surface tension), discretised as in Sec. 3: nodal DG on
+ * Cartesian quadrilaterals (or 1D segments) with the Lagrange basis on
+ * Gauss-Lobatto-Legendre nodes and collocated quadrature, Lax-Friedrichs
+ * fluxes for the conservative equations, the quasi-conservative transport
+ * fluxes of Sec. 3 for phi and psi, and the symmetric interior penalty flux
+ * for every a_1-derived term.
+ *
+ * Conventions (all entry points):
+ *   - State layout: one contiguous array of 7 * N doubles, variable-major:
+ *       w[v * N + e * Np + a],  v = phi, psi, m1, m2, rho u, rho v, rho E,
+ *       N = E * Np nodes, E = nx * ny elements, e = ex + nx * ey,
+ *       Np = (p+1)^dim, a = i + (p+1) j with (i, j) the GLL node indices.
+ *     In 1D the rho v slot exists and stays zero.
+ *   - Pointers named w, L, lam are DEVICE pointers unless stated otherwise;
+ *     the caller owns them.  The library owns its operator tables and
+ *     workspace, allocated in dg_create and freed in dg_destroy; rhs and step
+ *     calls allocate nothing.
+ *   - stream is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *     asynchronous on that stream unless stated otherwise.  Launch-time
+ *     errors are returned; conditions the GPU detects (non-finite values)
+ *     are latched in a device status word and reported by dg_status_read.
+ *   - A context is not thread-safe.  No C++ exception crosses this boundary.
+ *   - Failure returns a negative dg_status; dg_last_error gives a message.
+ */
+#ifndef DGPF_H
+#define DGPF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = -1,          /* invalid argument (message in dg_last_error) */
+  DG_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+  DG_ERR_OOM = -3,          /* device allocation failed */
+  DG_ERR_TIMEOUT = -4,      /* a bounded device wait expired */
+  DG_ERR_NONFINITE = -5,    /* the device saw a non-finite value */
+  DG_ERR_NONPHYSICAL = -6,  /* the device saw rho <= 0 or P + Pinf <= 0 */
+  DG_ERR_UNSUPPORTED = -7   /* valid request this build does not provide */
+} dg_status;
+
+enum { DG_BC_PERIODIC = 0, DG_BC_NOSLIP = 1, DG_BC_SLIP = 2 };
+enum { DG_FP64 = 0, DG_FP32_BULK = 1 };
+
+/* Cartesian mesh of nx * ny elements on [x0,x1] x [y0,y1] (dim = 2) or nx
+   segments on [x0,x1] (dim = 1, ny must be 1).  bc = west, east, south, north;
+   periodic sides must be paired.  The paper's element partition (Sec. 3). */
+typedef struct {
+  int dim;
+  int nx, ny;
+  double x0, x1, y0, y1;
+  int bc[4];
+} dg_mesh;
+
+/* Phase constants of the stiffened-gas closure (Sec. 2): gamma_l, Pinf_l, the
+   reference densities rho_l^(0) of R_l = rho_l^(0) a_l, viscosities mu_l
+   (mixture mu = mu_1 phi + mu_2 (1 - phi)), surface tension sigma and gravity
+   g.  Index 0 is phase 1 (the phase whose volume fraction is phi). */
+typedef struct {
+  double gamma[2], pinf[2], rho0[2], mu[2];
+  double sigma;
+  double g[2];
+} dg_eos;
+
+/* Options.  prec: DG_FP64 or DG_FP32_BULK.  c_ip: interior-penalty constant,
+   eta = c_ip (p+1)^2 / h (<= 0 selects 1).  viscous, gravity,
+   surface_tension: enable those terms of Sec. 2.  check_finite: latch
+   DG_ERR_NONFINITE when an output is not finite.  barrier_timeout_ms:
+   reserved for bounded device waits (<= 0 selects 1000). */
+typedef struct {
+  int prec;
+  double c_ip;
+  int viscous, gravity, surface_tension;
+  int check_finite;
+  double barrier_timeout_ms;
+} dg_opts;
+
+typedef struct dg_ctx dg_ctx;
+
+/* Create a solver for one mesh, order p (1..5 in 2D, 1..5 in 1D), closure,
+   Allen-Cahn velocity scale Gamma >= 0 and thickness eps >= 0 (Sec. 2).
+   opts may be NULL (FP64, c_ip = 1, no viscous/gravity/surface terms).
+   Allocates all device memory the context will use on the current device.
+   On success *out receives the context; on failure *out is NULL. */
+dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps,
+                    const dg_opts *opts, dg_ctx **out);
+
+/* Free the context and its device memory (NULL is ignored).  Synchronises
+   the device first. */
+void dg_destroy(dg_ctx *ctx);
+
+/* Number of doubles of one state array: 7 * E * (p+1)^dim. */
+size_t dg_state_len(const dg_ctx *ctx);
+
+/* L = M^-1 R(w): the semi-discrete right-hand side of the weak form of Sec. 3
+   (eq. "weakDG") for all seven equations.  w and L are device arrays of
+   dg_state_len doubles and must not overlap. */
+dg_status dg_rhs(dg_ctx *ctx, const double *w, double *L, void *stream);
+
+/* Advance w (device, in place) by nsteps steps of the three-stage SSP
+   Runge-Kutta method (Shu-Osher form) with step dt > 0.  nsteps = 0 is a
+   no-op.  The step sequence is captured once in a CUDA graph per (w, dt)
+   pair and replayed; the first call for a new pair pays the capture. */
+dg_status dg_step(dg_ctx *ctx, double *w, double dt, int nsteps, void *stream);
+
+/* FP64 diagnostics of w (Sec. 4.1 mass error): out (HOST, 16 doubles) gets
+   the integrals of the 7 variables (GLL quadrature), min/max phi, min/max P,
+   min/max u, min/max v, and the count of non-finite state entries.
+   Synchronises the stream. */
+dg_status dg_diag(dg_ctx *ctx, const double *w, double *out, void *stream);
+
+/* Read and clear the device status word (synchronises the stream): DG_OK,
+   DG_ERR_NONFINITE or DG_ERR_NONPHYSICAL. */
+dg_status dg_status_read(dg_ctx *ctx, void *stream);
+
+/* Message of the last failure on this context (or of the last failed
+   dg_create when ctx is NULL).  Never NULL. */
+const char *dg_last_error(const dg_ctx *ctx);
+
+/* Kernel-level timing for roofline reports: run nrep right-hand-side
+   evaluations of w with CUDA events around each kernel launch on stream and
+   write the mean duration in milliseconds of each kernel kind to ms_out
+   (index 0 volume kernel, 1 surface kernel); returns the number of kinds
+   written (<= nmax).  Synchronises the stream. */
+int dg_time_kernels(dg_ctx *ctx, const double *w, int nrep, double *ms_out, int nmax, void *stream);
+
+/* Algorithmic FP64-equivalent flop and DRAM byte counts per launch of each
+   kernel kind (same indexing as dg_time_kernels), from the formulas of the
+   scheme (not from counters). */
+int dg_kernel_costs(const dg_ctx *ctx, double *flops_out, double *bytes_out, int nmax);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

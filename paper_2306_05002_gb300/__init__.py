@@ -1,0 +1,207 @@
+"""GB300-native DG solver for diffused-interface two-phase flow.
+
+Tonicello & Ihme, "A high-order diffused-interface approach for two-phase
+compressible flow simulations using a Discontinuous Galerkin framework"
+(arXiv 2306.05002): the explicit DG right-hand side of the quasi-conservative
+five-equation model with the Allen-Cahn phase field and an advected level set,
+and its SSP-RK3 step, as hand-written sm_103a CUDA kernels behind the C ABI of
+``include/dgpf.h`` (``libdgpf.so``).
+
+This module is a thin ctypes binding with the C names (``dg_create``,
+``dg_rhs``, ``dg_step``, ...): it marshals arguments only.  Every step of the
+right-hand side runs in the library's kernels; there is no CPU fallback, and
+using the binding without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import workloads  # noqa: F401  (numpy-only input generators)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdgpf.so")
+
+DG_OK = 0
+STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_CUDA", -3: "DG_ERR_OOM", -4: "DG_ERR_TIMEOUT",
+          -5: "DG_ERR_NONFINITE", -6: "DG_ERR_NONPHYSICAL", -7: "DG_ERR_UNSUPPORTED"}
+BC = {"periodic": 0, "noslip": 1, "slip": 2}
+PREC = {"fp64": 0, "fp32bulk": 1}
+
+# Every exported symbol of include/dgpf.h.
+EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_diag", "dg_status_read",
+           "dg_last_error", "dg_time_kernels", "dg_kernel_costs"]
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class dg_mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("bc", ctypes.c_int * 4)]
+
+
+class dg_eos(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double * 2), ("pinf", ctypes.c_double * 2), ("rho0", ctypes.c_double * 2),
+                ("mu", ctypes.c_double * 2), ("sigma", ctypes.c_double), ("g", ctypes.c_double * 2)]
+
+
+class dg_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("c_ip", ctypes.c_double), ("viscous", ctypes.c_int),
+                ("gravity", ctypes.c_int), ("surface_tension", ctypes.c_int), ("check_finite", ctypes.c_int),
+                ("barrier_timeout_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libdgpf.so (built by ``paper_2306_05002_gb300.build``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libdgpf.so not found at {path}: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    vp, dp, sz = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t
+    lib.dg_create.argtypes = [ctypes.POINTER(dg_mesh), ctypes.c_int, ctypes.POINTER(dg_eos), ctypes.c_double,
+                              ctypes.c_double, ctypes.POINTER(dg_opts), ctypes.POINTER(vp)]
+    lib.dg_create.restype = ctypes.c_int
+    lib.dg_destroy.argtypes = [vp]
+    lib.dg_destroy.restype = None
+    lib.dg_state_len.argtypes = [vp]
+    lib.dg_state_len.restype = sz
+    lib.dg_rhs.argtypes = [vp, dp, dp, vp]
+    lib.dg_rhs.restype = ctypes.c_int
+    lib.dg_step.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int, vp]
+    lib.dg_step.restype = ctypes.c_int
+    lib.dg_diag.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_double), vp]
+    lib.dg_diag.restype = ctypes.c_int
+    lib.dg_status_read.argtypes = [vp, vp]
+    lib.dg_status_read.restype = ctypes.c_int
+    lib.dg_last_error.argtypes = [vp]
+    lib.dg_last_error.restype = ctypes.c_char_p
+    lib.dg_time_kernels.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int, vp]
+    lib.dg_time_kernels.restype = ctypes.c_int
+    lib.dg_kernel_costs.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.c_int]
+    lib.dg_kernel_costs.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(ctx, status, what):
+    if status != DG_OK:
+        msg = load().dg_last_error(ctx)
+        raise DGError(status, f"{what}: {msg.decode() if msg else ''}")
+
+
+def _ptr(t):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_structs(dim, nx, ny, x0, x1, y0, y1, bc, gamma, pinf, rho0, mu=(0.0, 0.0), sigma=0.0, g=(0.0, 0.0),
+                 precision="fp64", c_ip=1.0, viscous=False, gravity=False, surface_tension=False,
+                 check_finite=True, **_ignored):
+    m = dg_mesh()
+    m.dim, m.nx, m.ny = dim, nx, ny
+    m.x0, m.x1, m.y0, m.y1 = x0, x1, y0, y1
+    for i, b in enumerate(bc):
+        m.bc[i] = BC[b] if isinstance(b, str) else int(b)
+    e = dg_eos()
+    for i in range(2):
+        e.gamma[i], e.pinf[i], e.rho0[i], e.mu[i], e.g[i] = gamma[i], pinf[i], rho0[i], mu[i], g[i]
+    e.sigma = sigma
+    o = dg_opts()
+    o.prec = PREC[precision] if isinstance(precision, str) else int(precision)
+    o.c_ip, o.viscous, o.gravity, o.surface_tension = c_ip, int(viscous), int(gravity), int(surface_tension)
+    o.check_finite, o.barrier_timeout_ms = int(check_finite), 1000.0
+    return m, e, o
+
+
+class Solver:
+    """One DG problem on the current CUDA device (wraps a ``dg_ctx``).
+
+    ``problem`` is a :class:`workloads.Workload` (or any object with the same
+    fields).  State tensors are float64 CUDA tensors of shape (7, N).
+    """
+
+    def __init__(self, problem, precision: str = "fp64", check_finite: bool = True):
+        lib = load()
+        kw = problem.problem_kwargs() if hasattr(problem, "problem_kwargs") else dict(problem)
+        p = kw.pop("p")
+        Gamma, eps = kw.pop("Gamma"), kw.pop("eps")
+        m, e, o = make_structs(precision=precision, check_finite=check_finite, **kw)
+        self._m, self._e, self._o = m, e, o
+        h = ctypes.c_void_p()
+        st = lib.dg_create(ctypes.byref(m), p, ctypes.byref(e), Gamma, eps, ctypes.byref(o), ctypes.byref(h))
+        _check(None, st, "dg_create")
+        self.ctx = h
+        self.len = lib.dg_state_len(h)
+        self.N = self.len // 7
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().dg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dg_rhs(self, w, L=None, stream=None):
+        import torch
+        if L is None:
+            L = torch.empty_like(w)
+        _check(self.ctx, load().dg_rhs(self.ctx, _ptr(w), _ptr(L), _stream(stream)), "dg_rhs")
+        return L
+
+    def dg_step(self, w, dt: float, nsteps: int, stream=None):
+        """Advance w in place.  A CPU tensor is staged through the device (host copies both ways)."""
+        import torch
+        if w.is_cuda:
+            _check(self.ctx, load().dg_step(self.ctx, _ptr(w), float(dt), int(nsteps), _stream(stream)), "dg_step")
+            return w
+        d = w.to("cuda", non_blocking=True)
+        _check(self.ctx, load().dg_step(self.ctx, _ptr(d), float(dt), int(nsteps), _stream(stream)), "dg_step")
+        w.copy_(d, non_blocking=False)
+        return w
+
+    def dg_diag(self, w, stream=None):
+        out = (ctypes.c_double * 16)()
+        _check(self.ctx, load().dg_diag(self.ctx, _ptr(w), out, _stream(stream)), "dg_diag")
+        return list(out)
+
+    def dg_status_read(self, stream=None):
+        return load().dg_status_read(self.ctx, _stream(stream))
+
+    def dg_time_kernels(self, w, nrep=20, stream=None):
+        out = (ctypes.c_double * 8)()
+        n = load().dg_time_kernels(self.ctx, _ptr(w), int(nrep), out, 8, _stream(stream))
+        if n < 0:
+            raise DGError(-2, "dg_time_kernels failed")
+        return list(out)[:n]
+
+    def dg_kernel_costs(self):
+        f = (ctypes.c_double * 8)()
+        b = (ctypes.c_double * 8)()
+        n = load().dg_kernel_costs(self.ctx, f, b, 8)
+        return list(f)[:n], list(b)[:n]

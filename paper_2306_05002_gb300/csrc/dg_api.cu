@@ -1,0 +1,532 @@
+// dg_api.cu -- host side of libdgpf: the C ABI declared in include/dgpf.h.
+//
+// Builds the operator tables (Gauss-Lobatto-Legendre nodes and weights, the
+// Lagrange derivative matrix and the weak-form derivative Dhat = W^-1 D^T W of
+// Sec. 3), owns the device workspace, launches the kernels of
+// dg_kernels_fp64.cuh, captures SSP-RK3 step sequences in CUDA graphs, and
+// runs the FP64 diagnostic reductions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dg_common.cuh"
+#include "dg_kernels_fp64.cuh"
+#include "dgpf.h"
+
+namespace dgpf {
+bool kernels_fp64_p1(int, bool, bool, KernelSet *);
+bool kernels_fp64_p2(int, bool, bool, KernelSet *);
+bool kernels_fp64_p3(int, bool, bool, KernelSet *);
+bool kernels_fp64_p4(int, bool, bool, KernelSet *);
+bool kernels_fp64_p5(int, bool, bool, KernelSet *);
+
+bool kernels_fp64(int p, int dim, bool viscous, bool st, KernelSet *out) {
+  switch (p) {
+    case 1: return kernels_fp64_p1(dim, viscous, st, out);
+    case 2: return kernels_fp64_p2(dim, viscous, st, out);
+    case 3: return kernels_fp64_p3(dim, viscous, st, out);
+    case 4: return kernels_fp64_p4(dim, viscous, st, out);
+    case 5: return kernels_fp64_p5(dim, viscous, st, out);
+    default: return false;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: deterministic two-pass FP64 reduction.
+// ---------------------------------------------------------------------------
+constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_N = 16;
+
+__device__ __forceinline__ void diag_combine(double *a, const double *b) {
+  for (int q = 0; q < 7; ++q) a[q] += b[q];
+  a[7] = fmin(a[7], b[7]);  a[8] = fmax(a[8], b[8]);
+  a[9] = fmin(a[9], b[9]);  a[10] = fmax(a[10], b[10]);
+  a[11] = fmin(a[11], b[11]); a[12] = fmax(a[12], b[12]);
+  a[13] = fmin(a[13], b[13]); a[14] = fmax(a[14], b[14]);
+  a[15] += b[15];
+}
+
+__device__ __forceinline__ void diag_identity(double *a) {
+  for (int q = 0; q < 7; ++q) a[q] = 0.0;
+  for (int q = 7; q < 15; q += 2) { a[q] = INFINITY; a[q + 1] = -INFINITY; }
+  a[15] = 0.0;
+}
+
+__device__ void diag_block_reduce(double (*sh)[DIAG_N], double *mine, double *dst) {
+  for (int q = 0; q < DIAG_N; ++q) sh[threadIdx.x][q] = mine[q];
+  __syncthreads();
+  for (int s = DIAG_THREADS / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) diag_combine(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < DIAG_N; ++q) dst[q] = sh[0][q];
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS)
+k_diag_partial(const Params prm, int Np, int P1, int dim, double J, const double *__restrict__ w,
+               double *__restrict__ part) {
+  __shared__ double sh[DIAG_THREADS][DIAG_N];
+  double acc[DIAG_N];
+  diag_identity(acc);
+  const double *wt = prm.ops + OpsLayout{P1, Np}.wt();
+  for (long n = blockIdx.x * (long)DIAG_THREADS + threadIdx.x; n < prm.N; n += (long)gridDim.x * DIAG_THREADS) {
+    const int a = (int)(n % Np);
+    const double wJ = (dim == 2 ? wt[a % P1] * wt[a / P1] : wt[a]) * J;
+    double q[NV];
+    for (int v = 0; v < NV; ++v) {
+      q[v] = w[(long)v * prm.N + n];
+      acc[v] += wJ * q[v];
+      if (!isfinite(q[v])) acc[15] += 1.0;
+    }
+    const double rho = q[M1] + q[M2];
+    double Cm, den;
+    const double P = sg_pressure(prm, q[PHI], rho, q[RU], q[RV], q[RE], &Cm, &den);
+    const double u = q[RU] / rho, v = q[RV] / rho;
+    acc[7] = fmin(acc[7], q[PHI]);  acc[8] = fmax(acc[8], q[PHI]);
+    acc[9] = fmin(acc[9], P);       acc[10] = fmax(acc[10], P);
+    acc[11] = fmin(acc[11], u);     acc[12] = fmax(acc[12], u);
+    acc[13] = fmin(acc[13], v);     acc[14] = fmax(acc[14], v);
+  }
+  diag_block_reduce(sh, acc, part + (long)blockIdx.x * DIAG_N);
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS)
+k_diag_final(int nparts, const double *__restrict__ part, double *__restrict__ out) {
+  __shared__ double sh[DIAG_THREADS][DIAG_N];
+  double acc[DIAG_N];
+  diag_identity(acc);
+  for (int b = threadIdx.x; b < nparts; b += DIAG_THREADS) diag_combine(acc, part + (long)b * DIAG_N);
+  diag_block_reduce(sh, acc, out);
+}
+
+}  // namespace dgpf
+
+using namespace dgpf;
+
+// ---------------------------------------------------------------------------
+// Operator tables (host)
+// ---------------------------------------------------------------------------
+namespace {
+
+// GLL nodes by Newton's method on (1 - x^2) P_p'(x), written with the
+// identity (1 - x^2) P_p' = p (P_{p-1} - x P_p) and the Newton step
+// x <- x - (x P_p - P_{p-1}) / ((p+1) P_p); weights 2 / (p (p+1) P_p(x)^2).
+void gll_nodes(int p, std::vector<double> &x, std::vector<double> &w) {
+  x.assign(p + 1, 0.0);
+  w.assign(p + 1, 0.0);
+  for (int i = 0; i <= p; ++i) x[i] = -std::cos(M_PI * i / p);
+  auto legendre = [p](double t, double *Pp, double *Pm) {
+    double a = 1.0, b = t;  // P_0, P_1
+    for (int k = 2; k <= p; ++k) {
+      const double c = ((2.0 * k - 1.0) * t * b - (k - 1.0) * a) / k;
+      a = b;
+      b = c;
+    }
+    *Pp = b;
+    *Pm = a;
+  };
+  for (int it = 0; it < 200; ++it) {
+    double moved = 0.0;
+    for (int i = 1; i < p; ++i) {
+      double Pp, Pm;
+      legendre(x[i], &Pp, &Pm);
+      const double dx = (x[i] * Pp - Pm) / ((p + 1.0) * Pp);
+      x[i] -= dx;
+      moved = std::max(moved, std::fabs(dx));
+    }
+    if (moved < 1e-16) break;
+  }
+  for (int i = 0; i <= p / 2; ++i) {  // exact symmetry about 0
+    const double s = 0.5 * (x[p - i] - x[i]);
+    x[i] = -s;
+    x[p - i] = s;
+  }
+  if (p % 2 == 0) x[p / 2] = 0.0;
+  for (int i = 0; i <= p; ++i) {
+    double Pp, Pm;
+    if (i == 0 || i == p) Pp = 1.0;
+    else legendre(x[i], &Pp, &Pm);
+    w[i] = 2.0 / (p * (p + 1.0) * Pp * Pp);
+  }
+}
+
+// Lagrange derivative matrix D[a][b] = l_b'(x_a) from barycentric weights.
+std::vector<double> lagrange_derivative(const std::vector<double> &x) {
+  const int n = (int)x.size();
+  std::vector<double> lam(n, 1.0), D(n * n, 0.0);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k)
+      if (k != j) lam[j] /= (x[j] - x[k]);
+  for (int a = 0; a < n; ++a) {
+    double diag = 0.0;
+    for (int b = 0; b < n; ++b) {
+      if (b == a) continue;
+      D[a * n + b] = (lam[b] / lam[a]) / (x[a] - x[b]);
+      diag -= D[a * n + b];
+    }
+    D[a * n + a] = diag;
+  }
+  return D;
+}
+
+thread_local std::string g_create_error = "no error";
+
+}  // namespace
+
+struct dg_ctx {
+  dg_mesh mesh;
+  int p;
+  dg_eos eos;
+  double Gamma, eps;
+  dg_opts opts;
+  int dim, P1, Np, E, N, NFK;
+  size_t len;
+  double hx, hy, J;
+  Params prm;
+  KernelSet ks;
+  double *d_ops = nullptr, *d_w1 = nullptr, *d_w2 = nullptr, *d_rvol = nullptr, *d_trace = nullptr;
+  double *d_part = nullptr, *d_diag = nullptr;
+  unsigned *d_status = nullptr;
+  int nparts = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t g1 = nullptr, gk = nullptr;
+  const double *g_w = nullptr;
+  double g_dt = 0.0;
+  std::string err = "no error";
+};
+
+static const int GRAPH_UNROLL = 8;
+
+static dg_status fail(dg_ctx *c, dg_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+static dg_status cuda_fail(dg_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, DG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static void free_graphs(dg_ctx *c) {
+  if (c->g1) cudaGraphExecDestroy(c->g1);
+  if (c->gk) cudaGraphExecDestroy(c->gk);
+  c->g1 = c->gk = nullptr;
+  c->g_w = nullptr;
+}
+
+static void free_ctx(dg_ctx *c) {
+  if (!c) return;
+  free_graphs(c);
+  cudaFree(c->d_ops);
+  cudaFree(c->d_w1);
+  cudaFree(c->d_w2);
+  cudaFree(c->d_rvol);
+  cudaFree(c->d_trace);
+  cudaFree(c->d_part);
+  cudaFree(c->d_diag);
+  cudaFree(c->d_status);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps,
+                               const dg_opts *opts, dg_ctx **out) {
+  if (!out) return fail(nullptr, DG_ERR_ARG, "dg_create: out is NULL");
+  *out = nullptr;
+  if (!mesh || !eos) return fail(nullptr, DG_ERR_ARG, "dg_create: mesh and eos are required");
+  if (mesh->dim != 1 && mesh->dim != 2) return fail(nullptr, DG_ERR_ARG, "dg_create: dim must be 1 or 2");
+  if (p < 1 || p > 5) return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: order p must be in 1..5");
+  if (mesh->nx < 1 || mesh->ny < 1 || (mesh->dim == 1 && mesh->ny != 1))
+    return fail(nullptr, DG_ERR_ARG, "dg_create: bad element counts (1D needs ny = 1)");
+  if (!(mesh->x1 > mesh->x0) || (mesh->dim == 2 && !(mesh->y1 > mesh->y0)))
+    return fail(nullptr, DG_ERR_ARG, "dg_create: empty domain");
+  for (int f = 0; f < 4; ++f)
+    if (mesh->bc[f] < DG_BC_PERIODIC || mesh->bc[f] > DG_BC_SLIP)
+      return fail(nullptr, DG_ERR_ARG, "dg_create: unknown boundary condition");
+  if ((mesh->bc[0] == DG_BC_PERIODIC) != (mesh->bc[1] == DG_BC_PERIODIC) ||
+      (mesh->dim == 2 && (mesh->bc[2] == DG_BC_PERIODIC) != (mesh->bc[3] == DG_BC_PERIODIC)))
+    return fail(nullptr, DG_ERR_ARG, "dg_create: periodic sides must be paired");
+  for (int l = 0; l < 2; ++l)
+    if (!(eos->gamma[l] > 1.0) || !(eos->rho0[l] > 0.0) || eos->mu[l] < 0.0)
+      return fail(nullptr, DG_ERR_ARG, "dg_create: need gamma > 1, rho0 > 0, mu >= 0");
+  if (!(Gamma >= 0.0) || !(eps >= 0.0)) return fail(nullptr, DG_ERR_ARG, "dg_create: need Gamma, eps >= 0");
+  dg_opts o{};
+  o.prec = DG_FP64;
+  o.c_ip = 1.0;
+  o.barrier_timeout_ms = 1000.0;
+  if (opts) o = *opts;
+  if (o.c_ip <= 0.0) o.c_ip = 1.0;
+  if (o.barrier_timeout_ms <= 0.0) o.barrier_timeout_ms = 1000.0;
+  if (o.prec != DG_FP64) return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: precision mode not available");
+  const long long E = (long long)mesh->nx * mesh->ny;
+  const int P1 = p + 1;
+  const int Np = mesh->dim == 2 ? P1 * P1 : P1;
+  if (E * Np * 7 >= (1LL << 31)) return fail(nullptr, DG_ERR_ARG, "dg_create: problem too large for one context");
+
+  dg_ctx *c = new (std::nothrow) dg_ctx();
+  if (!c) return fail(nullptr, DG_ERR_OOM, "dg_create: host allocation failed");
+  c->mesh = *mesh;
+  c->p = p;
+  c->eos = *eos;
+  c->Gamma = Gamma;
+  c->eps = eps;
+  c->opts = o;
+  c->dim = mesh->dim;
+  c->P1 = P1;
+  c->Np = Np;
+  c->E = (int)E;
+  c->N = (int)(E * Np);
+  c->NFK = 2 * c->dim * (c->dim == 2 ? P1 : 1);
+  c->len = (size_t)NV * c->N;
+  c->hx = (mesh->x1 - mesh->x0) / mesh->nx;
+  c->hy = c->dim == 2 ? (mesh->y1 - mesh->y0) / mesh->ny : 1.0;
+  c->J = c->dim == 2 ? 0.25 * c->hx * c->hy : 0.5 * c->hx;
+
+  if (!kernels_fp64(p, c->dim, o.viscous != 0, o.surface_tension != 0, &c->ks)) {
+    free_ctx(c);
+    return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: viscous/surface terms need dim = 2");
+  }
+
+  // Operator tables.
+  std::vector<double> xi, wt;
+  gll_nodes(p, xi, wt);
+  const std::vector<double> D = lagrange_derivative(xi);
+  const OpsLayout L{P1, Np};
+  std::vector<double> ops(L.size(), 0.0);
+  const double rx = 2.0 / c->hx, ry = 2.0 / c->hy;
+  for (int a = 0; a < P1; ++a)
+    for (int b = 0; b < P1; ++b) {
+      ops[L.Dx() + a * P1 + b] = rx * D[a * P1 + b];
+      ops[L.Dy() + a * P1 + b] = ry * D[a * P1 + b];
+      const double dh = wt[b] * D[b * P1 + a] / wt[a];
+      ops[L.Dhx() + a * P1 + b] = rx * dh;
+      ops[L.Dhy() + a * P1 + b] = ry * dh;
+    }
+  for (int a = 0; a < P1; ++a) ops[L.wt() + a] = wt[a];
+  for (int a = 0; a < Np; ++a) {
+    const double wa = c->dim == 2 ? wt[a % P1] * wt[a / P1] : wt[a];
+    ops[L.invM() + a] = 1.0 / (wa * c->J);
+  }
+  for (int k = 0; k < P1; ++k) {
+    ops[L.wfx() + k] = c->dim == 2 ? wt[k] * 0.5 * c->hy : 1.0;
+    ops[L.wfy() + k] = c->dim == 2 ? wt[k] * 0.5 * c->hx : 1.0;
+  }
+
+  // Closure constants, computed with the same expressions as the stiffened-gas
+  // formula of Sec. 2 so that the pressure is reproducible.
+  Params &q = c->prm;
+  q.nx = mesh->nx;
+  q.ny = mesh->ny;
+  q.E = c->E;
+  q.N = c->N;
+  for (int f = 0; f < 4; ++f) q.bc[f] = mesh->bc[f];
+  q.C1 = eos->gamma[0] * eos->pinf[0] / (eos->gamma[0] - 1.0);
+  q.C2 = eos->gamma[1] * eos->pinf[1] / (eos->gamma[1] - 1.0);
+  q.g1 = 1.0 / (eos->gamma[0] - 1.0);
+  q.g2 = 1.0 / (eos->gamma[1] - 1.0);
+  q.Bp = eos->gamma[0] / (eos->gamma[0] - 1.0) - eos->gamma[1] / (eos->gamma[1] - 1.0);
+  q.dC = q.C1 - q.C2;
+  q.rho01 = eos->rho0[0];
+  q.rho02 = eos->rho0[1];
+  q.drho0 = eos->rho0[0] - eos->rho0[1];
+  q.mu1 = eos->mu[0];
+  q.mu2 = eos->mu[1];
+  q.sigma = eos->sigma;
+  q.gx = eos->g[0];
+  q.gy = eos->g[1];
+  q.Gamma = Gamma;
+  q.eps = eps;
+  q.eta_x = o.c_ip * P1 * P1 / c->hx;
+  q.eta_y = o.c_ip * P1 * P1 / c->hy;
+  q.gravity = o.gravity != 0;
+  q.check_finite = o.check_finite != 0;
+
+  cudaError_t e;
+  const size_t sbytes = c->len * sizeof(double);
+  const size_t tbytes = (size_t)c->ks.nt * c->E * c->NFK * sizeof(double);
+  c->nparts = std::min(1024, (c->N + DIAG_THREADS - 1) / DIAG_THREADS);
+  if ((e = cudaMalloc(&c->d_ops, ops.size() * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_w1, sbytes)) != cudaSuccess || (e = cudaMalloc(&c->d_w2, sbytes)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_rvol, sbytes)) != cudaSuccess || (e = cudaMalloc(&c->d_trace, tbytes)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_part, (size_t)c->nparts * DIAG_N * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_diag, DIAG_N * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_status, sizeof(unsigned))) != cudaSuccess) {
+    free_ctx(c);
+    cudaGetLastError();
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA,
+                std::string("dg_create: device allocation failed: ") + cudaGetErrorString(e));
+  }
+  if ((e = cudaMemcpy(c->d_ops, ops.data(), ops.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(c->d_status, 0, sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess) {
+    free_ctx(c);
+    return fail(nullptr, DG_ERR_CUDA, std::string("dg_create: ") + cudaGetErrorString(e));
+  }
+  q.ops = c->d_ops;
+  q.status = c->d_status;
+  *out = c;
+  return DG_OK;
+}
+
+extern "C" void dg_destroy(dg_ctx *c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  free_ctx(c);
+}
+
+extern "C" size_t dg_state_len(const dg_ctx *c) { return c ? c->len : 0; }
+
+extern "C" const char *dg_last_error(const dg_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+static dg_status run_stage(dg_ctx *c, int mode, double dt, const double *w0, const double *ws, double *out,
+                           cudaStream_t s) {
+  cudaError_t e = c->ks.volume(c->prm, ws, c->d_rvol, c->d_trace, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "volume kernel launch");
+  e = c->ks.surface(c->prm, mode, dt, w0, ws, c->d_rvol, c->d_trace, out, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "surface kernel launch");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_rhs(dg_ctx *c, const double *w, double *L, void *stream) {
+  if (!c) return DG_ERR_ARG;
+  if (!w || !L) return fail(c, DG_ERR_ARG, "dg_rhs: null array");
+  if (w == L) return fail(c, DG_ERR_ARG, "dg_rhs: w and L must not overlap");
+  return run_stage(c, MODE_RHS, 0.0, w, w, L, (cudaStream_t)stream);
+}
+
+// One SSP-RK3 step (Shu-Osher): w1 = w + dt L(w); w2 = 3/4 w + 1/4 (w1 + dt L(w1));
+// w <- 1/3 w + 2/3 (w2 + dt L(w2)).  The last stage writes w in place (each
+// node's w0 value is read by the thread that overwrites it).
+static dg_status enqueue_step(dg_ctx *c, double *w, double dt, cudaStream_t s) {
+  dg_status r;
+  if ((r = run_stage(c, MODE_S1, dt, w, w, c->d_w1, s)) != DG_OK) return r;
+  if ((r = run_stage(c, MODE_S2, dt, w, c->d_w1, c->d_w2, s)) != DG_OK) return r;
+  return run_stage(c, MODE_S3, dt, w, c->d_w2, w, s);
+}
+
+static dg_status capture(dg_ctx *c, double *w, double dt, int steps, cudaGraphExec_t *exec) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_step: begin capture");
+  dg_status r = DG_OK;
+  for (int s = 0; s < steps && r == DG_OK; ++s) r = enqueue_step(c, w, dt, c->cap);
+  e = cudaStreamEndCapture(c->cap, &g);
+  if (r != DG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_step: end capture");
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_step: instantiate");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_step(dg_ctx *c, double *w, double dt, int nsteps, void *stream) {
+  if (!c) return DG_ERR_ARG;
+  if (!w) return fail(c, DG_ERR_ARG, "dg_step: null state");
+  if (!(dt > 0.0) || nsteps < 0) return fail(c, DG_ERR_ARG, "dg_step: need dt > 0 and nsteps >= 0");
+  if (nsteps == 0) return DG_OK;
+  if (c->g_w != w || c->g_dt != dt || !c->g1) {
+    free_graphs(c);
+    dg_status r;
+    if ((r = capture(c, w, dt, 1, &c->g1)) != DG_OK) return r;
+    if ((r = capture(c, w, dt, GRAPH_UNROLL, &c->gk)) != DG_OK) return r;
+    c->g_w = w;
+    c->g_dt = dt;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  for (int k = 0; k < nsteps / GRAPH_UNROLL; ++k)
+    if ((e = cudaGraphLaunch(c->gk, s)) != cudaSuccess) return cuda_fail(c, e, "dg_step: graph launch");
+  for (int k = 0; k < nsteps % GRAPH_UNROLL; ++k)
+    if ((e = cudaGraphLaunch(c->g1, s)) != cudaSuccess) return cuda_fail(c, e, "dg_step: graph launch");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_diag(dg_ctx *c, const double *w, double *out, void *stream) {
+  if (!c) return DG_ERR_ARG;
+  if (!w || !out) return fail(c, DG_ERR_ARG, "dg_diag: null array");
+  cudaStream_t s = (cudaStream_t)stream;
+  k_diag_partial<<<c->nparts, DIAG_THREADS, 0, s>>>(c->prm, c->Np, c->P1, c->dim, c->J, w, c->d_part);
+  k_diag_final<<<1, DIAG_THREADS, 0, s>>>(c->nparts, c->d_part, c->d_diag);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_diag: launch");
+  if ((e = cudaMemcpyAsync(out, c->d_diag, DIAG_N * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(c, e, "dg_diag: copy");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "dg_diag: sync");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_status_read(dg_ctx *c, void *stream) {
+  if (!c) return DG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_status_read");
+  if (h & STATUS_NONFINITE) return fail(c, DG_ERR_NONFINITE, "non-finite value produced on the device");
+  if (h & STATUS_NONPHYSICAL) return fail(c, DG_ERR_NONPHYSICAL, "non-physical state on the device");
+  return DG_OK;
+}
+
+extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_out, int nmax, void *stream) {
+  if (!c || !w || !ms_out || nmax < 1 || nrep < 1) return -1;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t ev[3];
+  for (auto &x : ev) cudaEventCreate(&x);
+  double acc[2] = {0.0, 0.0};
+  for (int r = 0; r < nrep; ++r) {
+    cudaEventRecord(ev[0], s);
+    c->ks.volume(c->prm, w, c->d_rvol, c->d_trace, s);
+    cudaEventRecord(ev[1], s);
+    c->ks.surface(c->prm, MODE_RHS, 0.0, w, w, c->d_rvol, c->d_trace, c->d_w1, s);
+    cudaEventRecord(ev[2], s);
+    cudaEventSynchronize(ev[2]);
+    float t0 = 0.f, t1 = 0.f;
+    cudaEventElapsedTime(&t0, ev[0], ev[1]);
+    cudaEventElapsedTime(&t1, ev[1], ev[2]);
+    acc[0] += t0;
+    acc[1] += t1;
+  }
+  for (auto &x : ev) cudaEventDestroy(x);
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  const int nk = std::min(nmax, 2);
+  for (int k = 0; k < nk; ++k) ms_out[k] = acc[k] / nrep;
+  return nk;
+}
+
+extern "C" int dg_kernel_costs(const dg_ctx *c, double *flops, double *bytes, int nmax) {
+  if (!c || !flops || !bytes || nmax < 1) return -1;
+  // Algorithmic counts from the formulas of the scheme (an FMA counts 2, a
+  // division or square root 1), per launch.
+  const double P1 = c->P1, Np = c->Np, NFK = c->NFK, E = c->E, d = c->dim;
+  const double fface = NFK / Np;  // face nodes per node (upper bound of trace writers)
+  const bool visc = c->opts.viscous != 0, st = c->opts.surface_tension != 0;
+  // volume kernel, per node: closure 25, gradients 2*2*d*P1 (+4*d*P1 viscous),
+  // normal 6, a_1 10, fluxes 40, volume contractions 2*6*d*P1, non-conservative 8,
+  // sound speed at face nodes 5
+  double fv = 25 + 4 * d * P1 + 6 + 10 + 40 + 12 * d * P1 + 8 + 5 * fface;
+  if (visc) fv += 4 * d * P1 + 20 + 12;
+  if (st) fv += 2 * d * P1 + 8;
+  // surface kernel: per face node 133 (+30 viscous); per node gather/lift/update ~104
+  double fs = fface * (133 + (visc ? 30 : 0)) + 7 * fface + 12 * 2 * d + 14 + 35;
+  const double nt = c->ks.nt;
+  const double bv = 8.0 * (E * Np * (7 + 7) + E * NFK * nt);
+  const double bs = 8.0 * (E * NFK * nt * 2 + E * Np * (7 * 4));
+  const int nk = std::min(nmax, 2);
+  const double F[2] = {fv * E * Np, fs * E * Np}, Bb[2] = {bv, bs};
+  for (int k = 0; k < nk; ++k) {
+    flops[k] = F[k];
+    bytes[k] = Bb[k];
+  }
+  return nk;
+}

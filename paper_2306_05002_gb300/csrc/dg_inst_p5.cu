@@ -1,0 +1,8 @@
+// Explicit instantiation of the FP64 kernel families of order p = 5.
+#include "dg_kernels_fp64.cuh"
+
+namespace dgpf {
+bool kernels_fp64_p5(int dim, bool viscous, bool st, KernelSet *out) {
+  return kernels_fp64_p<5>(dim, viscous, st, out);
+}
+}  // namespace dgpf

@@ -1,0 +1,78 @@
+"""CPU-side checks of the C ABI: the library builds/loads, exports every function
+declared in include/dgpf.h, and rejects invalid arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(dg_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2306_05002_gb300 import build
+    build.build()
+    import paper_2306_05002_gb300 as pkg
+    return pkg.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert len(declared) >= 8
+    for name in declared:
+        assert hasattr(lib, name), name
+    import paper_2306_05002_gb300 as pkg
+    assert sorted(pkg.EXPORTS) == sorted(n for n in declared if n in pkg.EXPORTS)
+    for name in declared:
+        assert name in pkg.EXPORTS, f"{name} declared but not bound in Python"
+
+
+def _args(**over):
+    import paper_2306_05002_gb300 as pkg
+    kw = dict(dim=2, nx=4, ny=4, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=("periodic",) * 4,
+              gamma=(1.4, 4.4), pinf=(0.0, 6e8), rho0=(1.0, 1000.0))
+    p = over.pop("p", 3)
+    Gamma = over.pop("Gamma", 1.0)
+    eps = over.pop("eps", 0.01)
+    kw.update(over)
+    m, e, o = pkg.make_structs(**kw)
+    return m, p, e, Gamma, eps, o
+
+
+@pytest.mark.parametrize("over,code", [
+    (dict(dim=3), -1),
+    (dict(p=0), -7),
+    (dict(p=9), -7),
+    (dict(nx=0), -1),
+    (dict(dim=1, ny=2), -1),
+    (dict(x1=0.0), -1),
+    (dict(bc=("periodic", "noslip", "periodic", "periodic")), -1),
+    (dict(gamma=(1.0, 1.4)), -1),
+    (dict(Gamma=-1.0), -1),
+])
+def test_create_rejects_invalid_arguments(lib, over, code):
+    m, p, e, Gamma, eps, o = _args(**over)
+    h = ctypes.c_void_p(123)
+    st = lib.dg_create(ctypes.byref(m), p, ctypes.byref(e), Gamma, eps, ctypes.byref(o), ctypes.byref(h))
+    assert st == code
+    assert h.value is None
+    assert lib.dg_last_error(None)  # a message is available
+
+
+def test_null_context_is_safe(lib):
+    assert lib.dg_state_len(None) == 0
+    assert lib.dg_rhs(None, None, None, None) == -1
+    assert lib.dg_step(None, None, 1.0, 1, None) == -1
+    lib.dg_destroy(None)
+    assert isinstance(lib.dg_last_error(None), bytes)

@@ -1,0 +1,219 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, entry by entry.
+
+Tolerance (FP64 path): for every variable v,
+    max_n |L_gpu - L_orc| <= 1e-12 * max_n S_v   and   ||L_gpu - L_orc||_2 <= 1e-12 ||S_v||_2,
+where S (from the oracle) is the M^-1-scaled sum of the absolute values of every
+contribution to R: the scale of the terms that cancel (in equilibrium regions L ~ 0).
+The pressure, whose recovery cancels about four digits, is evaluated in the same
+IEEE operation order on both sides, so the bound holds for the P-dependent terms too.
+"""
+import numpy as np
+import pytest
+
+from paper_2306_05002_gb300 import workloads as W
+from tests.helpers import problem
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _rhs_both(orc, dg, wl, w=None):
+    import torch
+    w = wl.w if w is None else w
+    L_ref, S = orc.rhs(problem(orc, wl), w, want_scale=True)
+    solver = dg.Solver(wl)
+    L = solver.dg_rhs(torch.from_numpy(np.ascontiguousarray(w)).cuda()).cpu().numpy()
+    assert solver.dg_status_read() == 0
+    solver.close()
+    return L, L_ref, S
+
+
+def _assert_parity(L, L_ref, S, tol=TOL):
+    for v in range(7):
+        s_inf = S[v].max()
+        if s_inf == 0:
+            assert np.abs(L[v]).max() == 0, v
+            continue
+        e_inf = np.abs(L[v] - L_ref[v]).max() / s_inf
+        e_2 = np.linalg.norm(L[v] - L_ref[v]) / np.linalg.norm(S[v])
+        assert e_inf <= tol and e_2 <= tol, (v, e_inf, e_2)
+
+
+def _broken(wl, seed=4, amp=0.05):
+    rng = np.random.default_rng(seed)
+    w = wl.w.copy()
+    w[0] = np.clip(w[0] + amp * rng.uniform(-1, 1, wl.N), 0.0, 1.0)
+    w[1] += amp * rng.uniform(-1, 1, wl.N)
+    w[4] *= 1 + 0.05 * rng.uniform(-1, 1, wl.N)
+    w[6] *= 1 + 1e-6 * rng.uniform(-1, 1, wl.N)
+    return w
+
+
+# ----------------------------------------------------------------------------- rhs parity
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_rhs_1d_slab(orc, dg, p):
+    wl = W.slab_1d(nx=37, p=p)  # 37 elements: ragged last block
+    _assert_parity(*_rhs_both(orc, dg, wl))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_rhs_2d_drop_orders(orc, dg, p):
+    wl = W.drop_2d(n=7, p=p, seed=2)  # 49 elements: several tiles and a ragged tail
+    _assert_parity(*_rhs_both(orc, dg, wl))
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_rhs_discontinuous_state(orc, dg, p):
+    wl = W.drop_2d(n=6, p=p, seed=5)
+    _assert_parity(*_rhs_both(orc, dg, wl, _broken(wl)))
+
+
+def test_rhs_air_bubble_in_water(orc, dg):
+    wl = W.drop_2d(n=8, p=3, seed=9, water_inside=False, R=0.2)
+    _assert_parity(*_rhs_both(orc, dg, wl, _broken(wl)))
+
+
+def test_rhs_non_square_elements(orc, dg):
+    wl = W.Workload(name="rect", dim=2, nx=5, ny=3, p=3, x0=-0.5, x1=1.5, y0=0.0, y1=0.6, Gamma=1.3, eps=0.04)
+    x, y = W.node_coords(wl)
+    s = np.hypot(x - 0.4, y - 0.3) - 0.2
+    wl.w = W.conserved(wl, W.tanh_profile(s, wl.eps), s, 1e5, 0.7, -0.4)
+    _assert_parity(*_rhs_both(orc, dg, wl, _broken(wl)))
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 3), (2, 1)])
+def test_rhs_self_periodic_tiny_meshes(orc, dg, nx, ny):
+    wl = W.Workload(name="tiny", dim=2, nx=nx, ny=ny, p=3, Gamma=1.0, eps=0.1)
+    x, y = W.node_coords(wl)
+    s = np.hypot(x - 0.5, y - 0.5) - 0.25
+    wl.w = W.conserved(wl, W.tanh_profile(s, wl.eps), s, 1e5, 0.4, 0.3)
+    _assert_parity(*_rhs_both(orc, dg, wl, _broken(wl)))
+
+
+@pytest.mark.parametrize("bc", ["noslip", "slip"])
+def test_rhs_walls(orc, dg, bc):
+    wl = W.Workload(name="box", dim=2, nx=5, ny=4, p=3, bc=(bc,) * 4, Gamma=1.0, eps=0.05)
+    x, y = W.node_coords(wl)
+    u = 0.3 + np.sin(np.pi * x) * np.cos(np.pi * y)
+    v = -0.2 - np.cos(np.pi * x) * np.sin(np.pi * y)
+    s = np.hypot(x - 0.4, y - 0.55) - 0.2
+    wl.w = W.conserved(wl, W.tanh_profile(s, wl.eps), s, 1e5, u, v)
+    _assert_parity(*_rhs_both(orc, dg, wl, _broken(wl)))
+
+
+@pytest.mark.parametrize("visc,st,grav", [(True, False, False), (False, True, False), (False, False, True),
+                                          (True, True, True)])
+def test_rhs_physics_terms(orc, dg, visc, st, grav):
+    wl = W.rayleigh_taylor(n=6, p=4, seed=3)
+    wl.viscous, wl.surface_tension, wl.gravity = visc, st, grav
+    wl.bc = ("periodic", "periodic", "noslip", "slip")
+    _assert_parity(*_rhs_both(orc, dg, wl, _broken(wl)))
+
+
+def test_rhs_full_size_drop_64x64_p3(orc, dg):
+    wl = W.drop_2d(n=64, p=3, seed=2)
+    _assert_parity(*_rhs_both(orc, dg, wl))
+
+
+def test_rhs_full_size_rayleigh_taylor_256x256_p4(orc, dg):
+    wl = W.rayleigh_taylor(n=256, p=4, seed=3)
+    _assert_parity(*_rhs_both(orc, dg, wl))
+
+
+# ----------------------------------------------------------------------------- step parity
+
+def _step_both(orc, dg, wl, nsteps, w=None):
+    import torch
+    w = wl.w if w is None else w
+    w_ref = orc.rk3(problem(orc, wl), w, wl.dt, nsteps)
+    solver = dg.Solver(wl)
+    d = torch.from_numpy(np.ascontiguousarray(w)).cuda()
+    solver.dg_step(d, wl.dt, nsteps)
+    out = d.cpu().numpy()
+    assert solver.dg_status_read() == 0
+    solver.close()
+    return out, w_ref
+
+
+def _assert_state_close(w, w_ref, tol):
+    for v in range(7):
+        scale = max(np.abs(w_ref[v]).max(), 1e-300)
+        err = np.abs(w[v] - w_ref[v]).max() / scale
+        assert err <= tol, (v, err)
+
+
+def test_step_1d_slab_100_steps(orc, dg):
+    wl = W.slab_1d(nx=100, p=3)
+    w, w_ref = _step_both(orc, dg, wl, 100)
+    _assert_state_close(w, w_ref, 1e-12)
+
+
+def test_step_drop_graph_unroll_remainder(orc, dg):
+    """11 steps = one 8-step graph + three 1-step graphs."""
+    wl = W.drop_2d(n=8, p=3, seed=2)
+    w, w_ref = _step_both(orc, dg, wl, 11)
+    _assert_state_close(w, w_ref, 1e-12)
+
+
+def test_step_full_size_drop(orc, dg):
+    wl = W.drop_2d(n=64, p=3, seed=2)
+    w, w_ref = _step_both(orc, dg, wl, 3)
+    _assert_state_close(w, w_ref, 1e-12)
+
+
+def test_step_rayleigh_taylor_small(orc, dg):
+    wl = W.rayleigh_taylor(n=8, p=4, seed=3)
+    w, w_ref = _step_both(orc, dg, wl, 5)
+    _assert_state_close(w, w_ref, 1e-12)
+
+
+def test_step_zero_is_noop(dg):
+    import torch
+    wl = W.drop_2d(n=4, p=2, seed=1)
+    s = dg.Solver(wl)
+    d = torch.from_numpy(wl.w.copy()).cuda()
+    s.dg_step(d, wl.dt, 0)
+    assert np.array_equal(d.cpu().numpy(), wl.w)
+    s.close()
+
+
+def test_step_host_buffer_round_trip(orc, dg):
+    """A CPU tensor is staged through the device by the binding."""
+    import torch
+    wl = W.drop_2d(n=5, p=3, seed=2)
+    s = dg.Solver(wl)
+    h = torch.from_numpy(wl.w.copy())
+    s.dg_step(h, wl.dt, 2)
+    s.close()
+    _assert_state_close(h.numpy(), orc.rk3(problem(orc, wl), wl.w, wl.dt, 2), 1e-12)
+
+
+# ----------------------------------------------------------------------------- diagnostics
+
+@pytest.mark.parametrize("maker", [lambda: W.drop_2d(n=9, p=3, seed=2), lambda: W.slab_1d(nx=40, p=4),
+                                   lambda: W.rayleigh_taylor(n=6, p=4)])
+def test_diag_matches_oracle(orc, dg, maker):
+    import torch
+    wl = maker()
+    ref = orc.diag(problem(orc, wl), wl.w)
+    s = dg.Solver(wl)
+    got = np.array(s.dg_diag(torch.from_numpy(wl.w.copy()).cuda()))
+    s.close()
+    np.testing.assert_allclose(got[:7], ref[:7], rtol=1e-13, atol=1e-13 * np.abs(ref[:7]).max())
+    np.testing.assert_array_equal(got[7:9], ref[7:9])   # min/max phi are exact
+    np.testing.assert_array_equal(got[9:11], ref[9:11])  # P is reproduced bit for bit
+    np.testing.assert_allclose(got[11:15], ref[11:15], rtol=1e-15, atol=1e-300)
+    assert got[15] == ref[15] == 0
+
+
+def test_nonfinite_flag(dg):
+    import torch
+    wl = W.drop_2d(n=4, p=3, seed=1)
+    w = wl.w.copy()
+    w[6, 5] = np.nan
+    s = dg.Solver(wl)
+    s.dg_rhs(torch.from_numpy(w).cuda())
+    assert s.dg_status_read() == -5
+    assert s.dg_status_read() == 0  # cleared
+    s.close()
