@@ -38,7 +38,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="fp32bulk", choices=["fp32bulk", "fp64"])
+    ap.add_argument("--accuracy-steps", type=int, default=500,
+                    help="steps of the FP32-bulk vs FP64 accuracy comparison (the workload's 500)")
     ap.add_argument("--cpu-sample-steps", type=int, default=0,
                     help="oracle steps for the cpu_baseline leg (0 = size for ~15 s)")
     return ap.parse_args()
@@ -114,18 +116,22 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- roofline helpers
 
-KERNEL_SOURCES = ["paper_2306_05002_gb300/csrc/dg_kernels_fp64.cuh", "paper_2306_05002_gb300/csrc/dg_common.cuh"]
+KERNEL_SOURCES = {"fp64": ["paper_2306_05002_gb300/csrc/dg_kernels_fp64.cuh",
+                           "paper_2306_05002_gb300/csrc/dg_common.cuh"],
+                  "fp32bulk": ["paper_2306_05002_gb300/csrc/dg_kernels_fp32.cuh",
+                               "paper_2306_05002_gb300/csrc/dg_kernels_fp64.cuh",
+                               "paper_2306_05002_gb300/csrc/dg_common.cuh"]}
 
 
-def kernel_source_hash():
+def kernel_source_hash(precision="fp64"):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[precision]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, wl_name: str):
+def profiled_traffic(kernel: str, wl_name: str, precision: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{wl_name}.md")
     if not os.path.exists(path):
@@ -133,7 +139,7 @@ def profiled_traffic(kernel: str, wl_name: str):
     txt = open(path).read()
     m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m or not t or m.group(1) != kernel_source_hash():
+    if not m or not t or m.group(1) != kernel_source_hash(precision):
         return None
     return float(t.group(1))
 
@@ -194,6 +200,66 @@ def run_reference(args, rank, world):
 
 # --------------------------------------------------------------------------- our leg
 
+def time_path(dg, wl, precision, steps, warmup, flush, stream, local_rank, sample_clocks):
+    """K timed SSP-RK3 steps through dg_step, L2 flushed before each; returns timings and kernel data."""
+    import torch
+    solver = dg.Solver(wl, precision=precision)
+    w = torch.from_numpy(wl.w.copy()).cuda()
+    for _ in range(warmup):
+        solver.dg_step(w, wl.dt, 1)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank) if sample_clocks else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        solver.dg_step(w, wl.dt, 1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+    clk = clocks.stop() if clocks else None
+    status = solver.dg_status_read()
+    kms = solver.dg_time_kernels(w, nrep=20)
+    flops, bytes_ = solver.dg_kernel_costs()
+    return dict(solver=solver, w=w, ms=ms, wall=wall, clocks=clk, status=status, kms=kms, flops=flops,
+                bytes=bytes_)
+
+
+def accuracy(dg, wl, steps):
+    """Relative L2 error of phi, P, u of the FP32-bulk path against the FP64 path after `steps`."""
+    import numpy as np
+    import torch
+    out = {}
+    for prec in ("fp64", "fp32bulk"):
+        s = dg.Solver(wl, precision=prec)
+        d = torch.from_numpy(wl.w.copy()).cuda()
+        s.dg_step(d, wl.dt, steps)
+        out[prec] = d.cpu().numpy()
+        s.close()
+    # primitives on the host from the FP64 states (stiffened gas, Sec. 2)
+    def prim(w):
+        g1, g2 = wl.gamma
+        C1 = g1 * wl.pinf[0] / (g1 - 1.0)
+        C2 = g2 * wl.pinf[1] / (g2 - 1.0)
+        rho = w[2] + w[3]
+        rhoe = w[6] - 0.5 * (w[4] ** 2 + w[5] ** 2) / rho
+        P = (rhoe - (w[0] * C1 + (1 - w[0]) * C2)) / (w[0] / (g1 - 1.0) + (1 - w[0]) / (g2 - 1.0))
+        return P, w[4] / rho
+    P64, u64 = prim(out["fp64"])
+    P32, u32 = prim(out["fp32bulk"])
+    l2 = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"steps": steps, "reference": "FP64 GPU path (matches the FP64 oracle to 1e-12 per RHS)",
+            "l2_rel_alpha": l2(out["fp32bulk"][0], out["fp64"][0]), "l2_rel_p": l2(P32, P64),
+            "l2_rel_u": l2(u32, u64)}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2306_05002_gb300 as dg
@@ -209,41 +275,36 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     wl = workload(2 + rank)
-    solver = dg.Solver(wl, precision=args.precision)
-    w = torch.from_numpy(wl.w.copy()).cuda()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    other = "fp64" if args.precision == "fp32bulk" else None
 
-    for _ in range(args.warmup):
-        solver.dg_step(w, wl.dt, 1)
     barrier()
+    main = time_path(dg, wl, args.precision, args.steps, args.warmup, flush, stream, local_rank, True)
+    barrier()
+    ref = time_path(dg, wl, other, args.steps, args.warmup, flush, stream, local_rank, False) if other else None
 
-    clocks = ClockSampler(local_rank)
-    clocks.start()
-    time.sleep(0.3)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    barrier()
-    wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()
-        starts[k].record(stream)
-        solver.dg_step(w, wl.dt, 1)
-        ends[k].record(stream)
-    barrier()
-    wall = time.perf_counter() - wall0
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    clk = clocks.stop()
-    status = solver.dg_status_read()
-
-    # per-kernel durations for the roofline of the dominant kernel
-    kms = solver.dg_time_kernels(w, nrep=20)
-    flops, bytes_ = solver.dg_kernel_costs()
-    names = ["k_volume", "k_surface"]
+    # roofline of the dominant kernel of the timed path
+    names = ["k_volume", "k_surface"] if args.precision == "fp64" else ["k_volume32", "k_surface32"]
+    kms, flops, bytes_ = main["kms"], main["flops"], main["bytes"]
     dom = max(range(len(kms)), key=lambda i: kms[i])
-    achieved = flops[dom] / (kms[dom] * 1e-3) / 1e12
+    if args.precision == "fp64":
+        ach = flops[dom] / (kms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": names[dom], "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (ncu: 2 DFMA/clk/SM)"}
+    else:
+        hbm = peaks().get("hbm_gbs", 6800.0)
+        ach = bytes_[dom] / (kms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured"}
+    roof.update({"traffic": profiled_traffic(names[dom], wl.name, args.precision),
+                 "kernel_ms": dict(zip(names, kms)),
+                 "algorithmic_flops_per_launch": dict(zip(names, flops)),
+                 "algorithmic_bytes_per_launch": dict(zip(names, bytes_))})
 
     # end to end through the public API with a pinned host state: H2D, step, D2H
+    solver = main["solver"]
     host = torch.from_numpy(wl.w.copy()).pin_memory()
     for _ in range(2):
         solver.dg_step(host, wl.dt, 1)
@@ -255,35 +316,42 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
 
-    # max over ranks
-    tens = torch.tensor([ms, e2e_t], dtype=torch.float64, device="cuda")
+    acc = accuracy(dg, wl, args.accuracy_steps) if (args.precision == "fp32bulk" and rank == 0) else None
+
+    tens = torch.tensor([main["ms"], e2e_t, ref["ms"] if ref else 0.0], dtype=torch.float64, device="cuda")
     if dist:
         tdist.all_reduce(tens, op=tdist.ReduceOp.MAX)
-    ms_max, e2e_max = tens.tolist()
+    ms_max, e2e_max, ref_ms = tens.tolist()
 
     if rank == 0:
         units = 7 * wl.N * 3
         value = units * args.steps * world / (ms_max * 1e-3)
+        launches = 6 if args.precision == "fp64" else 8
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+                "data": "synthetic",
                 "config": config_of(wl, {"parallelism": f"replicas x{world}", "precision": args.precision,
-                                         "wall_s_timed_region": wall}),
-                "gpu_launches": 6 * args.steps,
-                "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved,
-                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                             "traffic": profiled_traffic(names[dom], wl.name),
-                             "kernel_ms": dict(zip(names, kms)),
-                             "algorithmic_flops_per_launch": dict(zip(names, flops)),
-                             "algorithmic_bytes_per_launch": dict(zip(names, bytes_))},
+                                         "wall_s_timed_region": main["wall"]}),
+                "gpu_launches": launches * args.steps,
+                "roofline": roof,
                 "e2e": {"value": units * e2e_steps * world / e2e_max, "unit": UNIT,
                         "h2d_bytes_per_step": 8 * 7 * wl.N, "d2h_bytes_per_step": 8 * 7 * wl.N},
-                "clocks": clk, "device_status": status}
+                "clocks": main["clocks"], "device_status": main["status"]}
+        if ref:
+            line["fp64"] = {"value": units * args.steps * world / (ref_ms * 1e-3), "unit": UNIT,
+                            "ms_per_step": ref_ms / args.steps, "kernel_ms": dict(zip(["k_volume", "k_surface"],
+                                                                                        ref["kms"])),
+                            "device_status": ref["status"]}
+            line["speedup_vs_fp64"] = ref_ms / ms_max
+        if acc:
+            line["accuracy"] = acc
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
         print(json.dumps(line), flush=True)
-    solver.close()
+    main["solver"].close()
+    if ref:
+        ref["solver"].close()
 
 
 def main():

@@ -17,6 +17,7 @@
 
 #include "dg_common.cuh"
 #include "dg_kernels_fp64.cuh"
+#include "dg_kernels_fp32.cuh"
 #include "dgpf.h"
 
 namespace dgpf {
@@ -25,6 +26,42 @@ bool kernels_fp64_p2(int, bool, bool, KernelSet *);
 bool kernels_fp64_p3(int, bool, bool, KernelSet *);
 bool kernels_fp64_p4(int, bool, bool, KernelSet *);
 bool kernels_fp64_p5(int, bool, bool, KernelSet *);
+
+bool kernels_fp32_p1(int, bool, bool, KernelSet32 *);
+bool kernels_fp32_p2(int, bool, bool, KernelSet32 *);
+bool kernels_fp32_p3(int, bool, bool, KernelSet32 *);
+bool kernels_fp32_p4(int, bool, bool, KernelSet32 *);
+bool kernels_fp32_p5(int, bool, bool, KernelSet32 *);
+
+bool kernels_fp32(int p, int dim, bool viscous, bool st, KernelSet32 *out) {
+  switch (p) {
+    case 1: return kernels_fp32_p1(dim, viscous, st, out);
+    case 2: return kernels_fp32_p2(dim, viscous, st, out);
+    case 3: return kernels_fp32_p3(dim, viscous, st, out);
+    case 4: return kernels_fp32_p4(dim, viscous, st, out);
+    case 5: return kernels_fp32_p5(dim, viscous, st, out);
+    default: return false;
+  }
+}
+
+// FP64 <-> FP32-bulk internal state (see dg_kernels_fp32.cuh).
+__global__ void k_to32(int N, double C2, double dC, const double *__restrict__ w, float *__restrict__ w32) {
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
+    const double phi = w[n];
+#pragma unroll
+    for (int v = 0; v < RE; ++v) w32[(long)v * N + n] = (float)w[(long)v * N + n];
+    w32[(long)RE * N + n] = (float)(w[(long)RE * N + n] - fma(dC, phi, C2));
+  }
+}
+
+__global__ void k_to64(int N, double C2, double dC, const float *__restrict__ w32, double *__restrict__ w) {
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
+    const double phi = (double)w32[n];
+#pragma unroll
+    for (int v = 0; v < RE; ++v) w[(long)v * N + n] = (double)w32[(long)v * N + n];
+    w[(long)RE * N + n] = (double)w32[(long)RE * N + n] + fma(dC, phi, C2);
+  }
+}
 
 bool kernels_fp64(int p, int dim, bool viscous, bool st, KernelSet *out) {
   switch (p) {
@@ -191,6 +228,12 @@ struct dg_ctx {
   double hx, hy, J;
   Params prm;
   KernelSet ks;
+  KernelSet32 ks32;
+  ParamsF pf;
+  int prec = DG_FP64;
+  float *d_opsf = nullptr, *d_ws32 = nullptr, *d_w1_32 = nullptr, *d_w2_32 = nullptr, *d_rvol32 = nullptr,
+        *d_trace32 = nullptr;
+  int conv_blocks = 1;
   double *d_ops = nullptr, *d_w1 = nullptr, *d_w2 = nullptr, *d_rvol = nullptr, *d_trace = nullptr;
   double *d_part = nullptr, *d_diag = nullptr;
   unsigned *d_status = nullptr;
@@ -232,6 +275,12 @@ static void free_ctx(dg_ctx *c) {
   cudaFree(c->d_part);
   cudaFree(c->d_diag);
   cudaFree(c->d_status);
+  cudaFree(c->d_opsf);
+  cudaFree(c->d_ws32);
+  cudaFree(c->d_w1_32);
+  cudaFree(c->d_w2_32);
+  cudaFree(c->d_rvol32);
+  cudaFree(c->d_trace32);
   if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
 }
@@ -264,7 +313,8 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
   if (opts) o = *opts;
   if (o.c_ip <= 0.0) o.c_ip = 1.0;
   if (o.barrier_timeout_ms <= 0.0) o.barrier_timeout_ms = 1000.0;
-  if (o.prec != DG_FP64) return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: precision mode not available");
+  if (o.prec != DG_FP64 && o.prec != DG_FP32_BULK)
+    return fail(nullptr, DG_ERR_ARG, "dg_create: precision must be DG_FP64 or DG_FP32_BULK");
   const long long E = (long long)mesh->nx * mesh->ny;
   const int P1 = p + 1;
   const int Np = mesh->dim == 2 ? P1 * P1 : P1;
@@ -289,7 +339,9 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
   c->hy = c->dim == 2 ? (mesh->y1 - mesh->y0) / mesh->ny : 1.0;
   c->J = c->dim == 2 ? 0.25 * c->hx * c->hy : 0.5 * c->hx;
 
-  if (!kernels_fp64(p, c->dim, o.viscous != 0, o.surface_tension != 0, &c->ks)) {
+  c->prec = o.prec;
+  if (!kernels_fp64(p, c->dim, o.viscous != 0, o.surface_tension != 0, &c->ks) ||
+      !kernels_fp32(p, c->dim, o.viscous != 0, o.surface_tension != 0, &c->ks32)) {
     free_ctx(c);
     return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: viscous/surface terms need dim = 2");
   }
@@ -348,13 +400,28 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
   q.gravity = o.gravity != 0;
   q.check_finite = o.check_finite != 0;
 
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
+  const bool f64 = c->prec == DG_FP64;
   const size_t sbytes = c->len * sizeof(double);
   const size_t tbytes = (size_t)c->ks.nt * c->E * c->NFK * sizeof(double);
   c->nparts = std::min(1024, (c->N + DIAG_THREADS - 1) / DIAG_THREADS);
-  if ((e = cudaMalloc(&c->d_ops, ops.size() * sizeof(double))) != cudaSuccess ||
-      (e = cudaMalloc(&c->d_w1, sbytes)) != cudaSuccess || (e = cudaMalloc(&c->d_w2, sbytes)) != cudaSuccess ||
-      (e = cudaMalloc(&c->d_rvol, sbytes)) != cudaSuccess || (e = cudaMalloc(&c->d_trace, tbytes)) != cudaSuccess ||
+  c->conv_blocks = std::max(1, std::min(152 * 8, (c->N + 255) / 256));
+  c->pf = to_float(c->prm);
+  std::vector<float> opsf(ops.begin(), ops.end());
+  auto alloc32 = [&](float **ptr, size_t n) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, n * sizeof(float));
+    return e == cudaSuccess;
+  };
+  if (!f64) {
+    const size_t n32 = c->len;
+    const size_t t32 = (size_t)c->ks32.nt * c->E * c->NFK;
+    alloc32(&c->d_opsf, opsf.size()) && alloc32(&c->d_ws32, n32) && alloc32(&c->d_w1_32, n32) &&
+        alloc32(&c->d_w2_32, n32) && alloc32(&c->d_rvol32, n32) && alloc32(&c->d_trace32, t32);
+  }
+  if (e != cudaSuccess || (e = cudaMalloc(&c->d_ops, ops.size() * sizeof(double))) != cudaSuccess ||
+      (f64 && ((e = cudaMalloc(&c->d_w1, sbytes)) != cudaSuccess || (e = cudaMalloc(&c->d_w2, sbytes)) != cudaSuccess ||
+               (e = cudaMalloc(&c->d_rvol, sbytes)) != cudaSuccess ||
+               (e = cudaMalloc(&c->d_trace, tbytes)) != cudaSuccess)) ||
       (e = cudaMalloc(&c->d_part, (size_t)c->nparts * DIAG_N * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&c->d_diag, DIAG_N * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&c->d_status, sizeof(unsigned))) != cudaSuccess) {
@@ -364,6 +431,8 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
                 std::string("dg_create: device allocation failed: ") + cudaGetErrorString(e));
   }
   if ((e = cudaMemcpy(c->d_ops, ops.data(), ops.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (!f64 && (e = cudaMemcpy(c->d_opsf, opsf.data(), opsf.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
+                   cudaSuccess) ||
       (e = cudaMemset(c->d_status, 0, sizeof(unsigned))) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess) {
     free_ctx(c);
@@ -394,11 +463,32 @@ static dg_status run_stage(dg_ctx *c, int mode, double dt, const double *w0, con
   return DG_OK;
 }
 
+// One FP32-bulk stage.  in64 (optional): read the FP64 state in the volume
+// kernel and write the FP32 internal state to c->d_ws32 on the way.
+static dg_status run_stage32(dg_ctx *c, int mode, float dt, const float *w0, const float *ws, float *out32,
+                             double *out64, cudaStream_t s, const double *in64 = nullptr) {
+  cudaError_t e = c->ks32.volume(c->prm, c->pf, c->d_opsf, ws, c->d_rvol32, c->d_trace32, in64,
+                                 in64 ? c->d_ws32 : nullptr, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "volume kernel launch");
+  e = c->ks32.surface(c->prm, c->pf, c->d_opsf, mode, dt, w0, ws, c->d_rvol32, c->d_trace32, out32, out64, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "surface kernel launch");
+  return DG_OK;
+}
+
+static dg_status convert(dg_ctx *c, bool to32, double *w, cudaStream_t s) {
+  if (to32) k_to32<<<c->conv_blocks, 256, 0, s>>>(c->N, c->prm.C2, c->prm.dC, w, c->d_ws32);
+  else k_to64<<<c->conv_blocks, 256, 0, s>>>(c->N, c->prm.C2, c->prm.dC, c->d_ws32, w);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "state conversion launch");
+}
+
 extern "C" dg_status dg_rhs(dg_ctx *c, const double *w, double *L, void *stream) {
   if (!c) return DG_ERR_ARG;
   if (!w || !L) return fail(c, DG_ERR_ARG, "dg_rhs: null array");
   if (w == L) return fail(c, DG_ERR_ARG, "dg_rhs: w and L must not overlap");
-  return run_stage(c, MODE_RHS, 0.0, w, w, L, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->prec == DG_FP64) return run_stage(c, MODE_RHS, 0.0, w, w, L, s);
+  return run_stage32(c, MODE_RHS, 0.f, c->d_ws32, c->d_ws32, nullptr, L, s, w);
 }
 
 // One SSP-RK3 step (Shu-Osher): w1 = w + dt L(w); w2 = 3/4 w + 1/4 (w1 + dt L(w1));
@@ -406,6 +496,14 @@ extern "C" dg_status dg_rhs(dg_ctx *c, const double *w, double *L, void *stream)
 // node's w0 value is read by the thread that overwrites it).
 static dg_status enqueue_step(dg_ctx *c, double *w, double dt, cudaStream_t s) {
   dg_status r;
+  if (c->prec != DG_FP64) {
+    // The first stage reads the FP64 state (and leaves the FP32 internal state
+    // in d_ws32); the last stage writes the FP64 state back.
+    const float d = (float)dt;
+    if ((r = run_stage32(c, MODE_S1, d, c->d_ws32, c->d_ws32, c->d_w1_32, nullptr, s, w)) != DG_OK) return r;
+    if ((r = run_stage32(c, MODE_S2, d, c->d_ws32, c->d_w1_32, c->d_w2_32, nullptr, s)) != DG_OK) return r;
+    return run_stage32(c, MODE_S3, d, c->d_ws32, c->d_w2_32, nullptr, w, s);
+  }
   if ((r = run_stage(c, MODE_S1, dt, w, w, c->d_w1, s)) != DG_OK) return r;
   if ((r = run_stage(c, MODE_S2, dt, w, c->d_w1, c->d_w2, s)) != DG_OK) return r;
   return run_stage(c, MODE_S3, dt, w, c->d_w2, w, s);
@@ -485,11 +583,21 @@ extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_
   for (auto &x : ev) cudaEventCreate(&x);
   double acc[2] = {0.0, 0.0};
   for (int r = 0; r < nrep; ++r) {
-    cudaEventRecord(ev[0], s);
-    c->ks.volume(c->prm, w, c->d_rvol, c->d_trace, s);
-    cudaEventRecord(ev[1], s);
-    c->ks.surface(c->prm, MODE_RHS, 0.0, w, w, c->d_rvol, c->d_trace, c->d_w1, s);
-    cudaEventRecord(ev[2], s);
+    if (c->prec == DG_FP64) {
+      cudaEventRecord(ev[0], s);
+      c->ks.volume(c->prm, w, c->d_rvol, c->d_trace, s);
+      cudaEventRecord(ev[1], s);
+      c->ks.surface(c->prm, MODE_RHS, 0.0, w, w, c->d_rvol, c->d_trace, c->d_w1, s);
+      cudaEventRecord(ev[2], s);
+    } else {  // one stage of the step as dg_step launches it (FP32 state in, FP32 stage out)
+      if (r == 0) convert(c, true, const_cast<double *>(w), s);
+      cudaEventRecord(ev[0], s);
+      c->ks32.volume(c->prm, c->pf, c->d_opsf, c->d_ws32, c->d_rvol32, c->d_trace32, nullptr, nullptr, s);
+      cudaEventRecord(ev[1], s);
+      c->ks32.surface(c->prm, c->pf, c->d_opsf, MODE_S2, 1e-9f, c->d_ws32, c->d_ws32, c->d_rvol32, c->d_trace32,
+                      c->d_w1_32, nullptr, s);
+      cudaEventRecord(ev[2], s);
+    }
     cudaEventSynchronize(ev[2]);
     float t0 = 0.f, t1 = 0.f;
     cudaEventElapsedTime(&t0, ev[0], ev[1]);
@@ -519,9 +627,14 @@ extern "C" int dg_kernel_costs(const dg_ctx *c, double *flops, double *bytes, in
   if (st) fv += 2 * d * P1 + 8;
   // surface kernel: per face node 133 (+30 viscous); per node gather/lift/update ~104
   double fs = fface * (133 + (visc ? 30 : 0)) + 7 * fface + 12 * 2 * d + 14 + 35;
-  const double nt = c->ks.nt;
-  const double bv = 8.0 * (E * Np * (7 + 7) + E * NFK * nt);
-  const double bs = 8.0 * (E * NFK * nt * 2 + E * Np * (7 * 4));
+  // Bytes: the volume kernel reads the state and writes the volume part and
+  // the face traces; the surface kernel reads both traces of every face node,
+  // the volume part, the stage input and the step start, and writes the stage.
+  const double nt = c->prec == DG_FP64 ? c->ks.nt : c->ks32.nt;
+  const double word = c->prec == DG_FP64 ? 8.0 : 4.0;
+  if (c->prec != DG_FP64) fv += 3 * 2 * d * P1;  // compression term of the reduced energy
+  const double bv = word * (E * Np * (7 + 7) + E * NFK * nt);
+  const double bs = word * (E * NFK * nt * 2 + E * Np * (7 * 4));
   const int nk = std::min(nmax, 2);
   const double F[2] = {fv * E * Np, fs * E * Np}, Bb[2] = {bv, bs};
   for (int k = 0; k < nk; ++k) {

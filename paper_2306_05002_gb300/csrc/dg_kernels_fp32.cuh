@@ -1,0 +1,511 @@
+// dg_kernels_fp32.cuh -- FP32-bulk kernels of the DG right-hand side (GB300, sm_103a).
+//
+// GB300 executes FP64 at about 1/73 of its FP32 rate, so this path keeps FP64
+// out of the stage loop.  Internally the state is held in FP32 with the total
+// energy replaced by the reduced energy
+//     rhoEt = rho E - Cmix(phi),   Cmix(phi) = C_2 + (C_1 - C_2) phi,
+//     C_l = gamma_l Pinf_l / (gamma_l - 1),
+// i.e. rho E minus the stiffened-gas constant of Sec. 2.  The pressure is then
+// P = (rhoEt - rho k) / (phi g_1 + (1 - phi) g_2) with no cancellation, so it
+// is accurate in FP32.  The FP64 pressure recovery happens once per dg_step
+// call, in the conversion kernels (k_to32 / k_to64).
+//
+// Evolution of rhoEt.  With the collocated GLL quadrature the weak-form volume
+// term satisfies summation by parts, and the right-hand side of rhoEt,
+// L(rhoEt) = L(rho E) - (C_1 - C_2) L(phi), equals -- exactly, in exact
+// arithmetic -- the energy equation of the paper with rhoEt in place of rho E
+// in the convective flux, B - (C_1 - C_2) = P (gamma_1 g_1 - gamma_2 g_2) as
+// the a_1 coefficient, and a compression term
+//     - sum_c D_ic Cmix(phi_c) (u_c - u_i)              (volume, per direction)
+//     - M^-1 int l_i 1/2 Cmix(phi+) (u+ - u-) . m       (faces).
+// Written with velocity differences, this term vanishes to rounding in a
+// uniform flow, which is what keeps the pressure at interfaces in FP32.
+// All other terms are those of the FP64 kernels (dg_kernels_fp64.cuh), but
+// written in the strong form, which summation by parts makes identical to the
+// weak form of Sec. 3:  L_i = -(div_h F)_i + M^-1 int l_i (F- - F^) . m.
+// Every derivative is contracted over differences, sum_c D_ic (f_c - f_i)
+// (D annihilates constants), and every face term is a difference F- - F^.
+// In FP32 this makes the rounding error scale with the variation of a field
+// rather than with its offset (P ~ 1e5, psi, phi ~ 1), and keeps a uniform
+// state exactly steady.
+//
+// The first stage of a step can read the FP64 state directly (converting it
+// on load and writing the FP32 internal state), and the last stage can write
+// the FP64 state directly, so a step is six launches.
+#pragma once
+
+#include "dg_common.cuh"
+#include "dg_kernels_fp64.cuh"
+
+namespace dgpf {
+
+// Single-precision copy of the closure constants.
+struct ParamsF {
+  float C2, dC, g1, g2, Bp;
+  float rho01, rho02, drho0, mu1, mu2, sigma, gx, gy, Gamma, eps, eta_x, eta_y;
+};
+
+__host__ inline ParamsF to_float(const Params &p) {
+  return ParamsF{(float)p.C2, (float)p.dC, (float)p.g1, (float)p.g2, (float)p.Bp, (float)p.rho01, (float)p.rho02,
+                 (float)p.drho0, (float)p.mu1, (float)p.mu2, (float)p.sigma, (float)p.gx, (float)p.gy,
+                 (float)p.Gamma, (float)p.eps, (float)p.eta_x, (float)p.eta_y};
+}
+
+// FP32 operator tables: same layout as OpsLayout, stored after the FP64 table.
+template <int P, int DIM, bool VISC, bool ST>
+__global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
+k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, const float *__restrict__ w,
+           float *__restrict__ rvol, float *__restrict__ tr, const double *__restrict__ w64,
+           float *__restrict__ w32out) {
+  using G = Geom<P, DIM, VISC, ST>;
+  constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
+  constexpr int P11 = P1 * P1;
+  constexpr int NS = 12;
+  __shared__ float s_op[2 * P11];
+  __shared__ float s_f[NS][EPB][NP];
+
+  for (int t = threadIdx.x; t < 2 * P11; t += blockDim.x) s_op[t] = opsf[t];
+  const float *Dx = s_op, *Dy = s_op + P11;
+
+  const int le_raw = threadIdx.x / NP;
+  const bool lane = le_raw < EPB;
+  const int le = lane ? le_raw : EPB - 1;
+  const int a = threadIdx.x % NP;
+  const int e = blockIdx.x * EPB + le;
+  const bool act = lane && e < prm.E;
+  const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
+  const int N = prm.N;
+  const long n = (long)(act ? e : 0) * NP + a;
+
+  float q[NV];
+  if (w64) {
+    // first stage: convert the FP64 state (the stiffened-gas constant leaves rho E in FP64)
+    double d[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) d[v] = act ? __ldg(w64 + (long)v * N + n) : (v == M1 || v == M2 ? 1.0 : 0.0);
+#pragma unroll
+    for (int v = 0; v < RE; ++v) q[v] = (float)d[v];
+    q[RE] = (float)(d[RE] - fma(prm.dC, d[PHI], prm.C2));
+    if (act) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) w32out[(long)v * N + n] = q[v];
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = act ? __ldg(w + (long)v * N + n) : (v == M1 || v == M2 ? 1.f : 0.f);
+  }
+  const float phi = q[PHI], psi = q[PSI];
+  const float rho = q[M1] + q[M2];
+  const float ir = 1.0f / rho;
+  const float u = q[RU] * ir;
+  const float v = DIM == 2 ? q[RV] * ir : 0.f;
+  const float k = 0.5f * (u * u + v * v);
+  const float Gm = fmaf(phi, pf.g1 - pf.g2, pf.g2);
+  const float Pr = (q[RE] - rho * k) / Gm;
+  const float Cm = fmaf(pf.dC, phi, pf.C2);
+  const float Bq = Pr * pf.Bp;  // B - (C_1 - C_2)
+
+  if (lane) {
+    s_f[0][le][a] = phi;
+    s_f[1][le][a] = psi;
+    s_f[2][le][a] = u;
+    s_f[3][le][a] = v;
+  }
+  __syncthreads();
+
+  float gpx = 0.f, gpy = 0.f, gsx = 0.f, gsy = 0.f, gux = 0.f, guy = 0.f, gvx = 0.f, gvy = 0.f, comp = 0.f;
+#pragma unroll
+  for (int c = 0; c < P1; ++c) {
+    const float dx = Dx[i * P1 + c];
+    const int ax = c + P1 * j;
+    const float phc = s_f[0][le][ax], uc = s_f[2][le][ax];
+    gpx = fmaf(dx, phc - phi, gpx);
+    gsx = fmaf(dx, s_f[1][le][ax] - psi, gsx);
+    comp = fmaf(dx * fmaf(pf.dC, phc, pf.C2), uc - u, comp);
+    if (VISC) {
+      gux = fmaf(dx, uc - u, gux);
+      gvx = fmaf(dx, s_f[3][le][ax] - v, gvx);
+    }
+    if (DIM == 2) {
+      const float dy = Dy[j * P1 + c];
+      const int ay = i + P1 * c;
+      const float phy = s_f[0][le][ay], vc = s_f[3][le][ay];
+      gpy = fmaf(dy, phy - phi, gpy);
+      gsy = fmaf(dy, s_f[1][le][ay] - psi, gsy);
+      comp = fmaf(dy * fmaf(pf.dC, phy, pf.C2), vc - v, comp);
+      if (VISC) {
+        guy = fmaf(dy, s_f[2][le][ay] - u, guy);
+        gvy = fmaf(dy, vc - v, gvy);
+      }
+    }
+  }
+
+  const float g2 = gsx * gsx + gsy * gsy;
+  float nx = 0.f, ny = 0.f;
+  if (g2 >= 1e-24f) {
+    const float r = rsqrtf(g2);
+    nx = gsx * r;
+    ny = gsy * r;
+  }
+  const float sphi = phi * (1.f - phi);
+  const float a1x = pf.Gamma * (pf.eps * gpx - sphi * nx);
+  const float a1y = pf.Gamma * (pf.eps * gpy - sphi * ny);
+
+  float txx = 0.f, txy = 0.f, tyy = 0.f, mu = 0.f;
+  if (VISC) {
+    mu = pf.mu1 * phi + pf.mu2 * (1.f - phi);
+    const float div3 = (gux + gvy) * (1.f / 3.f);
+    txx = 2.f * mu * (gux - div3);
+    tyy = 2.f * mu * (gvy - div3);
+    txy = mu * (guy + gvx);
+  }
+
+  float kappa = 0.f;
+  if (ST) {
+    if (lane) {
+      s_f[4][le][a] = nx;
+      s_f[5][le][a] = ny;
+    }
+    __syncthreads();
+    float dv = 0.f;
+#pragma unroll
+    for (int c = 0; c < P1; ++c) {
+      dv = fmaf(Dx[i * P1 + c], s_f[4][le][c + P1 * j] - nx, dv);
+      if (DIM == 2) dv = fmaf(Dy[j * P1 + c], s_f[5][le][i + P1 * c] - ny, dv);
+    }
+    kappa = -dv;
+  }
+
+  const float cE = pf.drho0 * k + Bq;
+  float F[NS];
+  F[0] = -a1x;
+  F[1] = -a1y;
+  F[2] = q[M1] * u - pf.rho01 * a1x;
+  F[3] = q[M1] * v - pf.rho01 * a1y;
+  F[4] = q[M2] * u + pf.rho02 * a1x;
+  F[5] = q[M2] * v + pf.rho02 * a1y;
+  F[6] = q[RU] * u + Pr - pf.drho0 * a1x * u - txx;
+  F[7] = q[RU] * v - pf.drho0 * a1y * u - txy;
+  F[8] = q[RV] * u - pf.drho0 * a1x * v - txy;
+  F[9] = q[RV] * v + Pr - pf.drho0 * a1y * v - tyy;
+  F[10] = (q[RE] + Pr) * u - cE * a1x - (txx * u + txy * v);
+  F[11] = (q[RE] + Pr) * v - cE * a1y - (txy * u + tyy * v);
+  __syncthreads();
+  if (lane) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) s_f[s][le][a] = F[s];
+  }
+  __syncthreads();
+
+  // Strong-form volume term -(div_h F)_i, contracted over differences.
+  float R[NV];
+#pragma unroll
+  for (int eq = 0; eq < 6; ++eq) {
+    float acc = 0.f;
+    const float fx = F[2 * eq], fy = F[2 * eq + 1];
+#pragma unroll
+    for (int c = 0; c < P1; ++c) {
+      acc = fmaf(Dx[i * P1 + c], s_f[2 * eq][le][c + P1 * j] - fx, acc);
+      if (DIM == 2) acc = fmaf(Dy[j * P1 + c], s_f[2 * eq + 1][le][i + P1 * c] - fy, acc);
+    }
+    R[eq == 0 ? PHI : eq + 1] = -acc;
+  }
+  R[PHI] -= u * gpx + v * gpy;
+  R[PSI] = -(u * gsx + v * gsy);
+  R[RE] -= comp;
+  if (prm.gravity) {
+    R[RU] += rho * pf.gx;
+    R[RV] += rho * pf.gy;
+    R[RE] += rho * (pf.gx * u + pf.gy * v);
+  }
+  if (ST) {
+    const float s = pf.sigma * kappa * sqrtf(gpx * gpx + gpy * gpy);
+    R[RU] += s * nx;
+    R[RV] += s * ny;
+    R[RE] += s * (u * nx + v * ny);
+  }
+  if (act) {
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) rvol[(long)vv * N + n] = R[vv];
+  }
+
+  const bool onW = i == 0, onE = i == P;
+  const bool onS = DIM == 2 && j == 0, onN = DIM == 2 && j == P;
+  if (act && (onW || onE || onS || onN)) {
+    const float c = sqrtf((Pr + (Pr + Cm) / Gm) * ir);
+    const float tx[NT_VISCOUS] = {phi, psi, q[M1], q[M2], q[RU], q[RV], q[RE], u, v, Pr, c, Bq,
+                                  0.f, 0.f, 0.f, 0.f, mu};
+    const long base = (long)e * NFK;
+    const long stride = (long)prm.E * NFK;
+    auto put = [&](int f, int kk, float gn, float nn, float t1, float t2) {
+      const long o = base + f * NK + kk;
+#pragma unroll
+      for (int qf = 0; qf < T_GPHI; ++qf) tr[qf * stride + o] = tx[qf];
+      tr[T_GPHI * stride + o] = gn;
+      tr[T_N * stride + o] = nn;
+      if (VISC) {
+        tr[T_TX * stride + o] = t1;
+        tr[T_TY * stride + o] = t2;
+        tr[T_MU * stride + o] = mu;
+      }
+    };
+    const int kx = DIM == 2 ? j : 0;
+    if (onW) put(0, kx, gpx, nx, txx, txy);
+    if (onE) put(1, kx, gpx, nx, txx, txy);
+    if (onS) put(2, i, gpy, ny, txy, tyy);
+    if (onN) put(3, i, gpy, ny, txy, tyy);
+  }
+}
+
+// Surface kernel of the FP32-bulk path.  mode MODE_RHS writes L for the
+// paper's variables in FP64 (out64, with L(rho E) = L(rhoEt) + (C_1-C_2) L(phi));
+// the stage modes write the FP32 internal state (out32).
+template <int P, int DIM, bool VISC, bool ST>
+__global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
+k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt,
+            const float *__restrict__ w0, const float *__restrict__ ws, const float *__restrict__ rvol,
+            const float *__restrict__ tr, float *__restrict__ out32, double *__restrict__ out64) {
+  using G = Geom<P, DIM, VISC, ST>;
+  constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK, NT = G::NT;
+  const OpsLayout L{P1, NP};
+  __shared__ float s_op[4 * P1 * P1 + 3 * P1 + NP];
+  __shared__ float s_surf[EPB][NFK][NV];
+  __shared__ float s_lift[EPB][NFK][6];
+
+  for (int t = threadIdx.x; t < L.size(); t += blockDim.x) s_op[t] = opsf[t];
+  __syncthreads();
+  const float *Dx = s_op + L.Dx(), *Dy = s_op + L.Dy();
+  const float *invM = s_op + L.invM(), *wfx = s_op + L.wfx(), *wfy = s_op + L.wfy();
+
+  const int le_raw = threadIdx.x / NP;
+  const bool lane = le_raw < EPB;
+  const int le = lane ? le_raw : EPB - 1;
+  const int a = threadIdx.x % NP;
+  const int e = blockIdx.x * EPB + le;
+  const bool act = lane && e < prm.E;
+  const long stride = (long)prm.E * NFK;
+
+  for (int t = a; t < NFK && lane; t += NP) {
+    const int f = t / NK, kk = t % NK;
+    const int e2 = act ? neighbour(prm, e, f) : -1;
+    const bool wall = e2 < 0;
+    const bool xf = f < 2;
+    const float sg = (f & 1) ? 1.f : -1.f;
+    float Tm[NT], Tp[NT];
+    const long om = (long)(act ? e : 0) * NFK + t;
+#pragma unroll
+    for (int qf = 0; qf < NT; ++qf) Tm[qf] = act ? __ldg(tr + qf * stride + om) : (qf == T_M1 ? 1.f : 0.f);
+    if (!wall) {
+      const long op = (long)e2 * NFK + (f ^ 1) * NK + kk;
+#pragma unroll
+      for (int qf = 0; qf < NT; ++qf) Tp[qf] = __ldg(tr + qf * stride + op);
+    } else {
+#pragma unroll
+      for (int qf = 0; qf < NT; ++qf) Tp[qf] = Tm[qf];
+      if (prm.bc[f] == BC_SLIP) {
+        if (xf) { Tp[T_RU] = -Tm[T_RU]; Tp[T_U] = -Tm[T_U]; }
+        else    { Tp[T_RV] = -Tm[T_RV]; Tp[T_V] = -Tm[T_V]; }
+      } else {
+        Tp[T_RU] = -Tm[T_RU]; Tp[T_U] = -Tm[T_U];
+        Tp[T_RV] = -Tm[T_RV]; Tp[T_V] = -Tm[T_V];
+      }
+    }
+    const float mx = xf ? sg : 0.f, my = xf ? 0.f : sg;
+    const float unm = Tm[T_U] * mx + Tm[T_V] * my;
+    const float unp = Tp[T_U] * mx + Tp[T_V] * my;
+    const float lam = fmaxf(fabsf(unm) + Tm[T_C], fabsf(unp) + Tp[T_C]);
+    const float wf = xf ? wfx[kk] : wfy[kk];
+
+    float S[NV];
+    {
+      const float Fm[5] = {Tm[T_M1] * unm, Tm[T_M2] * unm, Tm[T_RU] * unm + Tm[T_P] * mx,
+                           Tm[T_RV] * unm + Tm[T_P] * my, (Tm[T_RE] + Tm[T_P]) * unm};
+      const float Fp[5] = {Tp[T_M1] * unp, Tp[T_M2] * unp, Tp[T_RU] * unp + Tp[T_P] * mx,
+                           Tp[T_RV] * unp + Tp[T_P] * my, (Tp[T_RE] + Tp[T_P]) * unp};
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {  // F- - F^ = (F- - F+)/2 + lambda [[w]]
+        const int vv = M1 + c;
+        S[vv] = wf * (0.5f * (Fm[c] - Fp[c]) + lam * 0.5f * (Tp[vv] - Tm[vv]));
+      }
+    }
+    // compression term on the face: -1/2 Cmix(phi+) (u+ - u-) . m
+    S[RE] -= wf * 0.5f * fmaf(pf.dC, Tp[T_PHI], pf.C2) * (unp - unm);
+    S[PHI] = wf * (lam - unm) * 0.5f * (Tp[T_PHI] - Tm[T_PHI]);
+    S[PSI] = wf * (lam - unm) * 0.5f * (Tp[T_PSI] - Tm[T_PSI]);
+
+    float lift[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    {
+      // SIP flux minus the own trace of the a_1 flux, for every a_1-derived term:
+      // C^ a^.m - C- a-.m (at a wall no a_1 flux crosses: a^ = 0)
+      const float km = 0.5f * (Tm[T_U] * Tm[T_U] + Tm[T_V] * Tm[T_V]);
+      const float a1m = pf.Gamma * (pf.eps * Tm[T_GPHI] - Tm[T_PHI] * (1.f - Tm[T_PHI]) * Tm[T_N]) * sg;
+      const float Co[6] = {1.f, pf.rho01, -pf.rho02, pf.drho0 * Tm[T_U], pf.drho0 * Tm[T_V],
+                           Tm[T_B] + pf.drho0 * km};
+      const int slot[6] = {PHI, M1, M2, RU, RV, RE};
+      if (!wall) {
+        const float eta = xf ? pf.eta_x : pf.eta_y;
+        const float jump = Tp[T_PHI] - Tm[T_PHI];
+        const float gn = 0.5f * (Tp[T_GPHI] + Tm[T_GPHI]) * sg;
+        const float sharp =
+            0.5f * (Tp[T_PHI] * (1.f - Tp[T_PHI]) * Tp[T_N] + Tm[T_PHI] * (1.f - Tm[T_PHI]) * Tm[T_N]) * sg;
+        const float ahat = pf.Gamma * (pf.eps * (gn + eta * jump) - sharp);
+        const float kp = 0.5f * (Tp[T_U] * Tp[T_U] + Tp[T_V] * Tp[T_V]);
+        const float Cq[6] = {1.f, pf.rho01, -pf.rho02, pf.drho0 * 0.5f * (Tp[T_U] + Tm[T_U]),
+                             pf.drho0 * 0.5f * (Tp[T_V] + Tm[T_V]),
+                             0.5f * (Tp[T_B] + Tm[T_B]) + pf.drho0 * 0.5f * (kp + km)};
+        const float sym = -wf * 0.5f * pf.Gamma * pf.eps * jump;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          S[slot[c]] += wf * (Cq[c] * ahat - Co[c] * a1m);
+          lift[c] = Cq[c] * sym;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) S[slot[c]] -= wf * Co[c] * a1m;
+      }
+    }
+    if (VISC) {
+      const float eta = xf ? pf.eta_x : pf.eta_y;
+      const float mua = 0.5f * (Tp[T_MU] + Tm[T_MU]);
+      const float tmx = Tm[T_TX] * sg, tmy = Tm[T_TY] * sg;
+      const float tpx = Tp[T_TX] * sg, tpy = Tp[T_TY] * sg;
+      // tau^ . m - tau- . m
+      S[RU] += wf * (0.5f * (tpx - tmx) + eta * mua * (Tp[T_U] - Tm[T_U]));
+      S[RV] += wf * (0.5f * (tpy - tmy) + eta * mua * (Tp[T_V] - Tm[T_V]));
+      const float km = 0.5f * (Tm[T_U] * Tm[T_U] + Tm[T_V] * Tm[T_V]);
+      const float kp = 0.5f * (Tp[T_U] * Tp[T_U] + Tp[T_V] * Tp[T_V]);
+      const float tum = tmx * Tm[T_U] + tmy * Tm[T_V];
+      const float tup = tpx * Tp[T_U] + tpy * Tp[T_V];
+      S[RE] += wf * (0.5f * (tup - tum) + eta * mua * (kp - km));
+    }
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) s_surf[le][t][vv] = S[vv];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s_lift[le][t][c] = lift[c];
+  }
+  __syncthreads();
+
+  if (!act) return;
+  const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
+  float acc[NV] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  auto face_add = [&](int f, int kk) {
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) acc[vv] += s_surf[le][f * NK + kk][vv];
+  };
+  const int kx = DIM == 2 ? j : 0;
+  if (i == 0) face_add(0, kx);
+  if (i == P) face_add(1, kx);
+  if (DIM == 2 && j == 0) face_add(2, i);
+  if (DIM == 2 && j == P) face_add(3, i);
+  {
+    const int slot[6] = {PHI, M1, M2, RU, RV, RE};
+    const float lw = -Dx[0 * P1 + i], le_ = Dx[P * P1 + i];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      acc[slot[c]] += s_lift[le][0 * NK + kx][c] * lw + s_lift[le][1 * NK + kx][c] * le_;
+    if (DIM == 2) {
+      const float ls = -Dy[0 * P1 + j], ln = Dy[P * P1 + j];
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+        acc[slot[c]] += s_lift[le][2 * NK + i][c] * ls + s_lift[le][3 * NK + i][c] * ln;
+    }
+  }
+  const float im = invM[a];
+  const long n = (long)e * NP + a;
+  const int N = prm.N;
+  float Lv[NV];
+#pragma unroll
+  for (int vv = 0; vv < NV; ++vv) Lv[vv] = __ldg(rvol + (long)vv * N + n) + acc[vv] * im;
+  bool bad = false;
+  if (mode == MODE_RHS) {
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) {
+      double r = (double)Lv[vv];
+      if (vv == RE) r = fma(prm.dC, (double)Lv[PHI], r);
+      bad |= !isfinite(r);
+      out64[(long)vv * N + n] = r;
+    }
+  } else {
+    float r[NV];
+#pragma unroll
+    for (int vv = 0; vv < NV; ++vv) {
+      const long o = (long)vv * N + n;
+      const float st = fmaf(dt, Lv[vv], __ldg(ws + o));
+      if (mode == MODE_S1) r[vv] = st;
+      else if (mode == MODE_S2) r[vv] = 0.75f * __ldg(w0 + o) + 0.25f * st;
+      else r[vv] = (1.f / 3.f) * __ldg(w0 + o) + (2.f / 3.f) * st;
+      bad |= !isfinite(r[vv]);
+    }
+    if (out64) {
+      // last stage: hand back the FP64 state, restoring the stiffened-gas constant with the FP32 phi
+#pragma unroll
+      for (int vv = 0; vv < RE; ++vv) out64[(long)vv * N + n] = (double)r[vv];
+      out64[(long)RE * N + n] = (double)r[RE] + fma(prm.dC, (double)r[PHI], prm.C2);
+    } else {
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv) out32[(long)vv * N + n] = r[vv];
+    }
+  }
+  if (prm.check_finite && bad) atomicOr(prm.status, STATUS_NONFINITE);
+}
+
+// FP64 <-> FP32 internal state.  The stiffened-gas constant is removed from
+// rho E in FP64 with the FP64 phase field on entry, and restored with the
+// FP32 phase field on exit, so the pressure carried by the internal state is
+// the FP64 pressure and is handed back unchanged.
+__global__ void k_to32(int N, double C2, double dC, const double *__restrict__ w, float *__restrict__ w32);
+__global__ void k_to64(int N, double C2, double dC, const float *__restrict__ w32, double *__restrict__ w);
+
+struct KernelSet32 {
+  cudaError_t (*volume)(const Params &, const ParamsF &, const float *opsf, const float *w, float *rvol,
+                        float *trace, const double *w64, float *w32out, cudaStream_t);
+  cudaError_t (*surface)(const Params &, const ParamsF &, const float *opsf, int mode, float dt, const float *w0,
+                         const float *ws, const float *rvol, const float *trace, float *out32, double *out64,
+                         cudaStream_t);
+  int nt, epb, threads;
+};
+
+template <int P, int DIM, bool VISC, bool ST>
+cudaError_t launch_volume32(const Params &prm, const ParamsF &pf, const float *opsf, const float *w, float *rvol,
+                            float *trace, const double *w64, float *w32out, cudaStream_t s) {
+  using G = Geom<P, DIM, VISC, ST>;
+  const int blocks = (prm.E + G::EPB - 1) / G::EPB;
+  k_volume32<P, DIM, VISC, ST><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, w, rvol, trace, w64, w32out);
+  return cudaGetLastError();
+}
+
+template <int P, int DIM, bool VISC, bool ST>
+cudaError_t launch_surface32(const Params &prm, const ParamsF &pf, const float *opsf, int mode, float dt,
+                             const float *w0, const float *ws, const float *rvol, const float *trace, float *out32,
+                             double *out64, cudaStream_t s) {
+  using G = Geom<P, DIM, VISC, ST>;
+  const int blocks = (prm.E + G::EPB - 1) / G::EPB;
+  k_surface32<P, DIM, VISC, ST><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, mode, dt, w0, ws, rvol, trace, out32,
+                                                              out64);
+  return cudaGetLastError();
+}
+
+template <int P, int DIM, bool VISC, bool ST>
+KernelSet32 make_set32() {
+  using G = Geom<P, DIM, VISC, ST>;
+  return KernelSet32{&launch_volume32<P, DIM, VISC, ST>, &launch_surface32<P, DIM, VISC, ST>, G::NT, G::EPB,
+                     G::THREADS};
+}
+
+template <int P>
+bool kernels_fp32_p(int dim, bool viscous, bool st, KernelSet32 *out) {
+  if (dim == 1) {
+    if (viscous || st) return false;
+    *out = make_set32<P, 1, false, false>();
+    return true;
+  }
+  if (!viscous && !st) *out = make_set32<P, 2, false, false>();
+  else if (viscous && !st) *out = make_set32<P, 2, true, false>();
+  else if (!viscous && st) *out = make_set32<P, 2, false, true>();
+  else *out = make_set32<P, 2, true, true>();
+  return true;
+}
+
+bool kernels_fp32(int p, int dim, bool viscous, bool surface_tension, KernelSet32 *out);
+
+}  // namespace dgpf

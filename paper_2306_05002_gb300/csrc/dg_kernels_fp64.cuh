@@ -37,8 +37,18 @@ struct Geom {
   static constexpr int NF = 2 * DIM;                 // faces per element
   static constexpr int NK = DIM == 2 ? P1 : 1;       // nodes per face
   static constexpr int NFK = NF * NK;                // face nodes per element
-  static constexpr int EPB0 = 256 / NP;
-  static constexpr int EPB = EPB0 < 1 ? 1 : (EPB0 > 32 ? 32 : EPB0);
+  // Elements per block: the smallest count that fills at least 60 threads with
+  // under 7% of the last warp idle.  Small blocks spread a grid evenly over the
+  // 152 SMs (the FP64 path is bound by the per-SM FP64 pipe, so balance, not
+  // occupancy, decides its time).
+  static constexpr int pick_epb() {
+    for (int e = 1; e <= 64; ++e) {
+      const int t = e * NP, tp = ((t + 31) / 32) * 32;
+      if (t >= 60 && (tp - t) * 100 < 7 * tp) return e;
+    }
+    return (128 + NP - 1) / NP;
+  }
+  static constexpr int EPB = pick_epb();
   static constexpr int THREADS = ((EPB * NP + 31) / 32) * 32;
   static constexpr int NT = VISC ? NT_VISCOUS : NT_INVISCID;
   static constexpr int NSTAGE = 12;                  // staged fields per node
