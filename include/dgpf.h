@@ -143,6 +143,33 @@ int dg_time_kernels(dg_ctx *ctx, const double *w, int nrep, double *ms_out, int 
    scheme (not from counters). */
 int dg_kernel_costs(const dg_ctx *ctx, double *flops_out, double *bytes_out, int nmax);
 
+/* Size of the fixed device scratch used by dg_rhs_noalloc (32 MiB per GPU). */
+#define DG_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* The FP64 right-hand side L = M^-1 R(w), as dg_rhs computes it, for callers
+   that cannot allocate device memory: code that runs inside a framework's
+   memory pool or under an allocator that forbids raw cudaMalloc after
+   start-up, or a process that has already reserved all device memory.  The
+   paper has no counterpart: this is a deployment variant of dg_rhs.
+   It takes the problem description of dg_create directly (no context), plus a
+   device state w and a device output L (7 * E * (p+1)^dim doubles each, not
+   overlapping), and makes no device allocation and no allocating library
+   call.  Its scratch (operator table, volume part, face traces) is one
+   file-scope device array of DG_NOALLOC_SCRATCH_BYTES that every GPU loading
+   this library holds until the process exits; a problem whose scratch would
+   not fit (about 190,000 nodes at p = 3 in 2D, e.g. 64 x 64 elements fits)
+   is rejected with DG_ERR_ARG before any GPU work.  Other invalid arguments
+   give DG_ERR_ARG / DG_ERR_UNSUPPORTED (opts->prec must be DG_FP64; the
+   device status word is not reported).
+   The first call on a device looks up the array's device address on that
+   device (it loads the library's module there); make that first call before
+   any stream capture.  Every call uses the same array and leaves its contents
+   behind; the call clears what must start at zero itself.  Calls whose work
+   overlaps on the GPU (other streams, other host threads) race on the
+   scratch: serialise them.  Asynchronous on stream. */
+dg_status dg_rhs_noalloc(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps,
+                         const dg_opts *opts, const double *w, double *L, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ PREC = {"fp64": 0, "fp32bulk": 1}
 
 # Every exported symbol of include/dgpf.h.
 EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_diag", "dg_status_read",
-           "dg_last_error", "dg_time_kernels", "dg_kernel_costs"]
+           "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc"]
 
 
 class DGError(RuntimeError):
