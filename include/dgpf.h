@@ -143,6 +143,28 @@ int dg_time_kernels(dg_ctx *ctx, const double *w, int nrep, double *ms_out, int 
    scheme (not from counters). */
 int dg_kernel_costs(const dg_ctx *ctx, double *flops_out, double *bytes_out, int nmax);
 
+/* Batched ensemble: n independent 2D problems (each with its own mesh, order
+   p[k] in 1..5, closure eos[k], Gamma[k], eps[k]) advanced together by the
+   FP32-bulk path.  opts applies to all problems; opts->prec must be
+   DG_FP32_BULK, viscous and surface_tension must be 0 (gravity is allowed).
+   Problems of one order share one launch per kernel: the grid is the
+   concatenation of every problem's element tiles, each block locates its
+   problem through a first-block table and stages that problem's descriptor in
+   shared memory.  All device memory is allocated here (one pool).
+   dg_state_len of a batch context is the sum of the problems' state lengths;
+   the single-problem calls reject a batch context with DG_ERR_ARG. */
+dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p, const dg_eos *eos, const double *Gamma,
+                          const double *eps, const dg_opts *opts, dg_ctx **out);
+
+/* Advance every problem k of a batch by nsteps SSP-RK3 steps with its own step
+   dt[k] > 0.  w (HOST array of n pointers) gives each problem's DEVICE state
+   (layout as dg_step, in place); dt is a HOST array of n doubles.  The whole
+   step is one CUDA graph (captured on the first call; it reads the problem
+   descriptors from device memory, so new pointers or step sizes only
+   re-upload the descriptors).  nsteps = 0 is a no-op.  Asynchronous on
+   stream. */
+dg_status dg_batch_step(dg_ctx *ctx, double *const *w, const double *dt, int nsteps, void *stream);
+
 /* Size of the fixed device scratch used by dg_rhs_noalloc (32 MiB per GPU). */
 #define DG_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 

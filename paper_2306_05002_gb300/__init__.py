@@ -30,7 +30,8 @@ PREC = {"fp64": 0, "fp32bulk": 1}
 
 # Every exported symbol of include/dgpf.h.
 EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_diag", "dg_status_read",
-           "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc"]
+           "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc", "dg_batch_create",
+           "dg_batch_step"]
 
 
 class DGError(RuntimeError):
@@ -92,6 +93,13 @@ def load(path: str | None = None):
     lib.dg_kernel_costs.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.c_int]
     lib.dg_kernel_costs.restype = ctypes.c_int
+    lib.dg_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(dg_mesh), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(dg_eos), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(dg_opts), ctypes.POINTER(vp)]
+    lib.dg_batch_create.restype = ctypes.c_int
+    lib.dg_batch_step.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.c_int, vp]
+    lib.dg_batch_step.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -205,3 +213,51 @@ class Solver:
         b = (ctypes.c_double * 8)()
         n = load().dg_kernel_costs(self.ctx, f, b, 8)
         return list(f)[:n], list(b)[:n]
+
+
+class BatchSolver:
+    """Many independent 2D problems advanced together (wraps a batch ``dg_ctx``, FP32-bulk).
+
+    ``problems`` is a list of :class:`workloads.Workload`; ``dg_batch_step`` takes a list of
+    float64 CUDA state tensors (one per problem) and a list of step sizes.
+    """
+
+    def __init__(self, problems, precision: str = "fp32bulk"):
+        lib = load()
+        n = len(problems)
+        meshes = (dg_mesh * n)()
+        eoss = (dg_eos * n)()
+        ps = (ctypes.c_int * n)()
+        G = (ctypes.c_double * n)()
+        E = (ctypes.c_double * n)()
+        opts = None
+        for k, pb in enumerate(problems):
+            kw = pb.problem_kwargs()
+            ps[k] = kw.pop("p")
+            G[k], E[k] = kw.pop("Gamma"), kw.pop("eps")
+            m, e, o = make_structs(precision=precision, check_finite=False, **kw)
+            meshes[k], eoss[k] = m, e
+            opts = o if opts is None else opts
+        self._keep = (meshes, eoss, ps, G, E, opts)
+        h = ctypes.c_void_p()
+        st = lib.dg_batch_create(n, meshes, ps, eoss, G, E, ctypes.byref(opts), ctypes.byref(h))
+        _check(None, st, "dg_batch_create")
+        self.ctx = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().dg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dg_batch_step(self, ws, dts, nsteps: int, stream=None):
+        ptrs = (ctypes.c_void_p * self.n)(*[_ptr(w).value for w in ws])
+        dt = (ctypes.c_double * self.n)(*[float(x) for x in dts])
+        _check(self.ctx, load().dg_batch_step(self.ctx, ptrs, dt, int(nsteps), _stream(stream)), "dg_batch_step")
+        return ws

@@ -18,6 +18,7 @@
 #include "dg_common.cuh"
 #include "dg_kernels_fp64.cuh"
 #include "dg_kernels_fp32.cuh"
+#include "dg_batch.cuh"
 #include "dgpf.h"
 
 namespace dgpf {
@@ -217,7 +218,27 @@ thread_local std::string g_create_error = "no error";
 
 }  // namespace
 
+// A batch of independent problems advanced together (dg_batch_create).
+struct BatchGroup {
+  int p = 0;
+  std::vector<int> probs;          // problem indices of this order
+  BatchProb *d_probs = nullptr;    // descriptors, in the order of `probs`
+  int *d_block0 = nullptr;         // first block of each problem
+  int nblocks = 0;
+  BatchKernels k{};
+};
+
+struct BatchData {
+  int n = 0;
+  std::vector<BatchProb> h;        // descriptor of every problem (host copy)
+  std::vector<int> group_of, slot_of;
+  std::vector<BatchGroup> groups;
+  std::vector<size_t> len;         // state length of every problem
+  void *d_pool = nullptr;          // every FP32 buffer and table of the batch
+};
+
 struct dg_ctx {
+  BatchData *batch = nullptr;
   dg_mesh mesh;
   int p;
   dg_eos eos;
@@ -267,6 +288,14 @@ static void free_graphs(dg_ctx *c) {
 static void free_ctx(dg_ctx *c) {
   if (!c) return;
   free_graphs(c);
+  if (c->batch) {
+    for (auto &g : c->batch->groups) {
+      cudaFree(g.d_probs);
+      cudaFree(g.d_block0);
+    }
+    cudaFree(c->batch->d_pool);
+    delete c->batch;
+  }
   cudaFree(c->d_ops);
   cudaFree(c->d_w1);
   cudaFree(c->d_w2);
@@ -285,27 +314,98 @@ static void free_ctx(dg_ctx *c) {
   delete c;
 }
 
-extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps,
-                               const dg_opts *opts, dg_ctx **out) {
-  if (!out) return fail(nullptr, DG_ERR_ARG, "dg_create: out is NULL");
-  *out = nullptr;
-  if (!mesh || !eos) return fail(nullptr, DG_ERR_ARG, "dg_create: mesh and eos are required");
-  if (mesh->dim != 1 && mesh->dim != 2) return fail(nullptr, DG_ERR_ARG, "dg_create: dim must be 1 or 2");
-  if (p < 1 || p > 5) return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: order p must be in 1..5");
-  if (mesh->nx < 1 || mesh->ny < 1 || (mesh->dim == 1 && mesh->ny != 1))
-    return fail(nullptr, DG_ERR_ARG, "dg_create: bad element counts (1D needs ny = 1)");
-  if (!(mesh->x1 > mesh->x0) || (mesh->dim == 2 && !(mesh->y1 > mesh->y0)))
-    return fail(nullptr, DG_ERR_ARG, "dg_create: empty domain");
+// Validation shared by dg_create and dg_batch_create: NULL when valid.
+static const char *check_problem(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps,
+                                 dg_status *code) {
+  *code = DG_ERR_ARG;
+  if (!mesh || !eos) return "mesh and eos are required";
+  if (mesh->dim != 1 && mesh->dim != 2) return "dim must be 1 or 2";
+  if (p < 1 || p > 5) {
+    *code = DG_ERR_UNSUPPORTED;
+    return "order p must be in 1..5";
+  }
+  if (mesh->nx < 1 || mesh->ny < 1 || (mesh->dim == 1 && mesh->ny != 1)) return "bad element counts (1D needs ny = 1)";
+  if (!(mesh->x1 > mesh->x0) || (mesh->dim == 2 && !(mesh->y1 > mesh->y0))) return "empty domain";
   for (int f = 0; f < 4; ++f)
-    if (mesh->bc[f] < DG_BC_PERIODIC || mesh->bc[f] > DG_BC_SLIP)
-      return fail(nullptr, DG_ERR_ARG, "dg_create: unknown boundary condition");
+    if (mesh->bc[f] < DG_BC_PERIODIC || mesh->bc[f] > DG_BC_SLIP) return "unknown boundary condition";
   if ((mesh->bc[0] == DG_BC_PERIODIC) != (mesh->bc[1] == DG_BC_PERIODIC) ||
       (mesh->dim == 2 && (mesh->bc[2] == DG_BC_PERIODIC) != (mesh->bc[3] == DG_BC_PERIODIC)))
-    return fail(nullptr, DG_ERR_ARG, "dg_create: periodic sides must be paired");
+    return "periodic sides must be paired";
   for (int l = 0; l < 2; ++l)
-    if (!(eos->gamma[l] > 1.0) || !(eos->rho0[l] > 0.0) || eos->mu[l] < 0.0)
-      return fail(nullptr, DG_ERR_ARG, "dg_create: need gamma > 1, rho0 > 0, mu >= 0");
-  if (!(Gamma >= 0.0) || !(eps >= 0.0)) return fail(nullptr, DG_ERR_ARG, "dg_create: need Gamma, eps >= 0");
+    if (!(eos->gamma[l] > 1.0) || !(eos->rho0[l] > 0.0) || eos->mu[l] < 0.0) return "need gamma > 1, rho0 > 0, mu >= 0";
+  if (!(Gamma >= 0.0) || !(eps >= 0.0)) return "need Gamma, eps >= 0";
+  const long long Np = mesh->dim == 2 ? (long long)(p + 1) * (p + 1) : p + 1;
+  if ((long long)mesh->nx * mesh->ny * Np * 7 >= (1LL << 31)) return "problem too large for one context";
+  *code = DG_OK;
+  return nullptr;
+}
+
+// Operator table (OpsLayout) for one element size.
+static std::vector<double> build_ops(int dim, int p, double hx, double hy) {
+  const int P1 = p + 1, Np = dim == 2 ? P1 * P1 : P1;
+  const double J = dim == 2 ? 0.25 * hx * hy : 0.5 * hx;
+  std::vector<double> xi, wt;
+  gll_nodes(p, xi, wt);
+  const std::vector<double> D = lagrange_derivative(xi);
+  const OpsLayout L{P1, Np};
+  std::vector<double> ops(L.size(), 0.0);
+  const double rx = 2.0 / hx, ry = 2.0 / hy;
+  for (int a = 0; a < P1; ++a)
+    for (int b = 0; b < P1; ++b) {
+      ops[L.Dx() + a * P1 + b] = rx * D[a * P1 + b];
+      ops[L.Dy() + a * P1 + b] = ry * D[a * P1 + b];
+      const double dh = wt[b] * D[b * P1 + a] / wt[a];
+      ops[L.Dhx() + a * P1 + b] = rx * dh;
+      ops[L.Dhy() + a * P1 + b] = ry * dh;
+    }
+  for (int a = 0; a < P1; ++a) ops[L.wt() + a] = wt[a];
+  for (int a = 0; a < Np; ++a) {
+    const double wa = dim == 2 ? wt[a % P1] * wt[a / P1] : wt[a];
+    ops[L.invM() + a] = 1.0 / (wa * J);
+  }
+  for (int k = 0; k < P1; ++k) {
+    ops[L.wfx() + k] = dim == 2 ? wt[k] * 0.5 * hy : 1.0;
+    ops[L.wfy() + k] = dim == 2 ? wt[k] * 0.5 * hx : 1.0;
+  }
+  return ops;
+}
+
+// Kernel parameters of one problem.  The closure constants are computed with
+// the same expressions as the stiffened-gas formula of Sec. 2 so that the
+// pressure is reproducible.
+static Params make_params(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps, const dg_opts &o,
+                          double hx, double hy) {
+  const int P1 = p + 1, Np = mesh->dim == 2 ? P1 * P1 : P1;
+  Params q{};
+  q.nx = mesh->nx;
+  q.ny = mesh->ny;
+  q.E = mesh->nx * mesh->ny;
+  q.N = q.E * Np;
+  for (int f = 0; f < 4; ++f) q.bc[f] = mesh->bc[f];
+  q.C1 = eos->gamma[0] * eos->pinf[0] / (eos->gamma[0] - 1.0);
+  q.C2 = eos->gamma[1] * eos->pinf[1] / (eos->gamma[1] - 1.0);
+  q.g1 = 1.0 / (eos->gamma[0] - 1.0);
+  q.g2 = 1.0 / (eos->gamma[1] - 1.0);
+  q.Bp = eos->gamma[0] / (eos->gamma[0] - 1.0) - eos->gamma[1] / (eos->gamma[1] - 1.0);
+  q.dC = q.C1 - q.C2;
+  q.rho01 = eos->rho0[0];
+  q.rho02 = eos->rho0[1];
+  q.drho0 = eos->rho0[0] - eos->rho0[1];
+  q.mu1 = eos->mu[0];
+  q.mu2 = eos->mu[1];
+  q.sigma = eos->sigma;
+  q.gx = eos->g[0];
+  q.gy = eos->g[1];
+  q.Gamma = Gamma;
+  q.eps = eps;
+  q.eta_x = o.c_ip * P1 * P1 / hx;
+  q.eta_y = o.c_ip * P1 * P1 / hy;
+  q.gravity = o.gravity != 0;
+  q.check_finite = o.check_finite != 0;
+  return q;
+}
+
+static dg_opts normalised_opts(const dg_opts *opts) {
   dg_opts o{};
   o.prec = DG_FP64;
   o.c_ip = 1.0;
@@ -313,12 +413,22 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
   if (opts) o = *opts;
   if (o.c_ip <= 0.0) o.c_ip = 1.0;
   if (o.barrier_timeout_ms <= 0.0) o.barrier_timeout_ms = 1000.0;
+  return o;
+}
+
+extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps,
+                               const dg_opts *opts, dg_ctx **out) {
+  if (!out) return fail(nullptr, DG_ERR_ARG, "dg_create: out is NULL");
+  *out = nullptr;
+  dg_status code;
+  if (const char *why = check_problem(mesh, p, eos, Gamma, eps, &code))
+    return fail(nullptr, code, std::string("dg_create: ") + why);
+  const dg_opts o = normalised_opts(opts);
   if (o.prec != DG_FP64 && o.prec != DG_FP32_BULK)
     return fail(nullptr, DG_ERR_ARG, "dg_create: precision must be DG_FP64 or DG_FP32_BULK");
   const long long E = (long long)mesh->nx * mesh->ny;
   const int P1 = p + 1;
   const int Np = mesh->dim == 2 ? P1 * P1 : P1;
-  if (E * Np * 7 >= (1LL << 31)) return fail(nullptr, DG_ERR_ARG, "dg_create: problem too large for one context");
 
   dg_ctx *c = new (std::nothrow) dg_ctx();
   if (!c) return fail(nullptr, DG_ERR_OOM, "dg_create: host allocation failed");
@@ -346,59 +456,9 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
     return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: viscous/surface terms need dim = 2");
   }
 
-  // Operator tables.
-  std::vector<double> xi, wt;
-  gll_nodes(p, xi, wt);
-  const std::vector<double> D = lagrange_derivative(xi);
-  const OpsLayout L{P1, Np};
-  std::vector<double> ops(L.size(), 0.0);
-  const double rx = 2.0 / c->hx, ry = 2.0 / c->hy;
-  for (int a = 0; a < P1; ++a)
-    for (int b = 0; b < P1; ++b) {
-      ops[L.Dx() + a * P1 + b] = rx * D[a * P1 + b];
-      ops[L.Dy() + a * P1 + b] = ry * D[a * P1 + b];
-      const double dh = wt[b] * D[b * P1 + a] / wt[a];
-      ops[L.Dhx() + a * P1 + b] = rx * dh;
-      ops[L.Dhy() + a * P1 + b] = ry * dh;
-    }
-  for (int a = 0; a < P1; ++a) ops[L.wt() + a] = wt[a];
-  for (int a = 0; a < Np; ++a) {
-    const double wa = c->dim == 2 ? wt[a % P1] * wt[a / P1] : wt[a];
-    ops[L.invM() + a] = 1.0 / (wa * c->J);
-  }
-  for (int k = 0; k < P1; ++k) {
-    ops[L.wfx() + k] = c->dim == 2 ? wt[k] * 0.5 * c->hy : 1.0;
-    ops[L.wfy() + k] = c->dim == 2 ? wt[k] * 0.5 * c->hx : 1.0;
-  }
-
-  // Closure constants, computed with the same expressions as the stiffened-gas
-  // formula of Sec. 2 so that the pressure is reproducible.
+  const std::vector<double> ops = build_ops(c->dim, p, c->hx, c->hy);
+  c->prm = make_params(mesh, p, eos, Gamma, eps, o, c->hx, c->hy);
   Params &q = c->prm;
-  q.nx = mesh->nx;
-  q.ny = mesh->ny;
-  q.E = c->E;
-  q.N = c->N;
-  for (int f = 0; f < 4; ++f) q.bc[f] = mesh->bc[f];
-  q.C1 = eos->gamma[0] * eos->pinf[0] / (eos->gamma[0] - 1.0);
-  q.C2 = eos->gamma[1] * eos->pinf[1] / (eos->gamma[1] - 1.0);
-  q.g1 = 1.0 / (eos->gamma[0] - 1.0);
-  q.g2 = 1.0 / (eos->gamma[1] - 1.0);
-  q.Bp = eos->gamma[0] / (eos->gamma[0] - 1.0) - eos->gamma[1] / (eos->gamma[1] - 1.0);
-  q.dC = q.C1 - q.C2;
-  q.rho01 = eos->rho0[0];
-  q.rho02 = eos->rho0[1];
-  q.drho0 = eos->rho0[0] - eos->rho0[1];
-  q.mu1 = eos->mu[0];
-  q.mu2 = eos->mu[1];
-  q.sigma = eos->sigma;
-  q.gx = eos->g[0];
-  q.gy = eos->g[1];
-  q.Gamma = Gamma;
-  q.eps = eps;
-  q.eta_x = o.c_ip * P1 * P1 / c->hx;
-  q.eta_y = o.c_ip * P1 * P1 / c->hy;
-  q.gravity = o.gravity != 0;
-  q.check_finite = o.check_finite != 0;
 
   cudaError_t e = cudaSuccess;
   const bool f64 = c->prec == DG_FP64;
@@ -484,6 +544,7 @@ static dg_status convert(dg_ctx *c, bool to32, double *w, cudaStream_t s) {
 
 extern "C" dg_status dg_rhs(dg_ctx *c, const double *w, double *L, void *stream) {
   if (!c) return DG_ERR_ARG;
+  if (c->batch) return fail(c, DG_ERR_ARG, "dg_rhs: batch context (use dg_batch_step)");
   if (!w || !L) return fail(c, DG_ERR_ARG, "dg_rhs: null array");
   if (w == L) return fail(c, DG_ERR_ARG, "dg_rhs: w and L must not overlap");
   cudaStream_t s = (cudaStream_t)stream;
@@ -529,6 +590,7 @@ static dg_status capture(dg_ctx *c, double *w, double dt, int steps, cudaGraphEx
 
 extern "C" dg_status dg_step(dg_ctx *c, double *w, double dt, int nsteps, void *stream) {
   if (!c) return DG_ERR_ARG;
+  if (c->batch) return fail(c, DG_ERR_ARG, "dg_step: batch context (use dg_batch_step)");
   if (!w) return fail(c, DG_ERR_ARG, "dg_step: null state");
   if (!(dt > 0.0) || nsteps < 0) return fail(c, DG_ERR_ARG, "dg_step: need dt > 0 and nsteps >= 0");
   if (nsteps == 0) return DG_OK;
@@ -551,6 +613,7 @@ extern "C" dg_status dg_step(dg_ctx *c, double *w, double dt, int nsteps, void *
 
 extern "C" dg_status dg_diag(dg_ctx *c, const double *w, double *out, void *stream) {
   if (!c) return DG_ERR_ARG;
+  if (c->batch) return fail(c, DG_ERR_ARG, "dg_diag: batch context (use dg_batch_step)");
   if (!w || !out) return fail(c, DG_ERR_ARG, "dg_diag: null array");
   cudaStream_t s = (cudaStream_t)stream;
   k_diag_partial<<<c->nparts, DIAG_THREADS, 0, s>>>(c->prm, c->Np, c->P1, c->dim, c->J, w, c->d_part);
@@ -565,6 +628,7 @@ extern "C" dg_status dg_diag(dg_ctx *c, const double *w, double *out, void *stre
 
 extern "C" dg_status dg_status_read(dg_ctx *c, void *stream) {
   if (!c) return DG_ERR_ARG;
+  if (c->batch) return DG_OK;  // the batched kernels latch no status
   cudaStream_t s = (cudaStream_t)stream;
   unsigned h = 0;
   cudaError_t e = cudaMemcpyAsync(&h, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
@@ -577,7 +641,7 @@ extern "C" dg_status dg_status_read(dg_ctx *c, void *stream) {
 }
 
 extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_out, int nmax, void *stream) {
-  if (!c || !w || !ms_out || nmax < 1 || nrep < 1) return -1;
+  if (!c || c->batch || !w || !ms_out || nmax < 1 || nrep < 1) return -1;
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t ev[3];
   for (auto &x : ev) cudaEventCreate(&x);
@@ -613,7 +677,7 @@ extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_
 }
 
 extern "C" int dg_kernel_costs(const dg_ctx *c, double *flops, double *bytes, int nmax) {
-  if (!c || !flops || !bytes || nmax < 1) return -1;
+  if (!c || c->batch || !flops || !bytes || nmax < 1) return -1;
   // Algorithmic counts from the formulas of the scheme (an FMA counts 2, a
   // division or square root 1), per launch.
   const double P1 = c->P1, Np = c->Np, NFK = c->NFK, E = c->E, d = c->dim;
@@ -642,4 +706,216 @@ extern "C" int dg_kernel_costs(const dg_ctx *c, double *flops, double *bytes, in
     bytes[k] = Bb[k];
   }
   return nk;
+}
+
+// ---------------------------------------------------------------------------
+// Batched ensemble (FP32-bulk)
+// ---------------------------------------------------------------------------
+
+extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p, const dg_eos *eos,
+                                     const double *Gamma, const double *eps, const dg_opts *opts, dg_ctx **out) {
+  if (!out) return fail(nullptr, DG_ERR_ARG, "dg_batch_create: out is NULL");
+  *out = nullptr;
+  if (n < 1 || !meshes || !p || !eos || !Gamma || !eps)
+    return fail(nullptr, DG_ERR_ARG, "dg_batch_create: need n >= 1 and all arrays");
+  const dg_opts o = normalised_opts(opts);
+  if (o.prec != DG_FP32_BULK)
+    return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_batch_create: the batched form runs the FP32-bulk path only");
+  if (o.viscous || o.surface_tension)
+    return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_batch_create: viscous and surface-tension terms are not batched");
+  for (int k = 0; k < n; ++k) {
+    dg_status code;
+    if (const char *why = check_problem(meshes + k, p[k], eos + k, Gamma[k], eps[k], &code))
+      return fail(nullptr, code, "dg_batch_create: problem " + std::to_string(k) + ": " + why);
+    if (meshes[k].dim != 2)
+      return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_batch_create: the batched form is two-dimensional");
+  }
+  dg_ctx *c = new (std::nothrow) dg_ctx();
+  BatchData *b = c ? new (std::nothrow) BatchData() : nullptr;
+  if (!c || !b) {
+    delete c;
+    return fail(nullptr, DG_ERR_OOM, "dg_batch_create: host allocation failed");
+  }
+  c->batch = b;
+  c->opts = o;
+  c->prec = DG_FP32_BULK;
+  b->n = n;
+  b->h.resize(n);
+  b->group_of.assign(n, -1);
+  b->slot_of.assign(n, -1);
+  b->len.resize(n);
+
+  // Groups by order, problems in the given order within a group.
+  for (int k = 0; k < n; ++k) {
+    int g = -1;
+    for (size_t q = 0; q < b->groups.size(); ++q)
+      if (b->groups[q].p == p[k]) g = (int)q;
+    if (g < 0) {
+      BatchGroup grp;
+      grp.p = p[k];
+      if (!batch_kernels(p[k], &grp.k)) {
+        free_ctx(c);
+        return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_batch_create: order not available");
+      }
+      b->groups.push_back(grp);
+      g = (int)b->groups.size() - 1;
+    }
+    b->group_of[k] = g;
+    b->slot_of[k] = (int)b->groups[g].probs.size();
+    b->groups[g].probs.push_back(k);
+  }
+
+  // One pool for every FP32 buffer and table: per problem the table, the
+  // internal state, two stages, the volume part and the face traces.
+  std::vector<std::vector<float>> tables(n);
+  std::vector<size_t> off(n);
+  size_t total = 0;
+  auto take = [&](size_t floats) {
+    const size_t at = total;
+    total += (floats + 63) & ~size_t(63);  // 256-byte aligned slices
+    return at;
+  };
+  std::vector<size_t> o_ops(n), o_ws(n), o_w1(n), o_w2(n), o_rv(n), o_tr(n);
+  for (int k = 0; k < n; ++k) {
+    const dg_mesh &m = meshes[k];
+    const double hx = (m.x1 - m.x0) / m.nx, hy = (m.y1 - m.y0) / m.ny;
+    const std::vector<double> ops = build_ops(2, p[k], hx, hy);
+    tables[k].assign(ops.begin(), ops.end());
+    BatchProb &d = b->h[k];
+    d.prm = make_params(&m, p[k], eos + k, Gamma[k], eps[k], o, hx, hy);
+    d.prm.check_finite = 0;
+    d.pf = to_float(d.prm);
+    const size_t E = (size_t)m.nx * m.ny, P1 = p[k] + 1, NFK = 4 * P1;
+    const size_t len = NV * E * P1 * P1;
+    b->len[k] = len;
+    o_ops[k] = take(tables[k].size());
+    o_ws[k] = take(len);
+    o_w1[k] = take(len);
+    o_w2[k] = take(len);
+    o_rv[k] = take(len);
+    o_tr[k] = take((size_t)NT_INVISCID * E * NFK);
+  }
+  cudaError_t e = cudaMalloc(&b->d_pool, total * sizeof(float));
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    cudaGetLastError();
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA,
+                std::string("dg_batch_create: device allocation failed: ") + cudaGetErrorString(e));
+  }
+  float *pool = static_cast<float *>(b->d_pool);
+  for (int k = 0; k < n && e == cudaSuccess; ++k) {
+    BatchProb &d = b->h[k];
+    d.opsf = pool + o_ops[k];
+    d.ws = pool + o_ws[k];
+    d.w1 = pool + o_w1[k];
+    d.w2 = pool + o_w2[k];
+    d.rvol = pool + o_rv[k];
+    d.tr = pool + o_tr[k];
+    d.w64 = nullptr;
+    d.dt = 0.f;
+    d.prm.ops = nullptr;
+    d.prm.status = nullptr;
+    e = cudaMemcpy(pool + o_ops[k], tables[k].data(), tables[k].size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  for (auto &g : b->groups) {
+    if (e != cudaSuccess) break;
+    std::vector<int> block0(g.probs.size());
+    int nb = 0;
+    for (size_t q = 0; q < g.probs.size(); ++q) {
+      BatchProb &d = b->h[g.probs[q]];
+      d.block0 = nb;
+      block0[q] = nb;
+      nb += (d.prm.E + g.k.epb - 1) / g.k.epb;
+    }
+    g.nblocks = nb;
+    if ((e = cudaMalloc(&g.d_probs, g.probs.size() * sizeof(BatchProb))) != cudaSuccess) break;
+    if ((e = cudaMalloc(&g.d_block0, g.probs.size() * sizeof(int))) != cudaSuccess) break;
+    e = cudaMemcpy(g.d_block0, block0.data(), block0.size() * sizeof(int), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    cudaGetLastError();
+    return fail(nullptr, DG_ERR_CUDA, std::string("dg_batch_create: ") + cudaGetErrorString(e));
+  }
+  c->len = 0;
+  for (int k = 0; k < n; ++k) c->len += b->len[k];
+  *out = c;
+  return DG_OK;
+}
+
+// Upload the descriptors of every group (pageable source: the copy has read
+// the host data when the call returns).
+static dg_status upload_descriptors(dg_ctx *c, cudaStream_t s) {
+  BatchData *b = c->batch;
+  for (auto &g : b->groups) {
+    std::vector<BatchProb> tmp(g.probs.size());
+    for (size_t q = 0; q < g.probs.size(); ++q) tmp[q] = b->h[g.probs[q]];
+    const cudaError_t e =
+        cudaMemcpyAsync(g.d_probs, tmp.data(), tmp.size() * sizeof(BatchProb), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_batch_step: descriptor upload");
+  }
+  return DG_OK;
+}
+
+static dg_status enqueue_batch_step(dg_ctx *c, cudaStream_t s) {
+  for (int stage = 1; stage <= 3; ++stage) {
+    for (auto &g : c->batch->groups) {
+      cudaError_t e = g.k.launch(true, g.d_probs, g.d_block0, (int)g.probs.size(), stage, g.nblocks, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "batched volume kernel launch");
+    }
+    for (auto &g : c->batch->groups) {
+      cudaError_t e = g.k.launch(false, g.d_probs, g.d_block0, (int)g.probs.size(), stage, g.nblocks, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "batched surface kernel launch");
+    }
+  }
+  return DG_OK;
+}
+
+static dg_status capture_batch(dg_ctx *c, int steps, cudaGraphExec_t *exec) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_batch_step: begin capture");
+  dg_status r = DG_OK;
+  for (int k = 0; k < steps && r == DG_OK; ++k) r = enqueue_batch_step(c, c->cap);
+  e = cudaStreamEndCapture(c->cap, &g);
+  if (r != DG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_batch_step: end capture");
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_batch_step: instantiate");
+}
+
+extern "C" dg_status dg_batch_step(dg_ctx *c, double *const *w, const double *dt, int nsteps, void *stream) {
+  if (!c) return DG_ERR_ARG;
+  if (!c->batch) return fail(c, DG_ERR_ARG, "dg_batch_step: context was not made by dg_batch_create");
+  if (!w || !dt || nsteps < 0) return fail(c, DG_ERR_ARG, "dg_batch_step: need w, dt and nsteps >= 0");
+  BatchData *b = c->batch;
+  bool changed = false;
+  for (int k = 0; k < b->n; ++k) {
+    if (!w[k] || !(dt[k] > 0.0)) return fail(c, DG_ERR_ARG, "dg_batch_step: null state or dt <= 0");
+    if (b->h[k].w64 != w[k] || b->h[k].dt != (float)dt[k]) changed = true;
+    b->h[k].w64 = w[k];
+    b->h[k].dt = (float)dt[k];
+  }
+  if (nsteps == 0) return DG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (changed) {
+    const dg_status r = upload_descriptors(c, s);
+    if (r != DG_OK) return r;
+  }
+  if (!c->g1) {  // the graphs read the descriptors at run time: captured once
+    dg_status r;
+    if ((r = capture_batch(c, 1, &c->g1)) != DG_OK) return r;
+    if ((r = capture_batch(c, GRAPH_UNROLL, &c->gk)) != DG_OK) return r;
+  }
+  cudaError_t e;
+  for (int k = 0; k < nsteps / GRAPH_UNROLL; ++k)
+    if ((e = cudaGraphLaunch(c->gk, s)) != cudaSuccess) return cuda_fail(c, e, "dg_batch_step: graph launch");
+  for (int k = 0; k < nsteps % GRAPH_UNROLL; ++k)
+    if ((e = cudaGraphLaunch(c->g1, s)) != cudaSuccess) return cuda_fail(c, e, "dg_batch_step: graph launch");
+  return DG_OK;
 }

@@ -51,12 +51,14 @@ __host__ inline ParamsF to_float(const Params &p) {
                  (float)p.Gamma, (float)p.eps, (float)p.eta_x, (float)p.eta_y};
 }
 
-// FP32 operator tables: same layout as OpsLayout, stored after the FP64 table.
+// Volume kernel body for the element tile `blk` (EPB elements) of one problem.
+// opsf: FP32 operator table (OpsLayout).  w64 != NULL: read the FP64 state and
+// write the FP32 internal state to w32out (first stage of a step).
 template <int P, int DIM, bool VISC, bool ST>
-__global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
-k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, const float *__restrict__ w,
-           float *__restrict__ rvol, float *__restrict__ tr, const double *__restrict__ w64,
-           float *__restrict__ w32out) {
+__device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf, const float *__restrict__ opsf,
+                                           int blk, const float *__restrict__ w, float *__restrict__ rvol,
+                                           float *__restrict__ tr, const double *__restrict__ w64,
+                                           float *__restrict__ w32out) {
   using G = Geom<P, DIM, VISC, ST>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
   constexpr int P11 = P1 * P1;
@@ -71,7 +73,7 @@ k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, c
   const bool lane = le_raw < EPB;
   const int le = lane ? le_raw : EPB - 1;
   const int a = threadIdx.x % NP;
-  const int e = blockIdx.x * EPB + le;
+  const int e = blk * EPB + le;
   const bool act = lane && e < prm.E;
   const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
   const int N = prm.N;
@@ -140,9 +142,12 @@ k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, c
     }
   }
 
+  // n = 0 where |grad psi| cannot be told from zero: FP32 storage of a
+  // distance-like psi leaves ~1e-6 of noise in its gradient (the FP64 path
+  // uses 1e-12), so below 1e-4 the direction is noise.
   const float g2 = gsx * gsx + gsy * gsy;
   float nx = 0.f, ny = 0.f;
-  if (g2 >= 1e-24f) {
+  if (g2 >= 1e-8f) {
     const float r = rsqrtf(g2);
     nx = gsx * r;
     ny = gsy * r;
@@ -257,14 +262,24 @@ k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, c
   }
 }
 
-// Surface kernel of the FP32-bulk path.  mode MODE_RHS writes L for the
-// paper's variables in FP64 (out64, with L(rho E) = L(rhoEt) + (C_1-C_2) L(phi));
-// the stage modes write the FP32 internal state (out32).
 template <int P, int DIM, bool VISC, bool ST>
 __global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
-k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt,
-            const float *__restrict__ w0, const float *__restrict__ ws, const float *__restrict__ rvol,
-            const float *__restrict__ tr, float *__restrict__ out32, double *__restrict__ out64) {
+k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, const float *__restrict__ w,
+           float *__restrict__ rvol, float *__restrict__ tr, const double *__restrict__ w64,
+           float *__restrict__ w32out) {
+  vol32_body<P, DIM, VISC, ST>(prm, pf, opsf, blockIdx.x, w, rvol, tr, w64, w32out);
+}
+
+// Surface kernel body of the FP32-bulk path.  mode MODE_RHS writes L for the
+// paper's variables in FP64 (out64, with L(rho E) = L(rhoEt) + (C_1-C_2) L(phi));
+// the stage modes write the FP32 internal state (out32), or, when out64 is
+// given, the FP64 state (last stage of a step).
+template <int P, int DIM, bool VISC, bool ST>
+__device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf, const float *__restrict__ opsf,
+                                            int blk, int mode, float dt, const float *__restrict__ w0,
+                                            const float *__restrict__ ws, const float *__restrict__ rvol,
+                                            const float *__restrict__ tr, float *__restrict__ out32,
+                                            double *__restrict__ out64) {
   using G = Geom<P, DIM, VISC, ST>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK, NT = G::NT;
   const OpsLayout L{P1, NP};
@@ -281,7 +296,7 @@ k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, 
   const bool lane = le_raw < EPB;
   const int le = lane ? le_raw : EPB - 1;
   const int a = threadIdx.x % NP;
-  const int e = blockIdx.x * EPB + le;
+  const int e = blk * EPB + le;
   const bool act = lane && e < prm.E;
   const long stride = (long)prm.E * NFK;
 
@@ -447,6 +462,14 @@ k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, 
     }
   }
   if (prm.check_finite && bad) atomicOr(prm.status, STATUS_NONFINITE);
+}
+
+template <int P, int DIM, bool VISC, bool ST>
+__global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
+k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt,
+            const float *__restrict__ w0, const float *__restrict__ ws, const float *__restrict__ rvol,
+            const float *__restrict__ tr, float *__restrict__ out32, double *__restrict__ out64) {
+  surf32_body<P, DIM, VISC, ST>(prm, pf, opsf, blockIdx.x, mode, dt, w0, ws, rvol, tr, out32, out64);
 }
 
 // FP64 <-> FP32 internal state.  The stiffened-gas constant is removed from

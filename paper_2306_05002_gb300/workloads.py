@@ -239,3 +239,24 @@ def rayleigh_taylor(n: int = 256, p: int = 4, seed: int = 3, nsteps: int = 2000,
 def resized(wl_fn, **kw) -> Workload:
     """Convenience: build a workload with overridden sizes (used for small parity cases)."""
     return wl_fn(**kw)
+
+
+def ensemble(n: int = 256, seed: int = 4, nmin: int = 16, nmax: int = 128, orders=(2, 3, 4, 5),
+             Rmin: float = 0.05, Rmax: float = 0.2, u: float = 1.0, v: float = 0.5, P0: float = 1e5,
+             nsteps: int = 200) -> list:
+    """Independent 2D periodic drop / bubble problems with seeded sizes, orders, radii and centres:
+    N ~ U{nmin..nmax} (N x N quads), p ~ U(orders), water drop in air or air bubble in water
+    (half each), R ~ U[Rmin, Rmax], centre ~ U[0, 1]^2, eps = 0.75 h, own dt per problem."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        N = int(rng.integers(nmin, nmax + 1))
+        p = int(rng.choice(orders))
+        bubble = bool(rng.integers(0, 2))
+        R = float(rng.uniform(Rmin, Rmax))
+        c = rng.uniform(0.0, 1.0, size=2)
+        wl = drop_2d(n=N, p=p, R=R, u=u, v=v, P0=P0, nsteps=nsteps, center=c, water_inside=not bubble)
+        wl.name = f"ens{k}_{N}x{N}p{p}{'b' if bubble else 'd'}"
+        wl.meta.update(kind="bubble" if bubble else "drop", member=k, seed=seed)
+        out.append(wl)
+    return out

@@ -76,3 +76,20 @@ def test_null_context_is_safe(lib):
     assert lib.dg_step(None, None, 1.0, 1, None) == -1
     lib.dg_destroy(None)
     assert isinstance(lib.dg_last_error(None), bytes)
+
+
+def test_batch_create_rejects_unsupported_forms(lib):
+    """Checked before any device work: FP64 and viscous batches are not provided."""
+    import paper_2306_05002_gb300 as pkg
+    m, p, e, Gamma, eps, o = _args()
+    meshes = (pkg.dg_mesh * 1)(m)
+    eoss = (pkg.dg_eos * 1)(e)
+    ps = (ctypes.c_int * 1)(p)
+    G = (ctypes.c_double * 1)(Gamma)
+    E = (ctypes.c_double * 1)(eps)
+    h = ctypes.c_void_p()
+    o.prec = 0
+    assert lib.dg_batch_create(1, meshes, ps, eoss, G, E, ctypes.byref(o), ctypes.byref(h)) == -7
+    o.prec, o.viscous = 1, 1
+    assert lib.dg_batch_create(1, meshes, ps, eoss, G, E, ctypes.byref(o), ctypes.byref(h)) == -7
+    assert h.value is None

@@ -3,7 +3,8 @@ rho E - Cmix(phi), FP64 only where the pressure is recovered).
 
 * one right-hand side against the FP64 oracle: max_n |L - L_orc| <= 2e-6 max_n S_v per
   variable (S: the oracle's scale of the cancelling terms; FP32 has 6e-8 unit round-off
-  and a node sees a few tens of contributions);
+  and a node sees a few tens of contributions), plus, for phi and psi, the FP32 storage
+  error of the field carried through the transport derivative (see _storage_bound);
 * a full 500-step run of the 64 x 64, p = 3 drop against the FP64 path: relative L2
   error of phi and P <= 1e-5 (the accuracy target of this mode), u within 1e-3;
 * interface equilibrium: a uniform-(u, P) drop keeps P within 1e-5 relative.
@@ -18,6 +19,18 @@ pytestmark = pytest.mark.gpu
 TOL32 = 2e-6
 
 
+def _storage_bound(orc, wl, w):
+    """FP32 storage error of phi and psi carried through the transport derivative u.grad(f):
+    4 eps32 max|f| max|u| (2/h) max_i sum_c |D_ic| (S does not contain it: S holds |u.grad f|)."""
+    xi, _ = orc.gll(wl.p)
+    D = orc.lagrange_deriv(wl.p, xi)
+    prim = orc.primitives(problem(orc, wl), w)
+    umax = np.max(np.hypot(prim[1], prim[2]))
+    h = min(wl.hx, wl.hy)
+    g = 4 * np.finfo(np.float32).eps * umax * (2.0 / h) * np.abs(D).sum(axis=1).max()
+    return {0: g * np.abs(w[0]).max(), 1: g * np.abs(w[1]).max()}
+
+
 def _rhs32(orc, dg, wl, w=None):
     import torch
     w = wl.w if w is None else w
@@ -26,12 +39,13 @@ def _rhs32(orc, dg, wl, w=None):
     L = s.dg_rhs(torch.from_numpy(np.array(w)).cuda()).cpu().numpy()
     assert s.dg_status_read() == 0
     s.close()
+    extra = _storage_bound(orc, wl, w)
     for v in range(7):
         sc = S[v].max()
         if sc == 0:
             continue
-        err = np.abs(L[v] - L_ref[v]).max() / sc
-        assert err <= TOL32, (v, err)
+        err = np.abs(L[v] - L_ref[v]).max()
+        assert err <= TOL32 * sc + extra.get(v, 0.0), (v, err / sc, extra.get(v, 0.0) / sc)
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
