@@ -43,6 +43,8 @@ def parse():
                     help="steps of the FP32-bulk vs FP64 accuracy comparison (the workload's 500)")
     ap.add_argument("--batch-steps", type=int, default=10,
                     help="timed steps of the batched ensemble (0 skips the batched block)")
+    ap.add_argument("--adjoint-steps", type=int, default=200,
+                    help="trajectory length of the adjoint timing (0 skips it)")
     ap.add_argument("--cpu-sample-steps", type=int, default=0,
                     help="oracle steps for the cpu_baseline leg (0 = size for ~15 s)")
     return ap.parse_args()
@@ -156,6 +158,23 @@ def peaks():
 
 # FP64 ALU peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# --------------------------------------------------------------------------- ranks
+
+def reduce_max(values, device):
+    """Element-wise maximum over all ranks (a no-op without torch.distributed)."""
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if tdist.is_available() and tdist.is_initialized() and tdist.get_world_size() > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def weak_scaling_value(units_per_rank: float, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank advances its own replica; the slowest rank sets the time."""
+    return units_per_rank * steps * world / (ms_max * 1e-3)
 
 
 # --------------------------------------------------------------------------- oracle leg
@@ -312,6 +331,42 @@ def batched_block(dg, steps):
             "speedup_vs_fp64": ms_64 / ms_b, "l2": "working set > L2 (no flush needed)"}
 
 
+def adjoint_block(dg, steps, every=20):
+    """Gradient of J = 1/2 int (alpha_N - alpha*)^2 with respect to the initial state of the
+    128 x 128, p = 3 drop (level set with 16 seeded Fourier coefficients, seed 5/50/51),
+    FP64, checkpoints every 20 steps.  adjoint/forward = backward sweep (segment replay +
+    adjoint steps) / forward sweep (with checkpoint copies)."""
+    import numpy as np
+    import torch
+    from paper_2306_05002_gb300 import adjoint as A
+    from paper_2306_05002_gb300 import workloads as W
+    wl = W.adjoint_drop(n=128, p=3, nsteps=steps)
+    tgt = W.adjoint_drop(n=128, p=3, nsteps=steps, theta=np.random.default_rng(51).normal(0, 0.01, 16))
+    s = dg.Solver(wl)
+    x = torch.from_numpy(tgt.w.copy()).cuda()
+    s.dg_step(x, wl.dt, steps)
+    target = x[0].clone()
+    w0 = torch.from_numpy(wl.w.copy()).cuda()
+    _, wt = W.gll_points(3), None
+    A.forward(s, w0, wl.dt, 2, every)  # warm-up (graph capture)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    wN, ckpt = A.forward(s, w0, wl.dt, steps, every)
+    e[1].record()
+    lam = torch.zeros_like(wN)
+    lam[0] = wN[0] - target  # J's gradient up to the (positive) quadrature weights
+    lam0 = A.backward(s, ckpt, lam, wl.dt, steps, every)
+    e[2].record()
+    torch.cuda.synchronize()
+    tf, tb = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    ok = bool(torch.isfinite(lam0).all())
+    s.close()
+    return {"workload": "2D drop 128x128 quads p=3, FP64, 16 level-set Fourier parameters (seeds 5, 50, 51)",
+            "steps": steps, "checkpoint_every": every, "forward_ms": tf, "backward_ms": tb,
+            "adjoint_over_forward": tb / tf, "finite": ok}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2306_05002_gb300 as dg
@@ -370,15 +425,13 @@ def run_ours(args, rank, world, local_rank):
 
     acc = accuracy(dg, wl, args.accuracy_steps) if (args.precision == "fp32bulk" and rank == 0) else None
     batched = batched_block(dg, args.batch_steps) if (args.batch_steps > 0 and rank == 0) else None
+    adjoint = adjoint_block(dg, args.adjoint_steps) if (args.adjoint_steps > 0 and rank == 0) else None
 
-    tens = torch.tensor([main["ms"], e2e_t, ref["ms"] if ref else 0.0], dtype=torch.float64, device="cuda")
-    if dist:
-        tdist.all_reduce(tens, op=tdist.ReduceOp.MAX)
-    ms_max, e2e_max, ref_ms = tens.tolist()
+    ms_max, e2e_max, ref_ms = reduce_max([main["ms"], e2e_t, ref["ms"] if ref else 0.0], "cuda")
 
     if rank == 0:
         units = 7 * wl.N * 3
-        value = units * args.steps * world / (ms_max * 1e-3)
+        value = weak_scaling_value(units, args.steps, world, ms_max)
         launches = 6 if args.precision == "fp64" else 8
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -401,6 +454,8 @@ def run_ours(args, rank, world, local_rank):
             line["accuracy"] = acc
         if batched:
             line["batched"] = batched
+        if adjoint:
+            line["adjoint"] = adjoint
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
         print(json.dumps(line), flush=True)

@@ -143,6 +143,38 @@ int dg_time_kernels(dg_ctx *ctx, const double *w, int nrep, double *ms_out, int 
    scheme (not from counters). */
 int dg_kernel_costs(const dg_ctx *ctx, double *flops_out, double *bytes_out, int nmax);
 
+/* Discrete adjoint of the right-hand side: out = (dL/dw)^T lam at the state
+   w, the exact transpose of the Jacobian of dg_rhs (all seven equations, the
+   closure, normals, a_1, fluxes and SIP lifting of Sec. 2-3 differentiated by
+   hand).  Provided for FP64 contexts without viscous and surface-tension
+   terms (else DG_ERR_UNSUPPORTED).  w, lam, out: device arrays of
+   dg_state_len doubles; out must not overlap w or lam.  Where the two
+   one-sided wave speeds of the Lax-Friedrichs lambda tie, the derivative is
+   taken on the element's own side. */
+dg_status dg_rhs_vjp(dg_ctx *ctx, const double *w, const double *lam, double *out, void *stream);
+
+/* Reverse of one SSP-RK3 step: lam_n = (d w_{n+1} / d w_n)^T lam_np1 for the
+   step of size dt taken from w_n (device arrays).  The two intermediate
+   stages are recomputed from w_n, then three adjoint right-hand sides run in
+   reverse stage order.  lam_n may alias lam_np1 (not w_n).  Same
+   availability as dg_rhs_vjp.  Asynchronous on stream. */
+dg_status dg_adjoint_step(dg_ctx *ctx, const double *w_n, const double *lam_np1, double *lam_n, double dt,
+                          void *stream);
+
+/* Taped step for reverse sweeps.  dg_tape_len: doubles of one step's tape
+   (the two intermediate stages and the face traces of the three stages; 0 when
+   the context has no adjoint).  dg_step_tape: one SSP-RK3 step of w in place
+   (identical to dg_step with nsteps = 1) whose kernels write the stages and
+   traces into tape (device, dg_tape_len doubles).  dg_adjoint_step_tape: the
+   reverse of that step, lam_n = (d w_{n+1}/d w_n)^T lam_np1, from w_n and the
+   tape, with no recomputation (three adjoint right-hand sides).  A
+   checkpointed reverse sweep replays each segment with dg_step_tape and
+   walks back with dg_adjoint_step_tape.  Same availability as dg_rhs_vjp. */
+size_t dg_tape_len(const dg_ctx *ctx);
+dg_status dg_step_tape(dg_ctx *ctx, double *w, double dt, double *tape, void *stream);
+dg_status dg_adjoint_step_tape(dg_ctx *ctx, const double *w_n, const double *tape, const double *lam_np1,
+                               double *lam_n, double dt, void *stream);
+
 /* Batched ensemble: n independent 2D problems (each with its own mesh, order
    p[k] in 1..5, closure eos[k], Gamma[k], eps[k]) advanced together by the
    FP32-bulk path.  opts applies to all problems; opts->prec must be

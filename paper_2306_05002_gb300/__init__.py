@@ -31,7 +31,8 @@ PREC = {"fp64": 0, "fp32bulk": 1}
 # Every exported symbol of include/dgpf.h.
 EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_diag", "dg_status_read",
            "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc", "dg_batch_create",
-           "dg_batch_step"]
+           "dg_batch_step", "dg_rhs_vjp", "dg_adjoint_step", "dg_tape_len", "dg_step_tape",
+           "dg_adjoint_step_tape"]
 
 
 class DGError(RuntimeError):
@@ -100,6 +101,16 @@ def load(path: str | None = None):
     lib.dg_batch_step.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_int, vp]
     lib.dg_batch_step.restype = ctypes.c_int
+    lib.dg_rhs_vjp.argtypes = [vp, dp, dp, dp, vp]
+    lib.dg_rhs_vjp.restype = ctypes.c_int
+    lib.dg_adjoint_step.argtypes = [vp, dp, dp, dp, ctypes.c_double, vp]
+    lib.dg_adjoint_step.restype = ctypes.c_int
+    lib.dg_tape_len.argtypes = [vp]
+    lib.dg_tape_len.restype = sz
+    lib.dg_step_tape.argtypes = [vp, dp, ctypes.c_double, dp, vp]
+    lib.dg_step_tape.restype = ctypes.c_int
+    lib.dg_adjoint_step_tape.argtypes = [vp, dp, dp, dp, dp, ctypes.c_double, vp]
+    lib.dg_adjoint_step_tape.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -192,6 +203,40 @@ class Solver:
         _check(self.ctx, load().dg_step(self.ctx, _ptr(d), float(dt), int(nsteps), _stream(stream)), "dg_step")
         w.copy_(d, non_blocking=False)
         return w
+
+    def dg_rhs_vjp(self, w, lam, out=None, stream=None):
+        """out = (dL/dw)^T lam (FP64 contexts without viscous / surface-tension terms)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(w)
+        _check(self.ctx, load().dg_rhs_vjp(self.ctx, _ptr(w), _ptr(lam), _ptr(out), _stream(stream)), "dg_rhs_vjp")
+        return out
+
+    def dg_adjoint_step(self, w_n, lam_np1, dt: float, lam_n=None, stream=None):
+        """lam_n = (d w_{n+1} / d w_n)^T lam_np1 for one SSP-RK3 step of size dt from w_n."""
+        import torch
+        if lam_n is None:
+            lam_n = torch.empty_like(w_n)
+        _check(self.ctx, load().dg_adjoint_step(self.ctx, _ptr(w_n), _ptr(lam_np1), _ptr(lam_n), float(dt),
+                                                _stream(stream)), "dg_adjoint_step")
+        return lam_n
+
+    def dg_tape_len(self) -> int:
+        return int(load().dg_tape_len(self.ctx))
+
+    def dg_step_tape(self, w, dt: float, tape, stream=None):
+        """One SSP-RK3 step of w in place, recording its stages and traces into tape."""
+        _check(self.ctx, load().dg_step_tape(self.ctx, _ptr(w), float(dt), _ptr(tape), _stream(stream)),
+               "dg_step_tape")
+        return w
+
+    def dg_adjoint_step_tape(self, w_n, tape, lam_np1, dt: float, lam_n=None, stream=None):
+        import torch
+        if lam_n is None:
+            lam_n = torch.empty_like(w_n)
+        _check(self.ctx, load().dg_adjoint_step_tape(self.ctx, _ptr(w_n), _ptr(tape), _ptr(lam_np1), _ptr(lam_n),
+                                                     float(dt), _stream(stream)), "dg_adjoint_step_tape")
+        return lam_n
 
     def dg_diag(self, w, stream=None):
         out = (ctypes.c_double * 16)()

@@ -19,6 +19,7 @@
 #include "dg_kernels_fp64.cuh"
 #include "dg_kernels_fp32.cuh"
 #include "dg_batch.cuh"
+#include "dg_adjoint.cuh"
 #include "dgpf.h"
 
 namespace dgpf {
@@ -61,6 +62,23 @@ __global__ void k_to64(int N, double C2, double dC, const float *__restrict__ w3
 #pragma unroll
     for (int v = 0; v < RE; ++v) w[(long)v * N + n] = (double)w32[(long)v * N + n];
     w[(long)RE * N + n] = (double)w32[(long)RE * N + n] + fma(dC, phi, C2);
+  }
+}
+
+bool adj_kernels_p1(int, AdjKernels *);
+bool adj_kernels_p2(int, AdjKernels *);
+bool adj_kernels_p3(int, AdjKernels *);
+bool adj_kernels_p4(int, AdjKernels *);
+bool adj_kernels_p5(int, AdjKernels *);
+
+bool adj_kernels(int p, int dim, AdjKernels *out) {
+  switch (p) {
+    case 1: return adj_kernels_p1(dim, out);
+    case 2: return adj_kernels_p2(dim, out);
+    case 3: return adj_kernels_p3(dim, out);
+    case 4: return adj_kernels_p4(dim, out);
+    case 5: return adj_kernels_p5(dim, out);
+    default: return false;
   }
 }
 
@@ -252,6 +270,9 @@ struct dg_ctx {
   KernelSet32 ks32;
   ParamsF pf;
   int prec = DG_FP64;
+  AdjKernels adj{};
+  bool has_adj = false;
+  double *d_trbar = nullptr, *d_lam1 = nullptr, *d_lam2 = nullptr;
   float *d_opsf = nullptr, *d_ws32 = nullptr, *d_w1_32 = nullptr, *d_w2_32 = nullptr, *d_rvol32 = nullptr,
         *d_trace32 = nullptr;
   int conv_blocks = 1;
@@ -304,6 +325,9 @@ static void free_ctx(dg_ctx *c) {
   cudaFree(c->d_part);
   cudaFree(c->d_diag);
   cudaFree(c->d_status);
+  cudaFree(c->d_trbar);
+  cudaFree(c->d_lam1);
+  cudaFree(c->d_lam2);
   cudaFree(c->d_opsf);
   cudaFree(c->d_ws32);
   cudaFree(c->d_w1_32);
@@ -456,6 +480,8 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
     return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: viscous/surface terms need dim = 2");
   }
 
+  // The discrete adjoint covers the FP64 inviscid equations without surface tension.
+  c->has_adj = c->prec == DG_FP64 && !o.viscous && !o.surface_tension && adj_kernels(p, c->dim, &c->adj);
   const std::vector<double> ops = build_ops(c->dim, p, c->hx, c->hy);
   c->prm = make_params(mesh, p, eos, Gamma, eps, o, c->hx, c->hy);
   Params &q = c->prm;
@@ -483,6 +509,10 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
                (e = cudaMalloc(&c->d_rvol, sbytes)) != cudaSuccess ||
                (e = cudaMalloc(&c->d_trace, tbytes)) != cudaSuccess)) ||
       (e = cudaMalloc(&c->d_part, (size_t)c->nparts * DIAG_N * sizeof(double))) != cudaSuccess ||
+      (c->has_adj && ((e = cudaMalloc(&c->d_trbar, (size_t)NT_INVISCID * c->E * c->NFK * sizeof(double))) !=
+                          cudaSuccess ||
+                      (e = cudaMalloc(&c->d_lam1, sbytes)) != cudaSuccess ||
+                      (e = cudaMalloc(&c->d_lam2, sbytes)) != cudaSuccess)) ||
       (e = cudaMalloc(&c->d_diag, DIAG_N * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&c->d_status, sizeof(unsigned))) != cudaSuccess) {
     free_ctx(c);
@@ -918,4 +948,120 @@ extern "C" dg_status dg_batch_step(dg_ctx *c, double *const *w, const double *dt
   for (int k = 0; k < nsteps % GRAPH_UNROLL; ++k)
     if ((e = cudaGraphLaunch(c->g1, s)) != cudaSuccess) return cuda_fail(c, e, "dg_batch_step: graph launch");
   return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Discrete adjoint (FP64, inviscid, no surface tension)
+// ---------------------------------------------------------------------------
+
+// out = ca xa + cb (dL/dw(w))^T lam + cc yc + cd zd
+static dg_status run_vjp(dg_ctx *c, const double *w, const double *lam, double *out, double ca, const double *xa,
+                         double cb, double cc, const double *yc, double cd, const double *zd, cudaStream_t s) {
+  cudaError_t e = c->ks.volume(c->prm, w, c->d_rvol, c->d_trace, s);  // traces of w
+  if (e == cudaSuccess) e = c->adj.face(c->prm, lam, c->d_trace, c->d_trbar, s);
+  if (e == cudaSuccess) e = c->adj.volume(c->prm, w, lam, c->d_trbar, out, ca, xa, cb, cc, yc, cd, zd, s);
+  return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "adjoint kernel launch");
+}
+
+static dg_status adj_check(dg_ctx *c, const char *who) {
+  if (c->batch) return fail(c, DG_ERR_ARG, std::string(who) + ": batch context");
+  if (!c->has_adj)
+    return fail(c, DG_ERR_UNSUPPORTED,
+                std::string(who) + ": the adjoint covers the FP64 path without viscous and surface-tension terms");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_rhs_vjp(dg_ctx *c, const double *w, const double *lam, double *out, void *stream) {
+  if (!c) return DG_ERR_ARG;
+  dg_status r = adj_check(c, "dg_rhs_vjp");
+  if (r != DG_OK) return r;
+  if (!w || !lam || !out) return fail(c, DG_ERR_ARG, "dg_rhs_vjp: null array");
+  if (out == w || out == lam) return fail(c, DG_ERR_ARG, "dg_rhs_vjp: out must not overlap w or lam");
+  return run_vjp(c, w, lam, out, 0.0, nullptr, 1.0, 0.0, nullptr, 0.0, nullptr, (cudaStream_t)stream);
+}
+
+// Reverse of one SSP-RK3 step w_{n+1} = Phi(w_n) (Shu-Osher form):
+//   w1 = w + dt L(w), w2 = 3/4 w + 1/4 (w1 + dt L(w1)), w3 = 1/3 w + 2/3 (w2 + dt L(w2)).
+// Given lam3 = lam_{n+1}:
+//   lam2 = 2/3 lam3 + 2/3 dt L'(w2)^T lam3
+//   lam1 = 1/4 lam2 + 1/4 dt L'(w1)^T lam2
+//   lam_n = lam1 + dt L'(w)^T lam1 + 1/3 lam3 + 3/4 lam2
+// The stages w1, w2 are recomputed from w_n first.
+extern "C" dg_status dg_adjoint_step(dg_ctx *c, const double *w_n, const double *lam_np1, double *lam_n, double dt,
+                                     void *stream) {
+  if (!c) return DG_ERR_ARG;
+  dg_status r = adj_check(c, "dg_adjoint_step");
+  if (r != DG_OK) return r;
+  if (!w_n || !lam_np1 || !lam_n) return fail(c, DG_ERR_ARG, "dg_adjoint_step: null array");
+  if (lam_n == w_n) return fail(c, DG_ERR_ARG, "dg_adjoint_step: lam_n must not overlap w_n");
+  if (!(dt > 0.0)) return fail(c, DG_ERR_ARG, "dg_adjoint_step: need dt > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((r = run_stage(c, MODE_S1, dt, w_n, w_n, c->d_w1, s)) != DG_OK) return r;
+  if ((r = run_stage(c, MODE_S2, dt, w_n, c->d_w1, c->d_w2, s)) != DG_OK) return r;
+  if ((r = run_vjp(c, c->d_w2, lam_np1, c->d_lam2, 2.0 / 3.0, lam_np1, 2.0 / 3.0 * dt, 0.0, nullptr, 0.0, nullptr,
+                   s)) != DG_OK)
+    return r;
+  if ((r = run_vjp(c, c->d_w1, c->d_lam2, c->d_lam1, 0.25, c->d_lam2, 0.25 * dt, 0.0, nullptr, 0.0, nullptr, s)) !=
+      DG_OK)
+    return r;
+  return run_vjp(c, w_n, c->d_lam1, lam_n, 1.0, c->d_lam1, dt, 1.0 / 3.0, lam_np1, 0.75, c->d_lam2, s);
+}
+
+// ---------------------------------------------------------------------------
+// Taped step and its reverse (no recomputation in the reverse sweep)
+// ---------------------------------------------------------------------------
+// tape layout (doubles): w1 [7N] | w2 [7N] | traces of w, w1, w2 [3 x nt E NFK]
+
+extern "C" size_t dg_tape_len(const dg_ctx *c) {
+  if (!c || c->batch || !c->has_adj) return 0;
+  return 2 * c->len + 3 * (size_t)c->ks.nt * c->E * c->NFK;
+}
+
+static void tape_parts(dg_ctx *c, double *tape, double **w1, double **w2, double **tr) {
+  *w1 = tape;
+  *w2 = tape + c->len;
+  const size_t nt = (size_t)c->ks.nt * c->E * c->NFK;
+  for (int k = 0; k < 3; ++k) tr[k] = tape + 2 * c->len + k * nt;
+}
+
+extern "C" dg_status dg_step_tape(dg_ctx *c, double *w, double dt, double *tape, void *stream) {
+  if (!c) return DG_ERR_ARG;
+  dg_status r = adj_check(c, "dg_step_tape");
+  if (r != DG_OK) return r;
+  if (!w || !tape) return fail(c, DG_ERR_ARG, "dg_step_tape: null array");
+  if (!(dt > 0.0)) return fail(c, DG_ERR_ARG, "dg_step_tape: need dt > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *w1, *w2, *tr[3];
+  tape_parts(c, tape, &w1, &w2, tr);
+  const double *in[3] = {w, w1, w2};
+  double *out[3] = {w1, w2, w};
+  const int mode[3] = {MODE_S1, MODE_S2, MODE_S3};
+  for (int k = 0; k < 3; ++k) {
+    cudaError_t e = c->ks.volume(c->prm, in[k], c->d_rvol, tr[k], s);
+    if (e == cudaSuccess) e = c->ks.surface(c->prm, mode[k], dt, w, in[k], c->d_rvol, tr[k], out[k], s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_step_tape: kernel launch");
+  }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_adjoint_step_tape(dg_ctx *c, const double *w_n, const double *tape, const double *lam_np1,
+                                          double *lam_n, double dt, void *stream) {
+  if (!c) return DG_ERR_ARG;
+  dg_status r = adj_check(c, "dg_adjoint_step_tape");
+  if (r != DG_OK) return r;
+  if (!w_n || !tape || !lam_np1 || !lam_n) return fail(c, DG_ERR_ARG, "dg_adjoint_step_tape: null array");
+  if (!(dt > 0.0)) return fail(c, DG_ERR_ARG, "dg_adjoint_step_tape: need dt > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *w1, *w2, *tr[3];
+  tape_parts(c, const_cast<double *>(tape), &w1, &w2, tr);
+  auto vjp = [&](const double *w, const double *trace, const double *lam, double *out, double ca, const double *xa,
+                 double cb, double cc, const double *yc, double cd, const double *zd) {
+    cudaError_t e = c->adj.face(c->prm, lam, trace, c->d_trbar, s);
+    if (e == cudaSuccess) e = c->adj.volume(c->prm, w, lam, c->d_trbar, out, ca, xa, cb, cc, yc, cd, zd, s);
+    return e;
+  };
+  cudaError_t e = vjp(w2, tr[2], lam_np1, c->d_lam2, 2.0 / 3.0, lam_np1, 2.0 / 3.0 * dt, 0.0, nullptr, 0.0, nullptr);
+  if (e == cudaSuccess) e = vjp(w1, tr[1], c->d_lam2, c->d_lam1, 0.25, c->d_lam2, 0.25 * dt, 0.0, nullptr, 0.0, nullptr);
+  if (e == cudaSuccess) e = vjp(w_n, tr[0], c->d_lam1, lam_n, 1.0, c->d_lam1, dt, 1.0 / 3.0, lam_np1, 0.75, c->d_lam2);
+  return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_adjoint_step_tape: kernel launch");
 }

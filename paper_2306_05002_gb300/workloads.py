@@ -260,3 +260,37 @@ def ensemble(n: int = 256, seed: int = 4, nmin: int = 16, nmax: int = 128, order
         wl.meta.update(kind="bubble" if bubble else "drop", member=k, seed=seed)
         out.append(wl)
     return out
+
+
+def level_set_modes(wl: Workload, cx: float, cy: float):
+    """cos(k theta), sin(k theta), k = 1..8, of the polar angle about (cx, cy) (periodic
+    minimum image) at every node: shape (16, N), rows ordered (cos 1, sin 1, cos 2, ...)."""
+    x, y = node_coords(wl)
+    dx = x - cx
+    dy = y - cy
+    dx -= np.round(dx)
+    dy -= np.round(dy)
+    th = np.arctan2(dy, dx)
+    rows = []
+    for k in range(1, 9):
+        rows += [np.cos(k * th), np.sin(k * th)]
+    return np.array(rows)
+
+
+def adjoint_drop(n: int = 128, p: int = 3, seed: int = 5, theta=None, nsteps: int = 200, R: float = 0.15,
+                 u: float = 1.0, v: float = 0.5, P0: float = 1e5, eps_h: float = 0.75) -> Workload:
+    """Drop advection with a parametrised initial level set: psi0 = r - R - sum_k (theta_{2k-1} cos k th +
+    theta_{2k} sin k th) about the (seeded) drop centre, phi0 the tanh profile of r - R.
+    theta defaults to 16 draws of N(0, 0.01^2) from seed 50."""
+    rng = np.random.default_rng(seed)
+    cx, cy = rng.uniform(0.0, 1.0, size=2)
+    if theta is None:
+        theta = np.random.default_rng(50).normal(0.0, 0.01, size=16)
+    wl = drop_2d(n=n, p=p, R=R, u=u, v=v, P0=P0, eps_h=eps_h, nsteps=nsteps, center=(cx, cy))
+    x, y = node_coords(wl)
+    modes = level_set_modes(wl, cx, cy)
+    w = wl.w.copy()
+    w[1] = w[1] - np.asarray(theta) @ modes
+    wl.w = w
+    wl.meta.update(theta=list(map(float, theta)), seed=seed)
+    return wl

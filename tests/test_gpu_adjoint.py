@@ -1,0 +1,191 @@
+"""Discrete adjoint (FP64 path): dg_rhs_vjp and dg_adjoint_step against finite differences,
+and the gradient of an interface functional with respect to level-set parameters against
+central differences of the GPU forward map and of the oracle's forward map.
+
+The right-hand side has kinks (lambda = max of the one-sided wave speeds at every face), so a
+finite difference is only as good as the number of kinks its step straddles: the steps are
+small (1e-8 .. 1e-9 of the variable's scale), which the FP64 round-off still resolves to
+~1e-7.  Tolerances: 1e-5 for the column-by-column oracle Jacobian, 2e-6 for dot products."""
+import numpy as np
+import pytest
+
+from paper_2306_05002_gb300 import workloads as W
+from tests.helpers import mass_weights, problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _broken(wl, seed=3, amp=0.05):
+    import oracle
+    rng = np.random.default_rng(seed)
+    prim = oracle.primitives(oracle.Problem(**wl.problem_kwargs()), wl.w)
+    phi = np.clip(wl.w[0] + amp * rng.uniform(-1, 1, wl.N), 0.02, 0.98)
+    psi = wl.w[1] + amp * rng.uniform(-1, 1, wl.N)
+    P = prim[3] * (1 + 0.02 * rng.uniform(-1, 1, wl.N))
+    u = prim[1] + 0.3 + 0.05 * rng.uniform(-1, 1, wl.N)
+    v = prim[2] - 0.2 + 0.05 * rng.uniform(-1, 1, wl.N)
+    return W.conserved(wl, phi, psi, P, u, v)
+
+
+@pytest.mark.parametrize("maker", [lambda: W.drop_2d(n=3, p=2, seed=2), lambda: W.drop_2d(n=2, p=3, seed=3),
+                                   lambda: W.drop_2d(n=2, p=4, seed=4, water_inside=False),
+                                   lambda: W.slab_1d(nx=5, p=3)])
+def test_vjp_against_oracle_jacobian(orc, dg, maker):
+    """mu = J^T lam with J the oracle's Jacobian by central differences, column by column."""
+    import torch
+    wl = maker()
+    w = _broken(wl)
+    pb = problem(orc, wl)
+    rng = np.random.default_rng(1)
+    scale = np.abs(w).max(axis=1, keepdims=True)
+    lam = rng.normal(size=w.shape) / np.maximum(np.abs(orc.rhs(pb, w)).max(axis=1, keepdims=True), 1e-300)
+    mu_fd = np.zeros_like(w)
+    for v in range(7):
+        for j in range(wl.N):
+            h = 1e-8 * max(scale[v, 0], 1e-3)
+            wp, wm = w.copy(), w.copy()
+            wp[v, j] += h
+            wm[v, j] -= h
+            col = (orc.rhs(pb, wp) - orc.rhs(pb, wm)) / (2 * h)
+            mu_fd[v, j] = np.sum(lam * col)
+    s = dg.Solver(wl)
+    mu = s.dg_rhs_vjp(torch.from_numpy(w.copy()).cuda(), torch.from_numpy(lam).cuda()).cpu().numpy()
+    s.close()
+    for v in range(7):
+        ref = np.abs(mu_fd[v]).max()
+        assert np.abs(mu[v] - mu_fd[v]).max() <= 1e-5 * ref, (v, np.abs(mu[v] - mu_fd[v]).max() / ref)
+
+
+@pytest.mark.parametrize("maker", [lambda: W.drop_2d(n=16, p=3, seed=2), lambda: W.slab_1d(nx=40, p=4),
+                                   lambda: W.drop_2d(n=8, p=5, seed=7, water_inside=False)])
+def test_vjp_dot_product_with_directional_difference(dg, maker):
+    """<lam, J v> (central difference of dg_rhs along v) = <J^T lam, v>."""
+    import torch
+    wl = maker()
+    w = torch.from_numpy(_broken(wl)).cuda()
+    g = torch.Generator(device="cpu").manual_seed(0)
+    scale = w.abs().amax(dim=1, keepdim=True)
+    vdir = (torch.randn(w.shape, generator=g, dtype=torch.float64).cuda()) * scale
+    s = dg.Solver(wl)
+    L0 = s.dg_rhs(w)
+    lam = torch.randn(w.shape, generator=g, dtype=torch.float64).cuda() / L0.abs().amax(dim=1, keepdim=True)
+    h = 1e-9
+    Jv = (s.dg_rhs(w + h * vdir) - s.dg_rhs(w - h * vdir)) / (2 * h)
+    mu = s.dg_rhs_vjp(w, lam)
+    lhs = float((lam * Jv).sum())
+    rhs = float((mu * vdir).sum())
+    s.close()
+    assert abs(lhs - rhs) <= 2e-6 * max(abs(lhs), abs(rhs)), (lhs, rhs)
+
+
+def test_adjoint_step_dot_product(dg):
+    """<lam_{n+1}, dPhi v> (central difference of one SSP-RK3 step) = <lam_n, v>."""
+    import torch
+    wl = W.drop_2d(n=16, p=3, seed=4)
+    w = torch.from_numpy(_broken(wl, amp=0.01)).cuda()
+    g = torch.Generator(device="cpu").manual_seed(2)
+    scale = w.abs().amax(dim=1, keepdim=True)
+    vdir = torch.randn(w.shape, generator=g, dtype=torch.float64).cuda() * scale
+    lam1 = torch.randn(w.shape, generator=g, dtype=torch.float64).cuda() / scale
+    s = dg.Solver(wl)
+    h = 1e-9
+    wp, wm = (w + h * vdir).contiguous(), (w - h * vdir).contiguous()
+    s.dg_step(wp, wl.dt, 1)
+    s.dg_step(wm, wl.dt, 1)
+    lhs = float((lam1 * (wp - wm) / (2 * h)).sum())
+    lam0 = s.dg_adjoint_step(w, lam1, wl.dt)
+    rhs = float((lam0 * vdir).sum())
+    # in place (lam_n aliasing lam_{n+1}) gives the same result
+    lam_alias = lam1.clone()
+    s.dg_adjoint_step(w, lam_alias, wl.dt, lam_n=lam_alias)
+    # the taped step reproduces dg_step, and its reverse reproduces dg_adjoint_step
+    tape = torch.empty(s.dg_tape_len(), dtype=torch.float64, device="cuda")
+    wt, ws = w.clone(), w.clone()
+    s.dg_step_tape(wt, wl.dt, tape)
+    s.dg_step(ws, wl.dt, 1)
+    lam_t = s.dg_adjoint_step_tape(w, tape, lam1, wl.dt)
+    s.close()
+    assert abs(lhs - rhs) <= 2e-6 * max(abs(lhs), abs(rhs)), (lhs, rhs)
+    assert torch.equal(lam_alias, lam0)
+    assert torch.equal(wt, ws)
+    assert torch.equal(lam_t, lam0)
+
+
+def _objective(orc, wl, wN, target):
+    M = mass_weights(orc, wl)
+    return 0.5 * np.sum(M * (wN[0] - target) ** 2), M
+
+
+def test_level_set_parameter_gradient(orc, dg):
+    """dJ/dtheta by the adjoint (checkpointed trajectory) against central differences of J
+    through the GPU forward map; J = 1/2 int (alpha_N - alpha*)^2, alpha* from other parameters."""
+    import torch
+    from paper_2306_05002_gb300 import adjoint as A
+    n, steps, every = 16, 30, 7
+    base = W.adjoint_drop(n=n, p=3, nsteps=steps)
+    theta = np.array(base.meta["theta"])
+    tgt_wl = W.adjoint_drop(n=n, p=3, nsteps=steps, theta=np.random.default_rng(51).normal(0, 0.01, 16))
+    s = dg.Solver(base)
+    dt = base.dt
+
+    def run(wl):
+        x = torch.from_numpy(wl.w.copy()).cuda()
+        s.dg_step(x, dt, steps)
+        return x.cpu().numpy()
+    target = run(tgt_wl)[0]
+    wN, ckpt = A.forward(s, torch.from_numpy(base.w.copy()).cuda(), dt, steps, every)
+    J, M = _objective(orc, base, wN.cpu().numpy(), target)
+    lamN = torch.zeros_like(wN)
+    lamN[0] = torch.from_numpy(M * (wN[0].cpu().numpy() - target)).cuda()
+    lam0 = A.backward(s, ckpt, lamN, dt, steps, every).cpu().numpy()
+    lam0_recompute = A.backward(s, ckpt, lamN, dt, steps, every, tape=False).cpu().numpy()
+    np.testing.assert_array_equal(lam0, lam0_recompute)
+    modes = W.level_set_modes(base, base.meta["cx"], base.meta["cy"])
+    grad = -(modes @ lam0[1])          # psi0 = ... - theta . modes
+    fd = np.zeros(16)
+    for k in range(16):
+        h = 1e-5
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        Jp = _objective(orc, base, run(W.adjoint_drop(n=n, p=3, nsteps=steps, theta=tp)), target)[0]
+        Jm = _objective(orc, base, run(W.adjoint_drop(n=n, p=3, nsteps=steps, theta=tm)), target)[0]
+        fd[k] = (Jp - Jm) / (2 * h)
+    s.close()
+    assert J > 0
+    np.testing.assert_allclose(grad, fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
+
+
+def test_level_set_parameter_gradient_against_oracle(orc, dg):
+    """The same gradient on a small mesh against central differences of the oracle's own
+    forward map (the oracle-derived reference gradient)."""
+    import torch
+    from paper_2306_05002_gb300 import adjoint as A
+    n, steps = 6, 8
+    base = W.adjoint_drop(n=n, p=2, nsteps=steps)
+    theta = np.array(base.meta["theta"])
+    pb = problem(orc, base)
+    dt = base.dt
+    target = orc.rk3(pb, W.adjoint_drop(n=n, p=2, nsteps=steps,
+                                        theta=np.random.default_rng(51).normal(0, 0.01, 16)).w, dt, steps)[0]
+    s = dg.Solver(base)
+    wN, ckpt = A.forward(s, torch.from_numpy(base.w.copy()).cuda(), dt, steps, 3)
+    M = mass_weights(orc, base)
+    lamN = torch.zeros_like(wN)
+    lamN[0] = torch.from_numpy(M * (wN[0].cpu().numpy() - target)).cuda()
+    lam0 = A.backward(s, ckpt, lamN, dt, steps, 3).cpu().numpy()
+    s.close()
+    modes = W.level_set_modes(base, base.meta["cx"], base.meta["cy"])
+    grad = -(modes @ lam0[1])
+    fd = np.zeros(16)
+    for k in range(16):
+        h = 1e-5
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        Jp = _objective(orc, base, orc.rk3(pb, W.adjoint_drop(n=n, p=2, nsteps=steps, theta=tp).w, dt, steps),
+                        target)[0]
+        Jm = _objective(orc, base, orc.rk3(pb, W.adjoint_drop(n=n, p=2, nsteps=steps, theta=tm).w, dt, steps),
+                        target)[0]
+        fd[k] = (Jp - Jm) / (2 * h)
+    np.testing.assert_allclose(grad, fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
