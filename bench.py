@@ -43,6 +43,12 @@ def parse():
                     help="steps of the FP32-bulk vs FP64 accuracy comparison (the workload's 500)")
     ap.add_argument("--batch-steps", type=int, default=10,
                     help="timed steps of the batched ensemble (0 skips the batched block)")
+    ap.add_argument("--rt-steps", type=int, default=10,
+                    help="timed steps of the 256 x 256, p = 4 Rayleigh-Taylor block (0 skips it)")
+    ap.add_argument("--batch-problems", type=int, default=256,
+                    help="ensemble size of the batched block (smaller values for profiling)")
+    ap.add_argument("--adjoint-n", type=int, default=128,
+                    help="elements per direction of the adjoint block (smaller values for profiling)")
     ap.add_argument("--adjoint-steps", type=int, default=200,
                     help="trajectory length of the adjoint timing (0 skips it)")
     ap.add_argument("--cpu-sample-steps", type=int, default=0,
@@ -281,13 +287,13 @@ def accuracy(dg, wl, steps):
             "l2_rel_u": l2(u32, u64)}
 
 
-def batched_block(dg, steps):
+def batched_block(dg, steps, nprob=256):
     """Batched ensemble of 256 independent drop/bubble problems (meshes 16^2..128^2, p in 2..5,
     seed 4): one batched FP32-bulk step vs the same problems stepped one by one (FP32-bulk and
     FP64).  The working set (several GB) is far larger than L2, so no flush is needed."""
     import torch
     from paper_2306_05002_gb300 import workloads as W
-    wls = W.ensemble(n=256, seed=4)
+    wls = W.ensemble(n=nprob, seed=4)
     nodes = sum(wl.N for wl in wls)
     units = 7 * 3 * nodes
     states = [torch.from_numpy(wl.w.copy()).cuda() for wl in wls]
@@ -322,7 +328,7 @@ def batched_block(dg, steps):
 
     ms_32 = one_by_one("fp32bulk", 2)
     ms_64 = one_by_one("fp64", 1)
-    return {"workload": "256 independent 2D periodic drop/bubble problems, N x N quads with N ~ U{16..128}, "
+    return {"workload": f"{nprob} independent 2D periodic drop/bubble problems, N x N quads with N ~ U{{16..128}}, "
                         "p ~ U{2,3,4,5}, R ~ U[0.05,0.2], seeded centres (seed 4), u=(1,0.5), eps=0.75h, own dt",
             "problems": len(wls), "nodes": nodes, "steps": steps,
             "value": units / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b,
@@ -331,7 +337,40 @@ def batched_block(dg, steps):
             "speedup_vs_fp64": ms_64 / ms_b, "l2": "working set > L2 (no flush needed)"}
 
 
-def adjoint_block(dg, steps, every=20):
+def rt_block(dg, steps, n=256):
+    """Viscous Rayleigh-Taylor set-up (256 x 256 quads, p = 4, walls, gravity, surface tension,
+    seed 3): FP32-bulk and FP64 step times and the FP32-bulk error after the timed steps.
+    The state (92 MB FP64, 1.64M nodes) and the workspace exceed L2 together; no flush."""
+    import numpy as np
+    import torch
+    from paper_2306_05002_gb300 import workloads as W
+    wl = W.rayleigh_taylor(n=n, p=4, seed=3)
+    out = {"workload": f"2D viscous Rayleigh-Taylor {n}x{n} quads p=4, no-slip walls, g=-9.81, sigma=0.07, "
+                       "density ratio 3, seeded 8-mode interface", "nodes": wl.N, "steps": steps}
+    states = {}
+    for prec in ("fp32bulk", "fp64"):
+        s = dg.Solver(wl, precision=prec)
+        w = torch.from_numpy(wl.w.copy()).cuda()
+        s.dg_step(w, wl.dt, 2)
+        w.copy_(torch.from_numpy(wl.w))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.dg_step(w, wl.dt, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[prec] = {"ms_per_step": ms, "value": 21 * wl.N / (ms * 1e-3), "unit": UNIT,
+                     "device_status": s.dg_status_read()}
+        states[prec] = w.cpu().numpy()
+        s.close()
+    a, b = states["fp32bulk"], states["fp64"]
+    out["l2_rel_alpha"] = float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0]))
+    out["speedup_fp32bulk_vs_fp64"] = out["fp64"]["ms_per_step"] / out["fp32bulk"]["ms_per_step"]
+    return out
+
+
+def adjoint_block(dg, steps, every=20, n=128):
     """Gradient of J = 1/2 int (alpha_N - alpha*)^2 with respect to the initial state of the
     128 x 128, p = 3 drop (level set with 16 seeded Fourier coefficients, seed 5/50/51),
     FP64, checkpoints every 20 steps.  adjoint/forward = backward sweep (segment replay +
@@ -340,14 +379,13 @@ def adjoint_block(dg, steps, every=20):
     import torch
     from paper_2306_05002_gb300 import adjoint as A
     from paper_2306_05002_gb300 import workloads as W
-    wl = W.adjoint_drop(n=128, p=3, nsteps=steps)
-    tgt = W.adjoint_drop(n=128, p=3, nsteps=steps, theta=np.random.default_rng(51).normal(0, 0.01, 16))
+    wl = W.adjoint_drop(n=n, p=3, nsteps=steps)
+    tgt = W.adjoint_drop(n=n, p=3, nsteps=steps, theta=np.random.default_rng(51).normal(0, 0.01, 16))
     s = dg.Solver(wl)
     x = torch.from_numpy(tgt.w.copy()).cuda()
     s.dg_step(x, wl.dt, steps)
     target = x[0].clone()
     w0 = torch.from_numpy(wl.w.copy()).cuda()
-    _, wt = W.gll_points(3), None
     A.forward(s, w0, wl.dt, 2, every)  # warm-up (graph capture)
     torch.cuda.synchronize()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -362,7 +400,7 @@ def adjoint_block(dg, steps, every=20):
     tf, tb = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
     ok = bool(torch.isfinite(lam0).all())
     s.close()
-    return {"workload": "2D drop 128x128 quads p=3, FP64, 16 level-set Fourier parameters (seeds 5, 50, 51)",
+    return {"workload": f"2D drop {n}x{n} quads p=3, FP64, 16 level-set Fourier parameters (seeds 5, 50, 51)",
             "steps": steps, "checkpoint_every": every, "forward_ms": tf, "backward_ms": tb,
             "adjoint_over_forward": tb / tf, "finite": ok}
 
@@ -424,8 +462,11 @@ def run_ours(args, rank, world, local_rank):
     e2e_t = time.perf_counter() - t0
 
     acc = accuracy(dg, wl, args.accuracy_steps) if (args.precision == "fp32bulk" and rank == 0) else None
-    batched = batched_block(dg, args.batch_steps) if (args.batch_steps > 0 and rank == 0) else None
-    adjoint = adjoint_block(dg, args.adjoint_steps) if (args.adjoint_steps > 0 and rank == 0) else None
+    batched = (batched_block(dg, args.batch_steps, args.batch_problems)
+               if (args.batch_steps > 0 and rank == 0) else None)
+    adjoint = (adjoint_block(dg, args.adjoint_steps, n=args.adjoint_n)
+               if (args.adjoint_steps > 0 and rank == 0) else None)
+    rt = rt_block(dg, args.rt_steps) if (args.rt_steps > 0 and rank == 0) else None
 
     ms_max, e2e_max, ref_ms = reduce_max([main["ms"], e2e_t, ref["ms"] if ref else 0.0], "cuda")
 
@@ -456,6 +497,8 @@ def run_ours(args, rank, world, local_rank):
             line["batched"] = batched
         if adjoint:
             line["adjoint"] = adjoint
+        if rt:
+            line["rayleigh_taylor"] = rt
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
         print(json.dumps(line), flush=True)

@@ -137,7 +137,7 @@ def _stream(stream=None):
 
 def make_structs(dim, nx, ny, x0, x1, y0, y1, bc, gamma, pinf, rho0, mu=(0.0, 0.0), sigma=0.0, g=(0.0, 0.0),
                  precision="fp64", c_ip=1.0, viscous=False, gravity=False, surface_tension=False,
-                 check_finite=True, **_ignored):
+                 check_finite=True, barrier_timeout_ms=1000.0, **_ignored):
     m = dg_mesh()
     m.dim, m.nx, m.ny = dim, nx, ny
     m.x0, m.x1, m.y0, m.y1 = x0, x1, y0, y1
@@ -150,7 +150,7 @@ def make_structs(dim, nx, ny, x0, x1, y0, y1, bc, gamma, pinf, rho0, mu=(0.0, 0.
     o = dg_opts()
     o.prec = PREC[precision] if isinstance(precision, str) else int(precision)
     o.c_ip, o.viscous, o.gravity, o.surface_tension = c_ip, int(viscous), int(gravity), int(surface_tension)
-    o.check_finite, o.barrier_timeout_ms = int(check_finite), 1000.0
+    o.check_finite, o.barrier_timeout_ms = int(check_finite), float(barrier_timeout_ms)
     return m, e, o
 
 
@@ -161,12 +161,14 @@ class Solver:
     fields).  State tensors are float64 CUDA tensors of shape (7, N).
     """
 
-    def __init__(self, problem, precision: str = "fp64", check_finite: bool = True):
+    def __init__(self, problem, precision: str = "fp64", check_finite: bool = True,
+                 barrier_timeout_ms: float = 1000.0):
         lib = load()
         kw = problem.problem_kwargs() if hasattr(problem, "problem_kwargs") else dict(problem)
         p = kw.pop("p")
         Gamma, eps = kw.pop("Gamma"), kw.pop("eps")
-        m, e, o = make_structs(precision=precision, check_finite=check_finite, **kw)
+        m, e, o = make_structs(precision=precision, check_finite=check_finite,
+                               barrier_timeout_ms=barrier_timeout_ms, **kw)
         self._m, self._e, self._o = m, e, o
         h = ctypes.c_void_p()
         st = lib.dg_create(ctypes.byref(m), p, ctypes.byref(e), Gamma, eps, ctypes.byref(o), ctypes.byref(h))

@@ -120,3 +120,16 @@ def test_fp32bulk_conversion_round_trip_keeps_pressure(orc, dg):
     P0, P1 = orc.primitives(pb, wl.w)[3], orc.primitives(pb, d.cpu().numpy())[3]
     assert np.abs(P1 / P0 - 1).max() < 1e-6
     s.close()
+
+
+
+def test_fp32bulk_rayleigh_taylor_physics_tracks_fp64(orc, dg):
+    """Walls, viscous stress, gravity and surface tension in the FP32-bulk path: 20 steps of a
+    32 x 32, p = 4 Rayleigh-Taylor set-up stay within 1e-5 (relative L2) of the FP64 path in
+    phi and P."""
+    wl = W.rayleigh_taylor(n=32, p=4, seed=3)
+    w64 = _run(dg, wl, "fp64", 20)
+    w32 = _run(dg, wl, "fp32bulk", 20)
+    pb = problem(orc, wl)
+    assert _l2(w32[0], w64[0]) <= 1e-5
+    assert _l2(orc.primitives(pb, w32)[3], orc.primitives(pb, w64)[3]) <= 1e-5
