@@ -134,8 +134,10 @@ const char *dg_last_error(const dg_ctx *ctx);
 /* Kernel-level timing for roofline reports: run nrep right-hand-side
    evaluations of w with CUDA events around each kernel launch on stream and
    write the mean duration in milliseconds of each kernel kind to ms_out
-   (index 0 volume kernel, 1 surface kernel); returns the number of kinds
-   written (<= nmax).  Synchronises the stream. */
+   (index 0 volume kernel, 1 surface kernel, and for FP32-bulk contexts 2 the
+   fused kernel that dg_step runs: the surface part of one stage followed by
+   the volume part of the next); returns the number of kinds written
+   (<= nmax).  Synchronises the stream. */
 int dg_time_kernels(dg_ctx *ctx, const double *w, int nrep, double *ms_out, int nmax, void *stream);
 
 /* Algorithmic FP64-equivalent flop and DRAM byte counts per launch of each

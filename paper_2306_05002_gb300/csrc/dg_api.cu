@@ -274,7 +274,7 @@ struct dg_ctx {
   bool has_adj = false;
   double *d_trbar = nullptr, *d_lam1 = nullptr, *d_lam2 = nullptr;
   float *d_opsf = nullptr, *d_ws32 = nullptr, *d_w1_32 = nullptr, *d_w2_32 = nullptr, *d_rvol32 = nullptr,
-        *d_trace32 = nullptr;
+        *d_trace32 = nullptr, *d_rvol32b = nullptr, *d_trace32b = nullptr;
   int conv_blocks = 1;
   double *d_ops = nullptr, *d_w1 = nullptr, *d_w2 = nullptr, *d_rvol = nullptr, *d_trace = nullptr;
   double *d_part = nullptr, *d_diag = nullptr;
@@ -282,12 +282,14 @@ struct dg_ctx {
   int nparts = 0;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t g1 = nullptr, gk = nullptr;
+  cudaGraphExec_t grem[8] = {};  // FP32-bulk: graphs of 1..7 steps, captured on first use
   const double *g_w = nullptr;
   double g_dt = 0.0;
   std::string err = "no error";
 };
 
 static const int GRAPH_UNROLL = 8;
+static_assert(GRAPH_UNROLL <= (int)(sizeof(dg_ctx::grem) / sizeof(cudaGraphExec_t)), "remainder graph slots");
 
 static dg_status fail(dg_ctx *c, dg_status s, const std::string &msg) {
   if (c) c->err = msg;
@@ -303,6 +305,10 @@ static void free_graphs(dg_ctx *c) {
   if (c->g1) cudaGraphExecDestroy(c->g1);
   if (c->gk) cudaGraphExecDestroy(c->gk);
   c->g1 = c->gk = nullptr;
+  for (auto &g : c->grem) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
   c->g_w = nullptr;
 }
 
@@ -334,6 +340,8 @@ static void free_ctx(dg_ctx *c) {
   cudaFree(c->d_w2_32);
   cudaFree(c->d_rvol32);
   cudaFree(c->d_trace32);
+  cudaFree(c->d_rvol32b);
+  cudaFree(c->d_trace32b);
   if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
 }
@@ -502,7 +510,8 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
     const size_t n32 = c->len;
     const size_t t32 = (size_t)c->ks32.nt * c->E * c->NFK;
     alloc32(&c->d_opsf, opsf.size()) && alloc32(&c->d_ws32, n32) && alloc32(&c->d_w1_32, n32) &&
-        alloc32(&c->d_w2_32, n32) && alloc32(&c->d_rvol32, n32) && alloc32(&c->d_trace32, t32);
+        alloc32(&c->d_w2_32, n32) && alloc32(&c->d_rvol32, n32) && alloc32(&c->d_trace32, t32) &&
+        alloc32(&c->d_rvol32b, n32) && alloc32(&c->d_trace32b, t32);
   }
   if (e != cudaSuccess || (e = cudaMalloc(&c->d_ops, ops.size() * sizeof(double))) != cudaSuccess ||
       (f64 && ((e = cudaMalloc(&c->d_w1, sbytes)) != cudaSuccess || (e = cudaMalloc(&c->d_w2, sbytes)) != cudaSuccess ||
@@ -587,17 +596,44 @@ extern "C" dg_status dg_rhs(dg_ctx *c, const double *w, double *L, void *stream)
 // node's w0 value is read by the thread that overwrites it).
 static dg_status enqueue_step(dg_ctx *c, double *w, double dt, cudaStream_t s) {
   dg_status r;
-  if (c->prec != DG_FP64) {
-    // The first stage reads the FP64 state (and leaves the FP32 internal state
-    // in d_ws32); the last stage writes the FP64 state back.
-    const float d = (float)dt;
-    if ((r = run_stage32(c, MODE_S1, d, c->d_ws32, c->d_ws32, c->d_w1_32, nullptr, s, w)) != DG_OK) return r;
-    if ((r = run_stage32(c, MODE_S2, d, c->d_ws32, c->d_w1_32, c->d_w2_32, nullptr, s)) != DG_OK) return r;
-    return run_stage32(c, MODE_S3, d, c->d_ws32, c->d_w2_32, nullptr, w, s);
-  }
   if ((r = run_stage(c, MODE_S1, dt, w, w, c->d_w1, s)) != DG_OK) return r;
   if ((r = run_stage(c, MODE_S2, dt, w, c->d_w1, c->d_w2, s)) != DG_OK) return r;
   return run_stage(c, MODE_S3, dt, w, c->d_w2, w, s);
+}
+
+// `steps` FP32-bulk steps with the fused stage kernel: 1 + 3 steps launches.
+// The volume part of the first stage reads the FP64 state; the last stage
+// writes it back.  In between the state stays in FP32: converting it to FP64
+// and back at a step boundary returns the same FP32 values (the FP64 sum
+// rhoEt + Cmix(phi) is exact to far below half an FP32 unit of rhoEt), so
+// this is the same computation as `steps` separate calls of one step.
+// Buffers rotate so that no launch writes an array it also reads: the step
+// start alternates between A and B, the second stage is always in C, and the
+// volume part and traces alternate between the two buffers of each pair.
+static dg_status enqueue_steps32(dg_ctx *c, double *w, float dt, int steps, cudaStream_t s) {
+  float *A = c->d_ws32, *B = c->d_w1_32, *C = c->d_w2_32;
+  float *rv[2] = {c->d_rvol32, c->d_rvol32b}, *tr[2] = {c->d_trace32, c->d_trace32b};
+  int t = 0;
+  cudaError_t e = c->ks32.volume(c->prm, c->pf, c->d_opsf, A, rv[t], tr[t], w, A, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "volume kernel launch");
+  for (int k = 0; k < steps; ++k) {
+    const int mode[3] = {MODE_S1, MODE_S2, MODE_S3};
+    const float *ws[3] = {A, B, C};
+    float *out[3] = {B, C, B};
+    for (int st = 0; st < 3; ++st) {
+      if (st == 2 && k == steps - 1) {
+        e = c->ks32.surface(c->prm, c->pf, c->d_opsf, MODE_S3, dt, A, C, rv[t], tr[t], nullptr, w, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "surface kernel launch");
+        break;
+      }
+      e = c->ks32.surfvol(c->prm, c->pf, c->d_opsf, mode[st], dt, A, ws[st], rv[t], tr[t], out[st], rv[t ^ 1],
+                          tr[t ^ 1], s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "fused stage kernel launch");
+      t ^= 1;
+    }
+    std::swap(A, B);  // the new step start is in B
+  }
+  return DG_OK;
 }
 
 static dg_status capture(dg_ctx *c, double *w, double dt, int steps, cudaGraphExec_t *exec) {
@@ -605,7 +641,9 @@ static dg_status capture(dg_ctx *c, double *w, double dt, int steps, cudaGraphEx
   cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(c, e, "dg_step: begin capture");
   dg_status r = DG_OK;
-  for (int s = 0; s < steps && r == DG_OK; ++s) r = enqueue_step(c, w, dt, c->cap);
+  if (c->prec != DG_FP64) r = enqueue_steps32(c, w, (float)dt, steps, c->cap);
+  else
+    for (int s = 0; s < steps && r == DG_OK; ++s) r = enqueue_step(c, w, dt, c->cap);
   e = cudaStreamEndCapture(c->cap, &g);
   if (r != DG_OK) {
     if (g) cudaGraphDestroy(g);
@@ -636,7 +674,16 @@ extern "C" dg_status dg_step(dg_ctx *c, double *w, double dt, int nsteps, void *
   cudaError_t e;
   for (int k = 0; k < nsteps / GRAPH_UNROLL; ++k)
     if ((e = cudaGraphLaunch(c->gk, s)) != cudaSuccess) return cuda_fail(c, e, "dg_step: graph launch");
-  for (int k = 0; k < nsteps % GRAPH_UNROLL; ++k)
+  const int rem = nsteps % GRAPH_UNROLL;
+  if (c->prec != DG_FP64 && rem > 1) {  // FP32-bulk: the remainder as one graph (fewer launches)
+    if (!c->grem[rem]) {
+      dg_status r;
+      if ((r = capture(c, w, dt, rem, &c->grem[rem])) != DG_OK) return r;
+    }
+    if ((e = cudaGraphLaunch(c->grem[rem], s)) != cudaSuccess) return cuda_fail(c, e, "dg_step: graph launch");
+    return DG_OK;
+  }
+  for (int k = 0; k < rem; ++k)
     if ((e = cudaGraphLaunch(c->g1, s)) != cudaSuccess) return cuda_fail(c, e, "dg_step: graph launch");
   return DG_OK;
 }
@@ -673,17 +720,19 @@ extern "C" dg_status dg_status_read(dg_ctx *c, void *stream) {
 extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_out, int nmax, void *stream) {
   if (!c || c->batch || !w || !ms_out || nmax < 1 || nrep < 1) return -1;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaEvent_t ev[3];
+  const bool f64 = c->prec == DG_FP64;
+  const int nk = f64 ? 2 : 3;
+  cudaEvent_t ev[4];
   for (auto &x : ev) cudaEventCreate(&x);
-  double acc[2] = {0.0, 0.0};
+  double acc[3] = {0.0, 0.0, 0.0};
   for (int r = 0; r < nrep; ++r) {
-    if (c->prec == DG_FP64) {
+    if (f64) {
       cudaEventRecord(ev[0], s);
       c->ks.volume(c->prm, w, c->d_rvol, c->d_trace, s);
       cudaEventRecord(ev[1], s);
       c->ks.surface(c->prm, MODE_RHS, 0.0, w, w, c->d_rvol, c->d_trace, c->d_w1, s);
       cudaEventRecord(ev[2], s);
-    } else {  // one stage of the step as dg_step launches it (FP32 state in, FP32 stage out)
+    } else {  // the kernels of a step as dg_step launches them (FP32 state in, FP32 stage out)
       if (r == 0) convert(c, true, const_cast<double *>(w), s);
       cudaEventRecord(ev[0], s);
       c->ks32.volume(c->prm, c->pf, c->d_opsf, c->d_ws32, c->d_rvol32, c->d_trace32, nullptr, nullptr, s);
@@ -691,19 +740,22 @@ extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_
       c->ks32.surface(c->prm, c->pf, c->d_opsf, MODE_S2, 1e-9f, c->d_ws32, c->d_ws32, c->d_rvol32, c->d_trace32,
                       c->d_w1_32, nullptr, s);
       cudaEventRecord(ev[2], s);
+      c->ks32.surfvol(c->prm, c->pf, c->d_opsf, MODE_S2, 1e-9f, c->d_ws32, c->d_ws32, c->d_rvol32, c->d_trace32,
+                      c->d_w1_32, c->d_rvol32b, c->d_trace32b, s);
+      cudaEventRecord(ev[3], s);
     }
-    cudaEventSynchronize(ev[2]);
-    float t0 = 0.f, t1 = 0.f;
-    cudaEventElapsedTime(&t0, ev[0], ev[1]);
-    cudaEventElapsedTime(&t1, ev[1], ev[2]);
-    acc[0] += t0;
-    acc[1] += t1;
+    cudaEventSynchronize(ev[nk]);
+    for (int k = 0; k < nk; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      acc[k] += t;
+    }
   }
   for (auto &x : ev) cudaEventDestroy(x);
   if (cudaGetLastError() != cudaSuccess) return -1;
-  const int nk = std::min(nmax, 2);
-  for (int k = 0; k < nk; ++k) ms_out[k] = acc[k] / nrep;
-  return nk;
+  const int n = std::min(nmax, nk);
+  for (int k = 0; k < n; ++k) ms_out[k] = acc[k] / nrep;
+  return n;
 }
 
 extern "C" int dg_kernel_costs(const dg_ctx *c, double *flops, double *bytes, int nmax) {
@@ -729,8 +781,11 @@ extern "C" int dg_kernel_costs(const dg_ctx *c, double *flops, double *bytes, in
   if (c->prec != DG_FP64) fv += 3 * 2 * d * P1;  // compression term of the reduced energy
   const double bv = word * (E * Np * (7 + 7) + E * NFK * nt);
   const double bs = word * (E * NFK * nt * 2 + E * Np * (7 * 4));
-  const int nk = std::min(nmax, 2);
-  const double F[2] = {fv * E * Np, fs * E * Np}, Bb[2] = {bv, bs};
+  // The fused FP32-bulk stage kernel does both; its volume part takes the
+  // stage state from registers instead of reading it back.
+  const double bsv = bv + bs - word * E * Np * 7;
+  const int nk = std::min(nmax, c->prec == DG_FP64 ? 2 : 3);
+  const double F[3] = {fv * E * Np, fs * E * Np, (fv + fs) * E * Np}, Bb[3] = {bv, bs, bsv};
   for (int k = 0; k < nk; ++k) {
     flops[k] = F[k];
     bytes[k] = Bb[k];
@@ -805,7 +860,7 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
     total += (floats + 63) & ~size_t(63);  // 256-byte aligned slices
     return at;
   };
-  std::vector<size_t> o_ops(n), o_ws(n), o_w1(n), o_w2(n), o_rv(n), o_tr(n);
+  std::vector<size_t> o_ops(n), o_ws(n), o_w1(n), o_w2(n), o_rv(n), o_tr(n), o_rv2(n), o_tr2(n);
   for (int k = 0; k < n; ++k) {
     const dg_mesh &m = meshes[k];
     const double hx = (m.x1 - m.x0) / m.nx, hy = (m.y1 - m.y0) / m.ny;
@@ -824,6 +879,8 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
     o_w2[k] = take(len);
     o_rv[k] = take(len);
     o_tr[k] = take((size_t)NT_INVISCID * E * NFK);
+    o_rv2[k] = take(len);
+    o_tr2[k] = take((size_t)NT_INVISCID * E * NFK);
   }
   cudaError_t e = cudaMalloc(&b->d_pool, total * sizeof(float));
   if (e != cudaSuccess) {
@@ -839,8 +896,10 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
     d.ws = pool + o_ws[k];
     d.w1 = pool + o_w1[k];
     d.w2 = pool + o_w2[k];
-    d.rvol = pool + o_rv[k];
-    d.tr = pool + o_tr[k];
+    d.rvol[0] = pool + o_rv[k];
+    d.tr[0] = pool + o_tr[k];
+    d.rvol[1] = pool + o_rv2[k];
+    d.tr[1] = pool + o_tr2[k];
     d.w64 = nullptr;
     d.dt = 0.f;
     d.prm.ops = nullptr;
@@ -889,14 +948,11 @@ static dg_status upload_descriptors(dg_ctx *c, cudaStream_t s) {
 }
 
 static dg_status enqueue_batch_step(dg_ctx *c, cudaStream_t s) {
-  for (int stage = 1; stage <= 3; ++stage) {
+  const int kind[4] = {BK_VOLUME, BK_SURFVOL, BK_SURFVOL, BK_SURFACE};
+  for (int q = 0; q < 4; ++q) {
     for (auto &g : c->batch->groups) {
-      cudaError_t e = g.k.launch(true, g.d_probs, g.d_block0, (int)g.probs.size(), stage, g.nblocks, s);
-      if (e != cudaSuccess) return cuda_fail(c, e, "batched volume kernel launch");
-    }
-    for (auto &g : c->batch->groups) {
-      cudaError_t e = g.k.launch(false, g.d_probs, g.d_block0, (int)g.probs.size(), stage, g.nblocks, s);
-      if (e != cudaSuccess) return cuda_fail(c, e, "batched surface kernel launch");
+      cudaError_t e = g.k.launch(kind[q], g.d_probs, g.d_block0, (int)g.probs.size(), q, g.nblocks, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "batched stage kernel launch");
     }
   }
   return DG_OK;

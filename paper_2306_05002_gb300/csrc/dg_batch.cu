@@ -7,7 +7,9 @@
 // buffers, step size) in shared memory, and runs the same kernel body as the
 // single-problem FP32-bulk path (dg_kernels_fp32.cuh) on its tile.  Problems
 // of different size share a launch without padding; problems of different
-// order go to different launches (one per order present).
+// order go to different launches (one per order present).  A step is, per
+// order, one volume launch, two fused launches (surface part of a stage and
+// volume part of the next) and one surface launch.
 #include "dg_batch.cuh"
 
 namespace dgpf {
@@ -32,42 +34,54 @@ __device__ __forceinline__ const BatchProb &stage_descriptor(const BatchProb *__
   return *reinterpret_cast<const BatchProb *>(s_raw);
 }
 
+// Volume part of stage 1: reads the caller's FP64 state, writes the FP32
+// state, the volume part and the traces (buffer 0).
 template <int P>
 __global__ void __launch_bounds__(Geom<P, 2, false, false>::THREADS)
-k_volume32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ block0, int nprob, int stage) {
+k_volume32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ block0, int nprob) {
   __shared__ __align__(16) unsigned char s_raw[sizeof(BatchProb)];
   __shared__ int s_k;
   const BatchProb &b = stage_descriptor(probs, block0, nprob, s_raw, &s_k);
   const int blk = (int)blockIdx.x - b.block0;
-  const float *in = stage == 1 ? b.ws : (stage == 2 ? b.w1 : b.w2);
-  vol32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, blk, in, b.rvol, b.tr, stage == 1 ? b.w64 : nullptr,
-                                 stage == 1 ? b.ws : nullptr);
+  vol32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, blk, b.ws, b.rvol[0], b.tr[0], b.w64, b.ws);
 }
 
+// Surface part of stage `stage` (1 or 2) fused with the volume part of the
+// next stage; stage s reads buffer s-1 of each pair and writes the other.
 template <int P>
 __global__ void __launch_bounds__(Geom<P, 2, false, false>::THREADS)
-k_surface32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ block0, int nprob, int stage) {
+k_surfvol32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ block0, int nprob, int stage) {
   __shared__ __align__(16) unsigned char s_raw[sizeof(BatchProb)];
   __shared__ int s_k;
   const BatchProb &b = stage_descriptor(probs, block0, nprob, s_raw, &s_k);
   const int blk = (int)blockIdx.x - b.block0;
-  if (stage == 1)
-    surf32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, blk, MODE_S1, b.dt, b.ws, b.ws, b.rvol, b.tr, b.w1,
-                                    nullptr);
-  else if (stage == 2)
-    surf32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, blk, MODE_S2, b.dt, b.ws, b.w1, b.rvol, b.tr, b.w2,
-                                    nullptr);
-  else
-    surf32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, blk, MODE_S3, b.dt, b.ws, b.w2, b.rvol, b.tr, nullptr,
-                                    b.w64);
+  const int in = stage - 1, out = in ^ 1;
+  float r[NV];
+  surf32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, blk, stage == 1 ? MODE_S1 : MODE_S2, b.dt, b.ws,
+                                  stage == 1 ? b.ws : b.w1, b.rvol[in], b.tr[in], stage == 1 ? b.w1 : b.w2,
+                                  nullptr, r);
+  vol32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, blk, nullptr, b.rvol[out], b.tr[out], nullptr, nullptr, r);
+}
+
+// Surface part of stage 3: writes the caller's FP64 state.
+template <int P>
+__global__ void __launch_bounds__(Geom<P, 2, false, false>::THREADS)
+k_surface32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ block0, int nprob) {
+  __shared__ __align__(16) unsigned char s_raw[sizeof(BatchProb)];
+  __shared__ int s_k;
+  const BatchProb &b = stage_descriptor(probs, block0, nprob, s_raw, &s_k);
+  const int blk = (int)blockIdx.x - b.block0;
+  surf32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, blk, MODE_S3, b.dt, b.ws, b.w2, b.rvol[0], b.tr[0], nullptr,
+                                  b.w64);
 }
 
 template <int P>
-cudaError_t launch_batch(bool volume, const BatchProb *probs, const int *block0, int nprob, int stage, int nblocks,
+cudaError_t launch_batch(int kind, const BatchProb *probs, const int *block0, int nprob, int stage, int nblocks,
                          cudaStream_t s) {
   using G = Geom<P, 2, false, false>;
-  if (volume) k_volume32_batch<P><<<nblocks, G::THREADS, 0, s>>>(probs, block0, nprob, stage);
-  else k_surface32_batch<P><<<nblocks, G::THREADS, 0, s>>>(probs, block0, nprob, stage);
+  if (kind == BK_VOLUME) k_volume32_batch<P><<<nblocks, G::THREADS, 0, s>>>(probs, block0, nprob);
+  else if (kind == BK_SURFVOL) k_surfvol32_batch<P><<<nblocks, G::THREADS, 0, s>>>(probs, block0, nprob, stage);
+  else k_surface32_batch<P><<<nblocks, G::THREADS, 0, s>>>(probs, block0, nprob);
   return cudaGetLastError();
 }
 

@@ -11,14 +11,20 @@ struct BatchProb {
   Params prm;
   ParamsF pf;
   const float *opsf;                        // FP32 operator table (OpsLayout)
-  float *ws, *w1, *w2, *rvol, *tr;          // internal FP32 state, stages, volume part, traces
+  float *ws, *w1, *w2;                      // internal FP32 state and the two inner stages
+  float *rvol[2], *tr[2];                   // volume part and face traces, double-buffered (fused stages)
   double *w64;                              // the caller's FP64 state (read at stage 1, written at stage 3)
   float dt;                                 // this problem's step size
   int block0;                               // first block of this problem in its order's grid
 };
 
+// Kernel kinds of a batched step: the volume part of stage 1, the fused
+// surface part of stage s with the volume part of stage s+1 (s = 1, 2), and
+// the surface part of stage 3.
+enum BatchKind { BK_VOLUME = 0, BK_SURFVOL = 1, BK_SURFACE = 2 };
+
 struct BatchKernels {
-  cudaError_t (*launch)(bool volume, const BatchProb *probs, const int *block0, int nprob, int stage, int nblocks,
+  cudaError_t (*launch)(int kind, const BatchProb *probs, const int *block0, int nprob, int stage, int nblocks,
                         cudaStream_t s);
   int epb;
 };

@@ -31,7 +31,8 @@
 //
 // The first stage of a step can read the FP64 state directly (converting it
 // on load and writing the FP32 internal state), and the last stage can write
-// the FP64 state directly, so a step is six launches.
+// the FP64 state directly.  With the fused stage kernel (k_surfvol32 below)
+// n steps take 1 + 3n launches.
 #pragma once
 
 #include "dg_common.cuh"
@@ -53,12 +54,13 @@ __host__ inline ParamsF to_float(const Params &p) {
 
 // Volume kernel body for the element tile `blk` (EPB elements) of one problem.
 // opsf: FP32 operator table (OpsLayout).  w64 != NULL: read the FP64 state and
-// write the FP32 internal state to w32out (first stage of a step).
+// write the FP32 internal state to w32out (first stage of a step).  qin !=
+// NULL: the thread's node state is already in registers (fused kernel).
 template <int P, int DIM, bool VISC, bool ST>
 __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf, const float *__restrict__ opsf,
                                            int blk, const float *__restrict__ w, float *__restrict__ rvol,
                                            float *__restrict__ tr, const double *__restrict__ w64,
-                                           float *__restrict__ w32out) {
+                                           float *__restrict__ w32out, const float *qin = nullptr) {
   using G = Geom<P, DIM, VISC, ST>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
   constexpr int P11 = P1 * P1;
@@ -80,7 +82,10 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   const long n = (long)(act ? e : 0) * NP + a;
 
   float q[NV];
-  if (w64) {
+  if (qin) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = act ? qin[v] : (v == M1 || v == M2 ? 1.f : 0.f);
+  } else if (w64) {
     // first stage: convert the FP64 state (the stiffened-gas constant leaves rho E in FP64)
     double d[NV];
 #pragma unroll
@@ -274,12 +279,17 @@ k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, c
 // paper's variables in FP64 (out64, with L(rho E) = L(rhoEt) + (C_1-C_2) L(phi));
 // the stage modes write the FP32 internal state (out32), or, when out64 is
 // given, the FP64 state (last stage of a step).
+//
+// rout != NULL (stage modes): the stage result of the thread's node is also
+// left in rout, for a volume body that follows in the same kernel.  Every
+// thread of the block returns from this body (none leaves early), so such a
+// body may synchronise the block.
 template <int P, int DIM, bool VISC, bool ST>
 __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf, const float *__restrict__ opsf,
                                             int blk, int mode, float dt, const float *__restrict__ w0,
                                             const float *__restrict__ ws, const float *__restrict__ rvol,
                                             const float *__restrict__ tr, float *__restrict__ out32,
-                                            double *__restrict__ out64) {
+                                            double *__restrict__ out64, float *rout = nullptr) {
   using G = Geom<P, DIM, VISC, ST>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK, NT = G::NT;
   const OpsLayout L{P1, NP};
@@ -299,6 +309,19 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   const int e = blk * EPB + le;
   const bool act = lane && e < prm.E;
   const long stride = (long)prm.E * NFK;
+  const int N = prm.N;
+  const long n = (long)(act ? e : 0) * NP + a;
+
+  // The node's own inputs of the update are loaded first, so that their
+  // latency overlaps the trace loads and the face fluxes.
+  float Lv[NV], wsn[NV], w0n[NV];
+#pragma unroll
+  for (int vv = 0; vv < NV; ++vv) {
+    const long o = (long)vv * N + n;
+    Lv[vv] = act ? __ldg(rvol + o) : 0.f;
+    wsn[vv] = act && mode != MODE_RHS ? __ldg(ws + o) : 0.f;
+    w0n[vv] = act && (mode == MODE_S2 || mode == MODE_S3) ? __ldg(w0 + o) : 0.f;
+  }
 
   for (int t = a; t < NFK && lane; t += NP) {
     const int f = t / NK, kk = t % NK;
@@ -400,68 +423,69 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   }
   __syncthreads();
 
-  if (!act) return;
-  const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
-  float acc[NV] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  auto face_add = [&](int f, int kk) {
+  if (act) {
+    const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
+    float acc[NV] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    auto face_add = [&](int f, int kk) {
 #pragma unroll
-    for (int vv = 0; vv < NV; ++vv) acc[vv] += s_surf[le][f * NK + kk][vv];
-  };
-  const int kx = DIM == 2 ? j : 0;
-  if (i == 0) face_add(0, kx);
-  if (i == P) face_add(1, kx);
-  if (DIM == 2 && j == 0) face_add(2, i);
-  if (DIM == 2 && j == P) face_add(3, i);
-  {
-    const int slot[6] = {PHI, M1, M2, RU, RV, RE};
-    const float lw = -Dx[0 * P1 + i], le_ = Dx[P * P1 + i];
-#pragma unroll
-    for (int c = 0; c < 6; ++c)
-      acc[slot[c]] += s_lift[le][0 * NK + kx][c] * lw + s_lift[le][1 * NK + kx][c] * le_;
-    if (DIM == 2) {
-      const float ls = -Dy[0 * P1 + j], ln = Dy[P * P1 + j];
+      for (int vv = 0; vv < NV; ++vv) acc[vv] += s_surf[le][f * NK + kk][vv];
+    };
+    const int kx = DIM == 2 ? j : 0;
+    if (i == 0) face_add(0, kx);
+    if (i == P) face_add(1, kx);
+    if (DIM == 2 && j == 0) face_add(2, i);
+    if (DIM == 2 && j == P) face_add(3, i);
+    {
+      const int slot[6] = {PHI, M1, M2, RU, RV, RE};
+      const float lw = -Dx[0 * P1 + i], le_ = Dx[P * P1 + i];
 #pragma unroll
       for (int c = 0; c < 6; ++c)
-        acc[slot[c]] += s_lift[le][2 * NK + i][c] * ls + s_lift[le][3 * NK + i][c] * ln;
+        acc[slot[c]] += s_lift[le][0 * NK + kx][c] * lw + s_lift[le][1 * NK + kx][c] * le_;
+      if (DIM == 2) {
+        const float ls = -Dy[0 * P1 + j], ln = Dy[P * P1 + j];
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+          acc[slot[c]] += s_lift[le][2 * NK + i][c] * ls + s_lift[le][3 * NK + i][c] * ln;
+      }
     }
-  }
-  const float im = invM[a];
-  const long n = (long)e * NP + a;
-  const int N = prm.N;
-  float Lv[NV];
+    const float im = invM[a];
 #pragma unroll
-  for (int vv = 0; vv < NV; ++vv) Lv[vv] = __ldg(rvol + (long)vv * N + n) + acc[vv] * im;
-  bool bad = false;
-  if (mode == MODE_RHS) {
+    for (int vv = 0; vv < NV; ++vv) Lv[vv] += acc[vv] * im;
+    bool bad = false;
+    if (mode == MODE_RHS) {
 #pragma unroll
-    for (int vv = 0; vv < NV; ++vv) {
-      double r = (double)Lv[vv];
-      if (vv == RE) r = fma(prm.dC, (double)Lv[PHI], r);
-      bad |= !isfinite(r);
-      out64[(long)vv * N + n] = r;
-    }
-  } else {
-    float r[NV];
-#pragma unroll
-    for (int vv = 0; vv < NV; ++vv) {
-      const long o = (long)vv * N + n;
-      const float st = fmaf(dt, Lv[vv], __ldg(ws + o));
-      if (mode == MODE_S1) r[vv] = st;
-      else if (mode == MODE_S2) r[vv] = 0.75f * __ldg(w0 + o) + 0.25f * st;
-      else r[vv] = (1.f / 3.f) * __ldg(w0 + o) + (2.f / 3.f) * st;
-      bad |= !isfinite(r[vv]);
-    }
-    if (out64) {
-      // last stage: hand back the FP64 state, restoring the stiffened-gas constant with the FP32 phi
-#pragma unroll
-      for (int vv = 0; vv < RE; ++vv) out64[(long)vv * N + n] = (double)r[vv];
-      out64[(long)RE * N + n] = (double)r[RE] + fma(prm.dC, (double)r[PHI], prm.C2);
+      for (int vv = 0; vv < NV; ++vv) {
+        double r = (double)Lv[vv];
+        if (vv == RE) r = fma(prm.dC, (double)Lv[PHI], r);
+        bad |= !isfinite(r);
+        out64[(long)vv * N + n] = r;
+      }
     } else {
+      float r[NV];
 #pragma unroll
-      for (int vv = 0; vv < NV; ++vv) out32[(long)vv * N + n] = r[vv];
+      for (int vv = 0; vv < NV; ++vv) {
+        const float st = fmaf(dt, Lv[vv], wsn[vv]);
+        if (mode == MODE_S1) r[vv] = st;
+        else if (mode == MODE_S2) r[vv] = 0.75f * w0n[vv] + 0.25f * st;
+        else r[vv] = (1.f / 3.f) * w0n[vv] + (2.f / 3.f) * st;
+        bad |= !isfinite(r[vv]);
+      }
+      if (out64) {
+        // last stage: hand back the FP64 state, restoring the stiffened-gas constant with the FP32 phi
+#pragma unroll
+        for (int vv = 0; vv < RE; ++vv) out64[(long)vv * N + n] = (double)r[vv];
+        out64[(long)RE * N + n] = (double)r[RE] + fma(prm.dC, (double)r[PHI], prm.C2);
+      } else {
+#pragma unroll
+        for (int vv = 0; vv < NV; ++vv) out32[(long)vv * N + n] = r[vv];
+      }
+      if (rout) {
+#pragma unroll
+        for (int vv = 0; vv < NV; ++vv) rout[vv] = r[vv];
+      }
     }
+    if (prm.check_finite && bad) atomicOr(prm.status, STATUS_NONFINITE);
   }
-  if (prm.check_finite && bad) atomicOr(prm.status, STATUS_NONFINITE);
 }
 
 template <int P, int DIM, bool VISC, bool ST>
@@ -470,6 +494,28 @@ k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, 
             const float *__restrict__ w0, const float *__restrict__ ws, const float *__restrict__ rvol,
             const float *__restrict__ tr, float *__restrict__ out32, double *__restrict__ out64) {
   surf32_body<P, DIM, VISC, ST>(prm, pf, opsf, blockIdx.x, mode, dt, w0, ws, rvol, tr, out32, out64);
+}
+
+// Fused stage kernel: the surface part of stage s (mode MODE_S1..S3) followed,
+// in the same block, by the volume part of stage s+1 on the stage result.
+// The surface part of an element needs the face traces of its neighbours, so
+// it cannot follow the volume part of the same stage inside one launch; the
+// volume part of the next stage needs only the element's own new state, which
+// the thread of each node already holds.  So a step of SSP-RK3 is one volume
+// launch and three fused launches (and three fused launches per step when
+// several steps run back to back), and the stage state is handed from one
+// part to the other in registers.  The volume part and the traces go to the
+// other buffer of a pair (rvol_out, tr_out), because neighbouring blocks of
+// the same launch may still read rvol_in and tr_in.
+template <int P, int DIM, bool VISC, bool ST>
+__global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
+k_surfvol32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt,
+            const float *__restrict__ w0, const float *__restrict__ ws, const float *__restrict__ rvol_in,
+            const float *__restrict__ tr_in, float *__restrict__ out32, float *__restrict__ rvol_out,
+            float *__restrict__ tr_out) {
+  float r[NV];
+  surf32_body<P, DIM, VISC, ST>(prm, pf, opsf, blockIdx.x, mode, dt, w0, ws, rvol_in, tr_in, out32, nullptr, r);
+  vol32_body<P, DIM, VISC, ST>(prm, pf, opsf, blockIdx.x, nullptr, rvol_out, tr_out, nullptr, nullptr, r);
 }
 
 // FP64 <-> FP32 internal state.  The stiffened-gas constant is removed from
@@ -485,6 +531,9 @@ struct KernelSet32 {
   cudaError_t (*surface)(const Params &, const ParamsF &, const float *opsf, int mode, float dt, const float *w0,
                          const float *ws, const float *rvol, const float *trace, float *out32, double *out64,
                          cudaStream_t);
+  cudaError_t (*surfvol)(const Params &, const ParamsF &, const float *opsf, int mode, float dt, const float *w0,
+                         const float *ws, const float *rvol_in, const float *tr_in, float *out32, float *rvol_out,
+                         float *tr_out, cudaStream_t);
   int nt, epb, threads;
 };
 
@@ -509,10 +558,21 @@ cudaError_t launch_surface32(const Params &prm, const ParamsF &pf, const float *
 }
 
 template <int P, int DIM, bool VISC, bool ST>
+cudaError_t launch_surfvol32(const Params &prm, const ParamsF &pf, const float *opsf, int mode, float dt,
+                             const float *w0, const float *ws, const float *rvol_in, const float *tr_in,
+                             float *out32, float *rvol_out, float *tr_out, cudaStream_t s) {
+  using G = Geom<P, DIM, VISC, ST>;
+  const int blocks = (prm.E + G::EPB - 1) / G::EPB;
+  k_surfvol32<P, DIM, VISC, ST><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, mode, dt, w0, ws, rvol_in, tr_in,
+                                                              out32, rvol_out, tr_out);
+  return cudaGetLastError();
+}
+
+template <int P, int DIM, bool VISC, bool ST>
 KernelSet32 make_set32() {
   using G = Geom<P, DIM, VISC, ST>;
-  return KernelSet32{&launch_volume32<P, DIM, VISC, ST>, &launch_surface32<P, DIM, VISC, ST>, G::NT, G::EPB,
-                     G::THREADS};
+  return KernelSet32{&launch_volume32<P, DIM, VISC, ST>, &launch_surface32<P, DIM, VISC, ST>,
+                     &launch_surfvol32<P, DIM, VISC, ST>, G::NT, G::EPB, G::THREADS};
 }
 
 template <int P>

@@ -42,7 +42,9 @@ def test_vjp_against_oracle_jacobian(orc, dg, maker):
     rng = np.random.default_rng(1)
     scale = np.abs(w).max(axis=1, keepdims=True)
     Lmax = np.abs(orc.rhs(pb, w)).max(axis=1, keepdims=True)
-    lam = rng.normal(size=w.shape) / np.where(Lmax > 0, Lmax, 1.0)  # (rho v has L = 0 in 1D)
+    lam = rng.normal(size=w.shape) / np.where(Lmax > 0, Lmax, 1.0)
+    if wl.dim == 1:
+        lam[5] = 0.0  # rho v is not a variable of the 1D model (its state keeps rho v = 0)
     mu_fd = np.zeros_like(w)
     for v in range(7):
         for j in range(wl.N):
@@ -56,6 +58,8 @@ def test_vjp_against_oracle_jacobian(orc, dg, maker):
     mu = s.dg_rhs_vjp(torch.from_numpy(w.copy()).cuda(), torch.from_numpy(lam).cuda()).cpu().numpy()
     s.close()
     for v in range(7):
+        if wl.dim == 1 and v == 5:
+            continue
         ref = np.abs(mu_fd[v]).max()
         assert np.abs(mu[v] - mu_fd[v]).max() <= 1e-5 * ref, (v, np.abs(mu[v] - mu_fd[v]).max() / ref)
 

@@ -133,3 +133,31 @@ def test_fp32bulk_rayleigh_taylor_physics_tracks_fp64(orc, dg):
     pb = problem(orc, wl)
     assert _l2(w32[0], w64[0]) <= 1e-5
     assert _l2(orc.primitives(pb, w32)[3], orc.primitives(pb, w64)[3]) <= 1e-5
+
+
+@pytest.mark.parametrize("make,nsteps", [
+    (lambda: W.drop_2d(n=12, p=3, seed=2), 11),      # one 8-step graph + a 3-step graph
+    (lambda: W.drop_2d(n=9, p=5, seed=7), 2),         # the 2-step remainder graph alone
+    (lambda: W.rayleigh_taylor(n=8, p=4, seed=3), 9),  # walls, viscous, gravity, surface tension
+    (lambda: W.slab_1d(nx=40, p=3), 5),
+])
+def test_fp32bulk_multi_step_call_matches_single_steps(dg, make, nsteps):
+    """n steps in one call keep the FP32 state between steps and fuse the surface part of each
+    stage with the volume part of the next; n calls of one step convert to FP64 and back at every
+    step boundary.  The round trip is exact, so both agree to FP32 rounding (the fused kernel may
+    contract a few operations differently): max |a - b| <= 1e-6 max |b| per variable."""
+    import torch
+    wl = make()
+    s = dg.Solver(wl, precision="fp32bulk")
+    a = torch.from_numpy(wl.w.copy()).cuda()
+    b = a.clone()
+    s.dg_step(a, wl.dt, nsteps)
+    for _ in range(nsteps):
+        s.dg_step(b, wl.dt, 1)
+    assert s.dg_status_read() == 0
+    s.close()
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    assert not np.array_equal(b, wl.w)
+    for v in range(7):
+        sc = np.abs(b[v]).max()
+        assert np.abs(a[v] - b[v]).max() <= 1e-6 * max(sc, 1e-30), (v, np.abs(a[v] - b[v]).max(), sc)
