@@ -878,9 +878,9 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
     o_w1[k] = take(len);
     o_w2[k] = take(len);
     o_rv[k] = take(len);
-    o_tr[k] = take((size_t)NT_INVISCID * E * NFK);
+    o_tr[k] = take((size_t)NT32_INVISCID * E * NFK);
     o_rv2[k] = take(len);
-    o_tr2[k] = take((size_t)NT_INVISCID * E * NFK);
+    o_tr2[k] = take((size_t)NT32_INVISCID * E * NFK);
   }
   cudaError_t e = cudaMalloc(&b->d_pool, total * sizeof(float));
   if (e != cudaSuccess) {

@@ -43,7 +43,8 @@ k_volume32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ bl
   __shared__ int s_k;
   const BatchProb &b = stage_descriptor(probs, block0, nprob, s_raw, &s_k);
   const int blk = (int)blockIdx.x - b.block0;
-  vol32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, blk, b.ws, b.rvol[0], b.tr[0], b.w64, b.ws);
+  __shared__ float s_op[2 * (P + 1) * (P + 1)];
+  vol32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, s_op, false, blk, b.ws, b.rvol[0], b.tr[0], b.w64, b.ws);
 }
 
 // Surface part of stage `stage` (1 or 2) fused with the volume part of the
@@ -56,11 +57,13 @@ k_surfvol32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ b
   const BatchProb &b = stage_descriptor(probs, block0, nprob, s_raw, &s_k);
   const int blk = (int)blockIdx.x - b.block0;
   const int in = stage - 1, out = in ^ 1;
+  __shared__ float s_op[Geom<P, 2, false, false>::OPS];
   float r[NV];
-  surf32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, blk, stage == 1 ? MODE_S1 : MODE_S2, b.dt, b.ws,
+  surf32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, s_op, blk, stage == 1 ? MODE_S1 : MODE_S2, b.dt, b.ws,
                                   stage == 1 ? b.ws : b.w1, b.rvol[in], b.tr[in], stage == 1 ? b.w1 : b.w2,
                                   nullptr, r);
-  vol32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, blk, nullptr, b.rvol[out], b.tr[out], nullptr, nullptr, r);
+  vol32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, s_op, true, blk, nullptr, b.rvol[out], b.tr[out], nullptr,
+                                 nullptr, r);
 }
 
 // Surface part of stage 3: writes the caller's FP64 state.
@@ -71,8 +74,9 @@ k_surface32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ b
   __shared__ int s_k;
   const BatchProb &b = stage_descriptor(probs, block0, nprob, s_raw, &s_k);
   const int blk = (int)blockIdx.x - b.block0;
-  surf32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, blk, MODE_S3, b.dt, b.ws, b.w2, b.rvol[0], b.tr[0], nullptr,
-                                  b.w64);
+  __shared__ float s_op[Geom<P, 2, false, false>::OPS];
+  surf32_body<P, 2, false, false>(b.prm, b.pf, b.opsf, s_op, blk, MODE_S3, b.dt, b.ws, b.w2, b.rvol[0], b.tr[0],
+                                  nullptr, b.w64);
 }
 
 template <int P>

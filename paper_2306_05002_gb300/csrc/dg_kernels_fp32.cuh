@@ -52,23 +52,59 @@ __host__ inline ParamsF to_float(const Params &p) {
                  (float)p.Gamma, (float)p.eps, (float)p.eta_x, (float)p.eta_y};
 }
 
+// Face-trace record of the FP32-bulk kernels: the seven state values (in the
+// order of Var) and what needs the whole element -- d(phi)/d(axis normal to
+// the face), the level-set normal component on that axis and, viscous, the
+// stress components tau . e_axis.  Velocity, pressure, sound speed, B and the
+// mixture viscosity are recomputed from the state by the reader
+// (trace_derive), which is cheaper than moving them: 9 (11) words per face
+// node instead of 14 (17).
+enum TraceField32 { C_GPHI = 7, C_N = 8, C_TX = 9, C_TY = 10 };
+constexpr int NT32_INVISCID = 9;
+constexpr int NT32_VISCOUS = 11;
+
+// Fill T[T_U], T[T_V], T[T_P], T[T_C], T[T_B] (and T[T_MU]) from the state
+// values T[T_PHI..T_RE], with the operations of the volume body.
+template <int DIM, bool VISC>
+__device__ __forceinline__ void trace_derive(const ParamsF &pf, float *T) {
+  const float phi = T[T_PHI];
+  const float rho = T[T_M1] + T[T_M2];
+  const float ir = 1.0f / rho;
+  const float u = T[T_RU] * ir;
+  const float v = DIM == 2 ? T[T_RV] * ir : 0.f;
+  const float k = 0.5f * (u * u + v * v);
+  const float Gm = fmaf(phi, pf.g1 - pf.g2, pf.g2);
+  const float Pr = (T[T_RE] - rho * k) / Gm;
+  const float Cm = fmaf(pf.dC, phi, pf.C2);
+  T[T_U] = u;
+  T[T_V] = v;
+  T[T_P] = Pr;
+  T[T_C] = sqrtf((Pr + (Pr + Cm) / Gm) * ir);
+  T[T_B] = Pr * pf.Bp;
+  if (VISC) T[T_MU] = pf.mu1 * phi + pf.mu2 * (1.f - phi);
+}
+
 // Volume kernel body for the element tile `blk` (EPB elements) of one problem.
 // opsf: FP32 operator table (OpsLayout).  w64 != NULL: read the FP64 state and
 // write the FP32 internal state to w32out (first stage of a step).  qin !=
 // NULL: the thread's node state is already in registers (fused kernel).
+// s_op: the block's shared copy of the operator table; this body copies the
+// two derivative matrices into it unless ops_ready (the fused kernel's
+// surface part has copied the whole table and synchronised the block).
 template <int P, int DIM, bool VISC, bool ST>
 __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf, const float *__restrict__ opsf,
-                                           int blk, const float *__restrict__ w, float *__restrict__ rvol,
-                                           float *__restrict__ tr, const double *__restrict__ w64,
-                                           float *__restrict__ w32out, const float *qin = nullptr) {
+                                           float *s_op, bool ops_ready, int blk, const float *__restrict__ w,
+                                           float *__restrict__ rvol, float *__restrict__ tr,
+                                           const double *__restrict__ w64, float *__restrict__ w32out,
+                                           const float *qin = nullptr) {
   using G = Geom<P, DIM, VISC, ST>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
   constexpr int P11 = P1 * P1;
   constexpr int NS = 12;
-  __shared__ float s_op[2 * P11];
   __shared__ float s_f[NS][EPB][NP];
 
-  for (int t = threadIdx.x; t < 2 * P11; t += blockDim.x) s_op[t] = opsf[t];
+  if (!ops_ready)
+    for (int t = threadIdx.x; t < 2 * P11; t += blockDim.x) s_op[t] = opsf[t];
   const float *Dx = s_op, *Dy = s_op + P11;
 
   const int le_raw = threadIdx.x / NP;
@@ -109,7 +145,6 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   const float k = 0.5f * (u * u + v * v);
   const float Gm = fmaf(phi, pf.g1 - pf.g2, pf.g2);
   const float Pr = (q[RE] - rho * k) / Gm;
-  const float Cm = fmaf(pf.dC, phi, pf.C2);
   const float Bq = Pr * pf.Bp;  // B - (C_1 - C_2)
 
   if (lane) {
@@ -242,21 +277,17 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   const bool onW = i == 0, onE = i == P;
   const bool onS = DIM == 2 && j == 0, onN = DIM == 2 && j == P;
   if (act && (onW || onE || onS || onN)) {
-    const float c = sqrtf((Pr + (Pr + Cm) / Gm) * ir);
-    const float tx[NT_VISCOUS] = {phi, psi, q[M1], q[M2], q[RU], q[RV], q[RE], u, v, Pr, c, Bq,
-                                  0.f, 0.f, 0.f, 0.f, mu};
     const long base = (long)e * NFK;
     const long stride = (long)prm.E * NFK;
     auto put = [&](int f, int kk, float gn, float nn, float t1, float t2) {
       const long o = base + f * NK + kk;
 #pragma unroll
-      for (int qf = 0; qf < T_GPHI; ++qf) tr[qf * stride + o] = tx[qf];
-      tr[T_GPHI * stride + o] = gn;
-      tr[T_N * stride + o] = nn;
+      for (int qf = 0; qf < NV; ++qf) tr[qf * stride + o] = q[qf];
+      tr[C_GPHI * stride + o] = gn;
+      tr[C_N * stride + o] = nn;
       if (VISC) {
-        tr[T_TX * stride + o] = t1;
-        tr[T_TY * stride + o] = t2;
-        tr[T_MU * stride + o] = mu;
+        tr[C_TX * stride + o] = t1;
+        tr[C_TY * stride + o] = t2;
       }
     };
     const int kx = DIM == 2 ? j : 0;
@@ -272,7 +303,8 @@ __global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
 k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, const float *__restrict__ w,
            float *__restrict__ rvol, float *__restrict__ tr, const double *__restrict__ w64,
            float *__restrict__ w32out) {
-  vol32_body<P, DIM, VISC, ST>(prm, pf, opsf, blockIdx.x, w, rvol, tr, w64, w32out);
+  __shared__ float s_op[2 * Geom<P, DIM, VISC, ST>::P1 * Geom<P, DIM, VISC, ST>::P1];  // Dx, Dy
+  vol32_body<P, DIM, VISC, ST>(prm, pf, opsf, s_op, false, blockIdx.x, w, rvol, tr, w64, w32out);
 }
 
 // Surface kernel body of the FP32-bulk path.  mode MODE_RHS writes L for the
@@ -280,27 +312,26 @@ k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, c
 // the stage modes write the FP32 internal state (out32), or, when out64 is
 // given, the FP64 state (last stage of a step).
 //
+// s_op: the block's shared copy of the operator table (OpsLayout, Geom::OPS
+// floats), filled by this body.
+//
 // rout != NULL (stage modes): the stage result of the thread's node is also
 // left in rout, for a volume body that follows in the same kernel.  Every
 // thread of the block returns from this body (none leaves early), so such a
 // body may synchronise the block.
 template <int P, int DIM, bool VISC, bool ST>
 __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf, const float *__restrict__ opsf,
-                                            int blk, int mode, float dt, const float *__restrict__ w0,
+                                            float *s_op, int blk, int mode, float dt, const float *__restrict__ w0,
                                             const float *__restrict__ ws, const float *__restrict__ rvol,
                                             const float *__restrict__ tr, float *__restrict__ out32,
                                             double *__restrict__ out64, float *rout = nullptr) {
   using G = Geom<P, DIM, VISC, ST>;
-  constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK, NT = G::NT;
+  constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
+  constexpr int NC = VISC ? NT32_VISCOUS : NT32_INVISCID;
+  constexpr int FPT = (NFK + NP - 1) / NP;  // face nodes per thread
   const OpsLayout L{P1, NP};
-  __shared__ float s_op[4 * P1 * P1 + 3 * P1 + NP];
   __shared__ float s_surf[EPB][NFK][NV];
   __shared__ float s_lift[EPB][NFK][6];
-
-  for (int t = threadIdx.x; t < L.size(); t += blockDim.x) s_op[t] = opsf[t];
-  __syncthreads();
-  const float *Dx = s_op + L.Dx(), *Dy = s_op + L.Dy();
-  const float *invM = s_op + L.invM(), *wfx = s_op + L.wfx(), *wfy = s_op + L.wfy();
 
   const int le_raw = threadIdx.x / NP;
   const bool lane = le_raw < EPB;
@@ -312,8 +343,9 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   const int N = prm.N;
   const long n = (long)(act ? e : 0) * NP + a;
 
-  // The node's own inputs of the update are loaded first, so that their
-  // latency overlaps the trace loads and the face fluxes.
+  // Every global load of the body is issued first -- the node's own inputs of
+  // the update and both traces of its face nodes -- so that their latencies
+  // overlap each other and the copy of the operator table.
   float Lv[NV], wsn[NV], w0n[NV];
 #pragma unroll
   for (int vv = 0; vv < NV; ++vv) {
@@ -322,24 +354,59 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
     wsn[vv] = act && mode != MODE_RHS ? __ldg(ws + o) : 0.f;
     w0n[vv] = act && (mode == MODE_S2 || mode == MODE_S3) ? __ldg(w0 + o) : 0.f;
   }
+  float Cm_[FPT][NC], Cp_[FPT][NC];
+  int e2_[FPT];
+#pragma unroll
+  for (int fi = 0; fi < FPT; ++fi) {
+    const int t = a + fi * NP;
+    const bool fv = act && t < NFK;
+    const int f = fv ? t / NK : 0, kk = fv ? t % NK : 0;
+    const int e2 = fv ? neighbour(prm, e, f) : -1;
+    e2_[fi] = e2;
+    const long om = (long)(act ? e : 0) * NFK + (fv ? t : 0);
+#pragma unroll
+    for (int qf = 0; qf < NC; ++qf) Cm_[fi][qf] = fv ? __ldg(tr + qf * stride + om) : (qf == T_M1 ? 1.f : 0.f);
+    const long op = (long)(e2 >= 0 ? e2 : 0) * NFK + (f ^ 1) * NK + kk;
+#pragma unroll
+    for (int qf = 0; qf < NC; ++qf) Cp_[fi][qf] = e2 >= 0 ? __ldg(tr + qf * stride + op) : 0.f;
+  }
 
-  for (int t = a; t < NFK && lane; t += NP) {
+  for (int t = threadIdx.x; t < L.size(); t += blockDim.x) s_op[t] = opsf[t];
+  __syncthreads();
+  const float *Dx = s_op + L.Dx(), *Dy = s_op + L.Dy();
+  const float *invM = s_op + L.invM(), *wfx = s_op + L.wfx(), *wfy = s_op + L.wfy();
+
+#pragma unroll
+  for (int fi = 0; fi < FPT; ++fi) {
+    const int t = a + fi * NP;
+    if (!lane || t >= NFK) continue;
     const int f = t / NK, kk = t % NK;
-    const int e2 = act ? neighbour(prm, e, f) : -1;
-    const bool wall = e2 < 0;
+    const bool wall = e2_[fi] < 0;
     const bool xf = f < 2;
     const float sg = (f & 1) ? 1.f : -1.f;
-    float Tm[NT], Tp[NT];
-    const long om = (long)(act ? e : 0) * NFK + t;
+    float Tm[NT_VISCOUS], Tp[NT_VISCOUS];
 #pragma unroll
-    for (int qf = 0; qf < NT; ++qf) Tm[qf] = act ? __ldg(tr + qf * stride + om) : (qf == T_M1 ? 1.f : 0.f);
+    for (int qf = 0; qf < NV; ++qf) Tm[qf] = Cm_[fi][qf];
+    Tm[T_GPHI] = Cm_[fi][C_GPHI];
+    Tm[T_N] = Cm_[fi][C_N];
+    if (VISC) {
+      Tm[T_TX] = Cm_[fi][C_TX];
+      Tm[T_TY] = Cm_[fi][C_TY];
+    }
+    trace_derive<DIM, VISC>(pf, Tm);
     if (!wall) {
-      const long op = (long)e2 * NFK + (f ^ 1) * NK + kk;
 #pragma unroll
-      for (int qf = 0; qf < NT; ++qf) Tp[qf] = __ldg(tr + qf * stride + op);
+      for (int qf = 0; qf < NV; ++qf) Tp[qf] = Cp_[fi][qf];
+      Tp[T_GPHI] = Cp_[fi][C_GPHI];
+      Tp[T_N] = Cp_[fi][C_N];
+      if (VISC) {
+        Tp[T_TX] = Cp_[fi][C_TX];
+        Tp[T_TY] = Cp_[fi][C_TY];
+      }
+      trace_derive<DIM, VISC>(pf, Tp);
     } else {
 #pragma unroll
-      for (int qf = 0; qf < NT; ++qf) Tp[qf] = Tm[qf];
+      for (int qf = 0; qf < NT_VISCOUS; ++qf) Tp[qf] = Tm[qf];
       if (prm.bc[f] == BC_SLIP) {
         if (xf) { Tp[T_RU] = -Tm[T_RU]; Tp[T_U] = -Tm[T_U]; }
         else    { Tp[T_RV] = -Tm[T_RV]; Tp[T_V] = -Tm[T_V]; }
@@ -493,7 +560,8 @@ __global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
 k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt,
             const float *__restrict__ w0, const float *__restrict__ ws, const float *__restrict__ rvol,
             const float *__restrict__ tr, float *__restrict__ out32, double *__restrict__ out64) {
-  surf32_body<P, DIM, VISC, ST>(prm, pf, opsf, blockIdx.x, mode, dt, w0, ws, rvol, tr, out32, out64);
+  __shared__ float s_op[Geom<P, DIM, VISC, ST>::OPS];
+  surf32_body<P, DIM, VISC, ST>(prm, pf, opsf, s_op, blockIdx.x, mode, dt, w0, ws, rvol, tr, out32, out64);
 }
 
 // Fused stage kernel: the surface part of stage s (mode MODE_S1..S3) followed,
@@ -513,9 +581,12 @@ k_surfvol32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, 
             const float *__restrict__ w0, const float *__restrict__ ws, const float *__restrict__ rvol_in,
             const float *__restrict__ tr_in, float *__restrict__ out32, float *__restrict__ rvol_out,
             float *__restrict__ tr_out) {
+  __shared__ float s_op[Geom<P, DIM, VISC, ST>::OPS];  // one table for both parts
   float r[NV];
-  surf32_body<P, DIM, VISC, ST>(prm, pf, opsf, blockIdx.x, mode, dt, w0, ws, rvol_in, tr_in, out32, nullptr, r);
-  vol32_body<P, DIM, VISC, ST>(prm, pf, opsf, blockIdx.x, nullptr, rvol_out, tr_out, nullptr, nullptr, r);
+  surf32_body<P, DIM, VISC, ST>(prm, pf, opsf, s_op, blockIdx.x, mode, dt, w0, ws, rvol_in, tr_in, out32, nullptr,
+                                r);
+  vol32_body<P, DIM, VISC, ST>(prm, pf, opsf, s_op, true, blockIdx.x, nullptr, rvol_out, tr_out, nullptr, nullptr,
+                               r);
 }
 
 // FP64 <-> FP32 internal state.  The stiffened-gas constant is removed from
@@ -572,7 +643,8 @@ template <int P, int DIM, bool VISC, bool ST>
 KernelSet32 make_set32() {
   using G = Geom<P, DIM, VISC, ST>;
   return KernelSet32{&launch_volume32<P, DIM, VISC, ST>, &launch_surface32<P, DIM, VISC, ST>,
-                     &launch_surfvol32<P, DIM, VISC, ST>, G::NT, G::EPB, G::THREADS};
+                     &launch_surfvol32<P, DIM, VISC, ST>, VISC ? NT32_VISCOUS : NT32_INVISCID, G::EPB,
+                     G::THREADS};
 }
 
 template <int P>

@@ -52,6 +52,7 @@ struct Geom {
   static constexpr int THREADS = ((EPB * NP + 31) / 32) * 32;
   static constexpr int NT = VISC ? NT_VISCOUS : NT_INVISCID;
   static constexpr int NSTAGE = 12;                  // staged fields per node
+  static constexpr int OPS = 4 * P1 * P1 + 3 * P1 + NP;  // operator table (OpsLayout) size
 };
 
 // Neighbour of element e across face f (0 W, 1 E, 2 S, 3 N), or -1 at a wall.
