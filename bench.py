@@ -464,7 +464,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
 
-    acc = accuracy(dg, wl, args.accuracy_steps) if (args.precision == "fp32bulk" and rank == 0) else None
+    acc = (accuracy(dg, wl, args.accuracy_steps)
+           if (args.precision == "fp32bulk" and args.accuracy_steps > 0 and rank == 0) else None)
     batched = (batched_block(dg, args.batch_steps, args.batch_problems)
                if (args.batch_steps > 0 and rank == 0) else None)
     adjoint = (adjoint_block(dg, args.adjoint_steps, n=args.adjoint_n)

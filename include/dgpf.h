@@ -79,14 +79,12 @@ typedef struct {
 /* Options.  prec: DG_FP64 or DG_FP32_BULK.  c_ip: interior-penalty constant,
    eta = c_ip (p+1)^2 / h (<= 0 selects 1).  viscous, gravity,
    surface_tension: enable those terms of Sec. 2.  check_finite: latch
-   DG_ERR_NONFINITE when an output is not finite.  barrier_timeout_ms:
-   reserved for bounded device waits (<= 0 selects 1000). */
+   DG_ERR_NONFINITE when an output is not finite. */
 typedef struct {
   int prec;
   double c_ip;
   int viscous, gravity, surface_tension;
   int check_finite;
-  double barrier_timeout_ms;
 } dg_opts;
 
 typedef struct dg_ctx dg_ctx;
@@ -94,7 +92,8 @@ typedef struct dg_ctx dg_ctx;
 /* Create a solver for one mesh, order p (1..5 in 2D, 1..5 in 1D), closure,
    Allen-Cahn velocity scale Gamma >= 0 and thickness eps >= 0 (Sec. 2).
    opts may be NULL (FP64, c_ip = 1, no viscous/gravity/surface terms).
-   Allocates all device memory the context will use on the current device.
+   Allocates all device memory the context will use on the current device
+   (except the staging buffer of dg_step_host, allocated on its first call).
    On success *out receives the context; on failure *out is NULL. */
 dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps,
                     const dg_opts *opts, dg_ctx **out);
@@ -117,6 +116,16 @@ dg_status dg_rhs(dg_ctx *ctx, const double *w, double *L, void *stream);
    pair and replayed; the first call for a new pair pays the capture. */
 dg_status dg_step(dg_ctx *ctx, double *w, double dt, int nsteps, void *stream);
 
+/* dg_step on a HOST state: w_host (dg_state_len doubles, pinned memory
+   recommended; pageable works but is staged by the driver) is copied to the
+   device, advanced by nsteps SSP-RK3 steps and copied back, all on stream;
+   the call returns after the copy back has finished, so w_host holds the new
+   state on return.  The device copy lives in a staging buffer of
+   dg_state_len doubles that the context allocates on the first call and
+   keeps until dg_destroy (DG_ERR_OOM if that allocation fails).  No Sec. of
+   the paper corresponds: this is the host-side convenience of dg_step. */
+dg_status dg_step_host(dg_ctx *ctx, double *w_host, double dt, int nsteps, void *stream);
+
 /* FP64 diagnostics of w (Sec. 4.1 mass error): out (HOST, 16 doubles) gets
    the integrals of the 7 variables (GLL quadrature), min/max phi, min/max P,
    min/max u, min/max v, and the count of non-finite state entries.
@@ -131,9 +140,9 @@ dg_status dg_status_read(dg_ctx *ctx, void *stream);
    dg_create when ctx is NULL).  Never NULL. */
 const char *dg_last_error(const dg_ctx *ctx);
 
-/* Kernel-level timing for roofline reports: run nrep right-hand-side
-   evaluations of w with CUDA events around each kernel launch on stream and
-   write the mean duration in milliseconds of each kernel kind to ms_out
+/* Kernel-level timing for roofline reports: for each kernel kind, run nrep
+   launches on w back to back on stream between two CUDA events and write
+   the mean duration per launch in milliseconds to ms_out
    (index 0 volume kernel, 1 surface kernel, and for FP32-bulk contexts 2 the
    fused kernel that dg_step runs: the surface part of one stage followed by
    the volume part of the next); returns the number of kinds written

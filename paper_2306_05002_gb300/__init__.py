@@ -29,8 +29,8 @@ BC = {"periodic": 0, "noslip": 1, "slip": 2}
 PREC = {"fp64": 0, "fp32bulk": 1}
 
 # Every exported symbol of include/dgpf.h.
-EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_diag", "dg_status_read",
-           "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc", "dg_batch_create",
+EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_step_host", "dg_diag",
+           "dg_status_read", "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc", "dg_batch_create",
            "dg_batch_step", "dg_rhs_vjp", "dg_adjoint_step", "dg_tape_len", "dg_step_tape",
            "dg_adjoint_step_tape"]
 
@@ -54,8 +54,7 @@ class dg_eos(ctypes.Structure):
 
 class dg_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("c_ip", ctypes.c_double), ("viscous", ctypes.c_int),
-                ("gravity", ctypes.c_int), ("surface_tension", ctypes.c_int), ("check_finite", ctypes.c_int),
-                ("barrier_timeout_ms", ctypes.c_double)]
+                ("gravity", ctypes.c_int), ("surface_tension", ctypes.c_int), ("check_finite", ctypes.c_int)]
 
 
 _lib = None
@@ -83,6 +82,8 @@ def load(path: str | None = None):
     lib.dg_rhs.restype = ctypes.c_int
     lib.dg_step.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int, vp]
     lib.dg_step.restype = ctypes.c_int
+    lib.dg_step_host.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int, vp]
+    lib.dg_step_host.restype = ctypes.c_int
     lib.dg_diag.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_double), vp]
     lib.dg_diag.restype = ctypes.c_int
     lib.dg_status_read.argtypes = [vp, vp]
@@ -137,7 +138,7 @@ def _stream(stream=None):
 
 def make_structs(dim, nx, ny, x0, x1, y0, y1, bc, gamma, pinf, rho0, mu=(0.0, 0.0), sigma=0.0, g=(0.0, 0.0),
                  precision="fp64", c_ip=1.0, viscous=False, gravity=False, surface_tension=False,
-                 check_finite=True, barrier_timeout_ms=1000.0, **_ignored):
+                 check_finite=True, **_ignored):
     m = dg_mesh()
     m.dim, m.nx, m.ny = dim, nx, ny
     m.x0, m.x1, m.y0, m.y1 = x0, x1, y0, y1
@@ -150,7 +151,7 @@ def make_structs(dim, nx, ny, x0, x1, y0, y1, bc, gamma, pinf, rho0, mu=(0.0, 0.
     o = dg_opts()
     o.prec = PREC[precision] if isinstance(precision, str) else int(precision)
     o.c_ip, o.viscous, o.gravity, o.surface_tension = c_ip, int(viscous), int(gravity), int(surface_tension)
-    o.check_finite, o.barrier_timeout_ms = int(check_finite), float(barrier_timeout_ms)
+    o.check_finite = int(check_finite)
     return m, e, o
 
 
@@ -161,14 +162,12 @@ class Solver:
     fields).  State tensors are float64 CUDA tensors of shape (7, N).
     """
 
-    def __init__(self, problem, precision: str = "fp64", check_finite: bool = True,
-                 barrier_timeout_ms: float = 1000.0):
+    def __init__(self, problem, precision: str = "fp64", check_finite: bool = True):
         lib = load()
         kw = problem.problem_kwargs() if hasattr(problem, "problem_kwargs") else dict(problem)
         p = kw.pop("p")
         Gamma, eps = kw.pop("Gamma"), kw.pop("eps")
-        m, e, o = make_structs(precision=precision, check_finite=check_finite,
-                               barrier_timeout_ms=barrier_timeout_ms, **kw)
+        m, e, o = make_structs(precision=precision, check_finite=check_finite, **kw)
         self._m, self._e, self._o = m, e, o
         h = ctypes.c_void_p()
         st = lib.dg_create(ctypes.byref(m), p, ctypes.byref(e), Gamma, eps, ctypes.byref(o), ctypes.byref(h))
@@ -196,14 +195,16 @@ class Solver:
         return L
 
     def dg_step(self, w, dt: float, nsteps: int, stream=None):
-        """Advance w in place.  A CPU tensor is staged through the device (host copies both ways)."""
+        """Advance w in place.  A CPU tensor goes through dg_step_host (copied to the device and back
+        inside the library; pin it for full copy bandwidth)."""
         import torch
         if w.is_cuda:
             _check(self.ctx, load().dg_step(self.ctx, _ptr(w), float(dt), int(nsteps), _stream(stream)), "dg_step")
             return w
-        d = w.to("cuda", non_blocking=True)
-        _check(self.ctx, load().dg_step(self.ctx, _ptr(d), float(dt), int(nsteps), _stream(stream)), "dg_step")
-        w.copy_(d, non_blocking=False)
+        if w.dtype != torch.float64 or not w.is_contiguous() or w.numel() != self.len:
+            raise ValueError("dg_step: host state must be a contiguous float64 tensor of dg_state_len values")
+        _check(self.ctx, load().dg_step_host(self.ctx, ctypes.c_void_p(w.data_ptr()), float(dt), int(nsteps),
+                                             _stream(stream)), "dg_step_host")
         return w
 
     def dg_rhs_vjp(self, w, lam, out=None, stream=None):

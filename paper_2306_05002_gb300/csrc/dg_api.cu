@@ -244,6 +244,8 @@ struct BatchGroup {
   int *d_block0 = nullptr;         // first block of each problem
   int nblocks = 0;
   BatchKernels k{};
+  cudaStream_t stream = nullptr;   // capture branch of this group
+  cudaEvent_t done = nullptr;      // joins the branch back at the end of a captured sequence
 };
 
 struct BatchData {
@@ -253,6 +255,7 @@ struct BatchData {
   std::vector<BatchGroup> groups;
   std::vector<size_t> len;         // state length of every problem
   void *d_pool = nullptr;          // every FP32 buffer and table of the batch
+  cudaEvent_t fork = nullptr;      // starts the per-group branches of a captured sequence
 };
 
 struct dg_ctx {
@@ -277,6 +280,7 @@ struct dg_ctx {
         *d_trace32 = nullptr, *d_rvol32b = nullptr, *d_trace32b = nullptr;
   int conv_blocks = 1;
   double *d_ops = nullptr, *d_w1 = nullptr, *d_w2 = nullptr, *d_rvol = nullptr, *d_trace = nullptr;
+  double *d_hstate = nullptr;  // device copy of a host state (dg_step_host), allocated on first use
   double *d_part = nullptr, *d_diag = nullptr;
   unsigned *d_status = nullptr;
   int nparts = 0;
@@ -319,11 +323,15 @@ static void free_ctx(dg_ctx *c) {
     for (auto &g : c->batch->groups) {
       cudaFree(g.d_probs);
       cudaFree(g.d_block0);
+      if (g.stream) cudaStreamDestroy(g.stream);
+      if (g.done) cudaEventDestroy(g.done);
     }
+    if (c->batch->fork) cudaEventDestroy(c->batch->fork);
     cudaFree(c->batch->d_pool);
     delete c->batch;
   }
   cudaFree(c->d_ops);
+  cudaFree(c->d_hstate);
   cudaFree(c->d_w1);
   cudaFree(c->d_w2);
   cudaFree(c->d_rvol);
@@ -441,10 +449,8 @@ static dg_opts normalised_opts(const dg_opts *opts) {
   dg_opts o{};
   o.prec = DG_FP64;
   o.c_ip = 1.0;
-  o.barrier_timeout_ms = 1000.0;
   if (opts) o = *opts;
   if (o.c_ip <= 0.0) o.c_ip = 1.0;
-  if (o.barrier_timeout_ms <= 0.0) o.barrier_timeout_ms = 1000.0;
   return o;
 }
 
@@ -688,6 +694,34 @@ extern "C" dg_status dg_step(dg_ctx *c, double *w, double dt, int nsteps, void *
   return DG_OK;
 }
 
+extern "C" dg_status dg_step_host(dg_ctx *c, double *w_host, double dt, int nsteps, void *stream) {
+  if (!c) return DG_ERR_ARG;
+  if (c->batch) return fail(c, DG_ERR_ARG, "dg_step_host: batch context (use dg_batch_step)");
+  if (!w_host) return fail(c, DG_ERR_ARG, "dg_step_host: null state");
+  if (!(dt > 0.0) || nsteps < 0) return fail(c, DG_ERR_ARG, "dg_step_host: need dt > 0 and nsteps >= 0");
+  if (nsteps == 0) return DG_OK;
+  cudaError_t e;
+  if (!c->d_hstate && (e = cudaMalloc(&c->d_hstate, c->len * sizeof(double))) != cudaSuccess) {
+    c->d_hstate = nullptr;
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA,
+                std::string("dg_step_host: staging buffer: ") + cudaGetErrorString(e));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = c->len * sizeof(double);
+  if ((e = cudaMemcpyAsync(c->d_hstate, w_host, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(c, e, "dg_step_host: copy to device");
+  const dg_status r = dg_step(c, c->d_hstate, dt, nsteps, stream);
+  if (r != DG_OK) {
+    cudaStreamSynchronize(s);
+    return r;
+  }
+  if ((e = cudaMemcpyAsync(w_host, c->d_hstate, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(c, e, "dg_step_host: copy to host");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "dg_step_host: sync");
+  return DG_OK;
+}
+
 extern "C" dg_status dg_diag(dg_ctx *c, const double *w, double *out, void *stream) {
   if (!c) return DG_ERR_ARG;
   if (c->batch) return fail(c, DG_ERR_ARG, "dg_diag: batch context (use dg_batch_step)");
@@ -722,40 +756,39 @@ extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_
   cudaStream_t s = (cudaStream_t)stream;
   const bool f64 = c->prec == DG_FP64;
   const int nk = f64 ? 2 : 3;
-  cudaEvent_t ev[4];
-  for (auto &x : ev) cudaEventCreate(&x);
-  double acc[3] = {0.0, 0.0, 0.0};
-  for (int r = 0; r < nrep; ++r) {
+  // Each kind runs nrep times back to back between two events (as in a step,
+  // where the kernels follow each other in a graph): the mean includes the
+  // gap between dependent launches but no per-launch event overhead.
+  auto launch = [&](int k) {
     if (f64) {
-      cudaEventRecord(ev[0], s);
-      c->ks.volume(c->prm, w, c->d_rvol, c->d_trace, s);
-      cudaEventRecord(ev[1], s);
-      c->ks.surface(c->prm, MODE_RHS, 0.0, w, w, c->d_rvol, c->d_trace, c->d_w1, s);
-      cudaEventRecord(ev[2], s);
-    } else {  // the kernels of a step as dg_step launches them (FP32 state in, FP32 stage out)
-      if (r == 0) convert(c, true, const_cast<double *>(w), s);
-      cudaEventRecord(ev[0], s);
+      if (k == 0) c->ks.volume(c->prm, w, c->d_rvol, c->d_trace, s);
+      else c->ks.surface(c->prm, MODE_RHS, 0.0, w, w, c->d_rvol, c->d_trace, c->d_w1, s);
+    } else if (k == 0) {  // the kernels of a step as dg_step launches them (FP32 state in, FP32 stage out)
       c->ks32.volume(c->prm, c->pf, c->d_opsf, c->d_ws32, c->d_rvol32, c->d_trace32, nullptr, nullptr, s);
-      cudaEventRecord(ev[1], s);
+    } else if (k == 1) {
       c->ks32.surface(c->prm, c->pf, c->d_opsf, MODE_S2, 1e-9f, c->d_ws32, c->d_ws32, c->d_rvol32, c->d_trace32,
                       c->d_w1_32, nullptr, s);
-      cudaEventRecord(ev[2], s);
+    } else {
       c->ks32.surfvol(c->prm, c->pf, c->d_opsf, MODE_S2, 1e-9f, c->d_ws32, c->d_ws32, c->d_rvol32, c->d_trace32,
                       c->d_w1_32, c->d_rvol32b, c->d_trace32b, s);
-      cudaEventRecord(ev[3], s);
     }
-    cudaEventSynchronize(ev[nk]);
-    for (int k = 0; k < nk; ++k) {
-      float t = 0.f;
-      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
-      acc[k] += t;
-    }
+  };
+  if (!f64) convert(c, true, const_cast<double *>(w), s);
+  cudaEvent_t ev[2];
+  for (auto &x : ev) cudaEventCreate(&x);
+  for (int k = 0; k < nk; ++k) {
+    launch(k);  // warm-up
+    cudaEventRecord(ev[0], s);
+    for (int r = 0; r < nrep; ++r) launch(k);
+    cudaEventRecord(ev[1], s);
+    cudaEventSynchronize(ev[1]);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[0], ev[1]);
+    if (k < nmax) ms_out[k] = (double)t / nrep;
   }
   for (auto &x : ev) cudaEventDestroy(x);
   if (cudaGetLastError() != cudaSuccess) return -1;
-  const int n = std::min(nmax, nk);
-  for (int k = 0; k < n; ++k) ms_out[k] = acc[k] / nrep;
-  return n;
+  return std::min(nmax, nk);
 }
 
 extern "C" int dg_kernel_costs(const dg_ctx *c, double *flops, double *bytes, int nmax) {
@@ -922,6 +955,11 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
     e = cudaMemcpy(g.d_block0, block0.data(), block0.size() * sizeof(int), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (auto &g : b->groups) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     free_ctx(c);
     cudaGetLastError();
@@ -947,29 +985,39 @@ static dg_status upload_descriptors(dg_ctx *c, cudaStream_t s) {
   return DG_OK;
 }
 
-static dg_status enqueue_batch_step(dg_ctx *c, cudaStream_t s) {
+// One step of one order group: volume part of stage 1, two fused stage
+// kernels, surface part of stage 3.
+static dg_status enqueue_group_step(dg_ctx *c, const BatchGroup &g, cudaStream_t s) {
   const int kind[4] = {BK_VOLUME, BK_SURFVOL, BK_SURFVOL, BK_SURFACE};
   for (int q = 0; q < 4; ++q) {
-    for (auto &g : c->batch->groups) {
-      cudaError_t e = g.k.launch(kind[q], g.d_probs, g.d_block0, (int)g.probs.size(), q, g.nblocks, s);
-      if (e != cudaSuccess) return cuda_fail(c, e, "batched stage kernel launch");
-    }
+    cudaError_t e = g.k.launch(kind[q], g.d_probs, g.d_block0, (int)g.probs.size(), q, g.nblocks, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched stage kernel launch");
   }
   return DG_OK;
 }
 
+// The order groups share no data, so the captured graph holds one branch per
+// group (forked from and joined back to the capture stream): the groups' kernels
+// run concurrently and fill each other's tails.
 static dg_status capture_batch(dg_ctx *c, int steps, cudaGraphExec_t *exec) {
+  BatchData *b = c->batch;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(c, e, "dg_batch_step: begin capture");
   dg_status r = DG_OK;
-  for (int k = 0; k < steps && r == DG_OK; ++k) r = enqueue_batch_step(c, c->cap);
-  e = cudaStreamEndCapture(c->cap, &g);
-  if (r != DG_OK) {
-    if (g) cudaGraphDestroy(g);
-    return r;
+  e = cudaEventRecord(b->fork, c->cap);
+  for (auto &grp : b->groups) {
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(grp.stream, b->fork, 0);
+    for (int k = 0; k < steps && e == cudaSuccess && r == DG_OK; ++k) r = enqueue_group_step(c, grp, grp.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(grp.done, grp.stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cap, grp.done, 0);
   }
-  if (e != cudaSuccess) return cuda_fail(c, e, "dg_batch_step: end capture");
+  const cudaError_t e_end = cudaStreamEndCapture(c->cap, &g);
+  if (r != DG_OK || e != cudaSuccess || e_end != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (r != DG_OK) return r;
+    return cuda_fail(c, e != cudaSuccess ? e : e_end, "dg_batch_step: capture");
+  }
   e = cudaGraphInstantiate(exec, g, 0);
   cudaGraphDestroy(g);
   return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_batch_step: instantiate");

@@ -161,3 +161,4 @@ def test_fp32bulk_multi_step_call_matches_single_steps(dg, make, nsteps):
     for v in range(7):
         sc = np.abs(b[v]).max()
         assert np.abs(a[v] - b[v]).max() <= 1e-6 * max(sc, 1e-30), (v, np.abs(a[v] - b[v]).max(), sc)
+

@@ -210,15 +210,26 @@ def test_step_zero_is_noop(dg):
     s.close()
 
 
-def test_step_host_buffer_round_trip(orc, dg):
-    """A CPU tensor is staged through the device by the binding."""
+@pytest.mark.parametrize("precision,pinned", [("fp64", False), ("fp64", True), ("fp32bulk", True)])
+def test_step_host_buffer_round_trip(orc, dg, precision, pinned):
+    """dg_step_host (a CPU tensor, pageable or pinned) gives exactly dg_step on a device copy, and
+    the FP64 result matches the oracle."""
     import torch
     wl = W.drop_2d(n=5, p=3, seed=2)
-    s = dg.Solver(wl)
+    s = dg.Solver(wl, precision=precision)
     h = torch.from_numpy(wl.w.copy())
+    if pinned:
+        h = h.pin_memory()
+    d = torch.from_numpy(wl.w.copy()).cuda()
     s.dg_step(h, wl.dt, 2)
+    s.dg_step(d, wl.dt, 2)
+    s.dg_step(h, wl.dt, 3)  # the staging buffer is reused
+    s.dg_step(d, wl.dt, 3)
+    assert s.dg_status_read() == 0
     s.close()
-    _assert_steps_close(orc, wl, 2, h.numpy(), orc.rk3(problem(orc, wl), wl.w, wl.dt, 2))
+    assert np.array_equal(h.numpy(), d.cpu().numpy())
+    if precision == "fp64":
+        _assert_steps_close(orc, wl, 5, h.numpy(), orc.rk3(problem(orc, wl), wl.w, wl.dt, 5))
 
 
 # ----------------------------------------------------------------------------- diagnostics
