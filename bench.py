@@ -166,6 +166,37 @@ def peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+# Per-unit algorithmic figures.  FP32-bulk (HBM-bound): 168 B per node and RK stage -- read the
+# stage state and w^n, write the new stage, 7 FP64 words each -- i.e. 24 B per DOF-update; the fused
+# stage kernel completes one stage per launch, so its units are the nodes.  FP64 (FP64-pipe-bound):
+# the library's per-kernel flop counts (dg_kernel_costs, from the scheme's formulas).
+BYTES_PER_NODE_STAGE = 168
+
+
+def roofline(precision, names, kms, flops, bytes_, nodes):
+    # the kernel taking most of a step: FP64 runs a volume and a surface kernel per stage;
+    # FP32-bulk runs one volume, two fused and one surface kernel per single-step call
+    per_step = [3, 3] if precision == "fp64" else [1, 1, 2]
+    dom = max(range(len(kms)), key=lambda i: kms[i] * per_step[i])
+    if precision == "fp64":
+        ach = flops[dom] / (kms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": names[dom], "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "per_unit": "dg_kernel_costs flops per launch",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (ncu: 2 DFMA/clk/SM)"}
+    else:
+        dom = names.index("k_surfvol32")
+        hbm = peaks().get("hbm_gbs", 6800.0)
+        ach = BYTES_PER_NODE_STAGE * nodes / (kms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "per_unit": f"{BYTES_PER_NODE_STAGE} B per node and stage x {nodes} nodes",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured"}
+    roof.update({"kernel_ms": dict(zip(names, kms)),
+                 "kernel_flops_per_launch": dict(zip(names, flops)),
+                 "kernel_bytes_per_launch": dict(zip(names, bytes_))})
+    return roof
+
+
 # --------------------------------------------------------------------------- ranks
 
 def reduce_max(values, device):
@@ -309,6 +340,7 @@ def batched_block(dg, steps, nprob=256):
     t1.record()
     torch.cuda.synchronize()
     ms_b = t0.elapsed_time(t1) / steps
+    tiles = bs.dg_batch_tiles()
     bs.close()
 
     def one_by_one(precision, nrep):
@@ -334,7 +366,8 @@ def batched_block(dg, steps, nprob=256):
             "value": units / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b,
             "one_by_one_fp32bulk": {"value": units / (ms_32 * 1e-3), "ms_per_step": ms_32},
             "one_by_one_fp64": {"value": units / (ms_64 * 1e-3), "ms_per_step": ms_64},
-            "speedup_vs_fp64": ms_64 / ms_b, "l2": "working set > L2 (no flush needed)"}
+            "speedup_vs_fp64": ms_64 / ms_b, "l2": "working set > L2 (no flush needed)",
+            "tiles": tiles}
 
 
 def rt_block(dg, steps, n=256):
@@ -362,6 +395,9 @@ def rt_block(dg, steps, n=256):
         ms = e0.elapsed_time(e1) / steps
         out[prec] = {"ms_per_step": ms, "value": 21 * wl.N / (ms * 1e-3), "unit": UNIT,
                      "device_status": s.dg_status_read()}
+        names = ["k_volume", "k_surface"] if prec == "fp64" else ["k_volume32", "k_surface32", "k_surfvol32"]
+        f, b = s.dg_kernel_costs()
+        out[prec]["roofline"] = roofline(prec, names, s.dg_time_kernels(w, nrep=10), f, b, wl.N)
         states[prec] = w.cpu().numpy()
         s.close()
     a, b = states["fp32bulk"], states["fp64"]
@@ -432,24 +468,8 @@ def run_ours(args, rank, world, local_rank):
     # roofline of the dominant kernel of the timed path
     names = ["k_volume", "k_surface"] if args.precision == "fp64" else ["k_volume32", "k_surface32", "k_surfvol32"]
     kms, flops, bytes_ = main["kms"], main["flops"], main["bytes"]
-    # the kernel taking most of a step: FP64 runs a volume and a surface kernel per stage;
-    # FP32-bulk runs one volume, two fused and one surface kernel per single-step call
-    per_step = [3, 3] if args.precision == "fp64" else [1, 1, 2]
-    dom = max(range(len(kms)), key=lambda i: kms[i] * per_step[i])
-    if args.precision == "fp64":
-        ach = flops[dom] / (kms[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": names[dom], "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (ncu: 2 DFMA/clk/SM)"}
-    else:
-        hbm = peaks().get("hbm_gbs", 6800.0)
-        ach = bytes_[dom] / (kms[dom] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured"}
-    roof.update({"traffic": profiled_traffic(names[dom], wl.name, args.precision),
-                 "kernel_ms": dict(zip(names, kms)),
-                 "algorithmic_flops_per_launch": dict(zip(names, flops)),
-                 "algorithmic_bytes_per_launch": dict(zip(names, bytes_))})
+    roof = roofline(args.precision, names, kms, flops, bytes_, wl.N)
+    roof["traffic"] = profiled_traffic(roof["kernel"], wl.name, args.precision)
 
     # end to end through the public API with a pinned host state: H2D, step, D2H
     solver = main["solver"]

@@ -79,12 +79,16 @@ typedef struct {
 /* Options.  prec: DG_FP64 or DG_FP32_BULK.  c_ip: interior-penalty constant,
    eta = c_ip (p+1)^2 / h (<= 0 selects 1).  viscous, gravity,
    surface_tension: enable those terms of Sec. 2.  check_finite: latch
-   DG_ERR_NONFINITE when an output is not finite. */
+   DG_ERR_NONFINITE when an output is not finite.  batch_tile (batches
+   only): 0 lets the first dg_batch_step tune the tile of every order; 1..4
+   fixes tile variant batch_tile - 1 for all orders (see dg_batch_step);
+   other values are DG_ERR_ARG. */
 typedef struct {
   int prec;
   double c_ip;
   int viscous, gravity, surface_tension;
   int check_finite;
+  int batch_tile;
 } dg_opts;
 
 typedef struct dg_ctx dg_ctx;
@@ -93,7 +97,8 @@ typedef struct dg_ctx dg_ctx;
    Allen-Cahn velocity scale Gamma >= 0 and thickness eps >= 0 (Sec. 2).
    opts may be NULL (FP64, c_ip = 1, no viscous/gravity/surface terms).
    Allocates all device memory the context will use on the current device
-   (except the staging buffer of dg_step_host, allocated on its first call).
+   (except the staging buffer of dg_step_host, allocated on its first staged
+   call).
    On success *out receives the context; on failure *out is NULL. */
 dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps,
                     const dg_opts *opts, dg_ctx **out);
@@ -116,14 +121,16 @@ dg_status dg_rhs(dg_ctx *ctx, const double *w, double *L, void *stream);
    pair and replayed; the first call for a new pair pays the capture. */
 dg_status dg_step(dg_ctx *ctx, double *w, double dt, int nsteps, void *stream);
 
-/* dg_step on a HOST state: w_host (dg_state_len doubles, pinned memory
-   recommended; pageable works but is staged by the driver) is copied to the
-   device, advanced by nsteps SSP-RK3 steps and copied back, all on stream;
-   the call returns after the copy back has finished, so w_host holds the new
-   state on return.  The device copy lives in a staging buffer of
-   dg_state_len doubles that the context allocates on the first call and
-   keeps until dg_destroy (DG_ERR_OOM if that allocation fails).  No Sec. of
-   the paper corresponds: this is the host-side convenience of dg_step. */
+/* dg_step on a HOST state w_host (dg_state_len doubles); returns when
+   w_host holds the state after nsteps SSP-RK3 steps.  FP32-bulk contexts
+   with a page-locked, device-mapped w_host (cudaHostAlloc / cudaHostRegister
+   memory, e.g. a pinned torch tensor) read and write it in place from the
+   kernels over the host link: the first stage reads the FP64 state, the last
+   stage writes it.  Otherwise the state is copied to a device staging buffer
+   (dg_state_len doubles, allocated on the first such call and kept until
+   dg_destroy; DG_ERR_OOM if that fails), stepped and copied back, all on
+   stream; pageable memory works but is staged by the driver.  No Sec. of the
+   paper corresponds: this is the host-side form of dg_step. */
 dg_status dg_step_host(dg_ctx *ctx, double *w_host, double dt, int nsteps, void *stream);
 
 /* FP64 diagnostics of w (Sec. 4.1 mass error): out (HOST, 16 doubles) gets
@@ -202,11 +209,25 @@ dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p, const dg_e
 /* Advance every problem k of a batch by nsteps SSP-RK3 steps with its own step
    dt[k] > 0.  w (HOST array of n pointers) gives each problem's DEVICE state
    (layout as dg_step, in place); dt is a HOST array of n doubles.  The whole
-   step is one CUDA graph (captured on the first call; it reads the problem
-   descriptors from device memory, so new pointers or step sizes only
-   re-upload the descriptors).  nsteps = 0 is a no-op.  Asynchronous on
-   stream. */
+   step is one CUDA graph with one branch per order (captured on the first
+   call; it reads the problem descriptors from device memory, so new pointers
+   or step sizes only re-upload the descriptors).  Before the capture, the
+   first call tunes the tile of every order: it times NVAR = 4 compiled
+   variants (elements per block: the single-problem rule or twice it;
+   registers: the compiler's choice or at most 64 per thread) on the batch's
+   own first-stage and fused kernels, which read the states and write only
+   internal buffers, and keeps the fastest (synchronises the stream once).
+   nsteps = 0 is a no-op.  Otherwise asynchronous on stream. */
 dg_status dg_batch_step(dg_ctx *ctx, double *const *w, const double *dt, int nsteps, void *stream);
+
+/* Tiles chosen by the tuner of dg_batch_step, one entry per order present
+   (in order of first appearance): order p, elements per block, minimum
+   resident blocks per SM asked of the compiler (1: no register cap), and the
+   tuned time in ms of the stage-1 volume and two fused launches with the
+   chosen and with the default tile (any output pointer may be NULL).
+   Returns the number of entries written (<= nmax), 0 before the first
+   dg_batch_step, -1 for a context that is not a batch. */
+int dg_batch_tiles(const dg_ctx *ctx, int *p, int *epb, int *minb, double *ms_best, double *ms_default, int nmax);
 
 /* Size of the fixed device scratch used by dg_rhs_noalloc (32 MiB per GPU). */
 #define DG_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)

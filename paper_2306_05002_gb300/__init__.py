@@ -32,7 +32,7 @@ PREC = {"fp64": 0, "fp32bulk": 1}
 EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_step_host", "dg_diag",
            "dg_status_read", "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc", "dg_batch_create",
            "dg_batch_step", "dg_rhs_vjp", "dg_adjoint_step", "dg_tape_len", "dg_step_tape",
-           "dg_adjoint_step_tape"]
+           "dg_adjoint_step_tape", "dg_batch_tiles"]
 
 
 class DGError(RuntimeError):
@@ -54,7 +54,8 @@ class dg_eos(ctypes.Structure):
 
 class dg_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("c_ip", ctypes.c_double), ("viscous", ctypes.c_int),
-                ("gravity", ctypes.c_int), ("surface_tension", ctypes.c_int), ("check_finite", ctypes.c_int)]
+                ("gravity", ctypes.c_int), ("surface_tension", ctypes.c_int), ("check_finite", ctypes.c_int),
+                ("batch_tile", ctypes.c_int)]
 
 
 _lib = None
@@ -102,6 +103,9 @@ def load(path: str | None = None):
     lib.dg_batch_step.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_int, vp]
     lib.dg_batch_step.restype = ctypes.c_int
+    ip, dpp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    lib.dg_batch_tiles.argtypes = [vp, ip, ip, ip, dpp, dpp, ctypes.c_int]
+    lib.dg_batch_tiles.restype = ctypes.c_int
     lib.dg_rhs_vjp.argtypes = [vp, dp, dp, dp, vp]
     lib.dg_rhs_vjp.restype = ctypes.c_int
     lib.dg_adjoint_step.argtypes = [vp, dp, dp, dp, ctypes.c_double, vp]
@@ -195,8 +199,8 @@ class Solver:
         return L
 
     def dg_step(self, w, dt: float, nsteps: int, stream=None):
-        """Advance w in place.  A CPU tensor goes through dg_step_host (copied to the device and back
-        inside the library; pin it for full copy bandwidth)."""
+        """Advance w in place.  A CPU tensor goes through dg_step_host: a pinned one is read and
+        written in place by the FP32-bulk kernels, otherwise it is staged through the device."""
         import torch
         if w.is_cuda:
             _check(self.ctx, load().dg_step(self.ctx, _ptr(w), float(dt), int(nsteps), _stream(stream)), "dg_step")
@@ -270,7 +274,8 @@ class BatchSolver:
     float64 CUDA state tensors (one per problem) and a list of step sizes.
     """
 
-    def __init__(self, problems, precision: str = "fp32bulk"):
+    def __init__(self, problems, precision: str = "fp32bulk", tile: int = 0):
+        """tile: 0 tunes the tile of every order on the first step; 1..4 fixes variant tile - 1."""
         lib = load()
         n = len(problems)
         meshes = (dg_mesh * n)()
@@ -286,6 +291,7 @@ class BatchSolver:
             m, e, o = make_structs(precision=precision, check_finite=False, **kw)
             meshes[k], eoss[k] = m, e
             opts = o if opts is None else opts
+        opts.batch_tile = int(tile)
         self._keep = (meshes, eoss, ps, G, E, opts)
         h = ctypes.c_void_p()
         st = lib.dg_batch_create(n, meshes, ps, eoss, G, E, ctypes.byref(opts), ctypes.byref(h))
@@ -309,3 +315,14 @@ class BatchSolver:
         dt = (ctypes.c_double * self.n)(*[float(x) for x in dts])
         _check(self.ctx, load().dg_batch_step(self.ctx, ptrs, dt, int(nsteps), _stream(stream)), "dg_batch_step")
         return ws
+
+    def dg_batch_tiles(self):
+        """Tiles chosen by the tuner (after the first dg_batch_step): one dict per order."""
+        m = 8
+        p, epb, minb = (ctypes.c_int * m)(), (ctypes.c_int * m)(), (ctypes.c_int * m)()
+        best, dflt = (ctypes.c_double * m)(), (ctypes.c_double * m)()
+        n = load().dg_batch_tiles(self.ctx, p, epb, minb, best, dflt, m)
+        if n < 0:
+            raise DGError(-1, "dg_batch_tiles: not a batch context")
+        return [{"p": p[i], "epb": epb[i], "minb": minb[i], "ms": best[i], "ms_default_tile": dflt[i]}
+                for i in range(n)]

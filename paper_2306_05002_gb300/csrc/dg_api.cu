@@ -35,6 +35,23 @@ bool kernels_fp32_p3(int, bool, bool, KernelSet32 *);
 bool kernels_fp32_p4(int, bool, bool, KernelSet32 *);
 bool kernels_fp32_p5(int, bool, bool, KernelSet32 *);
 
+void batch_variants_p1(BatchVariant *);
+void batch_variants_p2(BatchVariant *);
+void batch_variants_p3(BatchVariant *);
+void batch_variants_p4(BatchVariant *);
+void batch_variants_p5(BatchVariant *);
+
+bool batch_variants(int p, BatchVariant *out) {
+  switch (p) {
+    case 1: batch_variants_p1(out); return true;
+    case 2: batch_variants_p2(out); return true;
+    case 3: batch_variants_p3(out); return true;
+    case 4: batch_variants_p4(out); return true;
+    case 5: batch_variants_p5(out); return true;
+    default: return false;
+  }
+}
+
 bool kernels_fp32(int p, int dim, bool viscous, bool st, KernelSet32 *out) {
   switch (p) {
     case 1: return kernels_fp32_p1(dim, viscous, st, out);
@@ -241,9 +258,11 @@ struct BatchGroup {
   int p = 0;
   std::vector<int> probs;          // problem indices of this order
   BatchProb *d_probs = nullptr;    // descriptors, in the order of `probs`
-  int *d_block0 = nullptr;         // first block of each problem
-  int nblocks = 0;
-  BatchKernels k{};
+  BatchVariant var[NVAR] = {};     // tile variants of this order
+  int *d_block0[NVAR] = {};        // first block of each problem, per variant
+  int nblocks[NVAR] = {};
+  int best = -1;                   // chosen variant (-1: not tuned yet)
+  double ms[NVAR] = {};            // tuning times (volume + two fused launches)
   cudaStream_t stream = nullptr;   // capture branch of this group
   cudaEvent_t done = nullptr;      // joins the branch back at the end of a captured sequence
 };
@@ -322,7 +341,7 @@ static void free_ctx(dg_ctx *c) {
   if (c->batch) {
     for (auto &g : c->batch->groups) {
       cudaFree(g.d_probs);
-      cudaFree(g.d_block0);
+      for (auto *p0 : g.d_block0) cudaFree(p0);
       if (g.stream) cudaStreamDestroy(g.stream);
       if (g.done) cudaEventDestroy(g.done);
     }
@@ -700,14 +719,28 @@ extern "C" dg_status dg_step_host(dg_ctx *c, double *w_host, double dt, int nste
   if (!w_host) return fail(c, DG_ERR_ARG, "dg_step_host: null state");
   if (!(dt > 0.0) || nsteps < 0) return fail(c, DG_ERR_ARG, "dg_step_host: need dt > 0 and nsteps >= 0");
   if (nsteps == 0) return DG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
+  // FP32-bulk reads the FP64 state once per call (first stage) and writes it
+  // once (last stage).  When w_host is page-locked and mapped into the device
+  // address space, those two kernels access it in place over the host link
+  // (NVLink-C2C on GB300), with no staging copies.
+  if (c->prec != DG_FP64) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, w_host) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+      const dg_status r = dg_step(c, static_cast<double *>(at.devicePointer), dt, nsteps, stream);
+      if (r != DG_OK) return r;
+      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "dg_step_host: sync");
+      return DG_OK;
+    }
+    cudaGetLastError();
+  }
   if (!c->d_hstate && (e = cudaMalloc(&c->d_hstate, c->len * sizeof(double))) != cudaSuccess) {
     c->d_hstate = nullptr;
     cudaGetLastError();
     return fail(c, e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA,
                 std::string("dg_step_host: staging buffer: ") + cudaGetErrorString(e));
   }
-  cudaStream_t s = (cudaStream_t)stream;
   const size_t bytes = c->len * sizeof(double);
   if ((e = cudaMemcpyAsync(c->d_hstate, w_host, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_fail(c, e, "dg_step_host: copy to device");
@@ -841,6 +874,8 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
     return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_batch_create: the batched form runs the FP32-bulk path only");
   if (o.viscous || o.surface_tension)
     return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_batch_create: viscous and surface-tension terms are not batched");
+  if (o.batch_tile < 0 || o.batch_tile > NVAR)
+    return fail(nullptr, DG_ERR_ARG, "dg_batch_create: batch_tile must be 0 (tune) or 1..4");
   for (int k = 0; k < n; ++k) {
     dg_status code;
     if (const char *why = check_problem(meshes + k, p[k], eos + k, Gamma[k], eps[k], &code))
@@ -871,7 +906,7 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
     if (g < 0) {
       BatchGroup grp;
       grp.p = p[k];
-      if (!batch_kernels(p[k], &grp.k)) {
+      if (!batch_variants(p[k], grp.var)) {
         free_ctx(c);
         return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_batch_create: order not available");
       }
@@ -941,18 +976,18 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
   }
   for (auto &g : b->groups) {
     if (e != cudaSuccess) break;
-    std::vector<int> block0(g.probs.size());
-    int nb = 0;
-    for (size_t q = 0; q < g.probs.size(); ++q) {
-      BatchProb &d = b->h[g.probs[q]];
-      d.block0 = nb;
-      block0[q] = nb;
-      nb += (d.prm.E + g.k.epb - 1) / g.k.epb;
-    }
-    g.nblocks = nb;
     if ((e = cudaMalloc(&g.d_probs, g.probs.size() * sizeof(BatchProb))) != cudaSuccess) break;
-    if ((e = cudaMalloc(&g.d_block0, g.probs.size() * sizeof(int))) != cudaSuccess) break;
-    e = cudaMemcpy(g.d_block0, block0.data(), block0.size() * sizeof(int), cudaMemcpyHostToDevice);
+    for (int v = 0; v < NVAR && e == cudaSuccess; ++v) {
+      std::vector<int> block0(g.probs.size());
+      int nb = 0;
+      for (size_t q = 0; q < g.probs.size(); ++q) {
+        block0[q] = nb;
+        nb += (b->h[g.probs[q]].prm.E + g.var[v].epb - 1) / g.var[v].epb;
+      }
+      g.nblocks[v] = nb;
+      if ((e = cudaMalloc(&g.d_block0[v], g.probs.size() * sizeof(int))) != cudaSuccess) break;
+      e = cudaMemcpy(g.d_block0[v], block0.data(), block0.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
@@ -985,15 +1020,58 @@ static dg_status upload_descriptors(dg_ctx *c, cudaStream_t s) {
   return DG_OK;
 }
 
-// One step of one order group: volume part of stage 1, two fused stage
-// kernels, surface part of stage 3.
-static dg_status enqueue_group_step(dg_ctx *c, const BatchGroup &g, cudaStream_t s) {
+// The first `nk` kernels of one step of one order group in tile variant v:
+// volume part of stage 1, two fused stage kernels, surface part of stage 3.
+static dg_status enqueue_group_step(dg_ctx *c, const BatchGroup &g, int v, cudaStream_t s, int nk = 4) {
   const int kind[4] = {BK_VOLUME, BK_SURFVOL, BK_SURFVOL, BK_SURFACE};
-  for (int q = 0; q < 4; ++q) {
-    cudaError_t e = g.k.launch(kind[q], g.d_probs, g.d_block0, (int)g.probs.size(), q, g.nblocks, s);
+  for (int q = 0; q < nk; ++q) {
+    cudaError_t e = g.var[v].launch(kind[q], g.d_probs, g.d_block0[v], (int)g.probs.size(), q, g.nblocks[v], s);
     if (e != cudaSuccess) return cuda_fail(c, e, "batched stage kernel launch");
   }
   return DG_OK;
+}
+
+// Tile autotuner: time every variant of every order group on the batch
+// itself -- the stage-1 volume kernel and the two fused kernels, which read
+// the caller's states and write only internal buffers -- and keep the
+// fastest.  Runs once, before the first step's graphs are captured.
+static dg_status tune_batch(dg_ctx *c, cudaStream_t s) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "dg_batch_step: tuning");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(c, cudaGetLastError(), "dg_batch_step: tuning");
+  }
+  dg_status r = DG_OK;
+  const int reps = 3;
+  if (c->opts.batch_tile > 0) {  // fixed by the caller: no timing
+    for (auto &g : c->batch->groups) g.best = c->opts.batch_tile - 1;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return DG_OK;
+  }
+  for (auto &g : c->batch->groups) {
+    for (int v = 0; v < NVAR && r == DG_OK; ++v) {
+      r = enqueue_group_step(c, g, v, s, 3);  // warm-up
+      cudaEventRecord(e0, s);
+      for (int k = 0; k < reps && r == DG_OK; ++k) r = enqueue_group_step(c, g, v, s, 3);
+      cudaEventRecord(e1, s);
+      const cudaError_t e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        if (r == DG_OK) r = cuda_fail(c, e != cudaSuccess ? e : cudaGetLastError(), "dg_batch_step: tuning");
+        break;
+      }
+      g.ms[v] = ms / reps;
+    }
+    if (r != DG_OK) break;
+    g.best = 0;
+    for (int v = 1; v < NVAR; ++v)
+      if (g.ms[v] < g.ms[g.best]) g.best = v;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return r;
 }
 
 // The order groups share no data, so the captured graph holds one branch per
@@ -1008,7 +1086,8 @@ static dg_status capture_batch(dg_ctx *c, int steps, cudaGraphExec_t *exec) {
   e = cudaEventRecord(b->fork, c->cap);
   for (auto &grp : b->groups) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(grp.stream, b->fork, 0);
-    for (int k = 0; k < steps && e == cudaSuccess && r == DG_OK; ++k) r = enqueue_group_step(c, grp, grp.stream);
+    for (int k = 0; k < steps && e == cudaSuccess && r == DG_OK; ++k)
+      r = enqueue_group_step(c, grp, grp.best, grp.stream);
     if (e == cudaSuccess) e = cudaEventRecord(grp.done, grp.stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cap, grp.done, 0);
   }
@@ -1021,6 +1100,24 @@ static dg_status capture_batch(dg_ctx *c, int steps, cudaGraphExec_t *exec) {
   e = cudaGraphInstantiate(exec, g, 0);
   cudaGraphDestroy(g);
   return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_batch_step: instantiate");
+}
+
+extern "C" int dg_batch_tiles(const dg_ctx *c, int *p, int *epb, int *minb, double *ms_best, double *ms_default,
+                              int nmax) {
+  if (!c || !c->batch || nmax < 0) return -1;
+  int n = 0;
+  for (const auto &g : c->batch->groups) {
+    if (g.best < 0) return 0;
+    if (n < nmax) {
+      if (p) p[n] = g.p;
+      if (epb) epb[n] = g.var[g.best].epb;
+      if (minb) minb[n] = g.var[g.best].minb;
+      if (ms_best) ms_best[n] = g.ms[g.best];
+      if (ms_default) ms_default[n] = g.ms[0];
+    }
+    ++n;
+  }
+  return std::min(n, nmax);
 }
 
 extern "C" dg_status dg_batch_step(dg_ctx *c, double *const *w, const double *dt, int nsteps, void *stream) {
@@ -1043,6 +1140,7 @@ extern "C" dg_status dg_batch_step(dg_ctx *c, double *const *w, const double *dt
   }
   if (!c->g1) {  // the graphs read the descriptors at run time: captured once
     dg_status r;
+    if ((r = tune_batch(c, s)) != DG_OK) return r;
     if ((r = capture_batch(c, 1, &c->g1)) != DG_OK) return r;
     if ((r = capture_batch(c, GRAPH_UNROLL, &c->gk)) != DG_OK) return r;
   }

@@ -91,13 +91,13 @@ __device__ __forceinline__ void trace_derive(const ParamsF &pf, float *T) {
 // s_op: the block's shared copy of the operator table; this body copies the
 // two derivative matrices into it unless ops_ready (the fused kernel's
 // surface part has copied the whole table and synchronised the block).
-template <int P, int DIM, bool VISC, bool ST>
+template <int P, int DIM, bool VISC, bool ST, int EPBX = 0>
 __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf, const float *__restrict__ opsf,
                                            float *s_op, bool ops_ready, int blk, const float *__restrict__ w,
                                            float *__restrict__ rvol, float *__restrict__ tr,
                                            const double *__restrict__ w64, float *__restrict__ w32out,
                                            const float *qin = nullptr) {
-  using G = Geom<P, DIM, VISC, ST>;
+  using G = Geom<P, DIM, VISC, ST, EPBX>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
   constexpr int P11 = P1 * P1;
   constexpr int NS = 12;
@@ -319,13 +319,13 @@ k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, c
 // left in rout, for a volume body that follows in the same kernel.  Every
 // thread of the block returns from this body (none leaves early), so such a
 // body may synchronise the block.
-template <int P, int DIM, bool VISC, bool ST>
+template <int P, int DIM, bool VISC, bool ST, int EPBX = 0>
 __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf, const float *__restrict__ opsf,
                                             float *s_op, int blk, int mode, float dt, const float *__restrict__ w0,
                                             const float *__restrict__ ws, const float *__restrict__ rvol,
                                             const float *__restrict__ tr, float *__restrict__ out32,
                                             double *__restrict__ out64, float *rout = nullptr) {
-  using G = Geom<P, DIM, VISC, ST>;
+  using G = Geom<P, DIM, VISC, ST, EPBX>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
   constexpr int NC = VISC ? NT32_VISCOUS : NT32_INVISCID;
   constexpr int FPT = (NFK + NP - 1) / NP;  // face nodes per thread

@@ -30,7 +30,9 @@
 
 namespace dgpf {
 
-template <int P, int DIM, bool VISC, bool ST>
+// Block geometry of one kernel family.  EPBX > 0 overrides the number of
+// elements per block (the batched kernels' tuned tile).
+template <int P, int DIM, bool VISC, bool ST, int EPBX = 0>
 struct Geom {
   static constexpr int P1 = P + 1;
   static constexpr int NP = DIM == 2 ? P1 * P1 : P1;
@@ -48,7 +50,7 @@ struct Geom {
     }
     return (128 + NP - 1) / NP;
   }
-  static constexpr int EPB = pick_epb();
+  static constexpr int EPB = EPBX > 0 ? EPBX : pick_epb();
   static constexpr int THREADS = ((EPB * NP + 31) / 32) * 32;
   static constexpr int NT = VISC ? NT_VISCOUS : NT_INVISCID;
   static constexpr int NSTAGE = 12;                  // staged fields per node

@@ -75,6 +75,7 @@ def test_null_context_is_safe(lib):
     assert lib.dg_rhs(None, None, None, None) == -1
     assert lib.dg_step(None, None, 1.0, 1, None) == -1
     assert lib.dg_step_host(None, None, 1.0, 1, None) == -1
+    assert lib.dg_batch_tiles(None, None, None, None, None, None, 4) == -1
     lib.dg_destroy(None)
     assert isinstance(lib.dg_last_error(None), bytes)
 
@@ -93,4 +94,6 @@ def test_batch_create_rejects_unsupported_forms(lib):
     assert lib.dg_batch_create(1, meshes, ps, eoss, G, E, ctypes.byref(o), ctypes.byref(h)) == -7
     o.prec, o.viscous = 1, 1
     assert lib.dg_batch_create(1, meshes, ps, eoss, G, E, ctypes.byref(o), ctypes.byref(h)) == -7
+    o.viscous, o.batch_tile = 0, 5
+    assert lib.dg_batch_create(1, meshes, ps, eoss, G, E, ctypes.byref(o), ctypes.byref(h)) == -1
     assert h.value is None

@@ -61,3 +61,37 @@ def test_batch_new_pointers_and_steps_are_picked_up(dg):
         wl2.w, wl2.dt = wl.w, 0.5 * wl.dt
         assert close(y.cpu().numpy(), _single(dg, wl2, 2), 2)
     bs.close()
+
+
+@pytest.mark.parametrize("tile", [1, 2, 3, 4])
+def test_every_tile_variant_matches_single_problem_runs(dg, tile):
+    """Each compiled tile (elements per block x register budget) gives the single-problem result."""
+    import torch
+    wls = W.ensemble(n=5, seed=6, nmin=3, nmax=10, orders=(1, 2, 3, 4, 5))
+    bs = dg.BatchSolver(wls, tile=tile)
+    states = [torch.from_numpy(wl.w.copy()).cuda() for wl in wls]
+    bs.dg_batch_step(states, [wl.dt for wl in wls], 2)
+    torch.cuda.synchronize()
+    tiles = bs.dg_batch_tiles()
+    assert sorted(t["p"] for t in tiles) == sorted({wl.p for wl in wls})
+    for wl, st in zip(wls, states):
+        ref = _single(dg, wl, 2)
+        got = st.cpu().numpy()
+        for v in range(7):
+            scale = max(np.abs(ref[v]).max(), 1e-300)
+            assert np.abs(got[v] - ref[v]).max() <= TOL_STAGE * 6 * scale, (wl.name, v)
+    bs.close()
+
+
+def test_tuner_reports_a_tile_per_order(dg):
+    import torch
+    wls = W.ensemble(n=6, seed=7, nmin=8, nmax=24, orders=(2, 3, 4, 5))
+    bs = dg.BatchSolver(wls)
+    assert bs.dg_batch_tiles() == []          # nothing tuned before the first step
+    states = [torch.from_numpy(wl.w.copy()).cuda() for wl in wls]
+    bs.dg_batch_step(states, [wl.dt for wl in wls], 1)
+    tiles = bs.dg_batch_tiles()
+    assert sorted(t["p"] for t in tiles) == sorted({wl.p for wl in wls})
+    for t in tiles:
+        assert t["epb"] >= 1 and t["minb"] >= 1 and 0 < t["ms"] <= t["ms_default_tile"]
+    bs.close()
