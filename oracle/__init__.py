@@ -103,6 +103,28 @@ class Problem:
         return s
 
 
+class _Velocity(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("u0", ctypes.c_double), ("v0", ctypes.c_double), ("T", ctypes.c_double)]
+
+
+VEL = {"uniform": 0, "rider_kothe": 1}
+
+
+@dataclass
+class Velocity:
+    """Prescribed velocity of the kinematic mode (Sec. 4.1): uniform (u0, v0), or the
+    Rider-Kothe vortex with period T."""
+    kind: str = "uniform"
+    u0: float = 1.0
+    v0: float = 0.0
+    T: float = 4.0
+
+    def _c(self) -> _Velocity:
+        s = _Velocity()
+        s.kind, s.u0, s.v0, s.T = VEL[self.kind], self.u0, self.v0, self.T
+        return s
+
+
 _lib = None
 
 
@@ -121,6 +143,11 @@ def lib():
         _lib.orc_rhs.argtypes = [pp, dp, dp, dp, dp]
         _lib.orc_rk3.argtypes = [pp, dp, ctypes.c_double, ctypes.c_int]
         _lib.orc_diag.argtypes = [pp, dp, dp]
+        vp = ctypes.POINTER(_Velocity)
+        _lib.orc_velocity_at.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
+        _lib.orc_velocity_at.restype = None
+        _lib.orc_kin_rhs.argtypes = [pp, vp, ctypes.c_double, dp, dp, dp]
+        _lib.orc_kin_rk4.argtypes = [pp, vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
     return _lib
 
 
@@ -199,3 +226,30 @@ def diag(pb: Problem, w):
     s = pb._c()
     _check(lib().orc_diag(ctypes.byref(s), _ptr(w), _ptr(out)), "diag")
     return out
+
+
+def velocity_at(vel: Velocity, x: float, y: float, t: float):
+    u, v = ctypes.c_double(), ctypes.c_double()
+    c = vel._c()
+    lib().orc_velocity_at(ctypes.byref(c), float(x), float(y), float(t), ctypes.byref(u), ctypes.byref(v))
+    return u.value, v.value
+
+
+def kin_rhs(pb: Problem, vel: Velocity, t: float, w, want_scale: bool = False):
+    """Kinematic mode: L = M^-1 R(w) at time t for w = (phi, psi), shape (2, N)."""
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(2, pb.N)
+    L = np.zeros((2, pb.N))
+    S = np.zeros((2, pb.N)) if want_scale else None
+    s, c = pb._c(), vel._c()
+    _check(lib().orc_kin_rhs(ctypes.byref(s), ctypes.byref(c), float(t), _ptr(w), _ptr(L), _ptr(S)), "kin_rhs")
+    return (L, S) if want_scale else L
+
+
+def kin_rk4(pb: Problem, vel: Velocity, w, t0: float, dt: float, nsteps: int):
+    """Return (phi, psi) after nsteps classical RK4 steps from time t0 (input left untouched)."""
+    w = np.array(w, dtype=np.float64).reshape(2, pb.N).copy()
+    s, c = pb._c(), vel._c()
+    _check(lib().orc_kin_rk4(ctypes.byref(s), ctypes.byref(c), _ptr(w), float(t0), float(dt), int(nsteps)),
+           "kin_rk4")
+    return w
+

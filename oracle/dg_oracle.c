@@ -22,7 +22,10 @@
  *     the conservative equations, and the symmetric interior penalty (SIP)
  *     flux for every a_l-derived term (Sec. 3);
  *   - viscous stress, gravity and CSF surface tension of Sec. 2;
- *   - three-stage SSP Runge-Kutta in time.
+ *   - three-stage SSP Runge-Kutta in time;
+ *   - the kinematic mode of Sec. 4.1: phase field and level set alone,
+ *     advected by a prescribed velocity (uniform, or the Rider-Kothe vortex),
+ *     with the classical four-stage Runge-Kutta method in time.
  *
  * Readings of points the paper leaves open (each is also listed in the
  * design notes of the repository):
@@ -46,7 +49,12 @@
  *     {tau.u}.m + eta {mu} (k+ - k-) for energy (no symmetric term);
  *   - walls: ghost state equal to the own state with the velocity (no-slip)
  *     or its normal component (slip) reversed; ghost gradients equal the own
- *     ones; no a_1 flux crosses a wall.
+ *     ones; no a_1 flux crosses a wall;
+ *   - kinematic mode: the velocity is the analytical field sampled at the
+ *     nodes, and the characteristic speed of the transport flux is the
+ *     advection speed alone, lambda = max(|u-.m|, |u+.m|) (there is no sound
+ *     speed in the kinematic system); everything else is the phi and psi
+ *     rows of the full scheme.
  */
 #include "dg_oracle.h"
 
@@ -724,3 +732,180 @@ int orc_diag(const orc_problem *pr, const double *w, double *out) {
     }
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Kinematic mode (Sec. 4.1)                                                */
+/* ------------------------------------------------------------------------ */
+
+void orc_velocity_at(const orc_velocity *vel, double x, double y, double t, double *u, double *v) {
+  if (vel->kind == ORC_VEL_RIDER_KOTHE) {
+    double sx = sin(M_PI * x), sy = sin(M_PI * y), c = cos(M_PI * t / vel->T);
+    *u = sx * sx * sin(2.0 * M_PI * y) * c;
+    *v = -sin(2.0 * M_PI * x) * sy * sy * c;
+  } else {
+    *u = vel->u0;
+    *v = vel->v0;
+  }
+}
+
+typedef struct {
+  double phi, psi, u, v;
+  double gphi[2], gpsi[2], n[2], a1[2], a1m[2];
+} knode_t;
+
+int orc_kin_rhs(const orc_problem *pr, const orc_velocity *vel, double t, const double *w, double *L,
+                double *S) {
+  geo_t g;
+  if (geo_init(&g, pr) || pr->dim != 2 || !vel) return -1;
+  for (int f = 0; f < 4; ++f)
+    if (pr->bc[f] != ORC_BC_PERIODIC) return -1;
+  const long N = g.N;
+  const int Np = g.Np, P1 = g.P1;
+  const double Gam = pr->Gamma, eps = pr->eps;
+  knode_t *nd = (knode_t *)calloc((size_t)N, sizeof(knode_t));
+  double *x = (double *)malloc(sizeof(double) * N), *y = (double *)malloc(sizeof(double) * N);
+  double *R = (double *)calloc((size_t)2 * N, sizeof(double));
+  double *A = (double *)calloc((size_t)2 * N, sizeof(double));
+  if (!nd || !x || !y || !R || !A) {
+    free(nd); free(x); free(y); free(R); free(A);
+    return -2;
+  }
+  acc_t ac = {R, A, NULL, N};
+  orc_nodes(pr, x, y);
+
+  /* 1. Nodal values and the prescribed velocity. */
+  for (long n = 0; n < N; ++n) {
+    nd[n].phi = w[n];
+    nd[n].psi = w[N + n];
+    orc_velocity_at(vel, x[n], y[n], t, &nd[n].u, &nd[n].v);
+  }
+  /* 2. Broken gradients of phi and psi. */
+  for (int e = 0; e < g.E; ++e)
+    for (int a = 0; a < Np; ++a) {
+      knode_t *k = &nd[(long)e * Np + a];
+      for (int b = 0; b < Np; ++b) {
+        const knode_t *s = &nd[(long)e * Np + b];
+        double gr[2];
+        grad_basis(&g, b, a, gr);
+        for (int d = 0; d < 2; ++d) {
+          k->gphi[d] += s->phi * gr[d];
+          k->gpsi[d] += s->psi * gr[d];
+        }
+      }
+    }
+  /* 3. Normal and a_1 = Gamma (eps grad phi - phi (1 - phi) n). */
+  for (long n = 0; n < N; ++n) {
+    knode_t *k = &nd[n];
+    double norm = sqrt(k->gpsi[0] * k->gpsi[0] + k->gpsi[1] * k->gpsi[1]);
+    double s = k->phi * (1.0 - k->phi);
+    for (int d = 0; d < 2; ++d) {
+      k->n[d] = norm < 1e-12 ? 0.0 : k->gpsi[d] / norm;
+      k->a1[d] = Gam * (eps * k->gphi[d] - s * k->n[d]);
+      k->a1m[d] = Gam * (fabs(eps * k->gphi[d]) + fabs(s * k->n[d]));
+    }
+  }
+  /* 4. Volume terms: int grad l_a . (-a_1) for phi, and the non-conservative
+        transport -int l_a u . grad f for phi and psi. */
+  for (int e = 0; e < g.E; ++e)
+    for (int k = 0; k < Np; ++k) {
+      const knode_t *q = &nd[(long)e * Np + k];
+      double wk = node_weight(&g, k) * g.J;
+      for (int a = 0; a < Np; ++a) {
+        double gr[2];
+        grad_basis(&g, a, k, gr);
+        if (gr[0] == 0.0 && gr[1] == 0.0) continue;
+        long n = (long)e * Np + a;
+        add(&ac, 0, n, -wk * (gr[0] * q->a1[0] + gr[1] * q->a1[1]),
+            wk * (fabs(gr[0]) * q->a1m[0] + fabs(gr[1]) * q->a1m[1]));
+      }
+      long n = (long)e * Np + k;
+      add(&ac, 0, n, -wk * (q->u * q->gphi[0] + q->v * q->gphi[1]),
+          wk * (fabs(q->u * q->gphi[0]) + fabs(q->v * q->gphi[1])));
+      add(&ac, 1, n, -wk * (q->u * q->gpsi[0] + q->v * q->gpsi[1]),
+          wk * (fabs(q->u * q->gpsi[0]) + fabs(q->v * q->gpsi[1])));
+    }
+  /* 5. Faces: transport (lambda - m.u-) [[f]] with lambda = max(|u-.m|, |u+.m|),
+        and the SIP flux of a_1 with its symmetric term (phi only). */
+  for (int e = 0; e < g.E; ++e)
+    for (int f = 0; f < 4; ++f) {
+      int e2 = neighbour(&g, e, f);
+      const double *m = face_m[f];
+      double hperp = f < 2 ? g.hx : g.hy;
+      double eta = pr->c_ip * (double)P1 * (double)P1 / hperp;
+      double Jf = 0.5 * (f < 2 ? g.hy : g.hx);
+      for (int k = 0; k < P1; ++k) {
+        long nm = (long)e * Np + face_node(&g, f, k);
+        const knode_t *tm = &nd[nm];
+        const knode_t *tp = &nd[(long)e2 * Np + face_node(&g, f ^ 1, k)];
+        double wf = g.wt[k] * Jf;
+        double unm = tm->u * m[0] + tm->v * m[1];
+        double unp = tp->u * m[0] + tp->v * m[1];
+        double lam = fmax(fabs(unm), fabs(unp));
+        double hj_phi = 0.5 * (tp->phi - tm->phi), hj_psi = 0.5 * (tp->psi - tm->psi);
+        add(&ac, 0, nm, wf * (lam - unm) * hj_phi, wf * (fabs(lam * hj_phi) + fabs(unm * hj_phi)));
+        add(&ac, 1, nm, wf * (lam - unm) * hj_psi, wf * (fabs(lam * hj_psi) + fabs(unm * hj_psi)));
+        double jump = tp->phi - tm->phi;
+        double gn = 0.5 * ((tp->gphi[0] + tm->gphi[0]) * m[0] + (tp->gphi[1] + tm->gphi[1]) * m[1]);
+        double sp = tp->phi * (1.0 - tp->phi), sm = tm->phi * (1.0 - tm->phi);
+        double sharp = 0.5 * (sp * (tp->n[0] * m[0] + tp->n[1] * m[1]) + sm * (tm->n[0] * m[0] + tm->n[1] * m[1]));
+        double ahat = Gam * (eps * (gn + eta * jump) - sharp);
+        double amag = Gam * (eps * (0.5 * (fabs(tp->gphi[0] * m[0] + tp->gphi[1] * m[1]) +
+                                           fabs(tm->gphi[0] * m[0] + tm->gphi[1] * m[1])) +
+                                    fabs(eta * jump)) +
+                             0.5 * (fabs(sp) + fabs(sm)));
+        add(&ac, 0, nm, wf * ahat, wf * amag);
+        double sym = 0.5 * Gam * eps * jump;
+        int a = face_node(&g, f, k);
+        for (int b = 0; b < Np; ++b) {
+          double gr[2];
+          grad_basis(&g, b, a, gr);
+          double gm = gr[0] * m[0] + gr[1] * m[1];
+          if (gm == 0.0) continue;
+          add(&ac, 0, (long)e * Np + b, -wf * sym * gm, wf * sym * gm);
+        }
+      }
+    }
+  /* 6. Inverse of the diagonal mass matrix. */
+  for (int e = 0; e < g.E; ++e)
+    for (int a = 0; a < Np; ++a) {
+      long n = (long)e * Np + a;
+      double Minv = 1.0 / (node_weight(&g, a) * g.J);
+      for (int v = 0; v < 2; ++v) {
+        L[v * N + n] = R[v * N + n] * Minv;
+        if (S) S[v * N + n] = A[v * N + n] * Minv;
+      }
+    }
+  free(nd); free(x); free(y); free(R); free(A);
+  return 0;
+}
+
+int orc_kin_rk4(const orc_problem *pr, const orc_velocity *vel, double *w, double t0, double dt, int nsteps) {
+  long N = orc_num_nodes(pr);
+  if (N < 0 || nsteps < 0) return -1;
+  size_t len = (size_t)2 * N;
+  double *k = (double *)malloc(len * sizeof(double));
+  double *acc = (double *)malloc(len * sizeof(double));
+  double *ws = (double *)malloc(len * sizeof(double));
+  if (!k || !acc || !ws) {
+    free(k); free(acc); free(ws);
+    return -2;
+  }
+  int rc = 0;
+  for (int s = 0; s < nsteps && rc == 0; ++s) {
+    /* Classical RK4: k1 = L(w, t), k2 = L(w + dt/2 k1, t + dt/2),
+       k3 = L(w + dt/2 k2, t + dt/2), k4 = L(w + dt k3, t + dt),
+       w <- w + dt/6 (k1 + 2 k2 + 2 k3 + k4), summed in that order. */
+    double t = t0 + s * dt;
+    rc = orc_kin_rhs(pr, vel, t, w, k, NULL);
+    for (size_t i = 0; i < len; ++i) { acc[i] = k[i]; ws[i] = w[i] + 0.5 * dt * k[i]; }
+    if (rc == 0) rc = orc_kin_rhs(pr, vel, t + 0.5 * dt, ws, k, NULL);
+    for (size_t i = 0; i < len; ++i) { acc[i] += 2.0 * k[i]; ws[i] = w[i] + 0.5 * dt * k[i]; }
+    if (rc == 0) rc = orc_kin_rhs(pr, vel, t + 0.5 * dt, ws, k, NULL);
+    for (size_t i = 0; i < len; ++i) { acc[i] += 2.0 * k[i]; ws[i] = w[i] + dt * k[i]; }
+    if (rc == 0) rc = orc_kin_rhs(pr, vel, t + dt, ws, k, NULL);
+    for (size_t i = 0; i < len; ++i) w[i] = w[i] + dt / 6.0 * (acc[i] + k[i]);
+  }
+  free(k); free(acc); free(ws);
+  return rc;
+}
+

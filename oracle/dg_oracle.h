@@ -60,6 +60,32 @@ int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double
 /* nsteps of three-stage SSP Runge-Kutta (Shu-Osher form), in place. */
 int orc_rk3(const orc_problem *pr, double *w, double dt, int nsteps);
 /*
+ * Kinematic mode (Sec. 4.1, "kinematic tests"): only the phase field and the
+ * level set, advected by a prescribed analytical velocity u(x, t):
+ *   d(phi)/dt + u . grad(phi) = div a_1,   d(psi)/dt + u . grad(psi) = 0,
+ * with a_1 as in the full model.  State w[v * N + n], v = 0 (phi), 1 (psi).
+ * Velocity kinds: uniform (u0, v0); Rider-Kothe vortex with period T:
+ *   u = sin^2(pi x) sin(2 pi y) cos(pi t / T),
+ *   v = -sin(2 pi x) sin^2(pi y) cos(pi t / T).
+ * Periodic boundaries only.
+ */
+#define ORC_KIN_NV 2
+enum { ORC_VEL_UNIFORM = 0, ORC_VEL_RIDER_KOTHE = 1 };
+typedef struct {
+  int kind;
+  double u0, v0;   /* uniform velocity */
+  double T;        /* Rider-Kothe period */
+} orc_velocity;
+
+/* Velocity at (x, y) and time t. */
+void orc_velocity_at(const orc_velocity *vel, double x, double y, double t, double *u, double *v);
+/* L = M^-1 R(w) of the kinematic system at time t; S (nullable) as in orc_rhs. */
+int orc_kin_rhs(const orc_problem *pr, const orc_velocity *vel, double t, const double *w, double *L,
+                double *S);
+/* nsteps of the classical four-stage Runge-Kutta method from time t0, in place. */
+int orc_kin_rk4(const orc_problem *pr, const orc_velocity *vel, double *w, double t0, double dt, int nsteps);
+
+/*
  * Diagnostics: out[0..6] = integrals of the 7 variables, out[7..8] = min/max
  * phi, out[9..10] = min/max P, out[11..12] = min/max u, out[13..14] =
  * min/max v, out[15] = number of non-finite state entries.
