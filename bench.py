@@ -49,6 +49,8 @@ def parse():
                     help="ensemble size of the batched block (smaller values for profiling)")
     ap.add_argument("--adjoint-n", type=int, default=128,
                     help="elements per direction of the adjoint block (smaller values for profiling)")
+    ap.add_argument("--kin-steps", type=int, default=200,
+                    help="timed RK4 steps of the kinematic Rider-Kothe block (0 skips it)")
     ap.add_argument("--adjoint-steps", type=int, default=200,
                     help="trajectory length of the adjoint timing (0 skips it)")
     ap.add_argument("--cpu-sample-steps", type=int, default=0,
@@ -406,6 +408,49 @@ def rt_block(dg, steps, n=256):
     return out
 
 
+def kinematic_block(dg, steps, n=64):
+    """Kinematic mode (Sec. 4.1), FP64, classical RK4: the Rider-Kothe vortex on n x n quads,
+    p = 3, timed over `steps` steps (2 fields x 4 right-hand sides per step per node); and the
+    full period T = 4 on 16 x 16, p = 3 (the paper's 64^2-DoF mesh): L1 error of phi against
+    the initial drop and the relative phase-field mass error (paper, p = 3: L1 1.75e-2)."""
+    import numpy as np
+    import torch
+    from paper_2306_05002_gb300 import workloads as W
+    wl = W.rider_kothe(n=n, p=3)
+    s = dg.KinematicSolver(wl)
+    w = torch.from_numpy(wl.w.copy()).cuda()
+    s.dg_kin_step(w, 0.0, wl.dt, 2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.dg_kin_step(w, 2 * wl.dt, wl.dt, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s.close()
+    small = W.rider_kothe(n=16, p=3)
+    s = dg.KinematicSolver(small)
+    w = torch.from_numpy(small.w.copy()).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.dg_kin_step(w, 0.0, small.dt, small.nsteps)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    wend = w.cpu().numpy()
+    s.close()
+    # GLL weights w_i = 2 / (p (p + 1) P_p(xi_i)^2)
+    from numpy.polynomial import legendre
+    xi = W.gll_points(3)
+    wt = 2.0 / (3 * 4 * legendre.Legendre.basis(3)(xi) ** 2)
+    M = np.tile(np.outer(wt, wt).ravel() * 0.25 * small.hx * small.hy, small.nx * small.ny)
+    return {"workload": f"Rider-Kothe vortex {n}x{n} quads p=3, T=4, eps=0.75h, Gamma=1, FP64, classical RK4",
+            "nodes": wl.N, "steps": steps, "ms_per_step": ms, "value": 2 * 4 * wl.N / (ms * 1e-3), "unit": UNIT,
+            "full_period_16x16p3": {"steps": small.nsteps, "wall_s": wall,
+                                    "l1_phi": float(np.sum(M * np.abs(wend[0] - small.w[0]))),
+                                    "mass_error": float(np.sum(M * (wend[0] - small.w[0])) / np.sum(M * small.w[0])),
+                                    "paper_l1_p3_64sq_dof": 1.75e-2}}
+
+
 def adjoint_block(dg, steps, every=20, n=128):
     """Gradient of J = 1/2 int (alpha_N - alpha*)^2 with respect to the initial state of the
     128 x 128, p = 3 drop (level set with 16 seeded Fourier coefficients, seed 5/50/51),
@@ -491,6 +536,7 @@ def run_ours(args, rank, world, local_rank):
     adjoint = (adjoint_block(dg, args.adjoint_steps, n=args.adjoint_n)
                if (args.adjoint_steps > 0 and rank == 0) else None)
     rt = rt_block(dg, args.rt_steps) if (args.rt_steps > 0 and rank == 0) else None
+    kin = kinematic_block(dg, args.kin_steps) if (args.kin_steps > 0 and rank == 0) else None
 
     ms_max, e2e_max, ref_ms = reduce_max([main["ms"], e2e_t, ref["ms"] if ref else 0.0], "cuda")
 
@@ -523,6 +569,8 @@ def run_ours(args, rank, world, local_rank):
             line["adjoint"] = adjoint
         if rt:
             line["rayleigh_taylor"] = rt
+        if kin:
+            line["kinematic"] = kin
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
         print(json.dumps(line), flush=True)

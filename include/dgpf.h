@@ -229,6 +229,46 @@ dg_status dg_batch_step(dg_ctx *ctx, double *const *w, const double *dt, int nst
    dg_batch_step, -1 for a context that is not a batch. */
 int dg_batch_tiles(const dg_ctx *ctx, int *p, int *epb, int *minb, double *ms_best, double *ms_default, int nmax);
 
+/* ---------------------------------------------------------------------------
+   Kinematic mode (Sec. 4.1, "kinematic tests"): the phase field phi and the
+   level set psi alone, advected by a prescribed analytical velocity,
+     d(phi)/dt + u . grad(phi) = div a_1,   d(psi)/dt + u . grad(psi) = 0,
+   discretised as the phi and psi rows of the full scheme (the transport speed
+   of the face flux is max(|u-.m|, |u+.m|): the kinematic system has no sound
+   speed) and integrated with the classical four-stage Runge-Kutta method, as
+   in the paper's Rider-Kothe test.  FP64.  The state is 2 x N doubles:
+   w[v * N + e * Np + a], v = 0 (phi), 1 (psi), layout as dg_rhs.
+   --------------------------------------------------------------------------- */
+typedef enum { DG_VEL_UNIFORM = 0, DG_VEL_RIDER_KOTHE = 1 } dg_velocity_kind;
+
+/* Prescribed velocity.  DG_VEL_UNIFORM: (u0, v0).  DG_VEL_RIDER_KOTHE: the
+   vortex of Sec. 4.1 with period T > 0,
+     u = sin^2(pi x) sin(2 pi y) cos(pi t / T),
+     v = -sin(2 pi x) sin^2(pi y) cos(pi t / T). */
+typedef struct {
+  int kind;
+  double u0, v0;
+  double T;
+} dg_velocity;
+
+/* Create a kinematic-mode context: 2D mesh with periodic boundaries on all
+   four sides, order p (1..5), Allen-Cahn Gamma >= 0 and eps >= 0, velocity,
+   interior-penalty constant c_ip (<= 0 selects 1).  dg_state_len gives 2 N;
+   dg_destroy releases it; the single-problem and batch calls of the full
+   model reject it (DG_ERR_ARG).  Errors as dg_create. */
+dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, double eps, const dg_velocity *vel, double c_ip,
+                        dg_ctx **out);
+
+/* L = M^-1 R(w) of the kinematic system at time t (device arrays of
+   dg_state_len doubles; must not overlap). */
+dg_status dg_kin_rhs(dg_ctx *ctx, const double *w, double t, double *L, void *stream);
+
+/* Advance w (device, in place) from time t0 by nsteps classical RK4 steps of
+   size dt > 0.  Captured once in a CUDA graph per (w, dt) pair (the graph reads
+   the start time from device memory, so t0 may change freely).  Asynchronous
+   on stream. */
+dg_status dg_kin_step(dg_ctx *ctx, double *w, double t0, double dt, int nsteps, void *stream);
+
 /* Size of the fixed device scratch used by dg_rhs_noalloc (32 MiB per GPU). */
 #define DG_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 

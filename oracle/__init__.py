@@ -148,6 +148,9 @@ def lib():
         _lib.orc_velocity_at.restype = None
         _lib.orc_kin_rhs.argtypes = [pp, vp, ctypes.c_double, dp, dp, dp]
         _lib.orc_kin_rk4.argtypes = [pp, vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        _lib.orc_reinit_sign.argtypes = [pp, dp, dp]
+        _lib.orc_reinit_rhs.argtypes = [pp, dp, dp, ctypes.c_double, dp]
+        _lib.orc_reinit.argtypes = [pp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
     return _lib
 
 
@@ -252,4 +255,31 @@ def kin_rk4(pb: Problem, vel: Velocity, w, t0: float, dt: float, nsteps: int):
     _check(lib().orc_kin_rk4(ctypes.byref(s), ctypes.byref(c), _ptr(w), float(t0), float(dt), int(nsteps)),
            "kin_rk4")
     return w
+
+
+def reinit_sign(pb: Problem, phi):
+    """Smeared sign S = tanh(psi0 / (2 eps |grad psi0|)) of psi0 = phi - 1/2 at every node."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(pb.N)
+    S = np.zeros(pb.N)
+    s = pb._c()
+    _check(lib().orc_reinit_sign(ctypes.byref(s), _ptr(phi), _ptr(S)), "reinit_sign")
+    return S
+
+
+def reinit_rhs(pb: Problem, S, psi, nu: float):
+    S = np.ascontiguousarray(S, dtype=np.float64).reshape(pb.N)
+    psi = np.ascontiguousarray(psi, dtype=np.float64).reshape(pb.N)
+    L = np.zeros(pb.N)
+    s = pb._c()
+    _check(lib().orc_reinit_rhs(ctypes.byref(s), _ptr(S), _ptr(psi), float(nu), _ptr(L)), "reinit_rhs")
+    return L
+
+
+def reinit(pb: Problem, phi, niter: int, nu: float, dtau: float):
+    """psi after niter pseudo-time SSP-RK3 steps from psi0 = phi - 1/2."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(pb.N)
+    psi = np.zeros(pb.N)
+    s = pb._c()
+    _check(lib().orc_reinit(ctypes.byref(s), _ptr(phi), _ptr(psi), int(niter), float(nu), float(dtau)), "reinit")
+    return psi
 

@@ -25,7 +25,8 @@
  *   - three-stage SSP Runge-Kutta in time;
  *   - the kinematic mode of Sec. 4.1: phase field and level set alone,
  *     advected by a prescribed velocity (uniform, or the Rider-Kothe vortex),
- *     with the classical four-stage Runge-Kutta method in time.
+ *     with the classical four-stage Runge-Kutta method in time;
+ *   - the level-set re-initialisation of the end of Sec. 3, in pseudo-time.
  *
  * Readings of points the paper leaves open (each is also listed in the
  * design notes of the repository):
@@ -54,7 +55,17 @@
  *     nodes, and the characteristic speed of the transport flux is the
  *     advection speed alone, lambda = max(|u-.m|, |u+.m|) (there is no sound
  *     speed in the kinematic system); everything else is the phi and psi
- *     rows of the full scheme.
+ *     rows of the full scheme;
+ *   - re-initialisation: the equation is taken as
+ *       d(psi)/d(tau) = S (1 - |grad psi|) + div(nu grad psi),
+ *     the sign with which |grad psi| relaxes to 1 (as printed, with
+ *     "+ S (1 - |grad psi|)" on the left-hand side, |grad psi| moves away
+ *     from 1 at the interface: a garbled sign); the smeared sign is evaluated
+ *     once from psi0 and its broken gradient (S = sign(psi0) where
+ *     |grad psi0| < 1e-12); its
+ *     diffusion carries the same SIP flux and penalty as a_1, with no flux
+ *     through walls; three-stage SSP Runge-Kutta in pseudo-time (the paper
+ *     names no pseudo-time integrator).
  */
 #include "dg_oracle.h"
 
@@ -906,6 +917,131 @@ int orc_kin_rk4(const orc_problem *pr, const orc_velocity *vel, double *w, doubl
     for (size_t i = 0; i < len; ++i) w[i] = w[i] + dt / 6.0 * (acc[i] + k[i]);
   }
   free(k); free(acc); free(ws);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Level-set re-initialisation (end of Sec. 3)                              */
+/* ------------------------------------------------------------------------ */
+
+/* Broken gradient of the nodal field f at every node. */
+static void broken_gradient(const geo_t *g, const double *f, double *gx, double *gy) {
+  for (int e = 0; e < g->E; ++e)
+    for (int a = 0; a < g->Np; ++a) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int b = 0; b < g->Np; ++b) {
+        double gr[2];
+        grad_basis(g, b, a, gr);
+        s0 += f[(long)e * g->Np + b] * gr[0];
+        s1 += f[(long)e * g->Np + b] * gr[1];
+      }
+      gx[(long)e * g->Np + a] = s0;
+      gy[(long)e * g->Np + a] = s1;
+    }
+}
+
+int orc_reinit_sign(const orc_problem *pr, const double *phi, double *S) {
+  geo_t g;
+  if (geo_init(&g, pr)) return -1;
+  const long N = g.N;
+  double *p0 = (double *)malloc(sizeof(double) * N), *gx = (double *)malloc(sizeof(double) * N),
+         *gy = (double *)malloc(sizeof(double) * N);
+  if (!p0 || !gx || !gy) {
+    free(p0); free(gx); free(gy);
+    return -2;
+  }
+  for (long n = 0; n < N; ++n) p0[n] = phi[n] - 0.5;
+  broken_gradient(&g, p0, gx, gy);
+  for (long n = 0; n < N; ++n) {
+    double gm = sqrt(gx[n] * gx[n] + gy[n] * gy[n]);
+    if (gm < 1e-12) S[n] = p0[n] > 0.0 ? 1.0 : (p0[n] < 0.0 ? -1.0 : 0.0);
+    else S[n] = tanh(p0[n] / (2.0 * pr->eps * gm));
+  }
+  free(p0); free(gx); free(gy);
+  return 0;
+}
+
+int orc_reinit_rhs(const orc_problem *pr, const double *S, const double *psi, double nu, double *L) {
+  geo_t g;
+  if (geo_init(&g, pr)) return -1;
+  const long N = g.N;
+  const int Np = g.Np, P1 = g.P1;
+  double *gx = (double *)malloc(sizeof(double) * N), *gy = (double *)malloc(sizeof(double) * N);
+  double *R = (double *)calloc((size_t)N, sizeof(double));
+  if (!gx || !gy || !R) {
+    free(gx); free(gy); free(R);
+    return -2;
+  }
+  broken_gradient(&g, psi, gx, gy);
+  /* Source S (1 - |grad psi|) (the sign that drives |grad psi| to 1, see the
+     header) and volume term int grad l_a . (-nu grad psi). */
+  for (int e = 0; e < g.E; ++e)
+    for (int k = 0; k < Np; ++k) {
+      long nk = (long)e * Np + k;
+      double wk = node_weight(&g, k) * g.J;
+      double gm = sqrt(gx[nk] * gx[nk] + gy[nk] * gy[nk]);
+      R[nk] += wk * S[nk] * (1.0 - gm);
+      for (int a = 0; a < Np; ++a) {
+        double gr[2];
+        grad_basis(&g, a, k, gr);
+        R[(long)e * Np + a] += -wk * nu * (gr[0] * gx[nk] + gr[1] * gy[nk]);
+      }
+    }
+  /* Faces: SIP flux nu ({grad psi}.m + eta (psi+ - psi-)) and the symmetric
+     term -1/2 nu (psi+ - psi-) grad l_b . m; nothing through walls. */
+  const int nf = g.dim == 2 ? 4 : 2, nk = g.dim == 2 ? P1 : 1;
+  for (int e = 0; e < g.E; ++e)
+    for (int f = 0; f < nf; ++f) {
+      int e2 = neighbour(&g, e, f);
+      if (e2 < 0) continue;
+      const double *m = face_m[f];
+      double hperp = f < 2 ? g.hx : g.hy;
+      double eta = pr->c_ip * (double)P1 * (double)P1 / hperp;
+      double Jf = g.dim == 2 ? 0.5 * (f < 2 ? g.hy : g.hx) : 1.0;
+      for (int k = 0; k < nk; ++k) {
+        int a = face_node(&g, f, k);
+        long nm = (long)e * Np + a, np_ = (long)e2 * Np + face_node(&g, f ^ 1, k);
+        double wf = (g.dim == 2 ? g.wt[k] : 1.0) * Jf;
+        double jump = psi[np_] - psi[nm];
+        double gn = 0.5 * ((gx[np_] + gx[nm]) * m[0] + (gy[np_] + gy[nm]) * m[1]);
+        R[nm] += wf * nu * (gn + eta * jump);
+        for (int b = 0; b < Np; ++b) {
+          double gr[2];
+          grad_basis(&g, b, a, gr);
+          double gmb = gr[0] * m[0] + gr[1] * m[1];
+          if (gmb != 0.0) R[(long)e * Np + b] += -wf * 0.5 * nu * jump * gmb;
+        }
+      }
+    }
+  for (int e = 0; e < g.E; ++e)
+    for (int a = 0; a < Np; ++a) {
+      long n = (long)e * Np + a;
+      L[n] = R[n] / (node_weight(&g, a) * g.J);
+    }
+  free(gx); free(gy); free(R);
+  return 0;
+}
+
+int orc_reinit(const orc_problem *pr, const double *phi, double *psi, int niter, double nu, double dtau) {
+  long N = orc_num_nodes(pr);
+  if (N < 0 || niter < 0) return -1;
+  double *S = (double *)malloc(sizeof(double) * N), *L = (double *)malloc(sizeof(double) * N);
+  double *p1 = (double *)malloc(sizeof(double) * N), *p2 = (double *)malloc(sizeof(double) * N);
+  if (!S || !L || !p1 || !p2) {
+    free(S); free(L); free(p1); free(p2);
+    return -2;
+  }
+  int rc = orc_reinit_sign(pr, phi, S);
+  for (long n = 0; n < N; ++n) psi[n] = phi[n] - 0.5;
+  for (int it = 0; it < niter && rc == 0; ++it) {
+    rc = orc_reinit_rhs(pr, S, psi, nu, L);
+    for (long n = 0; n < N; ++n) p1[n] = psi[n] + dtau * L[n];
+    if (rc == 0) rc = orc_reinit_rhs(pr, S, p1, nu, L);
+    for (long n = 0; n < N; ++n) p2[n] = 0.75 * psi[n] + 0.25 * (p1[n] + dtau * L[n]);
+    if (rc == 0) rc = orc_reinit_rhs(pr, S, p2, nu, L);
+    for (long n = 0; n < N; ++n) psi[n] = psi[n] / 3.0 + 2.0 / 3.0 * (p2[n] + dtau * L[n]);
+  }
+  free(S); free(L); free(p1); free(p2);
   return rc;
 }
 

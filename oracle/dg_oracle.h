@@ -86,6 +86,23 @@ int orc_kin_rhs(const orc_problem *pr, const orc_velocity *vel, double t, const 
 int orc_kin_rk4(const orc_problem *pr, const orc_velocity *vel, double *w, double t0, double dt, int nsteps);
 
 /*
+ * Level-set re-initialisation (end of Sec. 3): the pseudo-time equation
+ *   d(psi)/d(tau) = S (1 - |grad psi|) + div(nu grad psi),   psi(0) = psi0 = phi - 1/2,
+ * (the sign under which |grad psi| relaxes to 1; the paper prints the
+ * hyperbolic term with the opposite sign on the left-hand side)
+ * with the smeared sign S = tanh(psi0 / (2 eps |grad psi0|)) fixed from psi0.
+ * The hyperbolic term is a nodal source (broken gradient); the diffusion uses
+ * the SIP flux nu ({grad psi}.m + eta (psi+ - psi-)) with its symmetric term and
+ * no flux through walls; pseudo-time integration is three-stage SSP RK.
+ */
+/* S at every node from psi0 = phi - 1/2. */
+int orc_reinit_sign(const orc_problem *pr, const double *phi, double *S);
+/* L = M^-1 R(psi) of the re-initialisation equation for the sign S. */
+int orc_reinit_rhs(const orc_problem *pr, const double *S, const double *psi, double nu, double *L);
+/* psi <- psi0 = phi - 1/2, then niter SSP-RK3 steps of size dtau. */
+int orc_reinit(const orc_problem *pr, const double *phi, double *psi, int niter, double nu, double dtau);
+
+/*
  * Diagnostics: out[0..6] = integrals of the 7 variables, out[7..8] = min/max
  * phi, out[9..10] = min/max P, out[11..12] = min/max u, out[13..14] =
  * min/max v, out[15] = number of non-finite state entries.

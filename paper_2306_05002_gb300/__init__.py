@@ -32,7 +32,7 @@ PREC = {"fp64": 0, "fp32bulk": 1}
 EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_step_host", "dg_diag",
            "dg_status_read", "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc", "dg_batch_create",
            "dg_batch_step", "dg_rhs_vjp", "dg_adjoint_step", "dg_tape_len", "dg_step_tape",
-           "dg_adjoint_step_tape", "dg_batch_tiles"]
+           "dg_adjoint_step_tape", "dg_batch_tiles", "dg_kin_create", "dg_kin_rhs", "dg_kin_step"]
 
 
 class DGError(RuntimeError):
@@ -57,6 +57,12 @@ class dg_opts(ctypes.Structure):
                 ("gravity", ctypes.c_int), ("surface_tension", ctypes.c_int), ("check_finite", ctypes.c_int),
                 ("batch_tile", ctypes.c_int)]
 
+
+class dg_velocity(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("u0", ctypes.c_double), ("v0", ctypes.c_double), ("T", ctypes.c_double)]
+
+
+VEL = {"uniform": 0, "rider_kothe": 1}
 
 _lib = None
 
@@ -104,6 +110,13 @@ def load(path: str | None = None):
                                   ctypes.c_int, vp]
     lib.dg_batch_step.restype = ctypes.c_int
     ip, dpp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    lib.dg_kin_create.argtypes = [ctypes.POINTER(dg_mesh), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.POINTER(dg_velocity), ctypes.c_double, ctypes.POINTER(vp)]
+    lib.dg_kin_create.restype = ctypes.c_int
+    lib.dg_kin_rhs.argtypes = [vp, dp, ctypes.c_double, dp, vp]
+    lib.dg_kin_rhs.restype = ctypes.c_int
+    lib.dg_kin_step.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
+    lib.dg_kin_step.restype = ctypes.c_int
     lib.dg_batch_tiles.argtypes = [vp, ip, ip, ip, dpp, dpp, ctypes.c_int]
     lib.dg_batch_tiles.restype = ctypes.c_int
     lib.dg_rhs_vjp.argtypes = [vp, dp, dp, dp, vp]
@@ -326,3 +339,53 @@ class BatchSolver:
             raise DGError(-1, "dg_batch_tiles: not a batch context")
         return [{"p": p[i], "epb": epb[i], "minb": minb[i], "ms": best[i], "ms_default_tile": dflt[i]}
                 for i in range(n)]
+
+
+class KinematicSolver:
+    """Kinematic mode (Sec. 4.1): phi and psi advected by a prescribed velocity, classical RK4
+    (wraps a ``dg_kin_create`` context).  ``problem`` is a :class:`workloads.KinWorkload`; states
+    are float64 CUDA tensors of shape (2, N)."""
+
+    def __init__(self, problem):
+        lib = load()
+        m = dg_mesh()
+        m.dim, m.nx, m.ny = 2, problem.nx, problem.ny
+        m.x0, m.x1, m.y0, m.y1 = problem.x0, problem.x1, problem.y0, problem.y1
+        for i in range(4):
+            m.bc[i] = BC["periodic"]
+        v = dg_velocity()
+        v.kind, v.u0, v.v0, v.T = VEL[problem.vel], problem.u0, problem.v0, problem.T
+        self._keep = (m, v)
+        h = ctypes.c_void_p()
+        st = lib.dg_kin_create(ctypes.byref(m), problem.p, problem.Gamma, problem.eps, ctypes.byref(v),
+                               problem.c_ip, ctypes.byref(h))
+        _check(None, st, "dg_kin_create")
+        self.ctx = h
+        self.len = lib.dg_state_len(h)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().dg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dg_kin_rhs(self, w, t: float, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(w)
+        _check(self.ctx, load().dg_kin_rhs(self.ctx, _ptr(w), float(t), _ptr(out), _stream(stream)), "dg_kin_rhs")
+        return out
+
+    def dg_kin_step(self, w, t0: float, dt: float, nsteps: int, stream=None):
+        _check(self.ctx, load().dg_kin_step(self.ctx, _ptr(w), float(t0), float(dt), int(nsteps), _stream(stream)),
+               "dg_kin_step")
+        return w
+
+    def dg_status_read(self, stream=None):
+        return load().dg_status_read(self.ctx, _stream(stream))
+

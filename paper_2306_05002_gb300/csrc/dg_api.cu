@@ -20,6 +20,7 @@
 #include "dg_kernels_fp32.cuh"
 #include "dg_batch.cuh"
 #include "dg_adjoint.cuh"
+#include "dg_kin.cuh"
 #include "dgpf.h"
 
 namespace dgpf {
@@ -300,6 +301,12 @@ struct dg_ctx {
   int conv_blocks = 1;
   double *d_ops = nullptr, *d_w1 = nullptr, *d_w2 = nullptr, *d_rvol = nullptr, *d_trace = nullptr;
   double *d_hstate = nullptr;  // device copy of a host state (dg_step_host), allocated on first use
+  // kinematic mode (dg_kin_create)
+  bool kin = false;
+  KinParams kp{};
+  KinKernels kk{};
+  double *d_kacc = nullptr, *d_kwsA = nullptr, *d_kwsB = nullptr, *d_krvol = nullptr, *d_ktr = nullptr;
+  double *d_kt0 = nullptr, *d_kxi = nullptr;
   double *d_part = nullptr, *d_diag = nullptr;
   unsigned *d_status = nullptr;
   int nparts = 0;
@@ -351,6 +358,7 @@ static void free_ctx(dg_ctx *c) {
   }
   cudaFree(c->d_ops);
   cudaFree(c->d_hstate);
+  for (double *q : {c->d_kacc, c->d_kwsA, c->d_kwsB, c->d_krvol, c->d_ktr, c->d_kt0, c->d_kxi}) cudaFree(q);
   cudaFree(c->d_w1);
   cudaFree(c->d_w2);
   cudaFree(c->d_rvol);
@@ -608,7 +616,7 @@ static dg_status convert(dg_ctx *c, bool to32, double *w, cudaStream_t s) {
 
 extern "C" dg_status dg_rhs(dg_ctx *c, const double *w, double *L, void *stream) {
   if (!c) return DG_ERR_ARG;
-  if (c->batch) return fail(c, DG_ERR_ARG, "dg_rhs: batch context (use dg_batch_step)");
+  if (c->batch || c->kin) return fail(c, DG_ERR_ARG, "dg_rhs: batch or kinematic context");
   if (!w || !L) return fail(c, DG_ERR_ARG, "dg_rhs: null array");
   if (w == L) return fail(c, DG_ERR_ARG, "dg_rhs: w and L must not overlap");
   cudaStream_t s = (cudaStream_t)stream;
@@ -683,7 +691,7 @@ static dg_status capture(dg_ctx *c, double *w, double dt, int steps, cudaGraphEx
 
 extern "C" dg_status dg_step(dg_ctx *c, double *w, double dt, int nsteps, void *stream) {
   if (!c) return DG_ERR_ARG;
-  if (c->batch) return fail(c, DG_ERR_ARG, "dg_step: batch context (use dg_batch_step)");
+  if (c->batch || c->kin) return fail(c, DG_ERR_ARG, "dg_step: batch or kinematic context");
   if (!w) return fail(c, DG_ERR_ARG, "dg_step: null state");
   if (!(dt > 0.0) || nsteps < 0) return fail(c, DG_ERR_ARG, "dg_step: need dt > 0 and nsteps >= 0");
   if (nsteps == 0) return DG_OK;
@@ -715,7 +723,7 @@ extern "C" dg_status dg_step(dg_ctx *c, double *w, double dt, int nsteps, void *
 
 extern "C" dg_status dg_step_host(dg_ctx *c, double *w_host, double dt, int nsteps, void *stream) {
   if (!c) return DG_ERR_ARG;
-  if (c->batch) return fail(c, DG_ERR_ARG, "dg_step_host: batch context (use dg_batch_step)");
+  if (c->batch || c->kin) return fail(c, DG_ERR_ARG, "dg_step_host: batch or kinematic context");
   if (!w_host) return fail(c, DG_ERR_ARG, "dg_step_host: null state");
   if (!(dt > 0.0) || nsteps < 0) return fail(c, DG_ERR_ARG, "dg_step_host: need dt > 0 and nsteps >= 0");
   if (nsteps == 0) return DG_OK;
@@ -757,7 +765,7 @@ extern "C" dg_status dg_step_host(dg_ctx *c, double *w_host, double dt, int nste
 
 extern "C" dg_status dg_diag(dg_ctx *c, const double *w, double *out, void *stream) {
   if (!c) return DG_ERR_ARG;
-  if (c->batch) return fail(c, DG_ERR_ARG, "dg_diag: batch context (use dg_batch_step)");
+  if (c->batch || c->kin) return fail(c, DG_ERR_ARG, "dg_diag: batch or kinematic context");
   if (!w || !out) return fail(c, DG_ERR_ARG, "dg_diag: null array");
   cudaStream_t s = (cudaStream_t)stream;
   k_diag_partial<<<c->nparts, DIAG_THREADS, 0, s>>>(c->prm, c->Np, c->P1, c->dim, c->J, w, c->d_part);
@@ -785,7 +793,7 @@ extern "C" dg_status dg_status_read(dg_ctx *c, void *stream) {
 }
 
 extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_out, int nmax, void *stream) {
-  if (!c || c->batch || !w || !ms_out || nmax < 1 || nrep < 1) return -1;
+  if (!c || c->batch || c->kin || !w || !ms_out || nmax < 1 || nrep < 1) return -1;
   cudaStream_t s = (cudaStream_t)stream;
   const bool f64 = c->prec == DG_FP64;
   const int nk = f64 ? 2 : 3;
@@ -825,7 +833,7 @@ extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_
 }
 
 extern "C" int dg_kernel_costs(const dg_ctx *c, double *flops, double *bytes, int nmax) {
-  if (!c || c->batch || !flops || !bytes || nmax < 1) return -1;
+  if (!c || c->batch || c->kin || !flops || !bytes || nmax < 1) return -1;
   // Algorithmic counts from the formulas of the scheme (an FMA counts 2, a
   // division or square root 1), per launch.
   const double P1 = c->P1, Np = c->Np, NFK = c->NFK, E = c->E, d = c->dim;
@@ -1150,6 +1158,179 @@ extern "C" dg_status dg_batch_step(dg_ctx *c, double *const *w, const double *dt
   for (int k = 0; k < nsteps % GRAPH_UNROLL; ++k)
     if ((e = cudaGraphLaunch(c->g1, s)) != cudaSuccess) return cuda_fail(c, e, "dg_batch_step: graph launch");
   return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Kinematic mode (Sec. 4.1)
+// ---------------------------------------------------------------------------
+
+namespace dgpf {
+__global__ void k_kin_set_time(double *t0, double t);
+}
+
+extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, double eps, const dg_velocity *vel,
+                                   double c_ip, dg_ctx **out) {
+  if (!out) return fail(nullptr, DG_ERR_ARG, "dg_kin_create: out is NULL");
+  *out = nullptr;
+  if (!mesh || !vel) return fail(nullptr, DG_ERR_ARG, "dg_kin_create: mesh and velocity are required");
+  if (mesh->dim != 2) return fail(nullptr, DG_ERR_ARG, "dg_kin_create: the kinematic mode is two-dimensional");
+  if (p < 1 || p > 5) return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_kin_create: order p must be in 1..5");
+  if (mesh->nx < 1 || mesh->ny < 1 || (long long)mesh->nx * mesh->ny > (1LL << 26))
+    return fail(nullptr, DG_ERR_ARG, "dg_kin_create: need 1 <= nx, ny and a mesh of at most 2^26 elements");
+  if (!(mesh->x1 > mesh->x0) || !(mesh->y1 > mesh->y0)) return fail(nullptr, DG_ERR_ARG, "dg_kin_create: empty domain");
+  for (int f = 0; f < 4; ++f)
+    if (mesh->bc[f] != DG_BC_PERIODIC)
+      return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_kin_create: periodic boundaries only");
+  if (!(Gamma >= 0.0) || !(eps >= 0.0)) return fail(nullptr, DG_ERR_ARG, "dg_kin_create: need Gamma, eps >= 0");
+  if (vel->kind != DG_VEL_UNIFORM && vel->kind != DG_VEL_RIDER_KOTHE)
+    return fail(nullptr, DG_ERR_ARG, "dg_kin_create: unknown velocity kind");
+  if (vel->kind == DG_VEL_RIDER_KOTHE && !(vel->T > 0.0))
+    return fail(nullptr, DG_ERR_ARG, "dg_kin_create: the Rider-Kothe period must be > 0");
+  dg_ctx *c = new (std::nothrow) dg_ctx();
+  if (!c) return fail(nullptr, DG_ERR_OOM, "dg_kin_create: host allocation failed");
+  c->kin = true;
+  c->mesh = *mesh;
+  c->p = p;
+  c->dim = 2;
+  c->P1 = p + 1;
+  c->Np = c->P1 * c->P1;
+  c->E = mesh->nx * mesh->ny;
+  c->N = c->E * c->Np;
+  c->NFK = 4 * c->P1;
+  c->len = (size_t)2 * c->N;
+  c->hx = (mesh->x1 - mesh->x0) / mesh->nx;
+  c->hy = (mesh->y1 - mesh->y0) / mesh->ny;
+  if (!kin_kernels(p, &c->kk)) {
+    free_ctx(c);
+    return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_kin_create: order not available");
+  }
+  const double cip = c_ip > 0.0 ? c_ip : 1.0;
+  KinParams &k = c->kp;
+  k.nx = mesh->nx;
+  k.ny = mesh->ny;
+  k.E = c->E;
+  k.N = c->N;
+  k.x0 = mesh->x0;
+  k.y0 = mesh->y0;
+  k.hx = c->hx;
+  k.hy = c->hy;
+  k.Gamma = Gamma;
+  k.eps = eps;
+  k.eta_x = cip * c->P1 * c->P1 / c->hx;
+  k.eta_y = cip * c->P1 * c->P1 / c->hy;
+  k.vel = vel->kind;
+  k.u0 = vel->u0;
+  k.v0 = vel->v0;
+  k.T = vel->T;
+  k.check_finite = 1;
+  const std::vector<double> ops = build_ops(2, p, c->hx, c->hy);
+  std::vector<double> xi, wt;
+  gll_nodes(p, xi, wt);
+  const size_t sb = c->len * sizeof(double), tb = (size_t)NT_KIN * c->E * c->NFK * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  double **bufs[] = {&c->d_kacc, &c->d_kwsA, &c->d_kwsB, &c->d_krvol};
+  for (double **b : bufs)
+    if (e == cudaSuccess) e = cudaMalloc(b, sb);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_ktr, tb);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_kt0, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_kxi, xi.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_ops, ops.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_ops, ops.data(), ops.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_kxi, xi.data(), xi.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->d_kt0, 0, sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    cudaGetLastError();
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA,
+                std::string("dg_kin_create: ") + cudaGetErrorString(e));
+  }
+  k.ops = c->d_ops;
+  k.xi = c->d_kxi;
+  k.t0 = c->d_kt0;
+  k.status = c->d_status;
+  *out = c;
+  return DG_OK;
+}
+
+static dg_status kin_check(dg_ctx *c, const char *who) {
+  if (!c) return DG_ERR_ARG;
+  if (!c->kin) return fail(c, DG_ERR_ARG, std::string(who) + ": not a kinematic context (dg_kin_create)");
+  return DG_OK;
+}
+
+extern "C" dg_status dg_kin_rhs(dg_ctx *c, const double *w, double t, double *L, void *stream) {
+  dg_status r = kin_check(c, "dg_kin_rhs");
+  if (r != DG_OK) return r;
+  if (!w || !L || w == L) return fail(c, DG_ERR_ARG, "dg_kin_rhs: need distinct, non-null w and L");
+  cudaStream_t s = (cudaStream_t)stream;
+  k_kin_set_time<<<1, 1, 0, s>>>(c->d_kt0, t);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = c->kk.volume(c->kp, 0.0, 0.0, w, c->d_krvol, c->d_ktr, s);
+  if (e == cudaSuccess) e = c->kk.surface(c->kp, KIN_RHS, 0.0, w, c->d_krvol, c->d_ktr, nullptr, L, s);
+  return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_kin_rhs: launch");
+}
+
+// One classical RK4 step of the captured sequence: step k of the graph, stage
+// inputs w -> A -> B -> A, the last stage writes w in place.
+static dg_status enqueue_kin_step(dg_ctx *c, double *w, double dt, int k, cudaStream_t s) {
+  double *A = c->d_kwsA, *B = c->d_kwsB;
+  const double tstep = k * dt;
+  const double toff[4] = {0.0, 0.5 * dt, 0.5 * dt, dt};
+  const double *in[4] = {w, A, B, A};
+  double *out[4] = {A, B, A, w};
+  const int mode[4] = {KIN_K1, KIN_K2, KIN_K3, KIN_K4};
+  for (int st = 0; st < 4; ++st) {
+    cudaError_t e = c->kk.volume(c->kp, tstep, toff[st], in[st], c->d_krvol, c->d_ktr, s);
+    if (e == cudaSuccess) e = c->kk.surface(c->kp, mode[st], dt, w, c->d_krvol, c->d_ktr, c->d_kacc, out[st], s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_kin_step: launch");
+  }
+  return DG_OK;
+}
+
+static dg_status capture_kin(dg_ctx *c, double *w, double dt, int steps, cudaGraphExec_t *exec) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_kin_step: begin capture");
+  dg_status r = DG_OK;
+  for (int k = 0; k < steps && r == DG_OK; ++k) r = enqueue_kin_step(c, w, dt, k, c->cap);
+  e = cudaStreamEndCapture(c->cap, &g);
+  if (r != DG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_kin_step: end capture");
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_kin_step: instantiate");
+}
+
+extern "C" dg_status dg_kin_step(dg_ctx *c, double *w, double t0, double dt, int nsteps, void *stream) {
+  dg_status r = kin_check(c, "dg_kin_step");
+  if (r != DG_OK) return r;
+  if (!w) return fail(c, DG_ERR_ARG, "dg_kin_step: null state");
+  if (!(dt > 0.0) || nsteps < 0) return fail(c, DG_ERR_ARG, "dg_kin_step: need dt > 0 and nsteps >= 0");
+  if (nsteps == 0) return DG_OK;
+  if (c->g_w != w || c->g_dt != dt || !c->g1) {
+    free_graphs(c);
+    if ((r = capture_kin(c, w, dt, 1, &c->g1)) != DG_OK) return r;
+    if ((r = capture_kin(c, w, dt, GRAPH_UNROLL, &c->gk)) != DG_OK) return r;
+    c->g_w = w;
+    c->g_dt = dt;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  int done = 0;
+  while (done < nsteps && e == cudaSuccess) {
+    const bool big = nsteps - done >= GRAPH_UNROLL;
+    k_kin_set_time<<<1, 1, 0, s>>>(c->d_kt0, t0 + done * dt);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGraphLaunch(big ? c->gk : c->g1, s);
+    done += big ? GRAPH_UNROLL : 1;
+  }
+  return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_kin_step: launch");
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,20 @@
+// Kinematic-mode kernels (dg_kin.cuh) of orders 1..5.
+#include "dg_kin.cuh"
+
+namespace dgpf {
+
+bool kin_kernels(int p, KinKernels *out) {
+  switch (p) {
+    case 1: *out = {&launch_kin_volume<1>, &launch_kin_surface<1>}; return true;
+    case 2: *out = {&launch_kin_volume<2>, &launch_kin_surface<2>}; return true;
+    case 3: *out = {&launch_kin_volume<3>, &launch_kin_surface<3>}; return true;
+    case 4: *out = {&launch_kin_volume<4>, &launch_kin_surface<4>}; return true;
+    case 5: *out = {&launch_kin_volume<5>, &launch_kin_surface<5>}; return true;
+    default: return false;
+  }
+}
+
+// Sets the time base read by the kinematic kernels of a captured sequence.
+__global__ void k_kin_set_time(double *t0, double t) { *t0 = t; }
+
+}  // namespace dgpf

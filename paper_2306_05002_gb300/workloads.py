@@ -294,3 +294,115 @@ def adjoint_drop(n: int = 128, p: int = 3, seed: int = 5, theta=None, nsteps: in
     wl.w = w
     wl.meta.update(theta=list(map(float, theta)), seed=seed)
     return wl
+
+
+# ---------------------------------------------------------------------------
+# Kinematic mode (Sec. 4.1): phase field and level set, prescribed velocity
+# ---------------------------------------------------------------------------
+
+@dataclass
+class KinWorkload:
+    """A kinematic-mode problem: periodic 2D mesh, order, Allen-Cahn constants, prescribed
+    velocity (kind "uniform" with (u0, v0), or "rider_kothe" with period T), the initial
+    (phi, psi) state (2, N) and a time step."""
+    name: str
+    nx: int
+    ny: int
+    p: int
+    x0: float = -0.5
+    x1: float = 0.5
+    y0: float = -0.5
+    y1: float = 0.5
+    Gamma: float = 1.0
+    eps: float = 0.05
+    c_ip: float = 1.0
+    vel: str = "rider_kothe"
+    u0: float = 0.0
+    v0: float = 0.0
+    T: float = 4.0
+    w: Optional[np.ndarray] = None
+    dt: float = 0.0
+    nsteps: int = 0
+    meta: dict = field(default_factory=dict)
+    dim: int = 2
+
+    @property
+    def Np(self) -> int:
+        return (self.p + 1) ** 2
+
+    @property
+    def N(self) -> int:
+        return self.nx * self.ny * self.Np
+
+    @property
+    def hx(self) -> float:
+        return (self.x1 - self.x0) / self.nx
+
+    @property
+    def hy(self) -> float:
+        return (self.y1 - self.y0) / self.ny
+
+    def problem_kwargs(self) -> dict:
+        """The oracle's problem description (periodic 2D mesh and the Allen-Cahn constants)."""
+        return dict(dim=2, nx=self.nx, ny=self.ny, p=self.p, x0=self.x0, x1=self.x1, y0=self.y0, y1=self.y1,
+                    Gamma=self.Gamma, eps=self.eps, c_ip=self.c_ip)
+
+    def velocity_kwargs(self) -> dict:
+        return dict(kind=self.vel, u0=self.u0, v0=self.v0, T=self.T)
+
+
+def kin_stable_dt(wl: KinWorkload, umax: float) -> float:
+    """Advective limit 0.5 h / ((2p + 1) |u|max) and the parabolic limit of the SIP term."""
+    h = min(wl.hx, wl.hy)
+    q = 2 * wl.p + 1
+    dt = 0.5 * h / (q * max(umax, 1e-12))
+    if wl.Gamma * wl.eps > 0:
+        dt = min(dt, 0.1 * h * h / (q * q * wl.Gamma * wl.eps))
+    return dt
+
+
+def rider_kothe(n: int = 16, p: int = 3, T: float = 4.0, R: float = 0.15, center=(0.0, 0.25),
+                eps_h: float = 0.75, Gamma: float = 1.0) -> KinWorkload:
+    """Rider-Kothe vortex (Sec. 4.1): a drop of radius 0.15 centred at (0, 0.25) in the periodic
+    square [-0.5, 0.5]^2, stretched by the time-reversing shear flow of period T = 4.  Phase 1
+    is the drop; psi = R - r grows into it.  eps = 0.75 h (h: element width) and Gamma = |u|max
+    = 1, since the paper leaves both unstated for this test."""
+    wl = KinWorkload(name=f"rk2d_{n}x{n}p{p}", nx=n, ny=n, p=p, Gamma=Gamma, vel="rider_kothe", T=T)
+    wl.eps = eps_h * wl.hx
+    x, y = _kin_nodes(wl)
+    r = np.hypot(x - center[0], y - center[1])
+    s = R - r
+    wl.w = np.stack([tanh_profile(s, wl.eps), s])
+    wl.dt = kin_stable_dt(wl, 1.0)
+    wl.nsteps = int(np.ceil(T / wl.dt))
+    wl.dt = T / wl.nsteps
+    wl.meta = dict(R=R, center=center)
+    return wl
+
+
+def kin_drop(n: int = 16, p: int = 3, R: float = 0.15, u0: float = 1.0, v0: float = 0.0,
+             eps: float = 0.05, Gamma: float = 1.0) -> KinWorkload:
+    """Linear advection of a droplet (Sec. 4.1): radius 0.15 at the origin of the periodic square
+    [-0.5, 0.5]^2, constant velocity (1, 0), eps = 0.05; one period is t = 1."""
+    wl = KinWorkload(name=f"kdrop2d_{n}x{n}p{p}", nx=n, ny=n, p=p, Gamma=Gamma, eps=eps, vel="uniform",
+                     u0=u0, v0=v0)
+    x, y = _kin_nodes(wl)
+    s = R - np.hypot(x, y)
+    wl.w = np.stack([tanh_profile(s, eps), s])
+    wl.dt = kin_stable_dt(wl, np.hypot(u0, v0))
+    wl.nsteps = int(np.ceil(1.0 / wl.dt))
+    wl.dt = 1.0 / wl.nsteps
+    return wl
+
+
+def _kin_nodes(wl: KinWorkload):
+    xi = gll_points(wl.p)
+    P1 = wl.p + 1
+    e = np.arange(wl.nx * wl.ny)
+    ex, ey = e % wl.nx, e // wl.nx
+    a = np.arange(P1 * P1)
+    i, j = a % P1, a // P1
+    x = wl.x0 + wl.hx * (ex[:, None] + 0.5 * (xi[i][None, :] + 1.0))
+    y = wl.y0 + wl.hy * (ey[:, None] + 0.5 * (xi[j][None, :] + 1.0))
+    return x.ravel(), y.ravel()
+

@@ -97,3 +97,36 @@ def test_batch_create_rejects_unsupported_forms(lib):
     o.viscous, o.batch_tile = 0, 5
     assert lib.dg_batch_create(1, meshes, ps, eoss, G, E, ctypes.byref(o), ctypes.byref(h)) == -1
     assert h.value is None
+
+
+def _kin_args(**over):
+    import paper_2306_05002_gb300 as pkg
+    m = pkg.dg_mesh()
+    m.dim, m.nx, m.ny = over.pop("dim", 2), over.pop("nx", 4), over.pop("ny", 4)
+    m.x0, m.x1, m.y0, m.y1 = -0.5, 0.5, -0.5, 0.5
+    bc = over.pop("bc", ("periodic",) * 4)
+    for i in range(4):
+        m.bc[i] = pkg.BC[bc[i]]
+    v = pkg.dg_velocity()
+    v.kind, v.u0, v.v0, v.T = over.pop("kind", 1), 0.0, 0.0, over.pop("T", 4.0)
+    return m, over.pop("p", 3), over.pop("Gamma", 1.0), over.pop("eps", 0.05), v
+
+
+@pytest.mark.parametrize("over,code", [
+    (dict(dim=1, ny=1), -1),
+    (dict(p=0), -7),
+    (dict(bc=("periodic", "periodic", "noslip", "noslip")), -7),
+    (dict(kind=7), -1),
+    (dict(T=0.0), -1),
+    (dict(Gamma=-1.0), -1),
+])
+def test_kin_create_rejects_invalid_arguments(lib, over, code):
+    m, p, G, eps, v = _kin_args(**over)
+    h = ctypes.c_void_p(123)
+    assert lib.dg_kin_create(ctypes.byref(m), p, G, eps, ctypes.byref(v), 1.0, ctypes.byref(h)) == code
+    assert h.value is None
+
+
+def test_kin_calls_reject_other_contexts(lib):
+    assert lib.dg_kin_rhs(None, None, 0.0, None, None) == -1
+    assert lib.dg_kin_step(None, None, 0.0, 1.0, 1, None) == -1
