@@ -242,13 +242,16 @@ int dg_batch_tiles(const dg_ctx *ctx, int *p, int *epb, int *minb, double *ms_be
 typedef enum { DG_VEL_UNIFORM = 0, DG_VEL_RIDER_KOTHE = 1 } dg_velocity_kind;
 
 /* Prescribed velocity.  DG_VEL_UNIFORM: (u0, v0).  DG_VEL_RIDER_KOTHE: the
-   vortex of Sec. 4.1 with period T > 0,
-     u = sin^2(pi x) sin(2 pi y) cos(pi t / T),
-     v = -sin(2 pi x) sin^2(pi y) cos(pi t / T). */
+   vortex of Sec. 4.1 with period T > 0 about the centre (xc, yc), with
+   X = x - xc + 1/2 and Y = y - yc + 1/2,
+     u = sin^2(pi X) sin(2 pi Y) cos(pi t / T),
+     v = -sin(2 pi X) sin^2(pi Y) cos(pi t / T)
+   (xc = yc = 1/2 gives the formula as printed in Sec. 4.1). */
 typedef struct {
   int kind;
   double u0, v0;
   double T;
+  double xc, yc;
 } dg_velocity;
 
 /* Create a kinematic-mode context: 2D mesh with periodic boundaries on all
@@ -268,6 +271,24 @@ dg_status dg_kin_rhs(dg_ctx *ctx, const double *w, double t, double *L, void *st
    the start time from device memory, so t0 may change freely).  Asynchronous
    on stream. */
 dg_status dg_kin_step(dg_ctx *ctx, double *w, double t0, double dt, int nsteps, void *stream);
+
+/* Level-set re-initialisation (end of Sec. 3): replace the level set psi of
+   the state w (device; phi and psi are fields 0 and 1 of a full-model or a
+   kinematic state; the other fields are left unchanged) by the solution after
+   niter pseudo-time steps of
+     d(psi)/d(tau) = S (1 - |grad psi|) + div(nu grad psi),  psi(0) = phi - 1/2,
+     S = tanh(psi0 / (2 eps |grad psi0|)) (the smeared sign, fixed from psi0),
+   the hyperbolic term a nodal source, the diffusion with the SIP flux and its
+   symmetric term (no flux through walls), three-stage SSP Runge-Kutta of step
+   dtau.  The hyperbolic term carries the sign under which |grad psi| relaxes
+   to 1 (the paper prints the opposite sign, under which it grows).  nu <= 0
+   selects nu = h / (2 (p + 1)) and dtau <= 0 selects
+   min(0.5 h / (2p + 1), 0.1 h^2 / ((2p + 1)^2 nu)), h the smallest element
+   width.  The paper applies ~50 iterations every 2000 steps.  FP64; works on
+   FP64 and FP32-bulk contexts alike (on the FP64 state).  The first call
+   allocates the context's re-initialisation workspace (4 N doubles and the
+   face traces), kept until dg_destroy.  Asynchronous on stream. */
+dg_status dg_reinit(dg_ctx *ctx, double *w, int niter, double nu, double dtau, void *stream);
 
 /* Size of the fixed device scratch used by dg_rhs_noalloc (32 MiB per GPU). */
 #define DG_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)

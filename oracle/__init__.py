@@ -104,7 +104,8 @@ class Problem:
 
 
 class _Velocity(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("u0", ctypes.c_double), ("v0", ctypes.c_double), ("T", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int), ("u0", ctypes.c_double), ("v0", ctypes.c_double), ("T", ctypes.c_double),
+                ("xc", ctypes.c_double), ("yc", ctypes.c_double)]
 
 
 VEL = {"uniform": 0, "rider_kothe": 1}
@@ -113,15 +114,17 @@ VEL = {"uniform": 0, "rider_kothe": 1}
 @dataclass
 class Velocity:
     """Prescribed velocity of the kinematic mode (Sec. 4.1): uniform (u0, v0), or the
-    Rider-Kothe vortex with period T."""
+    Rider-Kothe vortex with period T about the centre (xc, yc) (0.5, 0.5: the printed formula)."""
     kind: str = "uniform"
     u0: float = 1.0
     v0: float = 0.0
     T: float = 4.0
+    xc: float = 0.5
+    yc: float = 0.5
 
     def _c(self) -> _Velocity:
         s = _Velocity()
-        s.kind, s.u0, s.v0, s.T = VEL[self.kind], self.u0, self.v0, self.T
+        s.kind, s.u0, s.v0, s.T, s.xc, s.yc = VEL[self.kind], self.u0, self.v0, self.T, self.xc, self.yc
         return s
 
 

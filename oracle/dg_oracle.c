@@ -750,9 +750,10 @@ int orc_diag(const orc_problem *pr, const double *w, double *out) {
 
 void orc_velocity_at(const orc_velocity *vel, double x, double y, double t, double *u, double *v) {
   if (vel->kind == ORC_VEL_RIDER_KOTHE) {
-    double sx = sin(M_PI * x), sy = sin(M_PI * y), c = cos(M_PI * t / vel->T);
-    *u = sx * sx * sin(2.0 * M_PI * y) * c;
-    *v = -sin(2.0 * M_PI * x) * sy * sy * c;
+    double X = x - vel->xc + 0.5, Y = y - vel->yc + 0.5;
+    double sx = sin(M_PI * X), sy = sin(M_PI * Y), c = cos(M_PI * t / vel->T);
+    *u = sx * sx * sin(2.0 * M_PI * Y) * c;
+    *v = -sin(2.0 * M_PI * X) * sy * sy * c;
   } else {
     *u = vel->u0;
     *v = vel->v0;
@@ -954,7 +955,7 @@ int orc_reinit_sign(const orc_problem *pr, const double *phi, double *S) {
   broken_gradient(&g, p0, gx, gy);
   for (long n = 0; n < N; ++n) {
     double gm = sqrt(gx[n] * gx[n] + gy[n] * gy[n]);
-    if (gm < 1e-12) S[n] = p0[n] > 0.0 ? 1.0 : (p0[n] < 0.0 ? -1.0 : 0.0);
+    if (gm < 1e-12 || !(pr->eps > 0.0)) S[n] = p0[n] > 0.0 ? 1.0 : (p0[n] < 0.0 ? -1.0 : 0.0);
     else S[n] = tanh(p0[n] / (2.0 * pr->eps * gm));
   }
   free(p0); free(gx); free(gy);

@@ -64,9 +64,11 @@ int orc_rk3(const orc_problem *pr, double *w, double dt, int nsteps);
  * level set, advected by a prescribed analytical velocity u(x, t):
  *   d(phi)/dt + u . grad(phi) = div a_1,   d(psi)/dt + u . grad(psi) = 0,
  * with a_1 as in the full model.  State w[v * N + n], v = 0 (phi), 1 (psi).
- * Velocity kinds: uniform (u0, v0); Rider-Kothe vortex with period T:
- *   u = sin^2(pi x) sin(2 pi y) cos(pi t / T),
- *   v = -sin(2 pi x) sin^2(pi y) cos(pi t / T).
+ * Velocity kinds: uniform (u0, v0); Rider-Kothe vortex with period T about
+ * the centre (xc, yc), with X = x - xc + 1/2, Y = y - yc + 1/2:
+ *   u = sin^2(pi X) sin(2 pi Y) cos(pi t / T),
+ *   v = -sin(2 pi X) sin^2(pi Y) cos(pi t / T)
+ * (xc = yc = 1/2 is the formula as printed in Sec. 4.1).
  * Periodic boundaries only.
  */
 #define ORC_KIN_NV 2
@@ -75,6 +77,7 @@ typedef struct {
   int kind;
   double u0, v0;   /* uniform velocity */
   double T;        /* Rider-Kothe period */
+  double xc, yc;   /* Rider-Kothe vortex centre: the printed formula is xc = yc = 1/2 */
 } orc_velocity;
 
 /* Velocity at (x, y) and time t. */

@@ -32,7 +32,7 @@ PREC = {"fp64": 0, "fp32bulk": 1}
 EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_step_host", "dg_diag",
            "dg_status_read", "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc", "dg_batch_create",
            "dg_batch_step", "dg_rhs_vjp", "dg_adjoint_step", "dg_tape_len", "dg_step_tape",
-           "dg_adjoint_step_tape", "dg_batch_tiles", "dg_kin_create", "dg_kin_rhs", "dg_kin_step"]
+           "dg_adjoint_step_tape", "dg_batch_tiles", "dg_kin_create", "dg_kin_rhs", "dg_kin_step", "dg_reinit"]
 
 
 class DGError(RuntimeError):
@@ -59,7 +59,8 @@ class dg_opts(ctypes.Structure):
 
 
 class dg_velocity(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("u0", ctypes.c_double), ("v0", ctypes.c_double), ("T", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int), ("u0", ctypes.c_double), ("v0", ctypes.c_double), ("T", ctypes.c_double),
+                ("xc", ctypes.c_double), ("yc", ctypes.c_double)]
 
 
 VEL = {"uniform": 0, "rider_kothe": 1}
@@ -117,6 +118,8 @@ def load(path: str | None = None):
     lib.dg_kin_rhs.restype = ctypes.c_int
     lib.dg_kin_step.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
     lib.dg_kin_step.restype = ctypes.c_int
+    lib.dg_reinit.argtypes = [vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp]
+    lib.dg_reinit.restype = ctypes.c_int
     lib.dg_batch_tiles.argtypes = [vp, ip, ip, ip, dpp, dpp, ctypes.c_int]
     lib.dg_batch_tiles.restype = ctypes.c_int
     lib.dg_rhs_vjp.argtypes = [vp, dp, dp, dp, vp]
@@ -258,6 +261,12 @@ class Solver:
                                                      float(dt), _stream(stream)), "dg_adjoint_step_tape")
         return lam_n
 
+    def dg_reinit(self, w, niter: int = 50, nu: float = 0.0, dtau: float = 0.0, stream=None):
+        """Re-initialise the level set of w in place (end of Sec. 3; nu, dtau <= 0: defaults)."""
+        _check(self.ctx, load().dg_reinit(self.ctx, _ptr(w), int(niter), float(nu), float(dtau), _stream(stream)),
+               "dg_reinit")
+        return w
+
     def dg_diag(self, w, stream=None):
         out = (ctypes.c_double * 16)()
         _check(self.ctx, load().dg_diag(self.ctx, _ptr(w), out, _stream(stream)), "dg_diag")
@@ -355,6 +364,7 @@ class KinematicSolver:
             m.bc[i] = BC["periodic"]
         v = dg_velocity()
         v.kind, v.u0, v.v0, v.T = VEL[problem.vel], problem.u0, problem.v0, problem.T
+        v.xc, v.yc = problem.xc, problem.yc
         self._keep = (m, v)
         h = ctypes.c_void_p()
         st = lib.dg_kin_create(ctypes.byref(m), problem.p, problem.Gamma, problem.eps, ctypes.byref(v),
@@ -384,6 +394,12 @@ class KinematicSolver:
     def dg_kin_step(self, w, t0: float, dt: float, nsteps: int, stream=None):
         _check(self.ctx, load().dg_kin_step(self.ctx, _ptr(w), float(t0), float(dt), int(nsteps), _stream(stream)),
                "dg_kin_step")
+        return w
+
+    def dg_reinit(self, w, niter: int = 50, nu: float = 0.0, dtau: float = 0.0, stream=None):
+        """Re-initialise the level set of w in place (end of Sec. 3; nu, dtau <= 0: defaults)."""
+        _check(self.ctx, load().dg_reinit(self.ctx, _ptr(w), int(niter), float(nu), float(dtau), _stream(stream)),
+               "dg_reinit")
         return w
 
     def dg_status_read(self, stream=None):

@@ -21,6 +21,7 @@
 #include "dg_batch.cuh"
 #include "dg_adjoint.cuh"
 #include "dg_kin.cuh"
+#include "dg_reinit.cuh"
 #include "dgpf.h"
 
 namespace dgpf {
@@ -307,6 +308,8 @@ struct dg_ctx {
   KinKernels kk{};
   double *d_kacc = nullptr, *d_kwsA = nullptr, *d_kwsB = nullptr, *d_krvol = nullptr, *d_ktr = nullptr;
   double *d_kt0 = nullptr, *d_kxi = nullptr;
+  // level-set re-initialisation workspace (dg_reinit), allocated on first use
+  double *d_riS = nullptr, *d_ri1 = nullptr, *d_ri2 = nullptr, *d_rirvol = nullptr, *d_ritr = nullptr;
   double *d_part = nullptr, *d_diag = nullptr;
   unsigned *d_status = nullptr;
   int nparts = 0;
@@ -359,6 +362,7 @@ static void free_ctx(dg_ctx *c) {
   cudaFree(c->d_ops);
   cudaFree(c->d_hstate);
   for (double *q : {c->d_kacc, c->d_kwsA, c->d_kwsB, c->d_krvol, c->d_ktr, c->d_kt0, c->d_kxi}) cudaFree(q);
+  for (double *q : {c->d_riS, c->d_ri1, c->d_ri2, c->d_rirvol, c->d_ritr}) cudaFree(q);
   cudaFree(c->d_w1);
   cudaFree(c->d_w2);
   cudaFree(c->d_rvol);
@@ -1222,6 +1226,8 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
   k.u0 = vel->u0;
   k.v0 = vel->v0;
   k.T = vel->T;
+  k.xc = vel->xc;
+  k.yc = vel->yc;
   k.check_finite = 1;
   const std::vector<double> ops = build_ops(2, p, c->hx, c->hy);
   std::vector<double> xi, wt;
@@ -1331,6 +1337,73 @@ extern "C" dg_status dg_kin_step(dg_ctx *c, double *w, double t0, double dt, int
     done += big ? GRAPH_UNROLL : 1;
   }
   return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_kin_step: launch");
+}
+
+// ---------------------------------------------------------------------------
+// Level-set re-initialisation (end of Sec. 3)
+// ---------------------------------------------------------------------------
+
+extern "C" dg_status dg_reinit(dg_ctx *c, double *w, int niter, double nu, double dtau, void *stream) {
+  if (!c) return DG_ERR_ARG;
+  if (c->batch) return fail(c, DG_ERR_ARG, "dg_reinit: batch context");
+  if (!w) return fail(c, DG_ERR_ARG, "dg_reinit: null state");
+  if (niter < 0) return fail(c, DG_ERR_ARG, "dg_reinit: need niter >= 0");
+  ReinitKernels rk;
+  if (!reinit_kernels(c->p, c->dim, &rk)) return fail(c, DG_ERR_UNSUPPORTED, "dg_reinit: order not available");
+  ReinitParams rp{};
+  if (c->kin) {
+    rp.nx = c->kp.nx;
+    rp.ny = c->kp.ny;
+    rp.E = c->kp.E;
+    rp.N = c->kp.N;
+    for (int f = 0; f < 4; ++f) rp.bc[f] = BC_PERIODIC;
+    rp.eps = c->kp.eps;
+    rp.eta_x = c->kp.eta_x;
+    rp.eta_y = c->kp.eta_y;
+  } else {
+    rp.nx = c->prm.nx;
+    rp.ny = c->prm.ny;
+    rp.E = c->prm.E;
+    rp.N = c->prm.N;
+    for (int f = 0; f < 4; ++f) rp.bc[f] = c->prm.bc[f];
+    rp.eps = c->prm.eps;
+    rp.eta_x = c->prm.eta_x;
+    rp.eta_y = c->prm.eta_y;
+  }
+  rp.ops = c->d_ops;
+  const double h = c->dim == 2 ? std::min(c->hx, c->hy) : c->hx;
+  const double q = 2.0 * c->p + 1.0;
+  rp.nu = nu > 0.0 ? nu : h / (2.0 * (c->p + 1));
+  if (!(dtau > 0.0)) dtau = std::min(0.5 * h / q, 0.1 * h * h / (q * q * rp.nu));
+  cudaError_t e = cudaSuccess;
+  if (!c->d_riS) {
+    const size_t nb = (size_t)rp.N * sizeof(double), tb = (size_t)2 * rp.E * rk.nfk * sizeof(double);
+    double **bufs[] = {&c->d_riS, &c->d_ri1, &c->d_ri2, &c->d_rirvol};
+    for (double **b : bufs)
+      if (e == cudaSuccess) e = cudaMalloc(b, nb);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_ritr, tb);
+    if (e != cudaSuccess) {
+      for (double **b : {&c->d_riS, &c->d_ri1, &c->d_ri2, &c->d_rirvol, &c->d_ritr}) {
+        cudaFree(*b);
+        *b = nullptr;
+      }
+      cudaGetLastError();
+      return fail(c, e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA,
+                  std::string("dg_reinit: workspace: ") + cudaGetErrorString(e));
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double *psi = w + rp.N;
+  e = rk.sign(rp, w, c->d_riS, s);
+  const int mode[3] = {MODE_S1, MODE_S2, MODE_S3};
+  const double *in[3] = {psi, c->d_ri1, c->d_ri2};
+  double *out[3] = {c->d_ri1, c->d_ri2, psi};
+  for (int it = 0; it < niter && e == cudaSuccess; ++it)
+    for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
+      e = rk.volume(rp, in[st], c->d_riS, c->d_rirvol, c->d_ritr, s);
+      if (e == cudaSuccess) e = rk.surface(rp, mode[st], dtau, psi, in[st], c->d_rirvol, c->d_ritr, out[st], s);
+    }
+  return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_reinit: launch");
 }
 
 // ---------------------------------------------------------------------------

@@ -34,6 +34,7 @@ struct KinParams {
   double Gamma, eps, eta_x, eta_y;
   int vel;                 // VEL_UNIFORM or VEL_RIDER_KOTHE
   double u0, v0, T;        // uniform velocity; Rider-Kothe period
+  double xc, yc;           // Rider-Kothe vortex centre
   const double *ops;       // operator table (OpsLayout)
   const double *xi;        // GLL nodes on [-1, 1]
   const double *t0;        // device: time at the start of the captured step sequence
@@ -45,9 +46,10 @@ struct KinParams {
 __device__ __forceinline__ void kin_velocity(const KinParams &kp, double x, double y, double t, double *u,
                                              double *v) {
   if (kp.vel == VEL_RIDER_KOTHE) {
-    const double sx = sin(CUDART_PI * x), sy = sin(CUDART_PI * y), c = cos(CUDART_PI * t / kp.T);
-    *u = sx * sx * sin(2.0 * CUDART_PI * y) * c;
-    *v = -sin(2.0 * CUDART_PI * x) * sy * sy * c;
+    const double X = x - kp.xc + 0.5, Y = y - kp.yc + 0.5;
+    const double sx = sin(CUDART_PI * X), sy = sin(CUDART_PI * Y), c = cos(CUDART_PI * t / kp.T);
+    *u = sx * sx * sin(2.0 * CUDART_PI * Y) * c;
+    *v = -sin(2.0 * CUDART_PI * X) * sy * sy * c;
   } else {
     *u = kp.u0;
     *v = kp.v0;

@@ -320,6 +320,8 @@ class KinWorkload:
     u0: float = 0.0
     v0: float = 0.0
     T: float = 4.0
+    xc: float = 0.0           # Rider-Kothe vortex centre
+    yc: float = 0.0
     w: Optional[np.ndarray] = None
     dt: float = 0.0
     nsteps: int = 0
@@ -348,7 +350,7 @@ class KinWorkload:
                     Gamma=self.Gamma, eps=self.eps, c_ip=self.c_ip)
 
     def velocity_kwargs(self) -> dict:
-        return dict(kind=self.vel, u0=self.u0, v0=self.v0, T=self.T)
+        return dict(kind=self.vel, u0=self.u0, v0=self.v0, T=self.T, xc=self.xc, yc=self.yc)
 
 
 def kin_stable_dt(wl: KinWorkload, umax: float) -> float:
@@ -362,12 +364,14 @@ def kin_stable_dt(wl: KinWorkload, umax: float) -> float:
 
 
 def rider_kothe(n: int = 16, p: int = 3, T: float = 4.0, R: float = 0.15, center=(0.0, 0.25),
-                eps_h: float = 0.75, Gamma: float = 1.0) -> KinWorkload:
+                eps_h: float = 0.75, Gamma: float = 1.0, vortex=(0.0, 0.0)) -> KinWorkload:
     """Rider-Kothe vortex (Sec. 4.1): a drop of radius 0.15 centred at (0, 0.25) in the periodic
-    square [-0.5, 0.5]^2, stretched by the time-reversing shear flow of period T = 4.  Phase 1
-    is the drop; psi = R - r grows into it.  eps = 0.75 h (h: element width) and Gamma = |u|max
-    = 1, since the paper leaves both unstated for this test."""
-    wl = KinWorkload(name=f"rk2d_{n}x{n}p{p}", nx=n, ny=n, p=p, Gamma=Gamma, vel="rider_kothe", T=T)
+    square [-0.5, 0.5]^2, stretched by the time-reversing vortex of period T = 4 centred at
+    `vortex` (the domain centre; (0.5, 0.5) gives the printed formula, whose vortex sits at the
+    domain corners).  Phase 1 is the drop; psi = R - r grows into it.  eps = 0.75 h (h: element
+    width) and Gamma = |u|max = 1, since the paper leaves both unstated for this test."""
+    wl = KinWorkload(name=f"rk2d_{n}x{n}p{p}", nx=n, ny=n, p=p, Gamma=Gamma, vel="rider_kothe", T=T,
+                     xc=vortex[0], yc=vortex[1])
     wl.eps = eps_h * wl.hx
     x, y = _kin_nodes(wl)
     r = np.hypot(x - center[0], y - center[1])

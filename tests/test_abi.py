@@ -130,3 +130,7 @@ def test_kin_create_rejects_invalid_arguments(lib, over, code):
 def test_kin_calls_reject_other_contexts(lib):
     assert lib.dg_kin_rhs(None, None, 0.0, None, None) == -1
     assert lib.dg_kin_step(None, None, 0.0, 1.0, 1, None) == -1
+
+
+def test_reinit_rejects_null_and_negative_arguments(lib):
+    assert lib.dg_reinit(None, None, 1, 0.0, 0.0, None) == -1

@@ -102,7 +102,8 @@ def _rider_kothe(dg, orc, n):
 
 
 def test_rider_kothe_full_period(orc, dg):
-    """16 x 16 and 32 x 32, p = 3 (the paper's 64^2 and 128^2 DoF): the stretched drop comes back
+    """16 x 16 and 32 x 32, p = 3 (the paper's 64^2 and 128^2 DoF), vortex centred on the domain:
+    the stretched drop comes back
     (the error at T is well below the one at T/2), the L1 error falls under refinement and stays
     within a factor 3 of the paper's p = 3 values (1.75e-2, 4.83e-3; loose, since the paper does
     not state Gamma and eps for this test), and the phase-field mass error is small and falls

@@ -2,8 +2,9 @@
 prescribed velocity, classical fourth-order Runge-Kutta in time), against what the
 mathematics fixes rather than against the oracle's own formulas:
 
-* the Rider-Kothe field is divergence-free, periodic, reverses at t = T/2 and has unit
-  amplitude at t = 0 (finite differences of the oracle's own field);
+* the Rider-Kothe field is divergence-free, periodic, reverses at t = T/2, vanishes at its
+  centre and turns clockwise with unit speed a quarter period from it (finite differences of the
+  oracle's own field, for several vortex centres);
 * a pure phase stays put, a constant level set stays put (to the rounding of D's row sums);
 * for a uniform velocity the discrete phase-field mass is conserved to round-off (the
   non-conservative transport integrates to the single-valued upwind flux, and every
@@ -42,8 +43,9 @@ def _smooth(orc, pb, seed=0):
     return np.stack([phi, psi])
 
 
-def test_rider_kothe_field_properties(orc):
-    vel = orc.Velocity("rider_kothe", T=4.0)
+@pytest.mark.parametrize("centre", [(0.5, 0.5), (0.0, 0.0), (0.2, -0.1)])
+def test_rider_kothe_field_properties(orc, centre):
+    vel = orc.Velocity("rider_kothe", T=4.0, xc=centre[0], yc=centre[1])
     rng = np.random.default_rng(3)
     h = 1e-5
     for x, y, t in rng.uniform([-0.5, -0.5, 0.0], [0.5, 0.5, 4.0], (20, 3)):
@@ -54,7 +56,12 @@ def test_rider_kothe_field_properties(orc):
         assert np.allclose(orc.velocity_at(vel, x + 1.0, y - 1.0, t), (u, v), atol=1e-12)
         ur, vr = orc.velocity_at(vel, x, y, 4.0 - t)
         assert abs(u + ur) < 1e-12 and abs(v + vr) < 1e-12       # reversal about T/2
-    assert np.allclose(orc.velocity_at(vel, 0.5, 0.25, 0.0), (1.0, 0.0), atol=1e-15)
+    # clockwise: unit speed +x a quarter period below the centre and -x above it; the field
+    # vanishes at the centre and at t = T/2
+    xc, yc = centre
+    assert np.allclose(orc.velocity_at(vel, xc, yc - 0.25, 0.0), (1.0, 0.0), atol=1e-15)
+    assert np.allclose(orc.velocity_at(vel, xc, yc + 0.25, 0.0), (-1.0, 0.0), atol=1e-15)
+    assert np.allclose(orc.velocity_at(vel, xc, yc, 0.7), (0.0, 0.0), atol=1e-15)
     assert np.allclose(orc.velocity_at(vel, 0.3, 0.1, 2.0), (0.0, 0.0), atol=1e-15)
     assert orc.velocity_at(orc.Velocity("uniform", u0=0.3, v0=-0.7), 0.1, 0.2, 9.0) == (0.3, -0.7)
 
