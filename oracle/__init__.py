@@ -25,7 +25,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dg_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-BC = {"periodic": 0, "noslip": 1, "slip": 2}
+BC = {"periodic": 0, "noslip": 1, "slip": 2, "pressure": 3}
 NV = 7
 
 
@@ -53,6 +53,7 @@ class _Problem(ctypes.Structure):
         ("sigma", ctypes.c_double), ("g", ctypes.c_double * 2),
         ("Gamma", ctypes.c_double), ("eps", ctypes.c_double), ("c_ip", ctypes.c_double),
         ("viscous", ctypes.c_int), ("gravity", ctypes.c_int), ("surface_tension", ctypes.c_int),
+        ("p_bc", ctypes.c_double * 4),
     ]
 
 
@@ -80,6 +81,7 @@ class Problem:
     viscous: bool = False
     gravity: bool = False
     surface_tension: bool = False
+    p_bc: tuple = (0.0, 0.0, 0.0, 0.0)
 
     @property
     def Np(self) -> int:
@@ -100,6 +102,8 @@ class Problem:
             s.rho0[i], s.mu[i], s.g[i] = self.rho0[i], self.mu[i], self.g[i]
         s.sigma, s.Gamma, s.eps, s.c_ip = self.sigma, self.Gamma, self.eps, self.c_ip
         s.viscous, s.gravity, s.surface_tension = int(self.viscous), int(self.gravity), int(self.surface_tension)
+        for i in range(4):
+            s.p_bc[i] = self.p_bc[i]
         return s
 
 

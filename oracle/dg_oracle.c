@@ -51,6 +51,12 @@
  *   - walls: ghost state equal to the own state with the velocity (no-slip)
  *     or its normal component (slip) reversed; ghost gradients equal the own
  *     ones; no a_1 flux crosses a wall;
+ *   - the Riemann-invariant boundary "with zero velocity and constant
+ *     pressure" (Sec. 4.2): the exterior state of the boundary Riemann problem
+ *     holds the own phi, psi and partial densities at rest at the prescribed
+ *     pressure (rho E from the stiffened-gas relation), and the
+ *     Lax-Friedrichs flux between the two states carries it in; gradients and
+ *     a_1 are treated as at a wall;
  *   - kinematic mode: the velocity is the analytical field sampled at the
  *     nodes, and the characteristic speed of the transport flux is the
  *     advection speed alone, lambda = max(|u-.m|, |u+.m|) (there is no sound
@@ -177,7 +183,7 @@ static int check_problem(const orc_problem *pr) {
   if (!(pr->x1 > pr->x0)) return -1;
   if (pr->dim == 2 && !(pr->y1 > pr->y0)) return -1;
   for (int f = 0; f < 4; ++f)
-    if (pr->bc[f] < ORC_BC_PERIODIC || pr->bc[f] > ORC_BC_SLIP) return -1;
+    if (pr->bc[f] < ORC_BC_PERIODIC || pr->bc[f] > ORC_BC_PRESSURE) return -1;
   if ((pr->bc[0] == ORC_BC_PERIODIC) != (pr->bc[1] == ORC_BC_PERIODIC)) return -1;
   if (pr->dim == 2 && (pr->bc[2] == ORC_BC_PERIODIC) != (pr->bc[3] == ORC_BC_PERIODIC)) return -1;
   for (int l = 0; l < 2; ++l)
@@ -551,7 +557,13 @@ int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double
         } else {
           ghost = *tm;
           int slip = pr->bc[f] == ORC_BC_SLIP;
-          if (slip) {
+          if (pr->bc[f] == ORC_BC_PRESSURE) {
+            /* exterior state at rest at p_bc: rho e = P (sum phi_l g_l) + sum phi_l C_l */
+            double ph1 = tm->q.phi, ph2 = 1.0 - tm->q.phi;
+            double wn[NV] = {tm->q.phi, tm->q.psi, tm->q.m1, tm->q.m2, 0.0, 0.0,
+                             pr->p_bc[f] * (ph1 * g.gi[0] + ph2 * g.gi[1]) + (ph1 * g.C[0] + ph2 * g.C[1])};
+            closure(&g, wn, &ghost.q);
+          } else if (slip) {
             double un = tm->q.ru * m[0] + tm->q.rv * m[1];
             ghost.q.ru = tm->q.ru - 2.0 * un * m[0];
             ghost.q.rv = tm->q.rv - 2.0 * un * m[1];

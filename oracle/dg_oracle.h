@@ -23,7 +23,7 @@ extern "C" {
 
 #define ORC_NV 7
 enum { ORC_PHI = 0, ORC_PSI = 1, ORC_M1 = 2, ORC_M2 = 3, ORC_RU = 4, ORC_RV = 5, ORC_RE = 6 };
-enum { ORC_BC_PERIODIC = 0, ORC_BC_NOSLIP = 1, ORC_BC_SLIP = 2 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_NOSLIP = 1, ORC_BC_SLIP = 2, ORC_BC_PRESSURE = 3 };
 
 typedef struct {
   int dim;            /* 1 or 2 */
@@ -37,6 +37,7 @@ typedef struct {
   double Gamma, eps;  /* Allen-Cahn velocity scale and interface thickness */
   double c_ip;        /* interior-penalty constant: eta = c_ip (p+1)^2 / h */
   int viscous, gravity, surface_tension;
+  double p_bc[4];     /* exterior pressure of ORC_BC_PRESSURE sides */
 } orc_problem;
 
 /* GLL nodes xi[0..p] (ascending) and weights wt[0..p] on [-1, 1]. */
