@@ -53,17 +53,27 @@ typedef enum {
   DG_ERR_UNSUPPORTED = -7   /* valid request this build does not provide */
 } dg_status;
 
-enum { DG_BC_PERIODIC = 0, DG_BC_NOSLIP = 1, DG_BC_SLIP = 2 };
+enum { DG_BC_PERIODIC = 0, DG_BC_NOSLIP = 1, DG_BC_SLIP = 2, DG_BC_PRESSURE = 3 };
 enum { DG_FP64 = 0, DG_FP32_BULK = 1 };
 
 /* Cartesian mesh of nx * ny elements on [x0,x1] x [y0,y1] (dim = 2) or nx
    segments on [x0,x1] (dim = 1, ny must be 1).  bc = west, east, south, north;
-   periodic sides must be paired.  The paper's element partition (Sec. 3). */
+   periodic sides must be paired.  The paper's element partition (Sec. 3).
+   Boundaries (Sec. 4.2): DG_BC_NOSLIP and DG_BC_SLIP walls (ghost state = own
+   state with the velocity, or its normal component, reversed), and
+   DG_BC_PRESSURE, the Riemann-invariant boundary "with zero velocity and
+   constant pressure" of the Rayleigh-Taylor and rising-bubble tests: the
+   exterior state of the boundary Riemann problem is the own phase field,
+   level set and partial densities at rest at pressure p_bc[side], and the
+   Lax-Friedrichs flux between the two carries it in.  No a_1 flux crosses a
+   wall or a pressure boundary, and ghost gradients equal the own ones.
+   p_bc is read for DG_BC_PRESSURE sides only. */
 typedef struct {
   int dim;
   int nx, ny;
   double x0, x1, y0, y1;
   int bc[4];
+  double p_bc[4];
 } dg_mesh;
 
 /* Phase constants of the stiffened-gas closure (Sec. 2): gamma_l, Pinf_l, the

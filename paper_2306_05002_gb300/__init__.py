@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libdgpf.so")
 DG_OK = 0
 STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_CUDA", -3: "DG_ERR_OOM", -4: "DG_ERR_TIMEOUT",
           -5: "DG_ERR_NONFINITE", -6: "DG_ERR_NONPHYSICAL", -7: "DG_ERR_UNSUPPORTED"}
-BC = {"periodic": 0, "noslip": 1, "slip": 2}
+BC = {"periodic": 0, "noslip": 1, "slip": 2, "pressure": 3}
 PREC = {"fp64": 0, "fp32bulk": 1}
 
 # Every exported symbol of include/dgpf.h.
@@ -44,7 +44,7 @@ class DGError(RuntimeError):
 class dg_mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
-                ("bc", ctypes.c_int * 4)]
+                ("bc", ctypes.c_int * 4), ("p_bc", ctypes.c_double * 4)]
 
 
 class dg_eos(ctypes.Structure):
@@ -158,12 +158,13 @@ def _stream(stream=None):
 
 def make_structs(dim, nx, ny, x0, x1, y0, y1, bc, gamma, pinf, rho0, mu=(0.0, 0.0), sigma=0.0, g=(0.0, 0.0),
                  precision="fp64", c_ip=1.0, viscous=False, gravity=False, surface_tension=False,
-                 check_finite=True, **_ignored):
+                 check_finite=True, p_bc=(0.0, 0.0, 0.0, 0.0), **_ignored):
     m = dg_mesh()
     m.dim, m.nx, m.ny = dim, nx, ny
     m.x0, m.x1, m.y0, m.y1 = x0, x1, y0, y1
     for i, b in enumerate(bc):
         m.bc[i] = BC[b] if isinstance(b, str) else int(b)
+        m.p_bc[i] = float(p_bc[i])
     e = dg_eos()
     for i in range(2):
         e.gamma[i], e.pinf[i], e.rho0[i], e.mu[i], e.g[i] = gamma[i], pinf[i], rho0[i], mu[i], g[i]

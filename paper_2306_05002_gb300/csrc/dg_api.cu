@@ -398,7 +398,9 @@ static const char *check_problem(const dg_mesh *mesh, int p, const dg_eos *eos, 
   if (mesh->nx < 1 || mesh->ny < 1 || (mesh->dim == 1 && mesh->ny != 1)) return "bad element counts (1D needs ny = 1)";
   if (!(mesh->x1 > mesh->x0) || (mesh->dim == 2 && !(mesh->y1 > mesh->y0))) return "empty domain";
   for (int f = 0; f < 4; ++f)
-    if (mesh->bc[f] < DG_BC_PERIODIC || mesh->bc[f] > DG_BC_SLIP) return "unknown boundary condition";
+    if (mesh->bc[f] < DG_BC_PERIODIC || mesh->bc[f] > DG_BC_PRESSURE) return "unknown boundary condition";
+  for (int f = 0; f < 4; ++f)
+    if (mesh->bc[f] == DG_BC_PRESSURE && !std::isfinite(mesh->p_bc[f])) return "pressure boundary needs a finite p_bc";
   if ((mesh->bc[0] == DG_BC_PERIODIC) != (mesh->bc[1] == DG_BC_PERIODIC) ||
       (mesh->dim == 2 && (mesh->bc[2] == DG_BC_PERIODIC) != (mesh->bc[3] == DG_BC_PERIODIC)))
     return "periodic sides must be paired";
@@ -452,7 +454,10 @@ static Params make_params(const dg_mesh *mesh, int p, const dg_eos *eos, double 
   q.ny = mesh->ny;
   q.E = mesh->nx * mesh->ny;
   q.N = q.E * Np;
-  for (int f = 0; f < 4; ++f) q.bc[f] = mesh->bc[f];
+  for (int f = 0; f < 4; ++f) {
+    q.bc[f] = mesh->bc[f];
+    q.p_bc[f] = mesh->bc[f] == DG_BC_PRESSURE ? mesh->p_bc[f] : 0.0;
+  }
   q.C1 = eos->gamma[0] * eos->pinf[0] / (eos->gamma[0] - 1.0);
   q.C2 = eos->gamma[1] * eos->pinf[1] / (eos->gamma[1] - 1.0);
   q.g1 = 1.0 / (eos->gamma[0] - 1.0);
@@ -526,7 +531,10 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
   }
 
   // The discrete adjoint covers the FP64 inviscid equations without surface tension.
-  c->has_adj = c->prec == DG_FP64 && !o.viscous && !o.surface_tension && adj_kernels(p, c->dim, &c->adj);
+  bool pressure_bc = false;
+  for (int f = 0; f < 4; ++f) pressure_bc |= mesh->bc[f] == DG_BC_PRESSURE;
+  c->has_adj = c->prec == DG_FP64 && !o.viscous && !o.surface_tension && !pressure_bc &&
+               adj_kernels(p, c->dim, &c->adj);
   const std::vector<double> ops = build_ops(c->dim, p, c->hx, c->hy);
   c->prm = make_params(mesh, p, eos, Gamma, eps, o, c->hx, c->hy);
   Params &q = c->prm;

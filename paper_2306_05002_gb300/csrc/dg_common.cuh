@@ -15,7 +15,7 @@ enum Var { PHI = 0, PSI = 1, M1 = 2, M2 = 3, RU = 4, RV = 5, RE = 6 };
 // What the surface kernel writes: the right-hand side itself, or one stage
 // of the three-stage SSP Runge-Kutta method in Shu-Osher form.
 enum Mode { MODE_RHS = 0, MODE_S1 = 1, MODE_S2 = 2, MODE_S3 = 3 };
-enum { BC_PERIODIC = 0, BC_NOSLIP = 1, BC_SLIP = 2 };
+enum { BC_PERIODIC = 0, BC_NOSLIP = 1, BC_SLIP = 2, BC_PRESSURE = 3 };
 
 // Face-trace record written by the volume kernel for every face node
 // (element-major, one record per (element, face, node along the face)).
@@ -36,6 +36,7 @@ constexpr unsigned STATUS_NONPHYSICAL = 2u;
 struct Params {
   int nx, ny, E, N;          // elements per direction, elements, nodes
   int bc[4];                 // west, east, south, north
+  double p_bc[4];            // exterior pressure of BC_PRESSURE sides
   // stiffened-gas closure (Sec. 2): C_l = gamma_l Pinf_l/(gamma_l-1), g_l = 1/(gamma_l-1),
   // B = rho_1 H_1 - rho_2 H_2 = P * Bp + dC
   double C1, C2, g1, g2, Bp, dC;

@@ -410,6 +410,11 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
       if (prm.bc[f] == BC_SLIP) {
         if (xf) { Tp[T_RU] = -Tm[T_RU]; Tp[T_U] = -Tm[T_U]; }
         else    { Tp[T_RV] = -Tm[T_RV]; Tp[T_V] = -Tm[T_V]; }
+      } else if (prm.bc[f] == BC_PRESSURE) {
+        // exterior state at rest at p_bc: the reduced energy is p_bc times the mixture 1/(gamma-1)
+        Tp[T_RU] = Tp[T_RV] = 0.f;
+        Tp[T_RE] = (float)prm.p_bc[f] * fmaf(Tp[T_PHI], pf.g1 - pf.g2, pf.g2);
+        trace_derive<DIM, VISC>(pf, Tp);
       } else {
         Tp[T_RU] = -Tm[T_RU]; Tp[T_U] = -Tm[T_U];
         Tp[T_RV] = -Tm[T_RV]; Tp[T_V] = -Tm[T_V];

@@ -319,6 +319,20 @@ k_surface(const Params prm, int mode, double dt, const double *__restrict__ w0, 
       if (bc == BC_SLIP) {  // reverse the normal component only
         if (xf) { Tp[T_RU] = -Tm[T_RU]; Tp[T_U] = -Tm[T_U]; }
         else    { Tp[T_RV] = -Tm[T_RV]; Tp[T_V] = -Tm[T_V]; }
+      } else if (bc == BC_PRESSURE) {
+        // exterior state: own phase field and partial densities, at rest, at p_bc;
+        // rho E from the stiffened-gas relation, then the closure of that state
+        const double phi = Tm[T_PHI], phi2 = __dsub_rn(1.0, phi);
+        const double den0 = __dadd_rn(__dmul_rn(phi, prm.g1), __dmul_rn(phi2, prm.g2));
+        const double Cm0 = __dadd_rn(__dmul_rn(phi, prm.C1), __dmul_rn(phi2, prm.C2));
+        const double rho = Tm[T_M1] + Tm[T_M2];
+        Tp[T_RU] = Tp[T_RV] = Tp[T_U] = Tp[T_V] = 0.0;
+        Tp[T_RE] = __dadd_rn(__dmul_rn(prm.p_bc[f], den0), Cm0);
+        double Cm, den;
+        const double Pg = sg_pressure(prm, phi, rho, 0.0, 0.0, Tp[T_RE], &Cm, &den);
+        Tp[T_P] = Pg;
+        Tp[T_C] = sqrt((Pg + (Pg + Cm) / den) / rho);
+        Tp[T_B] = fma(Pg, prm.Bp, prm.dC);
       } else {              // no-slip: reverse the velocity
         Tp[T_RU] = -Tm[T_RU]; Tp[T_U] = -Tm[T_U];
         Tp[T_RV] = -Tm[T_RV]; Tp[T_V] = -Tm[T_V];

@@ -55,6 +55,7 @@ class Workload:
     viscous: bool = False
     gravity: bool = False
     surface_tension: bool = False
+    p_bc: tuple = (0.0, 0.0, 0.0, 0.0)  # exterior pressure of "pressure" sides
     w: Optional[np.ndarray] = None   # (7, N) float64
     dt: float = 0.0
     nsteps: int = 0
@@ -83,7 +84,7 @@ class Workload:
     def problem_kwargs(self) -> dict:
         """Fields shared by the oracle's and the library's problem descriptions."""
         keys = ["dim", "nx", "ny", "p", "x0", "x1", "y0", "y1", "bc", "gamma", "pinf", "rho0", "mu",
-                "sigma", "g", "Gamma", "eps", "c_ip", "viscous", "gravity", "surface_tension"]
+                "sigma", "g", "Gamma", "eps", "c_ip", "viscous", "gravity", "surface_tension", "p_bc"]
         return {k: getattr(self, k) for k in keys}
 
 
@@ -233,6 +234,36 @@ def rayleigh_taylor(n: int = 256, p: int = 4, seed: int = 3, nsteps: int = 2000,
     wl.w = conserved(wl, phi, s, P, 0.0, 0.0)
     wl.dt = stable_dt(wl, 0.0, P_top)
     wl.meta = dict(P_top=P_top, a=a.tolist(), theta=theta.tolist(), seed=seed)
+    return wl
+
+
+def rayleigh_taylor_paper(nx: int = 10, ny: int = 40, p: int = 4, P_top: float = 1e5, eps_h: float = 0.75,
+                          Gamma: float = 2.21, Re: float = 3000.0) -> Workload:
+    """The paper's Rayleigh-Taylor domain (Sec. 4.2): [0, d] x [0, 4d], d = 1, interface
+    y = 2 + 0.1 cos(2 pi x), Atwood 0.5 (density ratio 3, heavy phase 1 on top), Re = 3000,
+    gravity -9.81; no-slip bottom, slip sides, and the Riemann-invariant top boundary at rest at
+    the hydrostatic top pressure.  Liquid-liquid closure as in `rayleigh_taylor`; no surface
+    tension (the paper names none for this test)."""
+    g = 9.81
+    rho1, rho2 = 3000.0, 1000.0
+    mu = rho1 * np.sqrt(g) / Re
+    wl = Workload(name=f"rtp2d_{nx}x{ny}p{p}", dim=2, nx=nx, ny=ny, p=p, x0=0.0, x1=1.0, y0=0.0, y1=4.0,
+                  bc=("slip", "slip", "noslip", "pressure"), p_bc=(0.0, 0.0, 0.0, P_top),
+                  gamma=(4.4, 4.4), pinf=(6e8, 6e8), rho0=(rho1, rho2), mu=(mu, mu), g=(0.0, -g),
+                  Gamma=Gamma, viscous=True, gravity=True)
+    wl.eps = eps_h * min(wl.hx, wl.hy)
+    x, y = node_coords(wl)
+    s = y - (2.0 + 0.1 * np.cos(2 * np.pi * x))   # grows into the heavy upper phase 1
+    phi = tanh_profile(s, wl.eps)
+    eta = 2.0 + 0.1 * np.cos(2 * np.pi * x)
+    def F(yy):  # antiderivative of phi along y
+        z = (yy - eta) / (2.0 * wl.eps)
+        az = np.abs(z)
+        return 0.5 * yy + wl.eps * (az + np.log1p(np.exp(-2.0 * az)) - np.log(2.0))
+    P = P_top + g * (rho2 * (4.0 - y) + (rho1 - rho2) * (F(4.0) - F(y)))
+    wl.w = conserved(wl, phi, s, P, 0.0, 0.0)
+    wl.dt = stable_dt(wl, 0.0, P_top)
+    wl.meta = dict(P_top=P_top)
     return wl
 
 

@@ -58,6 +58,7 @@ def _args(**over):
     (dict(dim=1, ny=2), -1),
     (dict(x1=0.0), -1),
     (dict(bc=("periodic", "noslip", "periodic", "periodic")), -1),
+    (dict(bc=("noslip", "noslip", "noslip", "pressure"), p_bc=(0.0, 0.0, 0.0, float("nan"))), -1),
     (dict(gamma=(1.0, 1.4)), -1),
     (dict(Gamma=-1.0), -1),
 ])

@@ -200,3 +200,16 @@ def test_level_set_parameter_gradient_against_oracle(orc, dg):
                         target)[0]
         fd[k] = (Jp - Jm) / (2 * h)
     np.testing.assert_allclose(grad, fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
+
+
+def test_adjoint_rejects_pressure_boundary(dg):
+    """The discrete adjoint covers periodic and wall boundaries; a pressure boundary is refused."""
+    import torch
+    wl = W.rayleigh_taylor_paper(nx=2, ny=4, p=2)
+    wl.viscous = False
+    s = dg.Solver(wl)
+    w = torch.from_numpy(wl.w.copy()).cuda()
+    with pytest.raises(dg.DGError):
+        s.dg_rhs_vjp(w, w.clone())
+    s.close()
+

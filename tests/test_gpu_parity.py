@@ -106,6 +106,36 @@ def test_rhs_walls(orc, dg, bc):
     _assert_parity(*_rhs_both(orc, dg, wl, _broken(wl)))
 
 
+@pytest.mark.parametrize("side", [0, 3])
+def test_rhs_pressure_boundary(orc, dg, side):
+    """The Riemann-invariant boundary at rest at constant pressure (Sec. 4.2) on one side, walls
+    elsewhere, with a moving, discontinuous state and a pressure different from the interior."""
+    bc = ["slip"] * 4
+    bc[side] = "pressure"
+    pbc = [0.0] * 4
+    pbc[side] = 0.9e5
+    wl = W.Workload(name="pbox", dim=2, nx=5, ny=4, p=3, bc=tuple(bc), p_bc=tuple(pbc), Gamma=1.0, eps=0.05)
+    x, y = W.node_coords(wl)
+    u = 0.3 + np.sin(np.pi * x) * np.cos(np.pi * y)
+    v = -0.2 - np.cos(np.pi * x) * np.sin(np.pi * y)
+    s = np.hypot(x - 0.4, y - 0.55) - 0.2
+    wl.w = W.conserved(wl, W.tanh_profile(s, wl.eps), s, 1e5, u, v)
+    _assert_parity(*_rhs_both(orc, dg, wl, _broken(wl)))
+
+
+def test_rhs_paper_rayleigh_taylor_domain(orc, dg):
+    """The paper's Rayleigh-Taylor domain [0, 1] x [0, 4]: slip sides, no-slip bottom, pressure
+    top, viscous stress and gravity."""
+    wl = W.rayleigh_taylor_paper(nx=4, ny=12, p=3)
+    _assert_parity(*_rhs_both(orc, dg, wl, _broken(wl)))
+
+
+def test_step_paper_rayleigh_taylor_domain(orc, dg):
+    wl = W.rayleigh_taylor_paper(nx=4, ny=12, p=3)
+    w, w_ref = _step_both(orc, dg, wl, 5)
+    _assert_steps_close(orc, wl, 5, w, w_ref)
+
+
 @pytest.mark.parametrize("visc,st,grav", [(True, False, False), (False, True, False), (False, False, True),
                                           (True, True, True)])
 def test_rhs_physics_terms(orc, dg, visc, st, grav):
