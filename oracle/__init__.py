@@ -23,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dg_oracle.c")
+_SRC_TRI = os.path.join(_HERE, "dg_oracle_tri.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 BC = {"periodic": 0, "noslip": 1, "slip": 2, "pressure": 3}
@@ -32,12 +33,12 @@ NV = 7
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/liboracle.so`` (gcc, FP64, no FMA contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "dg_oracle.h"))
+        os.path.getmtime(_SRC), os.path.getmtime(_SRC_TRI), os.path.getmtime(os.path.join(_HERE, "dg_oracle.h"))
     ):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(
             ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC", "-shared",
-             "-o", tmp, _SRC, "-lm"]
+             "-o", tmp, _SRC, _SRC_TRI, "-lm"]
         )
         os.replace(tmp, _LIB)
     return _LIB
@@ -155,6 +156,13 @@ def lib():
         _lib.orc_velocity_at.restype = None
         _lib.orc_kin_rhs.argtypes = [pp, vp, ctypes.c_double, dp, dp, dp]
         _lib.orc_kin_rk4.argtypes = [pp, vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        _lib.orc_tri_num_nodes.argtypes = [pp]
+        _lib.orc_tri_num_nodes.restype = ctypes.c_long
+        _lib.orc_tri_nodes.argtypes = [pp, dp, dp]
+        _lib.orc_tri_integral.argtypes = [pp, dp, dp]
+        _lib.orc_tri_mass.argtypes = [pp, ctypes.c_int, dp]
+        _lib.orc_tri_rhs.argtypes = [pp, vp, ctypes.c_double, dp, dp, dp]
+        _lib.orc_tri_rk4.argtypes = [pp, vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
         _lib.orc_reinit_sign.argtypes = [pp, dp, dp]
         _lib.orc_reinit_rhs.argtypes = [pp, dp, dp, ctypes.c_double, dp]
         _lib.orc_reinit.argtypes = [pp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
@@ -289,4 +297,53 @@ def reinit(pb: Problem, phi, niter: int, nu: float, dtau: float):
     s = pb._c()
     _check(lib().orc_reinit(ctypes.byref(s), _ptr(phi), _ptr(psi), int(niter), float(nu), float(dtau)), "reinit")
     return psi
+
+
+def tri_num_nodes(pb: Problem) -> int:
+    return int(lib().orc_tri_num_nodes(ctypes.byref(pb._c())))
+
+
+def tri_nodes(pb: Problem):
+    """Node coordinates of the triangulated mesh (kinematic mode on triangles)."""
+    N = tri_num_nodes(pb)
+    x, y = np.zeros(N), np.zeros(N)
+    s = pb._c()
+    _check(lib().orc_tri_nodes(ctypes.byref(s), _ptr(x), _ptr(y)), "tri_nodes")
+    return x, y
+
+
+def tri_integral(pb: Problem, f) -> float:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = ctypes.c_double()
+    s = pb._c()
+    _check(lib().orc_tri_integral(ctypes.byref(s), _ptr(f), ctypes.byref(out)), "tri_integral")
+    return out.value
+
+
+def tri_mass(pb: Problem, e: int):
+    """Mass matrix int l_i l_j of triangle e."""
+    Np = (pb.p + 1) * (pb.p + 2) // 2
+    M = np.zeros((Np, Np))
+    s = pb._c()
+    _check(lib().orc_tri_mass(ctypes.byref(s), int(e), _ptr(M)), "tri_mass")
+    return M
+
+
+def tri_rhs(pb: Problem, vel: Velocity, t: float, w, want_scale: bool = False):
+    N = tri_num_nodes(pb)
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(2, N)
+    L = np.zeros((2, N))
+    S = np.zeros((2, N)) if want_scale else None
+    s, c = pb._c(), vel._c()
+    _check(lib().orc_tri_rhs(ctypes.byref(s), ctypes.byref(c), float(t), _ptr(w), _ptr(L), _ptr(S)), "tri_rhs")
+    return (L, S) if want_scale else L
+
+
+def tri_rk4(pb: Problem, vel: Velocity, w, t0: float, dt: float, nsteps: int):
+    N = tri_num_nodes(pb)
+    w = np.array(w, dtype=np.float64).reshape(2, N).copy()
+    s, c = pb._c(), vel._c()
+    _check(lib().orc_tri_rk4(ctypes.byref(s), ctypes.byref(c), _ptr(w), float(t0), float(dt), int(nsteps)),
+           "tri_rk4")
+    return w
 

@@ -90,6 +90,22 @@ int orc_kin_rhs(const orc_problem *pr, const orc_velocity *vel, double t, const 
 int orc_kin_rk4(const orc_problem *pr, const orc_velocity *vel, double *w, double t0, double dt, int nsteps);
 
 /*
+ * Kinematic mode on triangles (the paper's mesh (b)): each Cartesian cell of
+ * the periodic rectangle split along its rising diagonal into two
+ * counter-clockwise triangles (element 2 (i + nx j) + type, type 0 = lower
+ * right, 1 = upper left), nodal basis of degree p <= 4 on equispaced nodes,
+ * collapsed Gauss-Legendre volume rule of (p+2)^2 points, (p+2)-point edge
+ * rule, full element mass matrix; see dg_oracle_tri.c.  State (2, N) with
+ * N = 2 nx ny (p+1)(p+2)/2.  Uses dim, nx, ny, p, domain, Gamma, eps, c_ip.
+ */
+long orc_tri_num_nodes(const orc_problem *pr);
+int orc_tri_nodes(const orc_problem *pr, double *x, double *y);
+int orc_tri_integral(const orc_problem *pr, const double *f, double *out);
+int orc_tri_mass(const orc_problem *pr, int e, double *M);
+int orc_tri_rhs(const orc_problem *pr, const orc_velocity *vel, double t, const double *w, double *L, double *S);
+int orc_tri_rk4(const orc_problem *pr, const orc_velocity *vel, double *w, double t0, double dt, int nsteps);
+
+/*
  * Level-set re-initialisation (end of Sec. 3): the pseudo-time equation
  *   d(psi)/d(tau) = S (1 - |grad psi|) + div(nu grad psi),   psi(0) = psi0 = phi - 1/2,
  * (the sign under which |grad psi| relaxes to 1; the paper prints the
