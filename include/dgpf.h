@@ -67,14 +67,22 @@ enum { DG_FP64 = 0, DG_FP32_BULK = 1 };
    level set and partial densities at rest at pressure p_bc[side], and the
    Lax-Friedrichs flux between the two carries it in.  No a_1 flux crosses a
    wall or a pressure boundary, and ghost gradients equal the own ones.
-   p_bc is read for DG_BC_PRESSURE sides only. */
+   p_bc is read for DG_BC_PRESSURE sides only.
+   elem: DG_ELEM_QUAD (0, the default of a zeroed struct) for the nx x ny
+   rectangles (the paper's mesh (a)); DG_ELEM_TRI (1) splits every rectangle
+   along its rising diagonal into two triangles, the paper's mesh (b), Sec. 4.1
+   -- the kinematic mode only (dg_kin_create); the full-model calls reject it
+   with DG_ERR_UNSUPPORTED. */
 typedef struct {
   int dim;
   int nx, ny;
   double x0, x1, y0, y1;
   int bc[4];
   double p_bc[4];
+  int elem;
 } dg_mesh;
+
+enum { DG_ELEM_QUAD = 0, DG_ELEM_TRI = 1 };
 
 /* Phase constants of the stiffened-gas closure (Sec. 2): gamma_l, Pinf_l, the
    reference densities rho_l^(0) of R_l = rho_l^(0) a_l, viscosities mu_l
@@ -265,12 +273,30 @@ typedef struct {
 } dg_velocity;
 
 /* Create a kinematic-mode context: 2D mesh with periodic boundaries on all
-   four sides, order p (1..5), Allen-Cahn Gamma >= 0 and eps >= 0, velocity,
-   interior-penalty constant c_ip (<= 0 selects 1).  dg_state_len gives 2 N;
-   dg_destroy releases it; the single-problem and batch calls of the full
-   model reject it (DG_ERR_ARG).  Errors as dg_create. */
+   four sides, order p (1..5 on rectangles, 1..4 on triangles), Allen-Cahn
+   Gamma >= 0 and eps >= 0, velocity, interior-penalty constant c_ip (<= 0
+   selects 1).  dg_state_len gives 2 N; dg_destroy releases it; the
+   single-problem and batch calls of the full model reject it (DG_ERR_ARG).
+   Errors as dg_create.
+   Rectangles (DG_ELEM_QUAD): GLL nodes, collocated quadrature, penalty
+   eta = c_ip (p+1)^2 / h.  Triangles (DG_ELEM_TRI, the paper's mesh (b)):
+   triangle 2 (i + nx j) + t of cell (i, j) has the counter-clockwise vertices
+   (x_i, y_j), (x_i+1, y_j), (x_i+1, y_j+1) for t = 0 and (x_i, y_j),
+   (x_i+1, y_j+1), (x_i, y_j+1) for t = 1; a nodal basis of degree p on the
+   (p+1)(p+2)/2 equispaced nodes of each triangle (see dg_kin_nodes), volume
+   integrals by the collapsed Gauss-Legendre rule of (p+2)^2 points, edge
+   integrals by (p+2)-point Gauss-Legendre, the full element mass matrix,
+   penalty eta = c_ip (p+1)(p+2) / h_e with h_e = 2 |T| / |e|. */
 dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, double eps, const dg_velocity *vel, double c_ip,
                         dg_ctx **out);
+
+/* Node coordinates of the kinematic-mode state of mesh and order p (host
+   arrays x, y of N = dg_state_len / 2 doubles each; host computation, no
+   device needed).  Element-major; within a rectangle the (p+1)^2 GLL nodes
+   x-fastest; within a triangle the equispaced nodes (r, s) = (-1 + 2i/p,
+   -1 + 2j/p), i + j <= p, i fastest, mapped by x = v1 + (1 + r)/2 (v2 - v1) +
+   (1 + s)/2 (v3 - v1).  DG_ERR_ARG / DG_ERR_UNSUPPORTED as dg_kin_create. */
+dg_status dg_kin_nodes(const dg_mesh *mesh, int p, double *x, double *y);
 
 /* L = M^-1 R(w) of the kinematic system at time t (device arrays of
    dg_state_len doubles; must not overlap). */
@@ -297,7 +323,8 @@ dg_status dg_kin_step(dg_ctx *ctx, double *w, double t0, double dt, int nsteps, 
    width.  The paper applies ~50 iterations every 2000 steps.  FP64; works on
    FP64 and FP32-bulk contexts alike (on the FP64 state).  The first call
    allocates the context's re-initialisation workspace (4 N doubles and the
-   face traces), kept until dg_destroy.  Asynchronous on stream. */
+   face traces), kept until dg_destroy.  Rectangles only: a triangle context
+   gives DG_ERR_UNSUPPORTED.  Asynchronous on stream. */
 dg_status dg_reinit(dg_ctx *ctx, double *w, int niter, double nu, double dtau, void *stream);
 
 /* Size of the fixed device scratch used by dg_rhs_noalloc (32 MiB per GPU). */

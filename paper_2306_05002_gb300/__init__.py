@@ -32,7 +32,8 @@ PREC = {"fp64": 0, "fp32bulk": 1}
 EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_step_host", "dg_diag",
            "dg_status_read", "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc", "dg_batch_create",
            "dg_batch_step", "dg_rhs_vjp", "dg_adjoint_step", "dg_tape_len", "dg_step_tape",
-           "dg_adjoint_step_tape", "dg_batch_tiles", "dg_kin_create", "dg_kin_rhs", "dg_kin_step", "dg_reinit"]
+           "dg_adjoint_step_tape", "dg_batch_tiles", "dg_kin_create", "dg_kin_rhs", "dg_kin_step", "dg_kin_nodes",
+           "dg_reinit"]
 
 
 class DGError(RuntimeError):
@@ -44,7 +45,7 @@ class DGError(RuntimeError):
 class dg_mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
-                ("bc", ctypes.c_int * 4), ("p_bc", ctypes.c_double * 4)]
+                ("bc", ctypes.c_int * 4), ("p_bc", ctypes.c_double * 4), ("elem", ctypes.c_int)]
 
 
 class dg_eos(ctypes.Structure):
@@ -114,6 +115,8 @@ def load(path: str | None = None):
     lib.dg_kin_create.argtypes = [ctypes.POINTER(dg_mesh), ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                   ctypes.POINTER(dg_velocity), ctypes.c_double, ctypes.POINTER(vp)]
     lib.dg_kin_create.restype = ctypes.c_int
+    lib.dg_kin_nodes.argtypes = [ctypes.POINTER(dg_mesh), ctypes.c_int, dp, dp]
+    lib.dg_kin_nodes.restype = ctypes.c_int
     lib.dg_kin_rhs.argtypes = [vp, dp, ctypes.c_double, dp, vp]
     lib.dg_kin_rhs.restype = ctypes.c_int
     lib.dg_kin_step.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
@@ -351,6 +354,35 @@ class BatchSolver:
                 for i in range(n)]
 
 
+ELEM = {"quad": 0, "tri": 1}
+
+
+def _kin_mesh(problem) -> dg_mesh:
+    m = dg_mesh()
+    m.dim, m.nx, m.ny = 2, problem.nx, problem.ny
+    m.x0, m.x1, m.y0, m.y1 = problem.x0, problem.x1, problem.y0, problem.y1
+    for i in range(4):
+        m.bc[i] = BC["periodic"]
+    m.elem = ELEM[getattr(problem, "elem", "quad")]
+    return m
+
+
+def dg_kin_nodes(problem):
+    """Node coordinates (x, y) of a kinematic-mode problem's state, from the library
+    (``dg_kin_nodes``): float64 numpy arrays of N = 2 nx ny (p+1)(p+2)/2 nodes on triangles,
+    nx ny (p+1)^2 on rectangles."""
+    import numpy as np
+    p = problem.p
+    per = (p + 1) * (p + 2) // 2 * 2 if getattr(problem, "elem", "quad") == "tri" else (p + 1) ** 2
+    N = problem.nx * problem.ny * per
+    x, y = np.zeros(N), np.zeros(N)
+    m = _kin_mesh(problem)
+    dpt = ctypes.POINTER(ctypes.c_double)
+    _check(None, load().dg_kin_nodes(ctypes.byref(m), p, x.ctypes.data_as(dpt), y.ctypes.data_as(dpt)),
+           "dg_kin_nodes")
+    return x, y
+
+
 class KinematicSolver:
     """Kinematic mode (Sec. 4.1): phi and psi advected by a prescribed velocity, classical RK4
     (wraps a ``dg_kin_create`` context).  ``problem`` is a :class:`workloads.KinWorkload`; states
@@ -358,11 +390,7 @@ class KinematicSolver:
 
     def __init__(self, problem):
         lib = load()
-        m = dg_mesh()
-        m.dim, m.nx, m.ny = 2, problem.nx, problem.ny
-        m.x0, m.x1, m.y0, m.y1 = problem.x0, problem.x1, problem.y0, problem.y1
-        for i in range(4):
-            m.bc[i] = BC["periodic"]
+        m = _kin_mesh(problem)
         v = dg_velocity()
         v.kind, v.u0, v.v0, v.T = VEL[problem.vel], problem.u0, problem.v0, problem.T
         v.xc, v.yc = problem.xc, problem.yc

@@ -22,6 +22,7 @@
 #include "dg_adjoint.cuh"
 #include "dg_kin.cuh"
 #include "dg_reinit.cuh"
+#include "dg_tri.cuh"
 #include "dgpf.h"
 
 namespace dgpf {
@@ -302,10 +303,12 @@ struct dg_ctx {
   int conv_blocks = 1;
   double *d_ops = nullptr, *d_w1 = nullptr, *d_w2 = nullptr, *d_rvol = nullptr, *d_trace = nullptr;
   double *d_hstate = nullptr;  // device copy of a host state (dg_step_host), allocated on first use
-  // kinematic mode (dg_kin_create)
-  bool kin = false;
+  // kinematic mode (dg_kin_create); tri: triangles (one fused kernel per stage)
+  bool kin = false, tri = false;
   KinParams kp{};
   KinKernels kk{};
+  TriKernels tk{};
+  int tri_grid = 0;
   double *d_kacc = nullptr, *d_kwsA = nullptr, *d_kwsB = nullptr, *d_krvol = nullptr, *d_ktr = nullptr;
   double *d_kt0 = nullptr, *d_kxi = nullptr;
   // level-set re-initialisation workspace (dg_reinit), allocated on first use
@@ -391,6 +394,10 @@ static const char *check_problem(const dg_mesh *mesh, int p, const dg_eos *eos, 
   *code = DG_ERR_ARG;
   if (!mesh || !eos) return "mesh and eos are required";
   if (mesh->dim != 1 && mesh->dim != 2) return "dim must be 1 or 2";
+  if (mesh->elem != DG_ELEM_QUAD) {
+    *code = mesh->elem == DG_ELEM_TRI ? DG_ERR_UNSUPPORTED : DG_ERR_ARG;
+    return "the two-phase flow model runs on rectangular elements only (elem = DG_ELEM_QUAD)";
+  }
   if (p < 1 || p > 5) {
     *code = DG_ERR_UNSUPPORTED;
     return "order p must be in 1..5";
@@ -1186,7 +1193,12 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
   *out = nullptr;
   if (!mesh || !vel) return fail(nullptr, DG_ERR_ARG, "dg_kin_create: mesh and velocity are required");
   if (mesh->dim != 2) return fail(nullptr, DG_ERR_ARG, "dg_kin_create: the kinematic mode is two-dimensional");
-  if (p < 1 || p > 5) return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_kin_create: order p must be in 1..5");
+  if (mesh->elem != DG_ELEM_QUAD && mesh->elem != DG_ELEM_TRI)
+    return fail(nullptr, DG_ERR_ARG, "dg_kin_create: elem must be DG_ELEM_QUAD or DG_ELEM_TRI");
+  const bool tri = mesh->elem == DG_ELEM_TRI;
+  if (p < 1 || p > (tri ? 4 : 5))
+    return fail(nullptr, DG_ERR_UNSUPPORTED,
+                tri ? "dg_kin_create: order p must be in 1..4 on triangles" : "dg_kin_create: order p must be in 1..5");
   if (mesh->nx < 1 || mesh->ny < 1 || (long long)mesh->nx * mesh->ny > (1LL << 26))
     return fail(nullptr, DG_ERR_ARG, "dg_kin_create: need 1 <= nx, ny and a mesh of at most 2^26 elements");
   if (!(mesh->x1 > mesh->x0) || !(mesh->y1 > mesh->y0)) return fail(nullptr, DG_ERR_ARG, "dg_kin_create: empty domain");
@@ -1201,18 +1213,19 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
   dg_ctx *c = new (std::nothrow) dg_ctx();
   if (!c) return fail(nullptr, DG_ERR_OOM, "dg_kin_create: host allocation failed");
   c->kin = true;
+  c->tri = tri;
   c->mesh = *mesh;
   c->p = p;
   c->dim = 2;
   c->P1 = p + 1;
-  c->Np = c->P1 * c->P1;
-  c->E = mesh->nx * mesh->ny;
+  c->Np = tri ? (p + 1) * (p + 2) / 2 : c->P1 * c->P1;
+  c->E = (tri ? 2 : 1) * mesh->nx * mesh->ny;
   c->N = c->E * c->Np;
-  c->NFK = 4 * c->P1;
+  c->NFK = tri ? 3 * (p + 2) : 4 * c->P1;
   c->len = (size_t)2 * c->N;
   c->hx = (mesh->x1 - mesh->x0) / mesh->nx;
   c->hy = (mesh->y1 - mesh->y0) / mesh->ny;
-  if (!kin_kernels(p, &c->kk)) {
+  if (tri ? !tri_kernels(p, &c->tk) : !kin_kernels(p, &c->kk)) {
     free_ctx(c);
     return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_kin_create: order not available");
   }
@@ -1230,6 +1243,7 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
   k.eps = eps;
   k.eta_x = cip * c->P1 * c->P1 / c->hx;
   k.eta_y = cip * c->P1 * c->P1 / c->hy;
+  k.eta_tri = cip * (p + 1) * (p + 2);
   k.vel = vel->kind;
   k.u0 = vel->u0;
   k.v0 = vel->v0;
@@ -1237,15 +1251,28 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
   k.xc = vel->xc;
   k.yc = vel->yc;
   k.check_finite = 1;
-  const std::vector<double> ops = build_ops(2, p, c->hx, c->hy);
+  const std::vector<double> ops = tri ? tri_tables(p) : build_ops(2, p, c->hx, c->hy);
+  if (ops.empty()) {
+    free_ctx(c);
+    return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_kin_create: reference tables could not be built");
+  }
   std::vector<double> xi, wt;
   gll_nodes(p, xi, wt);
   const size_t sb = c->len * sizeof(double), tb = (size_t)NT_KIN * c->E * c->NFK * sizeof(double);
   cudaError_t e = cudaSuccess;
+  // triangles: one fused kernel per stage, no volume residual or face traces
   double **bufs[] = {&c->d_kacc, &c->d_kwsA, &c->d_kwsB, &c->d_krvol};
   for (double **b : bufs)
-    if (e == cudaSuccess) e = cudaMalloc(b, sb);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_ktr, tb);
+    if (e == cudaSuccess && !(tri && b == &c->d_krvol)) e = cudaMalloc(b, sb);
+  if (e == cudaSuccess && !tri) e = cudaMalloc(&c->d_ktr, tb);
+  if (e == cudaSuccess && tri) {
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c->tk.fn, c->tk.threads, 0);
+    const long groups = (c->E + tri_group(p) - 1) / tri_group(p);
+    c->tri_grid = (int)std::max(1L, std::min(groups, (long)std::max(1, sms) * std::max(1, per_sm)));
+  }
   if (e == cudaSuccess) e = cudaMalloc(&c->d_kt0, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_kxi, xi.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_ops, ops.size() * sizeof(double));
@@ -1275,6 +1302,44 @@ static dg_status kin_check(dg_ctx *c, const char *who) {
   return DG_OK;
 }
 
+extern "C" dg_status dg_kin_nodes(const dg_mesh *mesh, int p, double *x, double *y) {
+  if (!mesh || !x || !y) return fail(nullptr, DG_ERR_ARG, "dg_kin_nodes: mesh, x and y are required");
+  if (mesh->dim != 2 || mesh->nx < 1 || mesh->ny < 1 || !(mesh->x1 > mesh->x0) || !(mesh->y1 > mesh->y0))
+    return fail(nullptr, DG_ERR_ARG, "dg_kin_nodes: need a non-empty 2D mesh");
+  if (mesh->elem != DG_ELEM_QUAD && mesh->elem != DG_ELEM_TRI)
+    return fail(nullptr, DG_ERR_ARG, "dg_kin_nodes: elem must be DG_ELEM_QUAD or DG_ELEM_TRI");
+  const bool tri = mesh->elem == DG_ELEM_TRI;
+  if (p < 1 || p > (tri ? 4 : 5)) return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_kin_nodes: order out of range");
+  const double hx = (mesh->x1 - mesh->x0) / mesh->nx, hy = (mesh->y1 - mesh->y0) / mesh->ny;
+  long n = 0;
+  if (!tri) {
+    std::vector<double> xi, wt;
+    gll_nodes(p, xi, wt);
+    for (int ey = 0; ey < mesh->ny; ++ey)
+      for (int ex = 0; ex < mesh->nx; ++ex)
+        for (int j = 0; j <= p; ++j)
+          for (int i = 0; i <= p; ++i, ++n) {
+            x[n] = mesh->x0 + hx * (ex + 0.5 * (xi[i] + 1.0));
+            y[n] = mesh->y0 + hy * (ey + 0.5 * (xi[j] + 1.0));
+          }
+    return DG_OK;
+  }
+  for (int cell = 0; cell < mesh->nx * mesh->ny; ++cell)
+    for (int type = 0; type < 2; ++type) {
+      const double xa = mesh->x0 + (cell % mesh->nx) * hx, ya = mesh->y0 + (cell / mesh->nx) * hy;
+      const double v[3][2] = {{xa, ya},
+                              {xa + hx, type == 0 ? ya : ya + hy},
+                              {type == 0 ? xa + hx : xa, ya + hy}};
+      for (int j = 0; j <= p; ++j)
+        for (int i = 0; i + j <= p; ++i, ++n) {
+          const double r = -1.0 + 2.0 * i / p, s = -1.0 + 2.0 * j / p;
+          x[n] = v[0][0] + 0.5 * (1.0 + r) * (v[1][0] - v[0][0]) + 0.5 * (1.0 + s) * (v[2][0] - v[0][0]);
+          y[n] = v[0][1] + 0.5 * (1.0 + r) * (v[1][1] - v[0][1]) + 0.5 * (1.0 + s) * (v[2][1] - v[0][1]);
+        }
+    }
+  return DG_OK;
+}
+
 extern "C" dg_status dg_kin_rhs(dg_ctx *c, const double *w, double t, double *L, void *stream) {
   dg_status r = kin_check(c, "dg_kin_rhs");
   if (r != DG_OK) return r;
@@ -1282,6 +1347,10 @@ extern "C" dg_status dg_kin_rhs(dg_ctx *c, const double *w, double t, double *L,
   cudaStream_t s = (cudaStream_t)stream;
   k_kin_set_time<<<1, 1, 0, s>>>(c->d_kt0, t);
   cudaError_t e = cudaGetLastError();
+  if (c->tri) {
+    if (e == cudaSuccess) e = c->tk.stage(c->kp, KIN_RHS, 0.0, 0.0, 0.0, w, nullptr, nullptr, L, c->tri_grid, s);
+    return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_kin_rhs: launch");
+  }
   if (e == cudaSuccess) e = c->kk.volume(c->kp, 0.0, 0.0, w, c->d_krvol, c->d_ktr, s);
   if (e == cudaSuccess) e = c->kk.surface(c->kp, KIN_RHS, 0.0, w, c->d_krvol, c->d_ktr, nullptr, L, s);
   return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_kin_rhs: launch");
@@ -1297,8 +1366,13 @@ static dg_status enqueue_kin_step(dg_ctx *c, double *w, double dt, int k, cudaSt
   double *out[4] = {A, B, A, w};
   const int mode[4] = {KIN_K1, KIN_K2, KIN_K3, KIN_K4};
   for (int st = 0; st < 4; ++st) {
-    cudaError_t e = c->kk.volume(c->kp, tstep, toff[st], in[st], c->d_krvol, c->d_ktr, s);
-    if (e == cudaSuccess) e = c->kk.surface(c->kp, mode[st], dt, w, c->d_krvol, c->d_ktr, c->d_kacc, out[st], s);
+    cudaError_t e;
+    if (c->tri) {
+      e = c->tk.stage(c->kp, mode[st], tstep, toff[st], dt, in[st], w, c->d_kacc, out[st], c->tri_grid, s);
+    } else {
+      e = c->kk.volume(c->kp, tstep, toff[st], in[st], c->d_krvol, c->d_ktr, s);
+      if (e == cudaSuccess) e = c->kk.surface(c->kp, mode[st], dt, w, c->d_krvol, c->d_ktr, c->d_kacc, out[st], s);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "dg_kin_step: launch");
   }
   return DG_OK;
@@ -1356,6 +1430,7 @@ extern "C" dg_status dg_reinit(dg_ctx *c, double *w, int niter, double nu, doubl
   if (c->batch) return fail(c, DG_ERR_ARG, "dg_reinit: batch context");
   if (!w) return fail(c, DG_ERR_ARG, "dg_reinit: null state");
   if (niter < 0) return fail(c, DG_ERR_ARG, "dg_reinit: need niter >= 0");
+  if (c->tri) return fail(c, DG_ERR_UNSUPPORTED, "dg_reinit: rectangular elements only");
   ReinitKernels rk;
   if (!reinit_kernels(c->p, c->dim, &rk)) return fail(c, DG_ERR_UNSUPPORTED, "dg_reinit: order not available");
   ReinitParams rp{};

@@ -35,6 +35,7 @@ struct KinParams {
   int vel;                 // VEL_UNIFORM or VEL_RIDER_KOTHE
   double u0, v0, T;        // uniform velocity; Rider-Kothe period
   double xc, yc;           // Rider-Kothe vortex centre
+  double eta_tri;          // triangles: c_ip (p+1)(p+2); the edge penalty is eta_tri / h_e
   const double *ops;       // operator table (OpsLayout)
   const double *xi;        // GLL nodes on [-1, 1]
   const double *t0;        // device: time at the start of the captured step sequence

@@ -1,0 +1,345 @@
+// dg_tri.cuh -- kinematic mode (Sec. 4.1) on triangular elements, the paper's
+// mesh (b): every cell of an nx x ny periodic Cartesian grid split along its
+// rising diagonal into a lower-right triangle (type 0, vertices (x_i, y_j),
+// (x_i+1, y_j), (x_i+1, y_j+1)) and an upper-left one (type 1, vertices
+// (x_i, y_j), (x_i+1, y_j+1), (x_i, y_j+1)); element 2 (i + nx j) + type.
+// FP64 (GB300, sm_103a).
+//
+// The same equations as dg_kin.cuh,
+//   d(phi)/dt + u . grad(phi) = div a_1,   a_1 = Gamma (eps grad phi - phi (1 - phi) n),
+//   d(psi)/dt + u . grad(psi) = 0,
+// with a nodal basis of degree p on the equispaced nodes of each triangle. A
+// triangle has no tensor-product structure and no collocated quadrature, so
+// the weak form is integrated with a collapsed Gauss-Legendre rule of (p+2)^2
+// points and (p+2)-point Gauss-Legendre edge rules, and L = M^-1 R with the
+// full element mass matrix.  Fluxes as on quadrilaterals: transport
+// (lambda - m.u-) [[f]] with lambda = max(|u-.m|, |u+.m|), and the SIP flux of
+// a_1 with its symmetric term, penalty eta = c_ip (p+1)(p+2) / h_e with
+// h_e = 2 |T| / |e|.
+//
+// One kernel per Runge-Kutta stage.  A persistent grid walks groups of EPB
+// triangles; each CTA stages the reference tables (basis values and
+// derivatives at the volume and edge points, the inverse reference mass matrix)
+// in shared memory once, then per group: the own and neighbour nodal values,
+// the integrand coefficients at every volume and edge point (one thread per
+// point), the weak-form sums (one thread per node) and M^-1 with the stage
+// update (one thread per node).  Neighbour values are read from the stage
+// input, which no stage writes, so the stages need no other synchronisation
+// than stream order.
+#pragma once
+
+#include <vector>
+
+#include "dg_kin.cuh"
+
+namespace dgpf {
+
+// Reference-table layout of order p, in doubles (built by tri_tables).
+struct TriLayout {
+  int NP, NQ1, NQV, NQE;
+  __host__ __device__ constexpr explicit TriLayout(int p)
+      : NP((p + 1) * (p + 2) / 2), NQ1(p + 2), NQV((p + 2) * (p + 2)), NQE(3 * (p + 2)) {}
+  // basis values and reference derivatives at the volume points, [q][n]
+  __host__ __device__ constexpr int bv() const { return 0; }
+  __host__ __device__ constexpr int brv() const { return bv() + NQV * NP; }
+  __host__ __device__ constexpr int bsv() const { return brv() + NQV * NP; }
+  // the same at the edge points, [f NQ1 + k][n]
+  __host__ __device__ constexpr int be() const { return bsv() + NQV * NP; }
+  __host__ __device__ constexpr int bre() const { return be() + NQE * NP; }
+  __host__ __device__ constexpr int bse() const { return bre() + NQE * NP; }
+  // inverse of the reference mass matrix sum_q w_q l_i l_j, [i][j]
+  __host__ __device__ constexpr int minv() const { return bse() + NQE * NP; }
+  // volume weights (collapsed factor included) and points
+  __host__ __device__ constexpr int wv() const { return minv() + NP * NP; }
+  __host__ __device__ constexpr int rv() const { return wv() + NQV; }
+  __host__ __device__ constexpr int sv() const { return rv() + NQV; }
+  // edge weights on [-1, 1] and edge points
+  __host__ __device__ constexpr int we() const { return sv() + NQV; }
+  __host__ __device__ constexpr int re() const { return we() + NQ1; }
+  __host__ __device__ constexpr int se() const { return re() + NQE; }
+  __host__ __device__ constexpr int size() const { return se() + NQE; }
+};
+
+template <int P>
+struct TriGeom {
+  static constexpr TriLayout L{P};
+  static constexpr int NP = L.NP, NQ1 = L.NQ1, NQV = L.NQV, NQE = L.NQE;
+  static constexpr int EPB = P >= 4 ? 6 : 8;
+  static constexpr int THREADS = 128;
+};
+
+// Affine map of one triangle: counter-clockwise vertices, det = d(x,y)/d(r,s),
+// inverse-map derivatives.
+struct TriMap {
+  double v[3][2];
+  double det, rx, ry, sx, sy;
+};
+
+__device__ __forceinline__ void tri_map_of(const KinParams &kp, int e, TriMap *g) {
+  const int cell = e >> 1, type = e & 1;
+  const int ci = cell % kp.nx, cj = cell / kp.nx;
+  const double x0 = kp.x0 + ci * kp.hx, y0 = kp.y0 + cj * kp.hy;
+  g->v[0][0] = x0;
+  g->v[0][1] = y0;
+  g->v[1][0] = x0 + kp.hx;
+  g->v[1][1] = type == 0 ? y0 : y0 + kp.hy;
+  g->v[2][0] = type == 0 ? x0 + kp.hx : x0;
+  g->v[2][1] = y0 + kp.hy;
+  const double xr = 0.5 * (g->v[1][0] - g->v[0][0]), yr = 0.5 * (g->v[1][1] - g->v[0][1]);
+  const double xs = 0.5 * (g->v[2][0] - g->v[0][0]), ys = 0.5 * (g->v[2][1] - g->v[0][1]);
+  g->det = xr * ys - xs * yr;
+  g->rx = ys / g->det;
+  g->ry = -xs / g->det;
+  g->sx = -yr / g->det;
+  g->sy = xr / g->det;
+}
+
+__device__ __forceinline__ void tri_point(const TriMap &g, double r, double s, double *x, double *y) {
+  *x = g.v[0][0] + 0.5 * (1.0 + r) * (g.v[1][0] - g.v[0][0]) + 0.5 * (1.0 + s) * (g.v[2][0] - g.v[0][0]);
+  *y = g.v[0][1] + 0.5 * (1.0 + r) * (g.v[1][1] - g.v[0][1]) + 0.5 * (1.0 + s) * (g.v[2][1] - g.v[0][1]);
+}
+
+// Periodic neighbour across edge f (0: v1 v2, 1: v2 v3, 2: v3 v1) and its edge index.
+// Type 0: bottom, right, diagonal; type 1: diagonal, top, left.
+__device__ __forceinline__ int tri_neighbour(const KinParams &kp, int e, int f, int *f2) {
+  const int cell = e >> 1, type = e & 1;
+  const int ci = cell % kp.nx, cj = cell / kp.nx;
+  if (type == 0) {
+    if (f == 0) { *f2 = 1; return 2 * (ci + kp.nx * (cj > 0 ? cj - 1 : kp.ny - 1)) + 1; }
+    if (f == 1) { *f2 = 2; return 2 * ((ci + 1 < kp.nx ? ci + 1 : 0) + kp.nx * cj) + 1; }
+    *f2 = 0;
+    return e + 1;
+  }
+  if (f == 0) { *f2 = 2; return e - 1; }
+  if (f == 1) { *f2 = 0; return 2 * (ci + kp.nx * (cj + 1 < kp.ny ? cj + 1 : 0)); }
+  *f2 = 1;
+  return 2 * ((ci > 0 ? ci - 1 : kp.nx - 1) + kp.nx * cj);
+}
+
+// phi, psi, their physical gradients, n and a_1 at one point, from the nodal
+// values f[2][NP] and the basis rows (values, r- and s-derivatives).
+struct TriPoint {
+  double phi, psi, gp[2], gs[2], n[2], a1[2];
+};
+
+template <int NP>
+__device__ __forceinline__ void tri_eval_point(const KinParams &kp, const TriMap &g, const double *fphi,
+                                               const double *fpsi, const double *B, const double *Br,
+                                               const double *Bs, TriPoint *o) {
+  double ph = 0.0, ps = 0.0, pr = 0.0, pq = 0.0, sr = 0.0, sq = 0.0;
+#pragma unroll
+  for (int n = 0; n < NP; ++n) {
+    ph = fma(B[n], fphi[n], ph);
+    ps = fma(B[n], fpsi[n], ps);
+    pr = fma(Br[n], fphi[n], pr);
+    pq = fma(Bs[n], fphi[n], pq);
+    sr = fma(Br[n], fpsi[n], sr);
+    sq = fma(Bs[n], fpsi[n], sq);
+  }
+  o->phi = ph;
+  o->psi = ps;
+  o->gp[0] = pr * g.rx + pq * g.sx;
+  o->gp[1] = pr * g.ry + pq * g.sy;
+  o->gs[0] = sr * g.rx + sq * g.sx;
+  o->gs[1] = sr * g.ry + sq * g.sy;
+  const double norm = sqrt(o->gs[0] * o->gs[0] + o->gs[1] * o->gs[1]);
+  const double sp = ph * (1.0 - ph);
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    o->n[d] = norm < 1e-12 ? 0.0 : o->gs[d] / norm;
+    o->a1[d] = kp.Gamma * (kp.eps * o->gp[d] - sp * o->n[d]);
+  }
+}
+
+// One stage: the right-hand side L = M^-1 R(win) at time *t0 + tstep + toff,
+// written as L (KIN_RHS) or as one classical RK4 stage (KIN_K1..K4, the same
+// updates as k_kin_surface; out may be w0, each node being read, then written,
+// by the same thread).
+template <int P>
+__global__ void __launch_bounds__(TriGeom<P>::THREADS)
+k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, const double *__restrict__ win,
+            const double *w0, double *__restrict__ acc, double *out) {
+  using G = TriGeom<P>;
+  constexpr TriLayout L = G::L;
+  constexpr int NP = G::NP, NQ1 = G::NQ1, NQV = G::NQV, NQE = G::NQE, EPB = G::EPB;
+  __shared__ double s_t[L.size()];
+  __shared__ double s_w[EPB][2][NP];
+  __shared__ double s_nb[EPB][3][2][NP];
+  __shared__ double s_cv[EPB][NQV][4];
+  __shared__ double s_ce[EPB][NQE][4];
+  __shared__ double s_R[EPB][2][NP];
+  for (int i = threadIdx.x; i < L.size(); i += blockDim.x) s_t[i] = kp.ops[i];
+  const double t = (*kp.t0 + tstep) + toff;
+  const int N = kp.N, ngroups = (kp.E + EPB - 1) / EPB;
+  bool bad = false;
+
+  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const int e0 = grp * EPB;
+    __syncthreads();  // tables staged; the previous group's shared data consumed
+    // 1. Own (slot 0) and neighbour (slots 1..3) nodal values.
+    for (int it = threadIdx.x; it < EPB * 4 * NP; it += blockDim.x) {
+      const int n = it % NP, slot = (it / NP) % 4, le = it / (4 * NP), e = e0 + le;
+      double a = 0.0, b = 0.0;
+      if (e < kp.E) {
+        int f2, src = e;
+        if (slot > 0) src = tri_neighbour(kp, e, slot - 1, &f2);
+        a = win[(long)src * NP + n];
+        b = win[N + (long)src * NP + n];
+      }
+      double *dst = slot == 0 ? s_w[le][0] : s_nb[le][slot - 1][0];
+      dst[n] = a;
+      dst[NP + n] = b;
+    }
+    __syncthreads();
+    // 2. Volume points: coefficients of l_n, dl_n/dr, dl_n/ds (phi) and l_n (psi).
+    for (int it = threadIdx.x; it < EPB * NQV; it += blockDim.x) {
+      const int le = it / NQV, q = it % NQV, e = e0 + le;
+      double c[4] = {0.0, 0.0, 0.0, 0.0};
+      if (e < kp.E) {
+        TriMap g;
+        tri_map_of(kp, e, &g);
+        TriPoint o;
+        tri_eval_point<NP>(kp, g, s_w[le][0], s_w[le][1], s_t + L.bv() + q * NP, s_t + L.brv() + q * NP,
+                           s_t + L.bsv() + q * NP, &o);
+        double x, y, u, v;
+        tri_point(g, s_t[L.rv() + q], s_t[L.sv() + q], &x, &y);
+        kin_velocity(kp, x, y, t, &u, &v);
+        const double wq = s_t[L.wv() + q] * g.det;
+        c[0] = -wq * (u * o.gp[0] + v * o.gp[1]);
+        c[1] = -wq * (o.a1[0] * g.rx + o.a1[1] * g.ry);
+        c[2] = -wq * (o.a1[0] * g.sx + o.a1[1] * g.sy);
+        c[3] = -wq * (u * o.gs[0] + v * o.gs[1]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) s_cv[le][q][k] = c[k];
+    }
+    // 3. Edge points: transport and SIP fluxes, the symmetric term.
+    for (int it = threadIdx.x; it < EPB * NQE; it += blockDim.x) {
+      const int le = it / NQE, fk = it % NQE, f = fk / NQ1, k = fk % NQ1, e = e0 + le;
+      double c[4] = {0.0, 0.0, 0.0, 0.0};
+      if (e < kp.E) {
+        int f2;
+        const int e2 = tri_neighbour(kp, e, f, &f2);
+        const int fk2 = f2 * NQ1 + (NQ1 - 1 - k);  // the same physical point, seen from the neighbour
+        TriMap g, g2;
+        tri_map_of(kp, e, &g);
+        tri_map_of(kp, e2, &g2);
+        TriPoint om, op;
+        tri_eval_point<NP>(kp, g, s_w[le][0], s_w[le][1], s_t + L.be() + fk * NP, s_t + L.bre() + fk * NP,
+                           s_t + L.bse() + fk * NP, &om);
+        tri_eval_point<NP>(kp, g2, s_nb[le][f][0], s_nb[le][f][1], s_t + L.be() + fk2 * NP,
+                           s_t + L.bre() + fk2 * NP, s_t + L.bse() + fk2 * NP, &op);
+        double x, y, x2, y2, u, v, u2, v2;
+        tri_point(g, s_t[L.re() + fk], s_t[L.se() + fk], &x, &y);
+        tri_point(g2, s_t[L.re() + fk2], s_t[L.se() + fk2], &x2, &y2);
+        kin_velocity(kp, x, y, t, &u, &v);
+        kin_velocity(kp, x2, y2, t, &u2, &v2);
+        // edge vector v[f] -> v[f+1], by selects (a dynamic index would put g in local memory)
+        const double ax = f == 0 ? g.v[0][0] : (f == 1 ? g.v[1][0] : g.v[2][0]);
+        const double ay = f == 0 ? g.v[0][1] : (f == 1 ? g.v[1][1] : g.v[2][1]);
+        const double bx = f == 0 ? g.v[1][0] : (f == 1 ? g.v[2][0] : g.v[0][0]);
+        const double by = f == 0 ? g.v[1][1] : (f == 1 ? g.v[2][1] : g.v[0][1]);
+        const double dx = bx - ax, dy = by - ay;
+        const double len = sqrt(dx * dx + dy * dy);
+        const double m0 = dy / len, m1 = -dx / len;
+        const double he = 2.0 * (2.0 * g.det) / len;
+        const double eta = kp.eta_tri / he;
+        const double wf = s_t[L.we() + k] * 0.5 * len;
+        const double unm = u * m0 + v * m1, unp = u2 * m0 + v2 * m1;
+        const double lam = fmax(fabs(unm), fabs(unp));
+        const double jump = op.phi - om.phi, hjs = 0.5 * (op.psi - om.psi);
+        const double gn = 0.5 * ((op.gp[0] + om.gp[0]) * m0 + (op.gp[1] + om.gp[1]) * m1);
+        const double sharp = 0.5 * (op.phi * (1.0 - op.phi) * (op.n[0] * m0 + op.n[1] * m1) +
+                                    om.phi * (1.0 - om.phi) * (om.n[0] * m0 + om.n[1] * m1));
+        const double ahat = kp.Gamma * (kp.eps * (gn + eta * jump) - sharp);
+        const double sym = 0.5 * kp.Gamma * kp.eps * jump;
+        c[0] = wf * ((lam - unm) * 0.5 * jump + ahat);
+        c[1] = -wf * sym * (g.rx * m0 + g.ry * m1);
+        c[2] = -wf * sym * (g.sx * m0 + g.sy * m1);
+        c[3] = wf * (lam - unm) * hjs;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s_ce[le][fk][q] = c[q];
+    }
+    __syncthreads();
+    // 4. Weak-form sums R_n (volume points, then edge points).
+    for (int it = threadIdx.x; it < EPB * NP; it += blockDim.x) {
+      const int le = it / NP, n = it % NP;
+      double rp = 0.0, rs = 0.0;
+#pragma unroll 4
+      for (int q = 0; q < NQV; ++q) {
+        const double *c = s_cv[le][q];
+        rp += c[0] * s_t[L.bv() + q * NP + n] + c[1] * s_t[L.brv() + q * NP + n] + c[2] * s_t[L.bsv() + q * NP + n];
+        rs += c[3] * s_t[L.bv() + q * NP + n];
+      }
+#pragma unroll 4
+      for (int q = 0; q < NQE; ++q) {
+        const double *c = s_ce[le][q];
+        rp += c[0] * s_t[L.be() + q * NP + n] + c[1] * s_t[L.bre() + q * NP + n] + c[2] * s_t[L.bse() + q * NP + n];
+        rs += c[3] * s_t[L.be() + q * NP + n];
+      }
+      s_R[le][0][n] = rp;
+      s_R[le][1][n] = rs;
+    }
+    __syncthreads();
+    // 5. L = M^-1 R / det and the stage update.
+    for (int it = threadIdx.x; it < EPB * NP; it += blockDim.x) {
+      const int le = it / NP, n = it % NP, e = e0 + le;
+      if (e >= kp.E) continue;
+      TriMap g;
+      tri_map_of(kp, e, &g);
+#pragma unroll
+      for (int vv = 0; vv < 2; ++vv) {
+        double a = 0.0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) a = fma(s_t[L.minv() + n * NP + j], s_R[le][vv][j], a);
+        const double Lv = a / g.det;
+        const long o = (long)vv * N + (long)e * NP + n;
+        double r;
+        if (mode == KIN_RHS) {
+          r = Lv;
+        } else {
+          const double base = w0[o];
+          if (mode == KIN_K1) {
+            acc[o] = Lv;
+            r = base + 0.5 * dt * Lv;
+          } else if (mode == KIN_K2) {
+            acc[o] += 2.0 * Lv;
+            r = base + 0.5 * dt * Lv;
+          } else if (mode == KIN_K3) {
+            acc[o] += 2.0 * Lv;
+            r = base + dt * Lv;
+          } else {
+            r = base + dt / 6.0 * (acc[o] + Lv);
+          }
+        }
+        bad |= !isfinite(r);
+        out[o] = r;
+      }
+    }
+  }
+  if (kp.check_finite && bad) atomicOr(kp.status, STATUS_NONFINITE);
+}
+
+struct TriKernels {
+  cudaError_t (*stage)(const KinParams &, int mode, double tstep, double toff, double dt, const double *win,
+                       const double *w0, double *acc, double *out, int grid, cudaStream_t);
+  const void *fn;  // the kernel, for the occupancy query
+  int threads;
+};
+
+template <int P>
+cudaError_t launch_tri_stage(const KinParams &kp, int mode, double tstep, double toff, double dt, const double *win,
+                             const double *w0, double *acc, double *out, int grid, cudaStream_t s) {
+  k_tri_stage<P><<<grid, TriGeom<P>::THREADS, 0, s>>>(kp, mode, tstep, toff, dt, win, w0, acc, out);
+  return cudaGetLastError();
+}
+
+// Kernels of order p (1..4); false for other orders.
+bool tri_kernels(int p, TriKernels *out);
+// Groups of triangles one CTA processes per pass (EPB of order p).
+int tri_group(int p);
+// Reference tables of order p in the TriLayout order; empty on failure.
+std::vector<double> tri_tables(int p);
+
+}  // namespace dgpf

@@ -358,14 +358,19 @@ class KinWorkload:
     nsteps: int = 0
     meta: dict = field(default_factory=dict)
     dim: int = 2
+    elem: str = "quad"        # "quad": the rectangles (mesh (a)); "tri": each split in two (mesh (b))
 
     @property
     def Np(self) -> int:
-        return (self.p + 1) ** 2
+        return (self.p + 1) * (self.p + 2) // 2 if self.elem == "tri" else (self.p + 1) ** 2
+
+    @property
+    def E(self) -> int:
+        return self.nx * self.ny * (2 if self.elem == "tri" else 1)
 
     @property
     def N(self) -> int:
-        return self.nx * self.ny * self.Np
+        return self.E * self.Np
 
     @property
     def hx(self) -> float:
@@ -385,24 +390,26 @@ class KinWorkload:
 
 
 def kin_stable_dt(wl: KinWorkload, umax: float) -> float:
-    """Advective limit 0.5 h / ((2p + 1) |u|max) and the parabolic limit of the SIP term."""
+    """Advective limit 0.5 h / ((2p + 1) |u|max) and the parabolic limit of the SIP term (h the
+    cell width); on triangles 0.4 of that (the split cells run stably up to about 0.7 of it for
+    p <= 3 and 0.5 for p = 4 on the Rider-Kothe drop)."""
     h = min(wl.hx, wl.hy)
     q = 2 * wl.p + 1
     dt = 0.5 * h / (q * max(umax, 1e-12))
     if wl.Gamma * wl.eps > 0:
         dt = min(dt, 0.1 * h * h / (q * q * wl.Gamma * wl.eps))
-    return dt
+    return dt * (0.4 if wl.elem == "tri" else 1.0)
 
 
 def rider_kothe(n: int = 16, p: int = 3, T: float = 4.0, R: float = 0.15, center=(0.0, 0.25),
-                eps_h: float = 0.75, Gamma: float = 1.0, vortex=(0.0, 0.0)) -> KinWorkload:
+                eps_h: float = 0.75, Gamma: float = 1.0, vortex=(0.0, 0.0), elem: str = "quad") -> KinWorkload:
     """Rider-Kothe vortex (Sec. 4.1): a drop of radius 0.15 centred at (0, 0.25) in the periodic
     square [-0.5, 0.5]^2, stretched by the time-reversing vortex of period T = 4 centred at
     `vortex` (the domain centre; (0.5, 0.5) gives the printed formula, whose vortex sits at the
     domain corners).  Phase 1 is the drop; psi = R - r grows into it.  eps = 0.75 h (h: element
     width) and Gamma = |u|max = 1, since the paper leaves both unstated for this test."""
-    wl = KinWorkload(name=f"rk2d_{n}x{n}p{p}", nx=n, ny=n, p=p, Gamma=Gamma, vel="rider_kothe", T=T,
-                     xc=vortex[0], yc=vortex[1])
+    wl = KinWorkload(name=f"rk2d_{n}x{n}p{p}" + ("tri" if elem == "tri" else ""), nx=n, ny=n, p=p, Gamma=Gamma,
+                     vel="rider_kothe", T=T, xc=vortex[0], yc=vortex[1], elem=elem)
     wl.eps = eps_h * wl.hx
     x, y = _kin_nodes(wl)
     r = np.hypot(x - center[0], y - center[1])
@@ -431,6 +438,8 @@ def kin_drop(n: int = 16, p: int = 3, R: float = 0.15, u0: float = 1.0, v0: floa
 
 
 def _kin_nodes(wl: KinWorkload):
+    if wl.elem == "tri":
+        return _tri_nodes(wl)
     xi = gll_points(wl.p)
     P1 = wl.p + 1
     e = np.arange(wl.nx * wl.ny)
@@ -439,5 +448,25 @@ def _kin_nodes(wl: KinWorkload):
     i, j = a % P1, a // P1
     x = wl.x0 + wl.hx * (ex[:, None] + 0.5 * (xi[i][None, :] + 1.0))
     y = wl.y0 + wl.hy * (ey[:, None] + 0.5 * (xi[j][None, :] + 1.0))
+    return x.ravel(), y.ravel()
+
+
+def _tri_nodes(wl: KinWorkload):
+    """Equispaced nodes of the split-rectangle triangles: cell (i, j) gives triangle 2 (i + nx j)
+    with vertices (x_i, y_j), (x_i+1, y_j), (x_i+1, y_j+1) and triangle 2 (i + nx j) + 1 with
+    (x_i, y_j), (x_i+1, y_j+1), (x_i, y_j+1); node (a, b), a + b <= p, a fastest, at barycentric
+    weights (1 - (a + b)/p, a/p, b/p) of the three vertices."""
+    p = wl.p
+    a = np.array([i for j in range(p + 1) for i in range(p + 1 - j)], dtype=float) / p
+    b = np.array([j for j in range(p + 1) for i in range(p + 1 - j)], dtype=float) / p
+    cell = np.arange(wl.nx * wl.ny)
+    xa = wl.x0 + (cell % wl.nx) * wl.hx
+    ya = wl.y0 + (cell // wl.nx) * wl.hy
+    x = np.empty((wl.nx * wl.ny, 2, len(a)))
+    y = np.empty_like(x)
+    x[:, 0] = xa[:, None] + wl.hx * (a + b)[None, :]
+    y[:, 0] = ya[:, None] + wl.hy * b[None, :]
+    x[:, 1] = xa[:, None] + wl.hx * a[None, :]
+    y[:, 1] = ya[:, None] + wl.hy * (a + b)[None, :]
     return x.ravel(), y.ravel()
 

@@ -105,6 +105,7 @@ def _kin_args(**over):
     m = pkg.dg_mesh()
     m.dim, m.nx, m.ny = over.pop("dim", 2), over.pop("nx", 4), over.pop("ny", 4)
     m.x0, m.x1, m.y0, m.y1 = -0.5, 0.5, -0.5, 0.5
+    m.elem = over.pop("elem", 0)
     bc = over.pop("bc", ("periodic",) * 4)
     for i in range(4):
         m.bc[i] = pkg.BC[bc[i]]
@@ -120,6 +121,8 @@ def _kin_args(**over):
     (dict(kind=7), -1),
     (dict(T=0.0), -1),
     (dict(Gamma=-1.0), -1),
+    (dict(elem=2), -1),
+    (dict(elem=1, p=5), -7),
 ])
 def test_kin_create_rejects_invalid_arguments(lib, over, code):
     m, p, G, eps, v = _kin_args(**over)
@@ -135,3 +138,43 @@ def test_kin_calls_reject_other_contexts(lib):
 
 def test_reinit_rejects_null_and_negative_arguments(lib):
     assert lib.dg_reinit(None, None, 1, 0.0, 0.0, None) == -1
+
+
+def test_full_model_rejects_triangles(lib):
+    import paper_2306_05002_gb300 as pkg
+    m, eos, o = pkg.make_structs(2, 4, 4, 0.0, 1.0, 0.0, 1.0, ("periodic",) * 4, (4.4, 1.4), (6e8, 0.0),
+                                 (1000.0, 1.0))
+    m.elem = 1
+    h = ctypes.c_void_p(123)
+    assert lib.dg_create(ctypes.byref(m), 3, ctypes.byref(eos), 1.0, 0.05, ctypes.byref(o), ctypes.byref(h)) == -7
+    assert h.value is None
+
+
+@pytest.mark.parametrize("elem,p", [("tri", 1), ("tri", 3), ("tri", 4), ("quad", 2), ("quad", 5)])
+def test_kin_nodes_match_oracle_and_workload(lib, orc, elem, p):
+    """dg_kin_nodes (host code of the library) against the oracle's and the input generator's node
+    coordinates: the state layout the three share."""
+    import numpy as np
+    import paper_2306_05002_gb300 as pkg
+    from paper_2306_05002_gb300 import workloads as W
+    wl = W.KinWorkload(name="t", nx=3, ny=2, p=p, x0=-0.3, x1=0.9, y0=0.1, y1=0.7, elem=elem)
+    x, y = pkg.dg_kin_nodes(wl)
+    pb = orc.Problem(**wl.problem_kwargs())
+    xo, yo = orc.tri_nodes(pb) if elem == "tri" else orc.nodes(pb)
+    xw, yw = W._kin_nodes(wl)
+    assert len(x) == wl.N == len(xo)
+    assert np.abs(x - xo).max() < 1e-15 and np.abs(y - yo).max() < 1e-15
+    assert np.abs(x - xw).max() < 1e-15 and np.abs(y - yw).max() < 1e-15
+
+
+def test_kin_nodes_rejects_invalid_arguments(lib):
+    import numpy as np
+    m, _, _, _, _ = _kin_args(elem=1)
+    x = np.zeros(1000)
+    dpt = ctypes.POINTER(ctypes.c_double)
+    assert lib.dg_kin_nodes(None, 3, x.ctypes.data_as(dpt), x.ctypes.data_as(dpt)) == -1
+    assert lib.dg_kin_nodes(ctypes.byref(m), 3, None, x.ctypes.data_as(dpt)) == -1
+    assert lib.dg_kin_nodes(ctypes.byref(m), 5, x.ctypes.data_as(dpt), x.ctypes.data_as(dpt)) == -7
+    m.elem = 3
+    assert lib.dg_kin_nodes(ctypes.byref(m), 3, x.ctypes.data_as(dpt), x.ctypes.data_as(dpt)) == -1
+
