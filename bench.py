@@ -51,6 +51,10 @@ def parse():
                     help="elements per direction of the adjoint block (smaller values for profiling)")
     ap.add_argument("--kin-steps", type=int, default=200,
                     help="timed RK4 steps of the kinematic Rider-Kothe block (0 skips it)")
+    ap.add_argument("--tri-steps", type=int, default=200,
+                    help="timed RK4 steps of the kinematic block on triangles (0 skips it)")
+    ap.add_argument("--tri-n", type=int, default=64,
+                    help="cells per direction of the timed triangle block (smaller values for profiling)")
     ap.add_argument("--adjoint-steps", type=int, default=200,
                     help="trajectory length of the adjoint timing (0 skips it)")
     ap.add_argument("--cpu-sample-steps", type=int, default=0,
@@ -453,6 +457,68 @@ def kinematic_block(dg, steps, n=64):
                                     "paper_l1_p3_64sq_dof": 1.75e-2}}
 
 
+def tri_flops_per_stage(p):
+    """Algorithmic FP64 flops of one triangle and one RK stage (both fields): phi, psi and their
+    r-, s-derivatives at the (p+2)^2 volume points (6 dot products of length Np) and at the 3 (p+2)
+    edge points on both sides, the weak-form sums at every node (4 basis terms at each volume and
+    edge point) and M^-1 R for two fields; 2 flops per multiply-add."""
+    Np, nqv, nqe = (p + 1) * (p + 2) // 2, (p + 2) ** 2, 3 * (p + 2)
+    return 12 * Np * nqv + 24 * Np * nqe + 8 * Np * (nqv + nqe) + 4 * Np * Np
+
+
+def triangle_block(dg, steps, n=64):
+    """Kinematic mode on triangles (the paper's mesh (b)), FP64, classical RK4: the Rider-Kothe
+    vortex on n x n cells split into 2 n^2 triangles, p = 3, timed over `steps` steps (one fused
+    kernel per stage, four per step); and the full period T = 4 on 16 x 16 cells (the paper's mesh
+    (b) 64^2-DoF row): L1 error of phi and the relative mass error (paper, p = 3: L1 1.58e-2)."""
+    import numpy as np
+    import torch
+    from paper_2306_05002_gb300 import workloads as W
+    wl = W.rider_kothe(n=n, p=3, elem="tri")
+    s = dg.KinematicSolver(wl)
+    w = torch.from_numpy(wl.w.copy()).cuda()
+    s.dg_kin_step(w, 0.0, wl.dt, 8)
+    s.dg_kin_step(w, 8 * wl.dt, wl.dt, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.dg_kin_step(w, 9 * wl.dt, wl.dt, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s.close()
+    flops = tri_flops_per_stage(wl.p) * wl.E
+    stage_ms = ms / 4
+    ach = flops / (stage_ms * 1e-3) / 1e12
+    small = W.rider_kothe(n=16, p=3, elem="tri")
+    s = dg.KinematicSolver(small)
+    w = torch.from_numpy(small.w.copy()).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.dg_kin_step(w, 0.0, small.dt, small.nsteps)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    wend = w.cpu().numpy()
+    s.close()
+    # int f = sum over triangles of sum_n f_n int l_n, with int l_n of the cubic equispaced basis
+    # (the triangle's Newton-Cotes weights): 1/30 at the vertices, 3/40 on the edges, 9/20 at the
+    # centroid, times the area
+    wn = np.array([1 / 30, 3 / 40, 3 / 40, 1 / 30, 3 / 40, 9 / 20, 3 / 40, 3 / 40, 3 / 40, 1 / 30])
+    M = np.tile(wn * 0.5 * small.hx * small.hy, small.E)
+    l1 = float(np.sum(M * np.abs(wend[0] - small.w[0])))
+    mass = float(np.sum(M * (wend[0] - small.w[0])) / np.sum(M * small.w[0]))
+    return {"workload": f"Rider-Kothe vortex {n}x{n} cells split into {wl.E} triangles, p=3, T=4, eps=0.75h, "
+                        f"Gamma=1, FP64, classical RK4",
+            "nodes": wl.N, "steps": steps, "ms_per_step": ms, "value": 2 * 4 * wl.N / (ms * 1e-3), "unit": UNIT,
+            "gpu_launches_per_step": 4,
+            "roofline": {"bound": "alu", "kernel": "k_tri_stage", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                         "per_unit": f"{tri_flops_per_stage(wl.p)} flops per triangle and stage x {wl.E} triangles",
+                         "duration": "step time / 4 (graph of back-to-back stage kernels; gaps included)"},
+            "full_period_16x16p3": {"steps": small.nsteps, "wall_s": wall, "l1_phi": l1,
+                                    "mass_error": mass, "paper_l1_p3_64sq_dof_mesh_b": 1.58e-2}}
+
+
 def adjoint_block(dg, steps, every=20, n=128):
     """Gradient of J = 1/2 int (alpha_N - alpha*)^2 with respect to the initial state of the
     128 x 128, p = 3 drop (level set with 16 seeded Fourier coefficients, seed 5/50/51),
@@ -539,6 +605,7 @@ def run_ours(args, rank, world, local_rank):
                if (args.adjoint_steps > 0 and rank == 0) else None)
     rt = rt_block(dg, args.rt_steps) if (args.rt_steps > 0 and rank == 0) else None
     kin = kinematic_block(dg, args.kin_steps) if (args.kin_steps > 0 and rank == 0) else None
+    tri = triangle_block(dg, args.tri_steps, args.tri_n) if (args.tri_steps > 0 and rank == 0) else None
 
     ms_max, e2e_max, ref_ms = reduce_max([main["ms"], e2e_t, ref["ms"] if ref else 0.0], "cuda")
 
@@ -573,6 +640,8 @@ def run_ours(args, rank, world, local_rank):
             line["rayleigh_taylor"] = rt
         if kin:
             line["kinematic"] = kin
+        if tri:
+            line["kinematic_triangles"] = tri
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
         print(json.dumps(line), flush=True)

@@ -310,7 +310,7 @@ struct dg_ctx {
   TriKernels tk{};
   int tri_grid = 0;
   double *d_kacc = nullptr, *d_kwsA = nullptr, *d_kwsB = nullptr, *d_krvol = nullptr, *d_ktr = nullptr;
-  double *d_kt0 = nullptr, *d_kxi = nullptr;
+  double *d_kt0 = nullptr, *d_kxi = nullptr, *d_ktv = nullptr;
   // level-set re-initialisation workspace (dg_reinit), allocated on first use
   double *d_riS = nullptr, *d_ri1 = nullptr, *d_ri2 = nullptr, *d_rirvol = nullptr, *d_ritr = nullptr;
   double *d_part = nullptr, *d_diag = nullptr;
@@ -364,7 +364,7 @@ static void free_ctx(dg_ctx *c) {
   }
   cudaFree(c->d_ops);
   cudaFree(c->d_hstate);
-  for (double *q : {c->d_kacc, c->d_kwsA, c->d_kwsB, c->d_krvol, c->d_ktr, c->d_kt0, c->d_kxi}) cudaFree(q);
+  for (double *q : {c->d_kacc, c->d_kwsA, c->d_kwsB, c->d_krvol, c->d_ktr, c->d_kt0, c->d_kxi, c->d_ktv}) cudaFree(q);
   for (double *q : {c->d_riS, c->d_ri1, c->d_ri2, c->d_rirvol, c->d_ritr}) cudaFree(q);
   cudaFree(c->d_w1);
   cudaFree(c->d_w2);
@@ -1244,6 +1244,7 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
   k.eta_x = cip * c->P1 * c->P1 / c->hx;
   k.eta_y = cip * c->P1 * c->P1 / c->hy;
   k.eta_tri = cip * (p + 1) * (p + 2);
+  if (tri) tri_constants(c->hx, c->hy, k.eta_tri, k.tc);
   k.vel = vel->kind;
   k.u0 = vel->u0;
   k.v0 = vel->v0;
@@ -1265,6 +1266,7 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
   for (double **b : bufs)
     if (e == cudaSuccess && !(tri && b == &c->d_krvol)) e = cudaMalloc(b, sb);
   if (e == cudaSuccess && !tri) e = cudaMalloc(&c->d_ktr, tb);
+  if (e == cudaSuccess && tri) e = cudaMalloc(&c->d_ktv, (size_t)2 * c->E * c->tk.points * sizeof(double));
   if (e == cudaSuccess && tri) {
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
@@ -1292,6 +1294,16 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
   k.xi = c->d_kxi;
   k.t0 = c->d_kt0;
   k.status = c->d_status;
+  k.tri_vel = c->d_ktv;
+  if (tri) {  // the spatial factor of the velocity at every quadrature point, once
+    e = c->tk.velocity_table(k, c->d_ktv, c->cap);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->cap);
+    if (e != cudaSuccess) {
+      free_ctx(c);
+      cudaGetLastError();
+      return fail(nullptr, DG_ERR_CUDA, std::string("dg_kin_create: velocity table: ") + cudaGetErrorString(e));
+    }
+  }
   *out = c;
   return DG_OK;
 }

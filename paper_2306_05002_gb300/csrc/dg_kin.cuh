@@ -28,6 +28,15 @@ enum KinMode { KIN_RHS = 0, KIN_K1 = 1, KIN_K2 = 2, KIN_K3 = 3, KIN_K4 = 4 };
 // Kinematic face-trace record: phi, psi, d(phi)/d(axis), n_axis, u_axis.
 enum { K_PHI = 0, K_PSI, K_GPHI, K_N, K_U, NT_KIN };
 
+// Constants of one triangle type of the split-rectangle mesh (dg_tri.cuh): det = d(x,y)/d(r,s),
+// its inverse, the inverse-map derivatives, and per edge f the outward unit normal m, half the
+// edge length, the penalty eta_tri / h_e and the reference components of grad l . m
+// (gr = rx m0 + ry m1, gs = sx m0 + sy m1).
+struct TriConst {
+  double det, idet, rx, ry, sx, sy;
+  double m0[3], m1[3], hl[3], eta[3], gr[3], gs[3];
+};
+
 struct KinParams {
   int nx, ny, E, N;
   double x0, y0, hx, hy;
@@ -36,6 +45,8 @@ struct KinParams {
   double u0, v0, T;        // uniform velocity; Rider-Kothe period
   double xc, yc;           // Rider-Kothe vortex centre
   double eta_tri;          // triangles: c_ip (p+1)(p+2); the edge penalty is eta_tri / h_e
+  TriConst tc[2];          // triangles: the two element types
+  const double *tri_vel;   // triangles: time-independent velocity factor at every quadrature point
   const double *ops;       // operator table (OpsLayout)
   const double *xi;        // GLL nodes on [-1, 1]
   const double *t0;        // device: time at the start of the captured step sequence

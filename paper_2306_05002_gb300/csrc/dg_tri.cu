@@ -6,13 +6,44 @@
 
 namespace dgpf {
 
+template <int P>
+static TriKernels tri_set() {
+  return {&launch_tri_stage<P>, &launch_tri_velocity_table<P>, (const void *)&k_tri_stage<P>, TriGeom<P>::THREADS,
+          TriGeom<P>::NQV + TriGeom<P>::NQE};
+}
+
 bool tri_kernels(int p, TriKernels *out) {
   switch (p) {
-    case 1: *out = {&launch_tri_stage<1>, (const void *)&k_tri_stage<1>, TriGeom<1>::THREADS}; return true;
-    case 2: *out = {&launch_tri_stage<2>, (const void *)&k_tri_stage<2>, TriGeom<2>::THREADS}; return true;
-    case 3: *out = {&launch_tri_stage<3>, (const void *)&k_tri_stage<3>, TriGeom<3>::THREADS}; return true;
-    case 4: *out = {&launch_tri_stage<4>, (const void *)&k_tri_stage<4>, TriGeom<4>::THREADS}; return true;
+    case 1: *out = tri_set<1>(); return true;
+    case 2: *out = tri_set<2>(); return true;
+    case 3: *out = tri_set<3>(); return true;
+    case 4: *out = tri_set<4>(); return true;
     default: return false;
+  }
+}
+
+void tri_constants(double hx, double hy, double eta_tri, TriConst tc[2]) {
+  for (int type = 0; type < 2; ++type) {
+    const double v[3][2] = {{0.0, 0.0}, {hx, type == 0 ? 0.0 : hy}, {type == 0 ? hx : 0.0, hy}};
+    TriConst &g = tc[type];
+    const double xr = 0.5 * (v[1][0] - v[0][0]), yr = 0.5 * (v[1][1] - v[0][1]);
+    const double xs = 0.5 * (v[2][0] - v[0][0]), ys = 0.5 * (v[2][1] - v[0][1]);
+    g.det = xr * ys - xs * yr;
+    g.idet = 1.0 / g.det;
+    g.rx = ys / g.det;
+    g.ry = -xs / g.det;
+    g.sx = -yr / g.det;
+    g.sy = xr / g.det;
+    for (int f = 0; f < 3; ++f) {
+      const int fn = (f + 1) % 3;
+      const double dx = v[fn][0] - v[f][0], dy = v[fn][1] - v[f][1], len = std::sqrt(dx * dx + dy * dy);
+      g.m0[f] = dy / len;
+      g.m1[f] = -dx / len;
+      g.hl[f] = 0.5 * len;
+      g.eta[f] = eta_tri / (2.0 * (2.0 * g.det) / len);  // h_e = 2 |T| / |e|, |T| = 2 det
+      g.gr[f] = g.rx * g.m0[f] + g.ry * g.m1[f];
+      g.gs[f] = g.sx * g.m0[f] + g.sy * g.m1[f];
+    }
   }
 }
 

@@ -25,7 +25,11 @@
 // point), the weak-form sums (one thread per node) and M^-1 with the stage
 // update (one thread per node).  Neighbour values are read from the stage
 // input, which no stage writes, so the stages need no other synchronisation
-// than stream order.
+// than stream order.  FP64 is the bound, so what does not change between
+// stages is computed once: the geometry of the two triangle types (host) and
+// the spatial factor of the velocity at every quadrature point (device, at
+// creation) -- the trigonometric functions would otherwise cost as much as the
+// scheme itself.
 #pragma once
 
 #include <vector>
@@ -68,35 +72,17 @@ struct TriGeom {
   static constexpr int THREADS = 128;
 };
 
-// Affine map of one triangle: counter-clockwise vertices, det = d(x,y)/d(r,s),
-// inverse-map derivatives.
-struct TriMap {
-  double v[3][2];
-  double det, rx, ry, sx, sy;
-};
 
-__device__ __forceinline__ void tri_map_of(const KinParams &kp, int e, TriMap *g) {
+// Counter-clockwise vertices of triangle e (cell (i, j), type e & 1).
+__device__ __forceinline__ void tri_vertices(const KinParams &kp, int e, double v[3][2]) {
   const int cell = e >> 1, type = e & 1;
-  const int ci = cell % kp.nx, cj = cell / kp.nx;
-  const double x0 = kp.x0 + ci * kp.hx, y0 = kp.y0 + cj * kp.hy;
-  g->v[0][0] = x0;
-  g->v[0][1] = y0;
-  g->v[1][0] = x0 + kp.hx;
-  g->v[1][1] = type == 0 ? y0 : y0 + kp.hy;
-  g->v[2][0] = type == 0 ? x0 + kp.hx : x0;
-  g->v[2][1] = y0 + kp.hy;
-  const double xr = 0.5 * (g->v[1][0] - g->v[0][0]), yr = 0.5 * (g->v[1][1] - g->v[0][1]);
-  const double xs = 0.5 * (g->v[2][0] - g->v[0][0]), ys = 0.5 * (g->v[2][1] - g->v[0][1]);
-  g->det = xr * ys - xs * yr;
-  g->rx = ys / g->det;
-  g->ry = -xs / g->det;
-  g->sx = -yr / g->det;
-  g->sy = xr / g->det;
-}
-
-__device__ __forceinline__ void tri_point(const TriMap &g, double r, double s, double *x, double *y) {
-  *x = g.v[0][0] + 0.5 * (1.0 + r) * (g.v[1][0] - g.v[0][0]) + 0.5 * (1.0 + s) * (g.v[2][0] - g.v[0][0]);
-  *y = g.v[0][1] + 0.5 * (1.0 + r) * (g.v[1][1] - g.v[0][1]) + 0.5 * (1.0 + s) * (g.v[2][1] - g.v[0][1]);
+  const double x0 = kp.x0 + (cell % kp.nx) * kp.hx, y0 = kp.y0 + (cell / kp.nx) * kp.hy;
+  v[0][0] = x0;
+  v[0][1] = y0;
+  v[1][0] = x0 + kp.hx;
+  v[1][1] = type == 0 ? y0 : y0 + kp.hy;
+  v[2][0] = type == 0 ? x0 + kp.hx : x0;
+  v[2][1] = y0 + kp.hy;
 }
 
 // Periodic neighbour across edge f (0: v1 v2, 1: v2 v3, 2: v3 v1) and its edge index.
@@ -116,21 +102,62 @@ __device__ __forceinline__ int tri_neighbour(const KinParams &kp, int e, int f, 
   return 2 * ((ci > 0 ? ci - 1 : kp.nx - 1) + kp.nx * cj);
 }
 
-// phi, psi, their physical gradients, n and a_1 at one point, from the nodal
-// values f[2][NP] and the basis rows (values, r- and s-derivatives).
+// The prescribed velocity is u(x, t) = c(t) U(x): c = cos(pi t / T) and U the spatial factor of
+// the Rider-Kothe vortex, or c = 1 and U = (u0, v0).  U is evaluated once, at every volume and
+// edge point of every triangle, when the context is created (k_tri_velocity_table); a stage
+// multiplies by c.  Table layout: [e][NQV + NQE][2], volume points first.
+__device__ __forceinline__ double tri_time_factor(const KinParams &kp, double t) {
+  return kp.vel == VEL_RIDER_KOTHE ? cos(CUDART_PI * t / kp.T) : 1.0;
+}
+
+template <int P>
+__global__ void k_tri_velocity_table(const KinParams kp, double *__restrict__ tab) {
+  using G = TriGeom<P>;
+  constexpr TriLayout L = G::L;
+  constexpr int NPT = G::NQV + G::NQE;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)kp.E * NPT) return;
+  const int e = (int)(i / NPT), q = (int)(i % NPT);
+  double v[3][2];
+  tri_vertices(kp, e, v);
+  const double r = q < G::NQV ? kp.ops[L.rv() + q] : kp.ops[L.re() + q - G::NQV];
+  const double s = q < G::NQV ? kp.ops[L.sv() + q] : kp.ops[L.se() + q - G::NQV];
+  const double x = v[0][0] + 0.5 * (1.0 + r) * (v[1][0] - v[0][0]) + 0.5 * (1.0 + s) * (v[2][0] - v[0][0]);
+  const double y = v[0][1] + 0.5 * (1.0 + r) * (v[1][1] - v[0][1]) + 0.5 * (1.0 + s) * (v[2][1] - v[0][1]);
+  double U = kp.u0, V = kp.v0;
+  if (kp.vel == VEL_RIDER_KOTHE) {
+    const double X = x - kp.xc + 0.5, Y = y - kp.yc + 0.5;
+    const double sx = sin(CUDART_PI * X), sy = sin(CUDART_PI * Y);
+    U = sx * sx * sin(2.0 * CUDART_PI * Y);
+    V = -sin(2.0 * CUDART_PI * X) * sy * sy;
+  }
+  tab[2 * i] = U;
+  tab[2 * i + 1] = V;
+}
+
+template <int P>
+cudaError_t launch_tri_velocity_table(const KinParams &kp, double *tab, cudaStream_t s) {
+  constexpr int NPT = TriGeom<P>::NQV + TriGeom<P>::NQE;
+  const long n = (long)kp.E * NPT;
+  k_tri_velocity_table<P><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(kp, tab);
+  return cudaGetLastError();
+}
+
+// phi, psi, their physical gradients and a_1 at one point, from the nodal values and the basis
+// rows (values, r- and s-derivatives) of a triangle of constants g.
 struct TriPoint {
   double phi, psi, gp[2], gs[2], n[2], a1[2];
 };
 
-template <int NP>
-__device__ __forceinline__ void tri_eval_point(const KinParams &kp, const TriMap &g, const double *fphi,
+template <int NP, bool PSI_VALUE>
+__device__ __forceinline__ void tri_eval_point(const KinParams &kp, const TriConst &g, const double *fphi,
                                                const double *fpsi, const double *B, const double *Br,
                                                const double *Bs, TriPoint *o) {
   double ph = 0.0, ps = 0.0, pr = 0.0, pq = 0.0, sr = 0.0, sq = 0.0;
 #pragma unroll
   for (int n = 0; n < NP; ++n) {
     ph = fma(B[n], fphi[n], ph);
-    ps = fma(B[n], fpsi[n], ps);
+    if (PSI_VALUE) ps = fma(B[n], fpsi[n], ps);  // psi itself is needed at the edges only
     pr = fma(Br[n], fphi[n], pr);
     pq = fma(Bs[n], fphi[n], pq);
     sr = fma(Br[n], fpsi[n], sr);
@@ -142,11 +169,12 @@ __device__ __forceinline__ void tri_eval_point(const KinParams &kp, const TriMap
   o->gp[1] = pr * g.ry + pq * g.sy;
   o->gs[0] = sr * g.rx + sq * g.sx;
   o->gs[1] = sr * g.ry + sq * g.sy;
-  const double norm = sqrt(o->gs[0] * o->gs[0] + o->gs[1] * o->gs[1]);
+  const double g2 = o->gs[0] * o->gs[0] + o->gs[1] * o->gs[1];
+  const double rn = g2 < 1e-24 ? 0.0 : rsqrt(g2);  // n = 0 where |grad psi| < 1e-12
   const double sp = ph * (1.0 - ph);
 #pragma unroll
   for (int d = 0; d < 2; ++d) {
-    o->n[d] = norm < 1e-12 ? 0.0 : o->gs[d] / norm;
+    o->n[d] = o->gs[d] * rn;
     o->a1[d] = kp.Gamma * (kp.eps * o->gp[d] - sp * o->n[d]);
   }
 }
@@ -162,6 +190,7 @@ k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
   using G = TriGeom<P>;
   constexpr TriLayout L = G::L;
   constexpr int NP = G::NP, NQ1 = G::NQ1, NQV = G::NQV, NQE = G::NQE, EPB = G::EPB;
+  constexpr int NPT = NQV + NQE;
   __shared__ double s_t[L.size()];
   __shared__ double s_w[EPB][2][NP];
   __shared__ double s_nb[EPB][3][2][NP];
@@ -169,7 +198,7 @@ k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
   __shared__ double s_ce[EPB][NQE][4];
   __shared__ double s_R[EPB][2][NP];
   for (int i = threadIdx.x; i < L.size(); i += blockDim.x) s_t[i] = kp.ops[i];
-  const double t = (*kp.t0 + tstep) + toff;
+  const double c = tri_time_factor(kp, (*kp.t0 + tstep) + toff);
   const int N = kp.N, ngroups = (kp.E + EPB - 1) / EPB;
   bool bad = false;
 
@@ -194,72 +223,56 @@ k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
     // 2. Volume points: coefficients of l_n, dl_n/dr, dl_n/ds (phi) and l_n (psi).
     for (int it = threadIdx.x; it < EPB * NQV; it += blockDim.x) {
       const int le = it / NQV, q = it % NQV, e = e0 + le;
-      double c[4] = {0.0, 0.0, 0.0, 0.0};
+      double cv[4] = {0.0, 0.0, 0.0, 0.0};
       if (e < kp.E) {
-        TriMap g;
-        tri_map_of(kp, e, &g);
+        const TriConst &g = kp.tc[e & 1];
         TriPoint o;
-        tri_eval_point<NP>(kp, g, s_w[le][0], s_w[le][1], s_t + L.bv() + q * NP, s_t + L.brv() + q * NP,
+        tri_eval_point<NP, false>(kp, g, s_w[le][0], s_w[le][1], s_t + L.bv() + q * NP, s_t + L.brv() + q * NP,
                            s_t + L.bsv() + q * NP, &o);
-        double x, y, u, v;
-        tri_point(g, s_t[L.rv() + q], s_t[L.sv() + q], &x, &y);
-        kin_velocity(kp, x, y, t, &u, &v);
+        const double2 U = __ldg(reinterpret_cast<const double2 *>(kp.tri_vel) + (long)e * NPT + q);
+        const double u = U.x * c, v = U.y * c;
         const double wq = s_t[L.wv() + q] * g.det;
-        c[0] = -wq * (u * o.gp[0] + v * o.gp[1]);
-        c[1] = -wq * (o.a1[0] * g.rx + o.a1[1] * g.ry);
-        c[2] = -wq * (o.a1[0] * g.sx + o.a1[1] * g.sy);
-        c[3] = -wq * (u * o.gs[0] + v * o.gs[1]);
+        cv[0] = -wq * (u * o.gp[0] + v * o.gp[1]);
+        cv[1] = -wq * (o.a1[0] * g.rx + o.a1[1] * g.ry);
+        cv[2] = -wq * (o.a1[0] * g.sx + o.a1[1] * g.sy);
+        cv[3] = -wq * (u * o.gs[0] + v * o.gs[1]);
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) s_cv[le][q][k] = c[k];
+      for (int k = 0; k < 4; ++k) s_cv[le][q][k] = cv[k];
     }
     // 3. Edge points: transport and SIP fluxes, the symmetric term.
     for (int it = threadIdx.x; it < EPB * NQE; it += blockDim.x) {
       const int le = it / NQE, fk = it % NQE, f = fk / NQ1, k = fk % NQ1, e = e0 + le;
-      double c[4] = {0.0, 0.0, 0.0, 0.0};
+      double ce[4] = {0.0, 0.0, 0.0, 0.0};
       if (e < kp.E) {
         int f2;
         const int e2 = tri_neighbour(kp, e, f, &f2);
         const int fk2 = f2 * NQ1 + (NQ1 - 1 - k);  // the same physical point, seen from the neighbour
-        TriMap g, g2;
-        tri_map_of(kp, e, &g);
-        tri_map_of(kp, e2, &g2);
+        const TriConst &g = kp.tc[e & 1], &g2 = kp.tc[e2 & 1];
         TriPoint om, op;
-        tri_eval_point<NP>(kp, g, s_w[le][0], s_w[le][1], s_t + L.be() + fk * NP, s_t + L.bre() + fk * NP,
+        tri_eval_point<NP, true>(kp, g, s_w[le][0], s_w[le][1], s_t + L.be() + fk * NP, s_t + L.bre() + fk * NP,
                            s_t + L.bse() + fk * NP, &om);
-        tri_eval_point<NP>(kp, g2, s_nb[le][f][0], s_nb[le][f][1], s_t + L.be() + fk2 * NP,
+        tri_eval_point<NP, true>(kp, g2, s_nb[le][f][0], s_nb[le][f][1], s_t + L.be() + fk2 * NP,
                            s_t + L.bre() + fk2 * NP, s_t + L.bse() + fk2 * NP, &op);
-        double x, y, x2, y2, u, v, u2, v2;
-        tri_point(g, s_t[L.re() + fk], s_t[L.se() + fk], &x, &y);
-        tri_point(g2, s_t[L.re() + fk2], s_t[L.se() + fk2], &x2, &y2);
-        kin_velocity(kp, x, y, t, &u, &v);
-        kin_velocity(kp, x2, y2, t, &u2, &v2);
-        // edge vector v[f] -> v[f+1], by selects (a dynamic index would put g in local memory)
-        const double ax = f == 0 ? g.v[0][0] : (f == 1 ? g.v[1][0] : g.v[2][0]);
-        const double ay = f == 0 ? g.v[0][1] : (f == 1 ? g.v[1][1] : g.v[2][1]);
-        const double bx = f == 0 ? g.v[1][0] : (f == 1 ? g.v[2][0] : g.v[0][0]);
-        const double by = f == 0 ? g.v[1][1] : (f == 1 ? g.v[2][1] : g.v[0][1]);
-        const double dx = bx - ax, dy = by - ay;
-        const double len = sqrt(dx * dx + dy * dy);
-        const double m0 = dy / len, m1 = -dx / len;
-        const double he = 2.0 * (2.0 * g.det) / len;
-        const double eta = kp.eta_tri / he;
-        const double wf = s_t[L.we() + k] * 0.5 * len;
-        const double unm = u * m0 + v * m1, unp = u2 * m0 + v2 * m1;
+        const double2 *vt = reinterpret_cast<const double2 *>(kp.tri_vel);
+        const double2 U = __ldg(vt + (long)e * NPT + NQV + fk), U2 = __ldg(vt + (long)e2 * NPT + NQV + fk2);
+        const double m0 = g.m0[f], m1 = g.m1[f];
+        const double unm = U.x * c * m0 + U.y * c * m1, unp = U2.x * c * m0 + U2.y * c * m1;
         const double lam = fmax(fabs(unm), fabs(unp));
+        const double wf = s_t[L.we() + k] * g.hl[f];
         const double jump = op.phi - om.phi, hjs = 0.5 * (op.psi - om.psi);
         const double gn = 0.5 * ((op.gp[0] + om.gp[0]) * m0 + (op.gp[1] + om.gp[1]) * m1);
         const double sharp = 0.5 * (op.phi * (1.0 - op.phi) * (op.n[0] * m0 + op.n[1] * m1) +
                                     om.phi * (1.0 - om.phi) * (om.n[0] * m0 + om.n[1] * m1));
-        const double ahat = kp.Gamma * (kp.eps * (gn + eta * jump) - sharp);
+        const double ahat = kp.Gamma * (kp.eps * (gn + g.eta[f] * jump) - sharp);
         const double sym = 0.5 * kp.Gamma * kp.eps * jump;
-        c[0] = wf * ((lam - unm) * 0.5 * jump + ahat);
-        c[1] = -wf * sym * (g.rx * m0 + g.ry * m1);
-        c[2] = -wf * sym * (g.sx * m0 + g.sy * m1);
-        c[3] = wf * (lam - unm) * hjs;
+        ce[0] = wf * ((lam - unm) * 0.5 * jump + ahat);
+        ce[1] = -wf * sym * g.gr[f];
+        ce[2] = -wf * sym * g.gs[f];
+        ce[3] = wf * (lam - unm) * hjs;
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) s_ce[le][fk][q] = c[q];
+      for (int q = 0; q < 4; ++q) s_ce[le][fk][q] = ce[q];
     }
     __syncthreads();
     // 4. Weak-form sums R_n (volume points, then edge points).
@@ -268,15 +281,15 @@ k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
       double rp = 0.0, rs = 0.0;
 #pragma unroll 4
       for (int q = 0; q < NQV; ++q) {
-        const double *c = s_cv[le][q];
-        rp += c[0] * s_t[L.bv() + q * NP + n] + c[1] * s_t[L.brv() + q * NP + n] + c[2] * s_t[L.bsv() + q * NP + n];
-        rs += c[3] * s_t[L.bv() + q * NP + n];
+        const double *cq = s_cv[le][q];
+        rp += cq[0] * s_t[L.bv() + q * NP + n] + cq[1] * s_t[L.brv() + q * NP + n] + cq[2] * s_t[L.bsv() + q * NP + n];
+        rs += cq[3] * s_t[L.bv() + q * NP + n];
       }
 #pragma unroll 4
       for (int q = 0; q < NQE; ++q) {
-        const double *c = s_ce[le][q];
-        rp += c[0] * s_t[L.be() + q * NP + n] + c[1] * s_t[L.bre() + q * NP + n] + c[2] * s_t[L.bse() + q * NP + n];
-        rs += c[3] * s_t[L.be() + q * NP + n];
+        const double *cq = s_ce[le][q];
+        rp += cq[0] * s_t[L.be() + q * NP + n] + cq[1] * s_t[L.bre() + q * NP + n] + cq[2] * s_t[L.bse() + q * NP + n];
+        rs += cq[3] * s_t[L.be() + q * NP + n];
       }
       s_R[le][0][n] = rp;
       s_R[le][1][n] = rs;
@@ -286,14 +299,13 @@ k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
     for (int it = threadIdx.x; it < EPB * NP; it += blockDim.x) {
       const int le = it / NP, n = it % NP, e = e0 + le;
       if (e >= kp.E) continue;
-      TriMap g;
-      tri_map_of(kp, e, &g);
+      const double idet = kp.tc[e & 1].idet;
 #pragma unroll
       for (int vv = 0; vv < 2; ++vv) {
         double a = 0.0;
 #pragma unroll
         for (int j = 0; j < NP; ++j) a = fma(s_t[L.minv() + n * NP + j], s_R[le][vv][j], a);
-        const double Lv = a / g.det;
+        const double Lv = a * idet;
         const long o = (long)vv * N + (long)e * NP + n;
         double r;
         if (mode == KIN_RHS) {
@@ -324,8 +336,10 @@ k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
 struct TriKernels {
   cudaError_t (*stage)(const KinParams &, int mode, double tstep, double toff, double dt, const double *win,
                        const double *w0, double *acc, double *out, int grid, cudaStream_t);
-  const void *fn;  // the kernel, for the occupancy query
+  cudaError_t (*velocity_table)(const KinParams &, double *tab, cudaStream_t);
+  const void *fn;  // the stage kernel, for the occupancy query
   int threads;
+  int points;      // volume + edge points per triangle (rows of the velocity table)
 };
 
 template <int P>
@@ -337,9 +351,11 @@ cudaError_t launch_tri_stage(const KinParams &kp, int mode, double tstep, double
 
 // Kernels of order p (1..4); false for other orders.
 bool tri_kernels(int p, TriKernels *out);
-// Groups of triangles one CTA processes per pass (EPB of order p).
+// Triangles one CTA processes per pass (EPB of order p).
 int tri_group(int p);
 // Reference tables of order p in the TriLayout order; empty on failure.
 std::vector<double> tri_tables(int p);
+// Constants of the two triangle types of cells hx x hy (penalty factor eta_tri = c_ip (p+1)(p+2)).
+void tri_constants(double hx, double hy, double eta_tri, TriConst tc[2]);
 
 }  // namespace dgpf

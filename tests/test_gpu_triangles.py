@@ -7,8 +7,9 @@ the oracle:
   of the persistent grid walks several groups;
 * RK4 steps (a graph of 8 steps plus single steps) against the oracle's RK4;
 * the Rider-Kothe vortex over a full period on 16 x 16 and 32 x 32 cells, p = 3: the drop comes
-  back, its mass is kept, and the L1 error falls under refinement and sits near the paper's
-  mesh (b) p = 3 values (a results-level comparison: the paper states neither Gamma nor eps).
+  back, its mass is kept to round-off, and the L1 error falls under refinement, matches the
+  rectangles' and sits near the paper's mesh (b) p = 3 values (a results-level comparison: the
+  paper states neither Gamma nor eps).
 """
 import numpy as np
 import pytest
@@ -89,10 +90,16 @@ def test_tri_reinit_is_rejected(dg):
     s.close()
 
 
-def _rider_kothe_tri(dg, orc, n):
+def _rider_kothe(dg, orc, n, elem):
     import torch
-    wl = W.rider_kothe(n=n, p=3, elem="tri")
+    wl = W.rider_kothe(n=n, p=3, elem=elem)
     pb = orc.Problem(**wl.problem_kwargs())
+    if elem == "tri":
+        integral = lambda f: orc.tri_integral(pb, f)
+    else:
+        _, wt = orc.gll(wl.p)
+        M = np.tile(np.outer(wt, wt).ravel() * 0.25 * wl.hx * wl.hy, wl.nx * wl.ny)
+        integral = lambda f: float(np.sum(M * f))
     s = dg.KinematicSolver(wl)
     w = torch.from_numpy(wl.w.copy()).cuda()
     half = wl.nsteps // 2
@@ -102,20 +109,27 @@ def _rider_kothe_tri(dg, orc, n):
     w_end = w.cpu().numpy()
     assert s.dg_status_read() == 0
     s.close()
-    l1_half = orc.tri_integral(pb, np.abs(w_half[0] - wl.w[0]))
-    l1_end = orc.tri_integral(pb, np.abs(w_end[0] - wl.w[0]))
-    mass_err = abs(orc.tri_integral(pb, w_end[0] - wl.w[0]) / orc.tri_integral(pb, wl.w[0]))
+    l1_half = integral(np.abs(w_half[0] - wl.w[0]))
+    l1_end = integral(np.abs(w_end[0] - wl.w[0]))
+    mass_err = abs(integral(w_end[0] - wl.w[0]) / integral(wl.w[0]))
     return l1_half, l1_end, mass_err
 
 
 def test_rider_kothe_full_period_on_triangles(orc, dg):
     """16 x 16 and 32 x 32 cells, each split in two, p = 3 (the paper's 64^2 and 128^2 mesh (b)
-    rows): the drop comes back, the L1 error falls under refinement and stays within a factor 3
-    of the paper's mesh (b), p = 3 values (1.58e-2, 4.03e-3), and the phase-field mass is kept."""
-    res = {n: _rider_kothe_tri(dg, orc, n) for n in (16, 32)}
+    rows): the drop comes back, the L1 error falls under refinement, it is close to the one on
+    the rectangles of the same cells (the paper finds the two meshes give almost the same
+    interface), it stays within a factor 4 of the paper's mesh (b), p = 3 values (1.58e-2,
+    4.03e-3; loose, since the paper states neither Gamma nor eps for this test), and the
+    phase-field mass error sits near round-off (the paper: 1e-10 down to machine precision for
+    p = 3): the velocity is exact at the quadrature points and the quadrature integrates the
+    transport of a divergence-free field almost exactly."""
+    tri = {n: _rider_kothe(dg, orc, n, "tri") for n in (16, 32)}
+    quad = {n: _rider_kothe(dg, orc, n, "quad") for n in (16, 32)}
     for n, paper in ((16, 1.58e-2), (32, 4.03e-3)):
-        l1_half, l1_end, mass_err = res[n]
-        assert l1_end < 0.5 * l1_half, (n, res)
-        assert l1_end < 3 * paper, (n, res)
-        assert mass_err < 1e-6, (n, res)
-    assert res[32][1] < 0.5 * res[16][1], res
+        l1_half, l1_end, mass_err = tri[n]
+        assert l1_end < 0.5 * l1_half, (n, tri)
+        assert l1_end < 4 * paper, (n, tri)
+        assert 0.67 < l1_end / quad[n][1] < 1.5, (n, tri, quad)
+        assert mass_err < 1e-10, (n, tri)
+    assert tri[32][1] < 0.5 * tri[16][1], tri
