@@ -224,11 +224,11 @@ def weak_scaling_value(units_per_rank: float, steps: int, world: int, ms_max: fl
 
 # --------------------------------------------------------------------------- oracle leg
 
-def oracle_rate(wl, steps: int):
+def oracle_rate(wl, steps: int, threads: int = 0):
     import oracle
     pb = oracle.Problem(**wl.problem_kwargs())
     t0 = time.perf_counter()
-    oracle.rk3(pb, wl.w, wl.dt, steps)
+    oracle.rk3(pb, wl.w, wl.dt, steps, threads=threads)
     dt = time.perf_counter() - t0
     return 7 * wl.N * 3 * steps / dt, dt
 
@@ -238,8 +238,20 @@ def cpu_baseline(wl, steps: int):
         _, t1 = oracle_rate(wl, 1)
         steps = max(1, min(200, int(15.0 / max(t1, 1e-3))))
     rate, secs = oracle_rate(wl, steps)
-    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+    line = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{steps} SSP-RK3 steps of the same workload ({secs:.1f} s, single-threaded plain C FP64)"}
+    # the same oracle source built with its element loops parallel (OpenMP), on every host core
+    try:
+        import oracle
+        cores = os.cpu_count() or 1
+        used = oracle.lib(openmp=True).orc_threads(cores)
+        oracle_rate(wl, 1, threads=used)
+        r_omp, s_omp = oracle_rate(wl, steps, threads=used)
+        line["openmp"] = {"value": r_omp, "unit": UNIT, "cores": used, "kind": "oracle (OpenMP over elements)",
+                          "sample": f"the same {steps} steps ({s_omp:.1f} s)"}
+    except Exception as exc:  # a host compiler without OpenMP: report the plain run only
+        line["openmp"] = {"unavailable": str(exc)[:200]}
+    return line
 
 
 def run_reference(args, rank, world):

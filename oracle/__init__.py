@@ -25,23 +25,27 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dg_oracle.c")
 _SRC_TRI = os.path.join(_HERE, "dg_oracle_tri.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 
 BC = {"periodic": 0, "noslip": 1, "slip": 2, "pressure": 3}
 NV = 7
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liboracle.so`` (gcc, FP64, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (gcc, FP64, no FMA contraction), or, with
+    ``openmp``, the same source with its element loops parallel into ``oracle/liboracle_omp.so``
+    (used only to time the oracle on all host cores; the tests pin the plain build)."""
+    out = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < max(
         os.path.getmtime(_SRC), os.path.getmtime(_SRC_TRI), os.path.getmtime(os.path.join(_HERE, "dg_oracle.h"))
     ):
-        tmp = _LIB + f".tmp{os.getpid()}"
+        tmp = out + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC", "-shared",
-             "-o", tmp, _SRC, _SRC_TRI, "-lm"]
+            ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC", "-shared"]
+            + (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, _SRC_TRI, "-lm"]
         )
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
 
 
 class _Problem(ctypes.Structure):
@@ -133,13 +137,16 @@ class Velocity:
         return s
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
+def lib(openmp: bool = False):
+    """The plain oracle library, or (``openmp``) its OpenMP build."""
+    _lib = _libs.get(openmp)
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        _lib = _libs[openmp] = ctypes.CDLL(build(openmp=openmp))
+        _lib.orc_threads.argtypes = [ctypes.c_int]
+        _lib.orc_threads.restype = ctypes.c_int
         dp = ctypes.POINTER(ctypes.c_double)
         pp = ctypes.POINTER(_Problem)
         _lib.orc_gll.argtypes = [ctypes.c_int, dp, dp]
@@ -230,12 +237,27 @@ def rhs(pb: Problem, w, want_scale: bool = False, want_parts: bool = False):
     return out[0] if len(out) == 1 else tuple(out)
 
 
-def rk3(pb: Problem, w, dt: float, nsteps: int):
-    """Return w after nsteps SSP-RK3 steps (input left untouched)."""
+def rk3(pb: Problem, w, dt: float, nsteps: int, threads: int = 0):
+    """Return w after nsteps SSP-RK3 steps (input left untouched).  threads > 0 runs the OpenMP
+    build on that many threads (bit-identical results)."""
     w = np.array(w, dtype=np.float64).reshape(NV, pb.N).copy()
     s = pb._c()
-    _check(lib().orc_rk3(ctypes.byref(s), _ptr(w), float(dt), int(nsteps)), "rk3")
+    L = lib(openmp=threads > 0)
+    if threads > 0:
+        L.orc_threads(int(threads))
+    _check(L.orc_rk3(ctypes.byref(s), _ptr(w), float(dt), int(nsteps)), "rk3")
     return w
+
+
+def rhs_threads(pb: Problem, w, threads: int):
+    """The right-hand side from the OpenMP build on `threads` threads (for its bitwise check)."""
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(NV, pb.N)
+    L = np.zeros((NV, pb.N))
+    s = pb._c()
+    lb = lib(openmp=True)
+    lb.orc_threads(int(threads))
+    _check(lb.orc_rhs(ctypes.byref(s), _ptr(w), _ptr(L), None, None), "rhs")
+    return L
 
 
 def diag(pb: Problem, w):

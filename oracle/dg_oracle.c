@@ -82,6 +82,27 @@
 #define NV ORC_NV
 #define MAXP 8
 
+/* Loops over elements (or nodes) whose iterations write only their own
+   element's (or node's) entries: the OpenMP build (-fopenmp) runs them in
+   parallel and computes bit-identical results; the plain build, the one the
+   tests pin, is single-threaded. */
+#ifdef _OPENMP
+#include <omp.h>
+#define OMP_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define OMP_FOR
+#endif
+
+int orc_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* One-dimensional operators                                                */
 /* ------------------------------------------------------------------------ */
@@ -389,6 +410,7 @@ int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double
   acc_t src = {R, A, parts ? parts + 2 * NV * N : NULL, N};
 
   /* 1. Pointwise closure at every node. */
+  OMP_FOR
   for (long n = 0; n < N; ++n) {
     double wn[NV];
     for (int v = 0; v < NV; ++v) wn[v] = w[v * N + n];
@@ -396,6 +418,7 @@ int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double
   }
 
   /* 2. Broken (element-local) gradients: grad f(x_a) = sum_b f_b grad l_b(x_a). */
+  OMP_FOR
   for (int e = 0; e < g.E; ++e) {
     for (int a = 0; a < Np; ++a) {
       node_t *t = &nd[(long)e * Np + a];
@@ -415,6 +438,7 @@ int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double
   }
 
   /* 3. Normal from the level set, a_1, viscous stress. */
+  OMP_FOR
   for (long n = 0; n < N; ++n) {
     node_t *t = &nd[n];
     double norm = sqrt(t->gpsi[0] * t->gpsi[0] + t->gpsi[1] * t->gpsi[1]);
@@ -436,6 +460,7 @@ int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double
 
   /* 4. Curvature kappa = -div n (broken derivative of the nodal normal). */
   if (pr->surface_tension) {
+    OMP_FOR
     for (int e = 0; e < g.E; ++e)
       for (int a = 0; a < Np; ++a) {
         double div = 0.0;
@@ -452,6 +477,7 @@ int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double
   /* 5. Volume term  sum_k w_k J grad l_a(x_k) . F_k  for the conservative
         fluxes F (moved to the right-hand side), written per equation as in
         the weak forms of Sec. 3. */
+  OMP_FOR
   for (int e = 0; e < g.E; ++e) {
     for (int k = 0; k < Np; ++k) {
       const node_t *t = &nd[(long)e * Np + k];
@@ -507,6 +533,7 @@ int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double
 
   /* 6. Non-conservative transport -int l_a u.grad(phi) (and psi), and the
         sources of Sec. 2 (gravity, CSF surface tension). */
+  OMP_FOR
   for (int e = 0; e < g.E; ++e)
     for (int a = 0; a < Np; ++a) {
       long n = (long)e * Np + a;
@@ -537,6 +564,7 @@ int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double
         "+" = neighbour trace (or wall ghost), m = outward unit normal. */
   const int nf = g.dim == 2 ? 4 : 2;
   const int nk = g.dim == 2 ? P1 : 1;
+  OMP_FOR
   for (int e = 0; e < g.E; ++e) {
     for (int f = 0; f < nf; ++f) {
       int e2 = neighbour(&g, e, f);
@@ -678,6 +706,7 @@ int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double
   }
 
   /* 8. Apply the inverse of the diagonal (collocated) mass matrix. */
+  OMP_FOR
   for (int e = 0; e < g.E; ++e)
     for (int a = 0; a < Np; ++a) {
       long n = (long)e * Np + a;

@@ -58,6 +58,11 @@ int orc_primitives(const orc_problem *pr, const double *w, double *prim);
  * penalty term) and source parts of L separately.
  */
 int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double *parts);
+
+/* Threads of the OpenMP build (liboracle_omp.so): n > 0 sets the count; returns
+   the count in use (1 in the plain build). */
+int orc_threads(int n);
+
 /* nsteps of three-stage SSP Runge-Kutta (Shu-Osher form), in place. */
 int orc_rk3(const orc_problem *pr, double *w, double dt, int nsteps);
 /*
