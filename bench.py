@@ -470,12 +470,16 @@ def kinematic_block(dg, steps, n=64):
 
 
 def tri_flops_per_stage(p):
-    """Algorithmic FP64 flops of one triangle and one RK stage (both fields): phi, psi and their
-    r-, s-derivatives at the (p+2)^2 volume points (6 dot products of length Np) and at the 3 (p+2)
-    edge points on both sides, the weak-form sums at every node (4 basis terms at each volume and
-    edge point) and M^-1 R for two fields; 2 flops per multiply-add."""
-    Np, nqv, nqe = (p + 1) * (p + 2) // 2, (p + 2) ** 2, 3 * (p + 2)
-    return 12 * Np * nqv + 24 * Np * nqe + 8 * Np * (nqv + nqe) + 4 * Np * Np
+    """Algorithmic FP64 flops of one triangle and one RK stage (both fields), 2 per multiply-add:
+    phi and its r-, s-derivatives and psi's at the (p+2)^2 volume points (5 dot products of length
+    Np); on both sides of the 3 (p+2) edge points phi, psi and psi's tangential derivative from the
+    p+1 edge nodes and the normal derivatives of phi and psi from all Np; the weak-form sums at
+    every node (4 basis terms per volume point, the lifted symmetric term at every edge point, the
+    edge fluxes of phi and psi on the edges through the node); M^-1 R for two fields."""
+    P1, Np, nq1 = p + 1, (p + 1) * (p + 2) // 2, p + 2
+    nqv, nqe = nq1 * nq1, 3 * nq1
+    return (10 * Np * nqv + 2 * nqe * (3 * P1 + 2 * Np) * 2 + 8 * Np * nqv + 2 * Np * nqe
+            + 12 * P1 * nq1 + 4 * Np * Np)
 
 
 def triangle_block(dg, steps, n=64):

@@ -1252,7 +1252,7 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
   k.xc = vel->xc;
   k.yc = vel->yc;
   k.check_finite = 1;
-  const std::vector<double> ops = tri ? tri_tables(p) : build_ops(2, p, c->hx, c->hy);
+  const std::vector<double> ops = tri ? tri_tables(p, k.tc) : build_ops(2, p, c->hx, c->hy);
   if (ops.empty()) {
     free_ctx(c);
     return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_kin_create: reference tables could not be built");

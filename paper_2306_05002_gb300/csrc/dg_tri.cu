@@ -157,7 +157,7 @@ bool spd_inverse(int n, const std::vector<double> &A, std::vector<double> &Ai) {
 
 }  // namespace
 
-std::vector<double> tri_tables(int p) {
+std::vector<double> tri_tables(int p, const TriConst tc[2]) {
   if (p < 1 || p > 4) return {};
   const TriLayout L(p);
   std::vector<double> t(L.size(), 0.0), gx, gw;
@@ -175,6 +175,7 @@ std::vector<double> tri_tables(int p) {
       basis(p, r, s, &t[L.bv() + q * L.NP], &t[L.brv() + q * L.NP], &t[L.bsv() + q * L.NP]);
     }
   // Edge points: parameter gx[k] along edge f from its first vertex to its second.
+  std::vector<double> l(L.NP), lr(L.NP), ls(L.NP);
   for (int f = 0; f < 3; ++f)
     for (int k = 0; k < L.NQ1; ++k) {
       const int fk = f * L.NQ1 + k;
@@ -183,7 +184,18 @@ std::vector<double> tri_tables(int p) {
       const double s = f == 0 ? -1.0 : (f == 1 ? u : -u);
       t[L.re() + fk] = r;
       t[L.se() + fk] = s;
-      basis(p, r, s, &t[L.be() + fk * L.NP], &t[L.bre() + fk * L.NP], &t[L.bse() + fk * L.NP]);
+      basis(p, r, s, l.data(), lr.data(), ls.data());
+      for (int m = 0; m <= p; ++m) {  // d/dt along the edge: (dr/dt, ds/dt) = (1, 0), (-1, 1), (0, -1)
+        const int n = tri_edge_node(p, f, m);
+        t[L.bev() + fk * L.P1 + m] = l[n];
+        t[L.bet() + fk * L.P1 + m] = f == 0 ? lr[n] : (f == 1 ? -lr[n] + ls[n] : -ls[n]);
+      }
+      for (int type = 0; type < 2; ++type) {
+        const TriConst &g = tc[type];
+        for (int n = 0; n < L.NP; ++n)
+          t[L.bn() + (type * L.NQE + fk) * L.NP + n] =
+              (lr[n] * g.rx + ls[n] * g.sx) * g.m0[f] + (lr[n] * g.ry + ls[n] * g.sy) * g.m1[f];
+      }
     }
   for (int k = 0; k < L.NQ1; ++k) t[L.we() + k] = gw[k];
   // Reference mass matrix sum_q w_q l_i l_j (exact: degree 2p <= 2 NQ1 - 2) and its inverse.

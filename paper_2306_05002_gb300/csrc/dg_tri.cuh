@@ -40,19 +40,24 @@ namespace dgpf {
 
 // Reference-table layout of order p, in doubles (built by tri_tables).
 struct TriLayout {
-  int NP, NQ1, NQV, NQE;
+  int P1, NP, NQ1, NQV, NQE;
   __host__ __device__ constexpr explicit TriLayout(int p)
-      : NP((p + 1) * (p + 2) / 2), NQ1(p + 2), NQV((p + 2) * (p + 2)), NQE(3 * (p + 2)) {}
+      : P1(p + 1), NP((p + 1) * (p + 2) / 2), NQ1(p + 2), NQV((p + 2) * (p + 2)), NQE(3 * (p + 2)) {}
   // basis values and reference derivatives at the volume points, [q][n]
   __host__ __device__ constexpr int bv() const { return 0; }
   __host__ __device__ constexpr int brv() const { return bv() + NQV * NP; }
   __host__ __device__ constexpr int bsv() const { return brv() + NQV * NP; }
-  // the same at the edge points, [f NQ1 + k][n]
-  __host__ __device__ constexpr int be() const { return bsv() + NQV * NP; }
-  __host__ __device__ constexpr int bre() const { return be() + NQE * NP; }
-  __host__ __device__ constexpr int bse() const { return bre() + NQE * NP; }
+  // at the edge points [f NQ1 + k], of the p+1 nodes of edge f only (tri_edge_node): the basis
+  // values and their derivative d/dt along the edge (t in [-1, 1] from its first vertex to its
+  // second); every other node's basis function vanishes on the edge, with its tangential
+  // derivative
+  __host__ __device__ constexpr int bev() const { return bsv() + NQV * NP; }
+  __host__ __device__ constexpr int bet() const { return bev() + NQE * P1; }
+  // physical derivative of every basis function along the outward normal of the edge, per
+  // triangle type, [type][f NQ1 + k][n]
+  __host__ __device__ constexpr int bn() const { return bet() + NQE * P1; }
   // inverse of the reference mass matrix sum_q w_q l_i l_j, [i][j]
-  __host__ __device__ constexpr int minv() const { return bse() + NQE * NP; }
+  __host__ __device__ constexpr int minv() const { return bn() + 2 * NQE * NP; }
   // volume weights (collapsed factor included) and points
   __host__ __device__ constexpr int wv() const { return minv() + NP * NP; }
   __host__ __device__ constexpr int rv() const { return wv() + NQV; }
@@ -63,6 +68,14 @@ struct TriLayout {
   __host__ __device__ constexpr int se() const { return re() + NQE; }
   __host__ __device__ constexpr int size() const { return se() + NQE; }
 };
+
+// Index of the m-th node of edge f -- node (m, 0) of edge 0 (s = -1), (p - m, m) of edge 1
+// (r + s = 0), (0, m) of edge 2 (r = -1) -- in the j-major node order, where node (i, j) sits at
+// j (p+1) - j (j-1)/2 + i.
+__host__ __device__ constexpr int tri_edge_node(int p, int f, int m) {
+  return (f == 0 ? 0 : m) * (p + 1) - (f == 0 ? 0 : m) * ((f == 0 ? 0 : m) - 1) / 2 +
+         (f == 0 ? m : (f == 1 ? p - m : 0));
+}
 
 template <int P>
 struct TriGeom {
@@ -179,6 +192,41 @@ __device__ __forceinline__ void tri_eval_point(const KinParams &kp, const TriCon
   }
 }
 
+// phi, psi, d(phi)/dm and n . m at one edge point, m = sgn x the outward normal of the
+// triangle's edge f (sgn = -1: a neighbour's trace, seen along the normal of the triangle being
+// updated).  hl: half the edge length (d/dt = hl d/dtau along the edge).
+struct TriEdgeTrace {
+  double phi, psi, dphi_m, n_m;
+};
+
+template <int P>
+__device__ __forceinline__ void tri_edge_trace(const double *s_t, const TriLayout &L, int type, int f, int fk,
+                                               const double *fphi, const double *fpsi, double hl, double sgn,
+                                               TriEdgeTrace *o) {
+  constexpr int P1 = P + 1, NP = (P + 1) * (P + 2) / 2;
+  const double *bev = s_t + L.bev() + fk * P1, *bet = s_t + L.bet() + fk * P1;
+  const double *bn = s_t + L.bn() + (type * L.NQE + fk) * NP;
+  double ph = 0.0, ps = 0.0, pt = 0.0, gp = 0.0, gs = 0.0;
+#pragma unroll
+  for (int m = 0; m < P1; ++m) {
+    const int n = tri_edge_node(P, f, m);
+    ph = fma(bev[m], fphi[n], ph);
+    ps = fma(bev[m], fpsi[n], ps);
+    pt = fma(bet[m], fpsi[n], pt);
+  }
+#pragma unroll
+  for (int n = 0; n < NP; ++n) {
+    gp = fma(bn[n], fphi[n], gp);
+    gs = fma(bn[n], fpsi[n], gs);
+  }
+  const double st = pt / hl;  // tangential derivative of psi
+  const double g2 = gs * gs + st * st;
+  o->phi = ph;
+  o->psi = ps;
+  o->dphi_m = sgn * gp;
+  o->n_m = g2 < 1e-24 ? 0.0 : sgn * gs * rsqrt(g2);  // n = 0 where |grad psi| < 1e-12
+}
+
 // One stage: the right-hand side L = M^-1 R(win) at time *t0 + tstep + toff,
 // written as L (KIN_RHS) or as one classical RK4 stage (KIN_K1..K4, the same
 // updates as k_kin_surface; out may be w0, each node being read, then written,
@@ -240,7 +288,9 @@ k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
 #pragma unroll
       for (int k = 0; k < 4; ++k) s_cv[le][q][k] = cv[k];
     }
-    // 3. Edge points: transport and SIP fluxes, the symmetric term.
+    // 3. Edge points: transport and SIP fluxes, the symmetric term.  On each side: phi and psi
+    //    from the p+1 edge nodes, the normal derivatives of phi and psi from all nodes (bn), the
+    //    tangential derivative of psi from the edge nodes -- n . m = (d psi/dm) / |grad psi|.
     for (int it = threadIdx.x; it < EPB * NQE; it += blockDim.x) {
       const int le = it / NQE, fk = it % NQE, f = fk / NQ1, k = fk % NQ1, e = e0 + le;
       double ce[4] = {0.0, 0.0, 0.0, 0.0};
@@ -249,11 +299,9 @@ k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
         const int e2 = tri_neighbour(kp, e, f, &f2);
         const int fk2 = f2 * NQ1 + (NQ1 - 1 - k);  // the same physical point, seen from the neighbour
         const TriConst &g = kp.tc[e & 1], &g2 = kp.tc[e2 & 1];
-        TriPoint om, op;
-        tri_eval_point<NP, true>(kp, g, s_w[le][0], s_w[le][1], s_t + L.be() + fk * NP, s_t + L.bre() + fk * NP,
-                           s_t + L.bse() + fk * NP, &om);
-        tri_eval_point<NP, true>(kp, g2, s_nb[le][f][0], s_nb[le][f][1], s_t + L.be() + fk2 * NP,
-                           s_t + L.bre() + fk2 * NP, s_t + L.bse() + fk2 * NP, &op);
+        TriEdgeTrace om, op;
+        tri_edge_trace<P>(s_t, L, e & 1, f, fk, s_w[le][0], s_w[le][1], g.hl[f], 1.0, &om);
+        tri_edge_trace<P>(s_t, L, e2 & 1, f2, fk2, s_nb[le][f][0], s_nb[le][f][1], g2.hl[f2], -1.0, &op);
         const double2 *vt = reinterpret_cast<const double2 *>(kp.tri_vel);
         const double2 U = __ldg(vt + (long)e * NPT + NQV + fk), U2 = __ldg(vt + (long)e2 * NPT + NQV + fk2);
         const double m0 = g.m0[f], m1 = g.m1[f];
@@ -261,35 +309,51 @@ k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
         const double lam = fmax(fabs(unm), fabs(unp));
         const double wf = s_t[L.we() + k] * g.hl[f];
         const double jump = op.phi - om.phi, hjs = 0.5 * (op.psi - om.psi);
-        const double gn = 0.5 * ((op.gp[0] + om.gp[0]) * m0 + (op.gp[1] + om.gp[1]) * m1);
-        const double sharp = 0.5 * (op.phi * (1.0 - op.phi) * (op.n[0] * m0 + op.n[1] * m1) +
-                                    om.phi * (1.0 - om.phi) * (om.n[0] * m0 + om.n[1] * m1));
+        const double gn = 0.5 * (op.dphi_m + om.dphi_m);
+        const double sharp = 0.5 * (op.phi * (1.0 - op.phi) * op.n_m + om.phi * (1.0 - om.phi) * om.n_m);
         const double ahat = kp.Gamma * (kp.eps * (gn + g.eta[f] * jump) - sharp);
         const double sym = 0.5 * kp.Gamma * kp.eps * jump;
-        ce[0] = wf * ((lam - unm) * 0.5 * jump + ahat);
-        ce[1] = -wf * sym * g.gr[f];
-        ce[2] = -wf * sym * g.gs[f];
-        ce[3] = wf * (lam - unm) * hjs;
+        ce[0] = wf * ((lam - unm) * 0.5 * jump + ahat);  // x l_n (edge nodes)
+        ce[1] = -wf * sym;                                // x d l_n / dm (all nodes)
+        ce[3] = wf * (lam - unm) * hjs;                   // x l_n (edge nodes), psi
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) s_ce[le][fk][q] = ce[q];
     }
     __syncthreads();
-    // 4. Weak-form sums R_n (volume points, then edge points).
+    // 4. Weak-form sums R_n: volume points, the lifted symmetric term at every edge point, and
+    //    the edge fluxes at the edges the node lies on.
     for (int it = threadIdx.x; it < EPB * NP; it += blockDim.x) {
       const int le = it / NP, n = it % NP;
       double rp = 0.0, rs = 0.0;
 #pragma unroll 4
       for (int q = 0; q < NQV; ++q) {
         const double *cq = s_cv[le][q];
-        rp += cq[0] * s_t[L.bv() + q * NP + n] + cq[1] * s_t[L.brv() + q * NP + n] + cq[2] * s_t[L.bsv() + q * NP + n];
-        rs += cq[3] * s_t[L.bv() + q * NP + n];
+        const double b = s_t[L.bv() + q * NP + n];
+        rp = fma(cq[0], b, rp);
+        rp = fma(cq[1], s_t[L.brv() + q * NP + n], rp);
+        rp = fma(cq[2], s_t[L.bsv() + q * NP + n], rp);
+        rs = fma(cq[3], b, rs);
       }
+      const double *bn = s_t + L.bn() + ((e0 + le) & 1) * NQE * NP;
 #pragma unroll 4
-      for (int q = 0; q < NQE; ++q) {
-        const double *cq = s_ce[le][q];
-        rp += cq[0] * s_t[L.be() + q * NP + n] + cq[1] * s_t[L.bre() + q * NP + n] + cq[2] * s_t[L.bse() + q * NP + n];
-        rs += cq[3] * s_t[L.be() + q * NP + n];
+      for (int q = 0; q < NQE; ++q) rp = fma(s_ce[le][q][1], bn[q * NP + n], rp);
+      int ni = n, nj = 0;  // node (i, j) of index n
+      while (ni > P - nj) {
+        ni -= P + 1 - nj;
+        ++nj;
+      }
+#pragma unroll 1
+      for (int f = 0; f < 3; ++f) {
+        const bool on = f == 0 ? nj == 0 : (f == 1 ? ni + nj == P : ni == 0);
+        if (!on) continue;
+        const int m = f == 0 ? ni : nj;  // its position along the edge (tri_edge_node)
+#pragma unroll
+        for (int k = 0; k < NQ1; ++k) {
+          const double l = s_t[L.bev() + (f * NQ1 + k) * (P + 1) + m];
+          rp = fma(s_ce[le][f * NQ1 + k][0], l, rp);
+          rs = fma(s_ce[le][f * NQ1 + k][3], l, rs);
+        }
       }
       s_R[le][0][n] = rp;
       s_R[le][1][n] = rs;
@@ -353,8 +417,9 @@ cudaError_t launch_tri_stage(const KinParams &kp, int mode, double tstep, double
 bool tri_kernels(int p, TriKernels *out);
 // Triangles one CTA processes per pass (EPB of order p).
 int tri_group(int p);
-// Reference tables of order p in the TriLayout order; empty on failure.
-std::vector<double> tri_tables(int p);
+// Tables of order p in the TriLayout order, the normal derivatives for the two triangle types
+// of constants tc; empty on failure.
+std::vector<double> tri_tables(int p, const TriConst tc[2]);
 // Constants of the two triangle types of cells hx x hy (penalty factor eta_tri = c_ip (p+1)(p+2)).
 void tri_constants(double hx, double hy, double eta_tri, TriConst tc[2]);
 
