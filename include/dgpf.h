@@ -343,8 +343,8 @@ dg_status dg_reinit(dg_ctx *ctx, double *w, int niter, double nu, double dtau, v
    this library holds until the process exits; a problem whose scratch would
    not fit (about 190,000 nodes at p = 3 in 2D, e.g. 64 x 64 elements fits)
    is rejected with DG_ERR_ARG before any GPU work.  Other invalid arguments
-   give DG_ERR_ARG / DG_ERR_UNSUPPORTED (opts->prec must be DG_FP64; the
-   device status word is not reported).
+   give DG_ERR_ARG / DG_ERR_UNSUPPORTED (opts->prec must be DG_FP64, mesh->elem
+   DG_ELEM_QUAD; the device status word is not reported).
    The first call on a device looks up the array's device address on that
    device (it loads the library's module there); make that first call before
    any stream capture.  Every call uses the same array and leaves its contents

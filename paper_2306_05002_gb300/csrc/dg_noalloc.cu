@@ -96,6 +96,7 @@ extern "C" dg_status dg_rhs_noalloc(const dg_mesh *mesh, int p, const dg_eos *eo
   // Arguments (same rules as dg_create / dg_rhs); nothing touches the GPU before they pass.
   if (!mesh || !eos || !w || !L || w == L) return DG_ERR_ARG;
   if (mesh->dim != 1 && mesh->dim != 2) return DG_ERR_ARG;
+  if (mesh->elem != DG_ELEM_QUAD) return mesh->elem == DG_ELEM_TRI ? DG_ERR_UNSUPPORTED : DG_ERR_ARG;
   if (p < 1 || p > 5) return DG_ERR_UNSUPPORTED;
   if (mesh->nx < 1 || mesh->ny < 1 || (mesh->dim == 1 && mesh->ny != 1)) return DG_ERR_ARG;
   if (!(mesh->x1 > mesh->x0) || (mesh->dim == 2 && !(mesh->y1 > mesh->y0))) return DG_ERR_ARG;

@@ -178,3 +178,19 @@ def test_kin_nodes_rejects_invalid_arguments(lib):
     m.elem = 3
     assert lib.dg_kin_nodes(ctypes.byref(m), 3, x.ctypes.data_as(dpt), x.ctypes.data_as(dpt)) == -1
 
+
+def test_noalloc_rejects_triangles_before_gpu_work(lib):
+    """The allocation-free right-hand side covers the rectangles only: a triangle mesh is refused
+    during argument checking, before any device call."""
+    import paper_2306_05002_gb300 as pkg
+    m, eos, o = pkg.make_structs(2, 4, 4, 0.0, 1.0, 0.0, 1.0, ("periodic",) * 4, (4.4, 1.4), (6e8, 0.0),
+                                 (1000.0, 1.0))
+    m.elem = 1
+    f = lib.dg_rhs_noalloc
+    f.argtypes = [ctypes.POINTER(pkg.dg_mesh), ctypes.c_int, ctypes.POINTER(pkg.dg_eos), ctypes.c_double,
+                  ctypes.c_double, ctypes.POINTER(pkg.dg_opts), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    assert f(ctypes.byref(m), 3, ctypes.byref(eos), 1.0, 0.05, ctypes.byref(o), 16, 4096, None) == -7
+    m.elem = 2
+    assert f(ctypes.byref(m), 3, ctypes.byref(eos), 1.0, 0.05, ctypes.byref(o), 16, 4096, None) == -1
+
