@@ -51,6 +51,10 @@ def parse():
                     help="elements per direction of the adjoint block (smaller values for profiling)")
     ap.add_argument("--kin-steps", type=int, default=200,
                     help="timed RK4 steps of the kinematic Rider-Kothe block (0 skips it)")
+    ap.add_argument("--reinit-iters", type=int, default=50,
+                    help="pseudo-time steps of the timed re-initialisation block (0 skips it)")
+    ap.add_argument("--rt-paper-steps", type=int, default=10,
+                    help="timed steps on the paper's Rayleigh-Taylor domain with the pressure top (0 skips)")
     ap.add_argument("--tri-steps", type=int, default=200,
                     help="timed RK4 steps of the kinematic block on triangles (0 skips it)")
     ap.add_argument("--tri-n", type=int, default=64,
@@ -390,16 +394,24 @@ def batched_block(dg, steps, nprob=256):
             "tiles": tiles}
 
 
-def rt_block(dg, steps, n=256):
+def rt_block(dg, steps, n=256, paper=False):
     """Viscous Rayleigh-Taylor set-up (256 x 256 quads, p = 4, walls, gravity, surface tension,
     seed 3): FP32-bulk and FP64 step times and the FP32-bulk error after the timed steps.
-    The state (92 MB FP64, 1.64M nodes) and the workspace exceed L2 together; no flush."""
+    The state (92 MB FP64, 1.64M nodes) and the workspace exceed L2 together; no flush.
+    paper: the paper's domain [0, 1] x [0, 4] on n x 4n quads instead (slip sides, no-slip bottom,
+    the Riemann-invariant pressure top, no surface tension)."""
     import numpy as np
     import torch
     from paper_2306_05002_gb300 import workloads as W
-    wl = W.rayleigh_taylor(n=n, p=4, seed=3)
-    out = {"workload": f"2D viscous Rayleigh-Taylor {n}x{n} quads p=4, no-slip walls, g=-9.81, sigma=0.07, "
-                       "density ratio 3, seeded 8-mode interface", "nodes": wl.N, "steps": steps}
+    if paper:
+        wl = W.rayleigh_taylor_paper(nx=n, ny=4 * n, p=4)
+        desc = (f"2D viscous Rayleigh-Taylor, the paper's domain [0,1]x[0,4] on {n}x{4 * n} quads p=4, slip sides, "
+                "no-slip bottom, Riemann-invariant pressure top, g=-9.81, density ratio 3, Re=3000")
+    else:
+        wl = W.rayleigh_taylor(n=n, p=4, seed=3)
+        desc = (f"2D viscous Rayleigh-Taylor {n}x{n} quads p=4, no-slip walls, g=-9.81, sigma=0.07, "
+                "density ratio 3, seeded 8-mode interface")
+    out = {"workload": desc, "nodes": wl.N, "steps": steps}
     states = {}
     for prec in ("fp32bulk", "fp64"):
         s = dg.Solver(wl, precision=prec)
@@ -424,6 +436,56 @@ def rt_block(dg, steps, n=256):
     out["l2_rel_alpha"] = float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0]))
     out["speedup_fp32bulk_vs_fp64"] = out["fp64"]["ms_per_step"] / out["fp32bulk"]["ms_per_step"]
     return out
+
+
+def kin_flops_per_node_stage(p):
+    """Algorithmic FP64 flops per node and RK stage of the kinematic mode on rectangles (both fields,
+    2 per multiply-add): the gradients of phi and psi and the weak-form term of -a_1 (six contractions
+    of length p+1), n, a_1, the transport terms and the velocity (23); per face node the transport and
+    SIP fluxes and the symmetric term (34, 4 (p+1) face nodes per (p+1)^2 nodes); the lifting, M^-1 and
+    the RK4 update (20)."""
+    P1 = p + 1
+    return 12 * P1 + 23 + 34 * 4 * P1 // (P1 * P1) + 20
+
+
+def reinit_flops_per_node_stage(p):
+    """Algorithmic FP64 flops per node and SSP-RK3 stage of the level-set re-initialisation (one field,
+    2 per multiply-add): the gradient and the weak-form diffusion term (four contractions of length
+    p+1), the source S (1 - |grad psi|) (9); per face node the SIP flux and the symmetric term (11,
+    4 (p+1) face nodes per (p+1)^2 nodes); the lifting, M^-1 and the stage update (14)."""
+    P1 = p + 1
+    return 8 * P1 + 9 + 11 * 4 * P1 // (P1 * P1) + 14
+
+
+def reinit_block(dg, iters, n=64):
+    """Level-set re-initialisation (end of Sec. 3) of the Rider-Kothe drop on n x n quads, p = 3, FP64:
+    `iters` pseudo-time SSP-RK3 steps with the default nu and dtau in one dg_reinit call (the paper
+    applies ~50 every 2000 steps); one sign kernel, then a volume and a surface kernel per stage."""
+    import torch
+    from paper_2306_05002_gb300 import workloads as W
+    wl = W.rider_kothe(n=n, p=3)
+    s = dg.KinematicSolver(wl)
+    w = torch.from_numpy(wl.w.copy()).cuda()
+    s.dg_reinit(w, 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.dg_reinit(w, iters)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    status = s.dg_status_read()
+    s.close()
+    per_iter = ms / iters
+    ach = reinit_flops_per_node_stage(wl.p) * wl.N * 3 / (per_iter * 1e-3) / 1e12
+    return {"workload": f"level-set re-initialisation of the Rider-Kothe drop, {n}x{n} quads p=3, FP64, "
+                        f"{iters} SSP-RK3 pseudo-time steps", "nodes": wl.N, "iterations": iters,
+            "ms_per_iteration": per_iter, "ms_total": ms, "gpu_launches": 1 + 6 * iters,
+            "device_status": status,
+            "roofline": {"bound": "alu", "kernel": "k_ri_volume + k_ri_surface", "achieved": ach,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                         "per_unit": f"{reinit_flops_per_node_stage(wl.p)} flops per node and stage x {wl.N} nodes",
+                         "duration": "call time / iterations / 3 stages (gaps included)"}}
 
 
 def kinematic_block(dg, steps, n=64):
@@ -461,8 +523,14 @@ def kinematic_block(dg, steps, n=64):
     xi = W.gll_points(3)
     wt = 2.0 / (3 * 4 * legendre.Legendre.basis(3)(xi) ** 2)
     M = np.tile(np.outer(wt, wt).ravel() * 0.25 * small.hx * small.hy, small.nx * small.ny)
+    ach = kin_flops_per_node_stage(wl.p) * wl.N * 4 / (ms * 1e-3) / 1e12
     return {"workload": f"Rider-Kothe vortex {n}x{n} quads p=3, T=4, eps=0.75h, Gamma=1, FP64, classical RK4",
             "nodes": wl.N, "steps": steps, "ms_per_step": ms, "value": 2 * 4 * wl.N / (ms * 1e-3), "unit": UNIT,
+            "gpu_launches_per_step": 8,
+            "roofline": {"bound": "alu", "kernel": "k_kin_volume + k_kin_surface", "achieved": ach,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                         "per_unit": f"{kin_flops_per_node_stage(wl.p)} flops per node and stage x {wl.N} nodes",
+                         "duration": "step time / 4 (two kernels per stage in a graph; gaps included)"},
             "full_period_16x16p3": {"steps": small.nsteps, "wall_s": wall,
                                     "l1_phi": float(np.sum(M * np.abs(wend[0] - small.w[0]))),
                                     "mass_error": float(np.sum(M * (wend[0] - small.w[0])) / np.sum(M * small.w[0])),
@@ -622,6 +690,8 @@ def run_ours(args, rank, world, local_rank):
     rt = rt_block(dg, args.rt_steps) if (args.rt_steps > 0 and rank == 0) else None
     kin = kinematic_block(dg, args.kin_steps) if (args.kin_steps > 0 and rank == 0) else None
     tri = triangle_block(dg, args.tri_steps, args.tri_n) if (args.tri_steps > 0 and rank == 0) else None
+    ri = reinit_block(dg, args.reinit_iters) if (args.reinit_iters > 0 and rank == 0) else None
+    rtp = rt_block(dg, args.rt_paper_steps, n=64, paper=True) if (args.rt_paper_steps > 0 and rank == 0) else None
 
     ms_max, e2e_max, ref_ms = reduce_max([main["ms"], e2e_t, ref["ms"] if ref else 0.0], "cuda")
 
@@ -658,6 +728,10 @@ def run_ours(args, rank, world, local_rank):
             line["kinematic"] = kin
         if tri:
             line["kinematic_triangles"] = tri
+        if ri:
+            line["reinit"] = ri
+        if rtp:
+            line["rayleigh_taylor_paper_domain"] = rtp
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
         print(json.dumps(line), flush=True)

@@ -4,6 +4,7 @@
     python -m paper_2306_05002_gb300 rt --n 256 --p 4 --steps 3
     python -m paper_2306_05002_gb300 slab --n 100 --p 3 --steps 1000 --precision fp64
     python -m paper_2306_05002_gb300 rk --n 64 --p 3 --steps 100 --elem tri
+    python -m paper_2306_05002_gb300 rk --n 64 --p 3 --steps 2 --reinit 50
 
 Workloads (``workloads.py``): ``slab`` (1D periodic water slab in air), ``drop`` (2D periodic
 water drop in air, seeded centre), ``rt`` (2D viscous Rayleigh-Taylor with walls, gravity and
@@ -27,6 +28,8 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["fp64", "fp32bulk"], default="fp32bulk")
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--elem", choices=["quad", "tri"], default="quad", help="element type (rk only)")
+    ap.add_argument("--reinit", type=int, default=0,
+                    help="rk on rectangles: level-set re-initialisation steps after the time steps")
     args = ap.parse_args(argv)
 
     import torch
@@ -77,6 +80,8 @@ def _kinematic(args, kw):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s.dg_kin_step(w, 0.0, wl.dt, args.steps)
+    if args.reinit > 0:
+        s.dg_reinit(w, args.reinit)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     status = s.dg_status_read()

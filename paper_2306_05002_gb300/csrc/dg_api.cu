@@ -1266,7 +1266,9 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
   for (double **b : bufs)
     if (e == cudaSuccess && !(tri && b == &c->d_krvol)) e = cudaMalloc(b, sb);
   if (e == cudaSuccess && !tri) e = cudaMalloc(&c->d_ktr, tb);
-  if (e == cudaSuccess && tri) e = cudaMalloc(&c->d_ktv, (size_t)2 * c->E * c->tk.points * sizeof(double));
+  // the velocity's spatial factor at every node (rectangles) or quadrature point (triangles)
+  const size_t vrows = tri ? (size_t)c->E * c->tk.points : (size_t)c->N;
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_ktv, 2 * vrows * sizeof(double));
   if (e == cudaSuccess && tri) {
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
@@ -1294,15 +1296,13 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
   k.xi = c->d_kxi;
   k.t0 = c->d_kt0;
   k.status = c->d_status;
-  k.tri_vel = c->d_ktv;
-  if (tri) {  // the spatial factor of the velocity at every quadrature point, once
-    e = c->tk.velocity_table(k, c->d_ktv, c->cap);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->cap);
-    if (e != cudaSuccess) {
-      free_ctx(c);
-      cudaGetLastError();
-      return fail(nullptr, DG_ERR_CUDA, std::string("dg_kin_create: velocity table: ") + cudaGetErrorString(e));
-    }
+  k.vel_tab = c->d_ktv;
+  e = tri ? c->tk.velocity_table(k, c->d_ktv, c->cap) : c->kk.velocity_table(k, c->d_ktv, c->cap);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->cap);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    cudaGetLastError();
+    return fail(nullptr, DG_ERR_CUDA, std::string("dg_kin_create: velocity table: ") + cudaGetErrorString(e));
   }
   *out = c;
   return DG_OK;

@@ -46,7 +46,8 @@ struct KinParams {
   double xc, yc;           // Rider-Kothe vortex centre
   double eta_tri;          // triangles: c_ip (p+1)(p+2); the edge penalty is eta_tri / h_e
   TriConst tc[2];          // triangles: the two element types
-  const double *tri_vel;   // triangles: time-independent velocity factor at every quadrature point
+  const double *vel_tab;   // spatial velocity factor U at every node (rectangles) or quadrature point
+                           // (triangles), see kin_velocity_factor
   const double *ops;       // operator table (OpsLayout)
   const double *xi;        // GLL nodes on [-1, 1]
   const double *t0;        // device: time at the start of the captured step sequence
@@ -54,18 +55,45 @@ struct KinParams {
   unsigned *status;
 };
 
-// Prescribed velocity at (x, y, t) (Sec. 4.1).
-__device__ __forceinline__ void kin_velocity(const KinParams &kp, double x, double y, double t, double *u,
-                                             double *v) {
+// Prescribed velocity (Sec. 4.1), u(x, t) = c(t) U(x): the Rider-Kothe vortex with
+// c = cos(pi t / T) and U = (sin^2(pi X) sin(2 pi Y), -sin(2 pi X) sin^2(pi Y)), or c = 1 and
+// U = (u0, v0).  U does not change between stages: it is evaluated once per node (rectangles) or
+// quadrature point (triangles) when the context is created, into KinParams::vel_tab, and a stage
+// multiplies by c -- the FP64 sines would otherwise cost more than the scheme.
+__device__ __forceinline__ void kin_velocity_factor(const KinParams &kp, double x, double y, double *U,
+                                                    double *V) {
   if (kp.vel == VEL_RIDER_KOTHE) {
     const double X = x - kp.xc + 0.5, Y = y - kp.yc + 0.5;
-    const double sx = sin(CUDART_PI * X), sy = sin(CUDART_PI * Y), c = cos(CUDART_PI * t / kp.T);
-    *u = sx * sx * sin(2.0 * CUDART_PI * Y) * c;
-    *v = -sin(2.0 * CUDART_PI * X) * sy * sy * c;
+    const double sx = sin(CUDART_PI * X), sy = sin(CUDART_PI * Y);
+    *U = sx * sx * sin(2.0 * CUDART_PI * Y);
+    *V = -sin(2.0 * CUDART_PI * X) * sy * sy;
   } else {
-    *u = kp.u0;
-    *v = kp.v0;
+    *U = kp.u0;
+    *V = kp.v0;
   }
+}
+
+__device__ __forceinline__ double kin_time_factor(const KinParams &kp, double t) {
+  return kp.vel == VEL_RIDER_KOTHE ? cos(CUDART_PI * t / kp.T) : 1.0;
+}
+
+// U at every node of the rectangles, [N][2].
+template <int P>
+__global__ void k_kin_velocity_table(const KinParams kp, double *__restrict__ tab) {
+  constexpr int P1 = P + 1, NP = P1 * P1;
+  const long n = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= kp.N) return;
+  const int e = (int)(n / NP), a = (int)(n % NP), i = a % P1, j = a / P1;
+  const int ex = e % kp.nx, ey = e / kp.nx;
+  const double x = kp.x0 + kp.hx * (ex + 0.5 * (__ldg(kp.xi + i) + 1.0));
+  const double y = kp.y0 + kp.hy * (ey + 0.5 * (__ldg(kp.xi + j) + 1.0));
+  kin_velocity_factor(kp, x, y, &tab[2 * n], &tab[2 * n + 1]);
+}
+
+template <int P>
+cudaError_t launch_kin_velocity_table(const KinParams &kp, double *tab, cudaStream_t s) {
+  k_kin_velocity_table<P><<<(unsigned)((kp.N + 255) / 256), 256, 0, s>>>(kp, tab);
+  return cudaGetLastError();
 }
 
 // Volume kernel: broken gradients, n, a_1, the volume term of -a_1, the
@@ -95,12 +123,9 @@ k_kin_volume(const KinParams kp, double tstep, double toff, const double *__rest
   const long n = (long)(act ? e : 0) * NP + a;
 
   const double phi = act ? __ldg(w + n) : 0.0, psi = act ? __ldg(w + N + n) : 0.0;
-  const int ex = (act ? e : 0) % kp.nx, ey = (act ? e : 0) / kp.nx;
-  const double x = kp.x0 + kp.hx * (ex + 0.5 * (__ldg(kp.xi + i) + 1.0));
-  const double y = kp.y0 + kp.hy * (ey + 0.5 * (__ldg(kp.xi + j) + 1.0));
-  const double t = (*kp.t0 + tstep) + toff;
-  double u, v;
-  kin_velocity(kp, x, y, t, &u, &v);
+  const double c = kin_time_factor(kp, (*kp.t0 + tstep) + toff);
+  const double2 U = __ldg(reinterpret_cast<const double2 *>(kp.vel_tab) + n);
+  const double u = U.x * c, v = U.y * c;
 
   if (lane) {
     s_f[0][le][a] = phi;
@@ -279,6 +304,7 @@ k_kin_surface(const KinParams kp, int mode, double dt, const double *w0, const d
 struct KinKernels {
   cudaError_t (*volume)(const KinParams &, double tstep, double toff, const double *w, double *rvol, double *tr,
                         cudaStream_t);
+  cudaError_t (*velocity_table)(const KinParams &, double *tab, cudaStream_t);
   cudaError_t (*surface)(const KinParams &, int mode, double dt, const double *w0, const double *rvol,
                          const double *tr, double *acc, double *out, cudaStream_t);
 };

@@ -115,14 +115,8 @@ __device__ __forceinline__ int tri_neighbour(const KinParams &kp, int e, int f, 
   return 2 * ((ci > 0 ? ci - 1 : kp.nx - 1) + kp.nx * cj);
 }
 
-// The prescribed velocity is u(x, t) = c(t) U(x): c = cos(pi t / T) and U the spatial factor of
-// the Rider-Kothe vortex, or c = 1 and U = (u0, v0).  U is evaluated once, at every volume and
-// edge point of every triangle, when the context is created (k_tri_velocity_table); a stage
-// multiplies by c.  Table layout: [e][NQV + NQE][2], volume points first.
-__device__ __forceinline__ double tri_time_factor(const KinParams &kp, double t) {
-  return kp.vel == VEL_RIDER_KOTHE ? cos(CUDART_PI * t / kp.T) : 1.0;
-}
-
+// The velocity table of the triangles (kin_velocity_factor): U at every volume and edge point of
+// every triangle, [e][NQV + NQE][2], volume points first.
 template <int P>
 __global__ void k_tri_velocity_table(const KinParams kp, double *__restrict__ tab) {
   using G = TriGeom<P>;
@@ -137,15 +131,7 @@ __global__ void k_tri_velocity_table(const KinParams kp, double *__restrict__ ta
   const double s = q < G::NQV ? kp.ops[L.sv() + q] : kp.ops[L.se() + q - G::NQV];
   const double x = v[0][0] + 0.5 * (1.0 + r) * (v[1][0] - v[0][0]) + 0.5 * (1.0 + s) * (v[2][0] - v[0][0]);
   const double y = v[0][1] + 0.5 * (1.0 + r) * (v[1][1] - v[0][1]) + 0.5 * (1.0 + s) * (v[2][1] - v[0][1]);
-  double U = kp.u0, V = kp.v0;
-  if (kp.vel == VEL_RIDER_KOTHE) {
-    const double X = x - kp.xc + 0.5, Y = y - kp.yc + 0.5;
-    const double sx = sin(CUDART_PI * X), sy = sin(CUDART_PI * Y);
-    U = sx * sx * sin(2.0 * CUDART_PI * Y);
-    V = -sin(2.0 * CUDART_PI * X) * sy * sy;
-  }
-  tab[2 * i] = U;
-  tab[2 * i + 1] = V;
+  kin_velocity_factor(kp, x, y, &tab[2 * i], &tab[2 * i + 1]);
 }
 
 template <int P>
@@ -246,7 +232,7 @@ k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
   __shared__ double s_ce[EPB][NQE][4];
   __shared__ double s_R[EPB][2][NP];
   for (int i = threadIdx.x; i < L.size(); i += blockDim.x) s_t[i] = kp.ops[i];
-  const double c = tri_time_factor(kp, (*kp.t0 + tstep) + toff);
+  const double c = kin_time_factor(kp, (*kp.t0 + tstep) + toff);
   const int N = kp.N, ngroups = (kp.E + EPB - 1) / EPB;
   bool bad = false;
 
@@ -277,7 +263,7 @@ k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
         TriPoint o;
         tri_eval_point<NP, false>(kp, g, s_w[le][0], s_w[le][1], s_t + L.bv() + q * NP, s_t + L.brv() + q * NP,
                            s_t + L.bsv() + q * NP, &o);
-        const double2 U = __ldg(reinterpret_cast<const double2 *>(kp.tri_vel) + (long)e * NPT + q);
+        const double2 U = __ldg(reinterpret_cast<const double2 *>(kp.vel_tab) + (long)e * NPT + q);
         const double u = U.x * c, v = U.y * c;
         const double wq = s_t[L.wv() + q] * g.det;
         cv[0] = -wq * (u * o.gp[0] + v * o.gp[1]);
@@ -302,7 +288,7 @@ k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
         TriEdgeTrace om, op;
         tri_edge_trace<P>(s_t, L, e & 1, f, fk, s_w[le][0], s_w[le][1], g.hl[f], 1.0, &om);
         tri_edge_trace<P>(s_t, L, e2 & 1, f2, fk2, s_nb[le][f][0], s_nb[le][f][1], g2.hl[f2], -1.0, &op);
-        const double2 *vt = reinterpret_cast<const double2 *>(kp.tri_vel);
+        const double2 *vt = reinterpret_cast<const double2 *>(kp.vel_tab);
         const double2 U = __ldg(vt + (long)e * NPT + NQV + fk), U2 = __ldg(vt + (long)e2 * NPT + NQV + fk2);
         const double m0 = g.m0[f], m1 = g.m1[f];
         const double unm = U.x * c * m0 + U.y * c * m1, unp = U2.x * c * m0 + U2.y * c * m1;
