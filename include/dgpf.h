@@ -50,7 +50,7 @@ typedef enum {
   DG_ERR_TIMEOUT = -4,      /* a bounded device wait expired */
   DG_ERR_NONFINITE = -5,    /* the device saw a non-finite value */
   DG_ERR_NONPHYSICAL = -6,  /* the device saw rho <= 0 or P + Pinf <= 0 */
-  DG_ERR_UNSUPPORTED = -7   /* valid request this build does not provide */
+  DG_ERR_UNSUPPORTED = -7   /* valid request the library does not implement */
 } dg_status;
 
 enum { DG_BC_PERIODIC = 0, DG_BC_NOSLIP = 1, DG_BC_SLIP = 2, DG_BC_PRESSURE = 3 };
