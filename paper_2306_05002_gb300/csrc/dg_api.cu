@@ -560,7 +560,7 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
   };
   if (!f64) {
     const size_t n32 = c->len;
-    const size_t t32 = (size_t)c->ks32.nt * c->E * c->NFK;
+    const size_t t32 = (size_t)TRW32 * c->E * c->NFK;  // one padded record per face node
     alloc32(&c->d_opsf, opsf.size()) && alloc32(&c->d_ws32, n32) && alloc32(&c->d_w1_32, n32) &&
         alloc32(&c->d_w2_32, n32) && alloc32(&c->d_rvol32, n32) && alloc32(&c->d_trace32, t32) &&
         alloc32(&c->d_rvol32b, n32) && alloc32(&c->d_trace32b, t32);
@@ -973,9 +973,9 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
     o_w1[k] = take(len);
     o_w2[k] = take(len);
     o_rv[k] = take(len);
-    o_tr[k] = take((size_t)NT32_INVISCID * E * NFK);
+    o_tr[k] = take((size_t)TRW32 * E * NFK);
     o_rv2[k] = take(len);
-    o_tr2[k] = take((size_t)NT32_INVISCID * E * NFK);
+    o_tr2[k] = take((size_t)TRW32 * E * NFK);
   }
   cudaError_t e = cudaMalloc(&b->d_pool, total * sizeof(float));
   if (e != cudaSuccess) {

@@ -62,6 +62,10 @@ __host__ inline ParamsF to_float(const Params &p) {
 enum TraceField32 { C_GPHI = 7, C_N = 8, C_TX = 9, C_TY = 10 };
 constexpr int NT32_INVISCID = 9;
 constexpr int NT32_VISCOUS = 11;
+// The FP32 face traces are stored one 48-byte record per face node ([E * NFK][TRW32] floats, the
+// words in TraceField32 order, the rest padding), so that a record moves in three 128-bit
+// accesses instead of nine or eleven scalar ones.
+constexpr int TRW32 = 12;
 
 // Fill T[T_U], T[T_V], T[T_P], T[T_C], T[T_B] (and T[T_MU]) from the state
 // values T[T_PHI..T_RE], with the operations of the volume body.
@@ -278,17 +282,12 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   const bool onS = DIM == 2 && j == 0, onN = DIM == 2 && j == P;
   if (act && (onW || onE || onS || onN)) {
     const long base = (long)e * NFK;
-    const long stride = (long)prm.E * NFK;
     auto put = [&](int f, int kk, float gn, float nn, float t1, float t2) {
-      const long o = base + f * NK + kk;
-#pragma unroll
-      for (int qf = 0; qf < NV; ++qf) tr[qf * stride + o] = q[qf];
-      tr[C_GPHI * stride + o] = gn;
-      tr[C_N * stride + o] = nn;
-      if (VISC) {
-        tr[C_TX * stride + o] = t1;
-        tr[C_TY * stride + o] = t2;
-      }
+      float4 *rec = reinterpret_cast<float4 *>(tr) + (base + f * NK + kk) * (TRW32 / 4);
+      rec[0] = make_float4(q[0], q[1], q[2], q[3]);
+      rec[1] = make_float4(q[4], q[5], q[6], gn);
+      if (VISC) rec[2] = make_float4(nn, t1, t2, 0.f);
+      else reinterpret_cast<float *>(rec + 2)[0] = nn;
     };
     const int kx = DIM == 2 ? j : 0;
     if (onW) put(0, kx, gpx, nx, txx, txy);
@@ -305,6 +304,26 @@ k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, c
            float *__restrict__ w32out) {
   __shared__ float s_op[2 * Geom<P, DIM, VISC, ST>::P1 * Geom<P, DIM, VISC, ST>::P1];  // Dx, Dy
   vol32_body<P, DIM, VISC, ST>(prm, pf, opsf, s_op, false, blockIdx.x, w, rvol, tr, w64, w32out);
+}
+
+// The NC words of face-trace record o (three 128-bit loads, or two and one word), or, when the
+// record does not exist, zeros with m1 = m1_default (a finite density for the closure).
+template <int NC>
+__device__ __forceinline__ void load_trace32(const float *__restrict__ tr, long o, bool valid, float *T,
+                                             float m1_default) {
+#pragma unroll
+  for (int qf = 0; qf < NC; ++qf) T[qf] = qf == T_M1 ? m1_default : 0.f;
+  if (!valid) return;
+  const float4 *rec = reinterpret_cast<const float4 *>(tr) + o * (TRW32 / 4);
+  const float4 a = __ldg(rec), b = __ldg(rec + 1);
+  T[0] = a.x; T[1] = a.y; T[2] = a.z; T[3] = a.w;
+  T[4] = b.x; T[5] = b.y; T[6] = b.z; T[7] = b.w;
+  if (NC > 9) {
+    const float4 c = __ldg(rec + 2);
+    T[8] = c.x; T[9] = c.y; T[10] = c.z;
+  } else if (NC > 8) {
+    T[8] = __ldg(reinterpret_cast<const float *>(rec + 2));
+  }
 }
 
 // Surface kernel body of the FP32-bulk path.  mode MODE_RHS writes L for the
@@ -339,7 +358,6 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   const int a = threadIdx.x % NP;
   const int e = blk * EPB + le;
   const bool act = lane && e < prm.E;
-  const long stride = (long)prm.E * NFK;
   const int N = prm.N;
   const long n = (long)(act ? e : 0) * NP + a;
 
@@ -364,11 +382,9 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
     const int e2 = fv ? neighbour(prm, e, f) : -1;
     e2_[fi] = e2;
     const long om = (long)(act ? e : 0) * NFK + (fv ? t : 0);
-#pragma unroll
-    for (int qf = 0; qf < NC; ++qf) Cm_[fi][qf] = fv ? __ldg(tr + qf * stride + om) : (qf == T_M1 ? 1.f : 0.f);
     const long op = (long)(e2 >= 0 ? e2 : 0) * NFK + (f ^ 1) * NK + kk;
-#pragma unroll
-    for (int qf = 0; qf < NC; ++qf) Cp_[fi][qf] = e2 >= 0 ? __ldg(tr + qf * stride + op) : 0.f;
+    load_trace32<NC>(tr, om, fv, Cm_[fi], 1.f);
+    load_trace32<NC>(tr, op, e2 >= 0, Cp_[fi], 0.f);
   }
 
   for (int t = threadIdx.x; t < L.size(); t += blockDim.x) s_op[t] = opsf[t];
