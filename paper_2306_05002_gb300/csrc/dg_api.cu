@@ -66,22 +66,27 @@ bool kernels_fp32(int p, int dim, bool viscous, bool st, KernelSet32 *out) {
   }
 }
 
-// FP64 <-> FP32-bulk internal state (see dg_kernels_fp32.cuh).
-__global__ void k_to32(int N, double C2, double dC, const double *__restrict__ w, float *__restrict__ w32) {
+// FP64 <-> FP32-bulk internal state (see dg_kernels_fp32.cuh).  The FP64 state is field-major
+// ([7][N]); the FP32 internal state one record of SW32 floats per node (aos: the inviscid kernels)
+// or field-major (the viscous kernels).
+__global__ void k_to32(int N, double C2, double dC, int aos, const double *__restrict__ w, float *__restrict__ w32) {
   for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
     const double phi = w[n];
+    auto at = [&](int v) -> float & { return aos ? w32[n * SW32 + v] : w32[(long)v * N + n]; };
 #pragma unroll
-    for (int v = 0; v < RE; ++v) w32[(long)v * N + n] = (float)w[(long)v * N + n];
-    w32[(long)RE * N + n] = (float)(w[(long)RE * N + n] - fma(dC, phi, C2));
+    for (int v = 0; v < RE; ++v) at(v) = (float)w[(long)v * N + n];
+    at(RE) = (float)(w[(long)RE * N + n] - fma(dC, phi, C2));
+    if (aos) w32[n * SW32 + NV] = 0.f;
   }
 }
 
-__global__ void k_to64(int N, double C2, double dC, const float *__restrict__ w32, double *__restrict__ w) {
+__global__ void k_to64(int N, double C2, double dC, int aos, const float *__restrict__ w32, double *__restrict__ w) {
   for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
-    const double phi = (double)w32[n];
+    auto at = [&](int v) { return aos ? w32[n * SW32 + v] : w32[(long)v * N + n]; };
+    const double phi = (double)at(PHI);
 #pragma unroll
-    for (int v = 0; v < RE; ++v) w[(long)v * N + n] = (double)w32[(long)v * N + n];
-    w[(long)RE * N + n] = (double)w32[(long)RE * N + n] + fma(dC, phi, C2);
+    for (int v = 0; v < RE; ++v) w[(long)v * N + n] = (double)at(v);
+    w[(long)RE * N + n] = (double)at(RE) + fma(dC, phi, C2);
   }
 }
 
@@ -559,7 +564,7 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
     return e == cudaSuccess;
   };
   if (!f64) {
-    const size_t n32 = c->len;
+    const size_t n32 = (size_t)SW32 * c->N;  // one padded record per node (inviscid kernels)
     const size_t t32 = (size_t)TRW32 * c->E * c->NFK;  // one padded record per face node
     alloc32(&c->d_opsf, opsf.size()) && alloc32(&c->d_ws32, n32) && alloc32(&c->d_w1_32, n32) &&
         alloc32(&c->d_w2_32, n32) && alloc32(&c->d_rvol32, n32) && alloc32(&c->d_trace32, t32) &&
@@ -627,8 +632,9 @@ static dg_status run_stage32(dg_ctx *c, int mode, float dt, const float *w0, con
 }
 
 static dg_status convert(dg_ctx *c, bool to32, double *w, cudaStream_t s) {
-  if (to32) k_to32<<<c->conv_blocks, 256, 0, s>>>(c->N, c->prm.C2, c->prm.dC, w, c->d_ws32);
-  else k_to64<<<c->conv_blocks, 256, 0, s>>>(c->N, c->prm.C2, c->prm.dC, c->d_ws32, w);
+  const int aos = !c->opts.viscous;  // the node-record layout of the inviscid FP32 kernels
+  if (to32) k_to32<<<c->conv_blocks, 256, 0, s>>>(c->N, c->prm.C2, c->prm.dC, aos, w, c->d_ws32);
+  else k_to64<<<c->conv_blocks, 256, 0, s>>>(c->N, c->prm.C2, c->prm.dC, aos, c->d_ws32, w);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "state conversion launch");
 }
@@ -966,15 +972,15 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
     d.prm.check_finite = 0;
     d.pf = to_float(d.prm);
     const size_t E = (size_t)m.nx * m.ny, P1 = p[k] + 1, NFK = 4 * P1;
-    const size_t len = NV * E * P1 * P1;
+    const size_t len = NV * E * P1 * P1, len32 = SW32 * E * P1 * P1;  // FP64 state; FP32 node records
     b->len[k] = len;
     o_ops[k] = take(tables[k].size());
-    o_ws[k] = take(len);
-    o_w1[k] = take(len);
-    o_w2[k] = take(len);
-    o_rv[k] = take(len);
+    o_ws[k] = take(len32);
+    o_w1[k] = take(len32);
+    o_w2[k] = take(len32);
+    o_rv[k] = take(len32);
     o_tr[k] = take((size_t)TRW32 * E * NFK);
-    o_rv2[k] = take(len);
+    o_rv2[k] = take(len32);
     o_tr2[k] = take((size_t)TRW32 * E * NFK);
   }
   cudaError_t e = cudaMalloc(&b->d_pool, total * sizeof(float));

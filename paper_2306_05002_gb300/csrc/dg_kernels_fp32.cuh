@@ -66,6 +66,36 @@ constexpr int NT32_VISCOUS = 11;
 // words in TraceField32 order, the rest padding), so that a record moves in three 128-bit
 // accesses instead of nine or eleven scalar ones.
 constexpr int TRW32 = 12;
+// The FP32 internal state and volume parts of the inviscid kernels are stored one 32-byte record
+// per node ([N][SW32] floats: the seven variables and a padding word), moved in two 128-bit
+// accesses; the viscous kernels keep them field-major ([7][N]), where the records did not pay
+// (256x256 p4 Rayleigh-Taylor step 0.301 -> 0.316 ms), while the inviscid batch gained 11%.
+constexpr int SW32 = 8;
+
+template <bool AOS>
+__device__ __forceinline__ void load_node32(const float *__restrict__ w, long n, int N, float *q) {
+  if (AOS) {
+    const float4 *r = reinterpret_cast<const float4 *>(w) + 2 * n;
+    const float4 a = __ldg(r), b = __ldg(r + 1);
+    q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
+    q[4] = b.x; q[5] = b.y; q[6] = b.z;
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = __ldg(w + (long)v * N + n);
+  }
+}
+
+template <bool AOS>
+__device__ __forceinline__ void store_node32(float *w, long n, int N, const float *q) {
+  if (AOS) {
+    float4 *r = reinterpret_cast<float4 *>(w) + 2 * n;
+    r[0] = make_float4(q[0], q[1], q[2], q[3]);
+    r[1] = make_float4(q[4], q[5], q[6], 0.f);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[(long)v * N + n] = q[v];
+  }
+}
 
 // Fill T[T_U], T[T_V], T[T_P], T[T_C], T[T_B] (and T[T_MU]) from the state
 // values T[T_PHI..T_RE], with the operations of the volume body.
@@ -133,13 +163,12 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
 #pragma unroll
     for (int v = 0; v < RE; ++v) q[v] = (float)d[v];
     q[RE] = (float)(d[RE] - fma(prm.dC, d[PHI], prm.C2));
-    if (act) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) w32out[(long)v * N + n] = q[v];
-    }
+    if (act) store_node32<!VISC>(w32out, n, N, q);
+  } else if (act) {
+    load_node32<!VISC>(w, n, N, q);
   } else {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) q[v] = act ? __ldg(w + (long)v * N + n) : (v == M1 || v == M2 ? 1.f : 0.f);
+    for (int v = 0; v < NV; ++v) q[v] = v == M1 || v == M2 ? 1.f : 0.f;
   }
   const float phi = q[PHI], psi = q[PSI];
   const float rho = q[M1] + q[M2];
@@ -273,10 +302,7 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
     R[RV] += s * ny;
     R[RE] += s * (u * nx + v * ny);
   }
-  if (act) {
-#pragma unroll
-    for (int vv = 0; vv < NV; ++vv) rvol[(long)vv * N + n] = R[vv];
-  }
+  if (act) store_node32<!VISC>(rvol, n, N, R);
 
   const bool onW = i == 0, onE = i == P;
   const bool onS = DIM == 2 && j == 0, onN = DIM == 2 && j == P;
@@ -366,11 +392,11 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   // overlap each other and the copy of the operator table.
   float Lv[NV], wsn[NV], w0n[NV];
 #pragma unroll
-  for (int vv = 0; vv < NV; ++vv) {
-    const long o = (long)vv * N + n;
-    Lv[vv] = act ? __ldg(rvol + o) : 0.f;
-    wsn[vv] = act && mode != MODE_RHS ? __ldg(ws + o) : 0.f;
-    w0n[vv] = act && (mode == MODE_S2 || mode == MODE_S3) ? __ldg(w0 + o) : 0.f;
+  for (int vv = 0; vv < NV; ++vv) Lv[vv] = wsn[vv] = w0n[vv] = 0.f;
+  if (act) {
+    load_node32<!VISC>(rvol, n, N, Lv);
+    if (mode != MODE_RHS) load_node32<!VISC>(ws, n, N, wsn);
+    if (mode == MODE_S2 || mode == MODE_S3) load_node32<!VISC>(w0, n, N, w0n);
   }
   float Cm_[FPT][NC], Cp_[FPT][NC];
   int e2_[FPT];
@@ -564,8 +590,7 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
         for (int vv = 0; vv < RE; ++vv) out64[(long)vv * N + n] = (double)r[vv];
         out64[(long)RE * N + n] = (double)r[RE] + fma(prm.dC, (double)r[PHI], prm.C2);
       } else {
-#pragma unroll
-        for (int vv = 0; vv < NV; ++vv) out32[(long)vv * N + n] = r[vv];
+        store_node32<!VISC>(out32, n, N, r);
       }
       if (rout) {
 #pragma unroll
@@ -596,8 +621,12 @@ k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, 
 // part to the other in registers.  The volume part and the traces go to the
 // other buffer of a pair (rvol_out, tr_out), because neighbouring blocks of
 // the same launch may still read rvol_in and tr_in.
+// Residency of the viscous variants: at most 80 registers a thread (65,536 / (THREADS x 80) CTAs
+// per SM), which the surface-tension variant otherwise exceeds, one CTA per SM fewer and 6% slower
+// at p = 4.
 template <int P, int DIM, bool VISC, bool ST>
-__global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
+__global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS,
+                                  VISC ? 65536 / (Geom<P, DIM, VISC, ST>::THREADS * 80) : 1)
 k_surfvol32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt,
             const float *__restrict__ w0, const float *__restrict__ ws, const float *__restrict__ rvol_in,
             const float *__restrict__ tr_in, float *__restrict__ out32, float *__restrict__ rvol_out,
@@ -614,8 +643,8 @@ k_surfvol32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, 
 // rho E in FP64 with the FP64 phase field on entry, and restored with the
 // FP32 phase field on exit, so the pressure carried by the internal state is
 // the FP64 pressure and is handed back unchanged.
-__global__ void k_to32(int N, double C2, double dC, const double *__restrict__ w, float *__restrict__ w32);
-__global__ void k_to64(int N, double C2, double dC, const float *__restrict__ w32, double *__restrict__ w);
+__global__ void k_to32(int N, double C2, double dC, int aos, const double *__restrict__ w, float *__restrict__ w32);
+__global__ void k_to64(int N, double C2, double dC, int aos, const float *__restrict__ w32, double *__restrict__ w);
 
 struct KernelSet32 {
   cudaError_t (*volume)(const Params &, const ParamsF &, const float *opsf, const float *w, float *rvol,
