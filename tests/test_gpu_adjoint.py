@@ -122,6 +122,28 @@ def test_adjoint_step_dot_product(dg):
     assert torch.equal(lam_t, lam0)
 
 
+def test_adjoint_step_dot_product_full_size(dg):
+    """The same identity on the 128 x 128, p = 3 drop the benchmark's adjoint block differentiates
+    (262,144 nodes, the level-set parametrisation with seeded coefficients): the adjoint step is
+    the transpose of the step's Jacobian at full size."""
+    import torch
+    wl = W.adjoint_drop(n=128, p=3, theta=np.random.default_rng(50).normal(0, 0.01, 16), nsteps=1)
+    w = torch.from_numpy(wl.w.copy()).cuda()
+    g = torch.Generator(device="cpu").manual_seed(3)
+    scale = w.abs().amax(dim=1, keepdim=True)
+    vdir = torch.randn(w.shape, generator=g, dtype=torch.float64).cuda() * scale
+    lam1 = torch.randn(w.shape, generator=g, dtype=torch.float64).cuda() / scale
+    s = dg.Solver(wl)
+    h = 1e-9
+    wp, wm = (w + h * vdir).contiguous(), (w - h * vdir).contiguous()
+    s.dg_step(wp, wl.dt, 1)
+    s.dg_step(wm, wl.dt, 1)
+    lhs = float((lam1 * (wp - wm) / (2 * h)).sum())
+    rhs = float((s.dg_adjoint_step(w, lam1, wl.dt) * vdir).sum())
+    s.close()
+    assert abs(lhs - rhs) <= 2e-6 * max(abs(lhs), abs(rhs)), (lhs, rhs)
+
+
 def _objective(orc, wl, wN, target):
     M = mass_weights(orc, wl)
     return 0.5 * np.sum(M * (wN[0] - target) ** 2), M

@@ -95,3 +95,27 @@ def test_tuner_reports_a_tile_per_order(dg):
     for t in tiles:
         assert t["epb"] >= 1 and t["minb"] >= 1 and 0 < t["ms"] <= t["ms_default_tile"]
     bs.close()
+
+
+def test_full_ensemble_sampled_problems_match_single_runs(dg):
+    """The 256-problem ensemble the benchmark times (seed 4, 35.2M nodes, tuned tiles): after two
+    batched steps every state is finite, and eight problems spread over the four orders agree
+    with their single-problem FP32-bulk runs to the stage tolerance."""
+    import torch
+    wls = W.ensemble(n=256, seed=4)
+    bs = dg.BatchSolver(wls)
+    states = [torch.from_numpy(wl.w.copy()).cuda() for wl in wls]
+    bs.dg_batch_step(states, [wl.dt for wl in wls], 2)
+    torch.cuda.synchronize()
+    assert all(bool(torch.isfinite(st).all()) for st in states)
+    picks = []
+    for p in (2, 3, 4, 5):
+        idx = [k for k, wl in enumerate(wls) if wl.p == p]
+        picks += [idx[0], idx[-1]]
+    for k in picks:
+        ref = _single(dg, wls[k], 2)
+        got = states[k].cpu().numpy()
+        for v in range(7):
+            scale = max(np.abs(ref[v]).max(), 1e-300)
+            assert np.abs(got[v] - ref[v]).max() <= TOL_STAGE * 3 * 2 * scale, (wls[k].name, v)
+    bs.close()
