@@ -314,7 +314,7 @@ struct dg_ctx {
   KinKernels kk{};
   TriKernels tk{};
   int tri_grid = 0;
-  double *d_kacc = nullptr, *d_kwsA = nullptr, *d_kwsB = nullptr, *d_krvol = nullptr, *d_ktr = nullptr;
+  double *d_kacc = nullptr, *d_kwsA = nullptr, *d_kwsB = nullptr;
   double *d_kt0 = nullptr, *d_kxi = nullptr, *d_ktv = nullptr;
   // level-set re-initialisation workspace (dg_reinit), allocated on first use
   double *d_riS = nullptr, *d_ri1 = nullptr, *d_ri2 = nullptr, *d_rirvol = nullptr, *d_ritr = nullptr;
@@ -369,7 +369,7 @@ static void free_ctx(dg_ctx *c) {
   }
   cudaFree(c->d_ops);
   cudaFree(c->d_hstate);
-  for (double *q : {c->d_kacc, c->d_kwsA, c->d_kwsB, c->d_krvol, c->d_ktr, c->d_kt0, c->d_kxi, c->d_ktv}) cudaFree(q);
+  for (double *q : {c->d_kacc, c->d_kwsA, c->d_kwsB, c->d_kt0, c->d_kxi, c->d_ktv}) cudaFree(q);
   for (double *q : {c->d_riS, c->d_ri1, c->d_ri2, c->d_rirvol, c->d_ritr}) cudaFree(q);
   cudaFree(c->d_w1);
   cudaFree(c->d_w2);
@@ -1265,13 +1265,12 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
   }
   std::vector<double> xi, wt;
   gll_nodes(p, xi, wt);
-  const size_t sb = c->len * sizeof(double), tb = (size_t)NT_KIN * c->E * c->NFK * sizeof(double);
+  const size_t sb = c->len * sizeof(double);
   cudaError_t e = cudaSuccess;
-  // triangles: one fused kernel per stage, no volume residual or face traces
-  double **bufs[] = {&c->d_kacc, &c->d_kwsA, &c->d_kwsB, &c->d_krvol};
+  // one kernel per stage on either element type: no volume residual or face traces in memory
+  double **bufs[] = {&c->d_kacc, &c->d_kwsA, &c->d_kwsB};
   for (double **b : bufs)
-    if (e == cudaSuccess && !(tri && b == &c->d_krvol)) e = cudaMalloc(b, sb);
-  if (e == cudaSuccess && !tri) e = cudaMalloc(&c->d_ktr, tb);
+    if (e == cudaSuccess) e = cudaMalloc(b, sb);
   // the velocity's spatial factor at every node (rectangles) or quadrature point (triangles)
   const size_t vrows = tri ? (size_t)c->E * c->tk.points : (size_t)c->N;
   if (e == cudaSuccess) e = cudaMalloc(&c->d_ktv, 2 * vrows * sizeof(double));
@@ -1369,8 +1368,7 @@ extern "C" dg_status dg_kin_rhs(dg_ctx *c, const double *w, double t, double *L,
     if (e == cudaSuccess) e = c->tk.stage(c->kp, KIN_RHS, 0.0, 0.0, 0.0, w, nullptr, nullptr, L, c->tri_grid, s);
     return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_kin_rhs: launch");
   }
-  if (e == cudaSuccess) e = c->kk.volume(c->kp, 0.0, 0.0, w, c->d_krvol, c->d_ktr, s);
-  if (e == cudaSuccess) e = c->kk.surface(c->kp, KIN_RHS, 0.0, w, c->d_krvol, c->d_ktr, nullptr, L, s);
+  if (e == cudaSuccess) e = c->kk.stage(c->kp, KIN_RHS, 0.0, 0.0, 0.0, w, nullptr, nullptr, L, s);
   return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_kin_rhs: launch");
 }
 
@@ -1388,8 +1386,7 @@ static dg_status enqueue_kin_step(dg_ctx *c, double *w, double dt, int k, cudaSt
     if (c->tri) {
       e = c->tk.stage(c->kp, mode[st], tstep, toff[st], dt, in[st], w, c->d_kacc, out[st], c->tri_grid, s);
     } else {
-      e = c->kk.volume(c->kp, tstep, toff[st], in[st], c->d_krvol, c->d_ktr, s);
-      if (e == cudaSuccess) e = c->kk.surface(c->kp, mode[st], dt, w, c->d_krvol, c->d_ktr, c->d_kacc, out[st], s);
+      e = c->kk.stage(c->kp, mode[st], tstep, toff[st], dt, in[st], w, c->d_kacc, out[st], s);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "dg_kin_step: launch");
   }

@@ -5,11 +5,11 @@ namespace dgpf {
 
 bool kin_kernels(int p, KinKernels *out) {
   switch (p) {
-    case 1: *out = {&launch_kin_volume<1>, &launch_kin_velocity_table<1>, &launch_kin_surface<1>}; return true;
-    case 2: *out = {&launch_kin_volume<2>, &launch_kin_velocity_table<2>, &launch_kin_surface<2>}; return true;
-    case 3: *out = {&launch_kin_volume<3>, &launch_kin_velocity_table<3>, &launch_kin_surface<3>}; return true;
-    case 4: *out = {&launch_kin_volume<4>, &launch_kin_velocity_table<4>, &launch_kin_surface<4>}; return true;
-    case 5: *out = {&launch_kin_volume<5>, &launch_kin_velocity_table<5>, &launch_kin_surface<5>}; return true;
+    case 1: *out = {&launch_kin_stage<1>, &launch_kin_velocity_table<1>}; return true;
+    case 2: *out = {&launch_kin_stage<2>, &launch_kin_velocity_table<2>}; return true;
+    case 3: *out = {&launch_kin_stage<3>, &launch_kin_velocity_table<3>}; return true;
+    case 4: *out = {&launch_kin_stage<4>, &launch_kin_velocity_table<4>}; return true;
+    case 5: *out = {&launch_kin_stage<5>, &launch_kin_velocity_table<5>}; return true;
     default: return false;
   }
 }

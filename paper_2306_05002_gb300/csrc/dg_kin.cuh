@@ -11,7 +11,9 @@
 // speed alone, as the kinematic system has no sound speed -- and the SIP flux
 // of a_1 with its lifted symmetric term.  The velocity is the analytical field
 // sampled at each node.  Time integration is the classical four-stage
-// Runge-Kutta method, fused into the surface kernel.  Periodic meshes only.
+// Runge-Kutta method; each stage is one launch (k_kin_stage), which also
+// evaluates the neighbours' face traces from their nodal values.  Periodic
+// meshes only.
 #pragma once
 
 #include <math_constants.h>
@@ -22,11 +24,9 @@
 namespace dgpf {
 
 enum { VEL_UNIFORM = 0, VEL_RIDER_KOTHE = 1 };
-// What the kinematic surface kernel writes: the right-hand side, or one stage
-// of classical RK4 (w0: step start, acc: k1 + 2 k2 + 2 k3 so far).
+// What a kinematic stage kernel writes: the right-hand side, or one stage of
+// classical RK4 (w0: step start, acc: k1 + 2 k2 + 2 k3 so far).
 enum KinMode { KIN_RHS = 0, KIN_K1 = 1, KIN_K2 = 2, KIN_K3 = 3, KIN_K4 = 4 };
-// Kinematic face-trace record: phi, psi, d(phi)/d(axis), n_axis, u_axis.
-enum { K_PHI = 0, K_PSI, K_GPHI, K_N, K_U, NT_KIN };
 
 // Constants of one triangle type of the split-rectangle mesh (dg_tri.cuh): det = d(x,y)/d(r,s),
 // its inverse, the inverse-map derivatives, and per edge f the outward unit normal m, half the
@@ -96,21 +96,56 @@ cudaError_t launch_kin_velocity_table(const KinParams &kp, double *tab, cudaStre
   return cudaGetLastError();
 }
 
-// Volume kernel: broken gradients, n, a_1, the volume term of -a_1, the
-// non-conservative transport of phi and psi, and the face traces.  The stage
-// time is *kp.t0 + (step dt) + (stage offset), as the two host-side parts
-// tstep = step index x dt and toff = stage fraction x dt.
+// Periodic neighbour across face f (0 W, 1 E, 2 S, 3 N).
+__device__ __forceinline__ int kin_neighbour(const KinParams &kp, int e, int f) {
+  const int ex = e % kp.nx, ey = e / kp.nx;
+  switch (f) {
+    case 0: return ex > 0 ? e - 1 : e + kp.nx - 1;
+    case 1: return ex < kp.nx - 1 ? e + 1 : e - kp.nx + 1;
+    case 2: return ey > 0 ? e - kp.nx : e + kp.nx * (kp.ny - 1);
+    default: return ey < kp.ny - 1 ? e + kp.nx : e - kp.nx * (kp.ny - 1);
+  }
+}
+
+// Node index of face node kk of face f (0 W, 1 E, 2 S, 3 N) in the x-fastest GLL order.
+template <int P>
+__device__ __forceinline__ int kin_face_node(int f, int kk) {
+  constexpr int P1 = P + 1;
+  return f == 0 ? kk * P1 : (f == 1 ? P + kk * P1 : (f == 2 ? kk : kk + P * P1));
+}
+
+// One stage of the kinematic mode in one launch: broken gradients, n, a_1,
+// the volume term of -a_1 (D^ contractions) and the non-conservative
+// transport at every node; at every face node the transport flux
+// (lambda - m.u-) [[f]] and the SIP flux of a_1 with its lifted symmetric
+// term, the neighbour's trace being evaluated here from its nodal values (a
+// row of the neighbour's element), not read from a trace buffer; then M^-1
+// and the right-hand side or an RK4 stage:
+//   K1: acc = L,        out = w0 + dt/2 L
+//   K2: acc += 2 L,     out = w0 + dt/2 L
+//   K3: acc += 2 L,     out = w0 + dt L
+//   K4: out = w0 + dt/6 (acc + L)   (out may be w0: each node is read, then
+//                                    written, by the same thread)
+// Neighbour values come from the stage input, which no stage writes, so the
+// stages need no synchronisation beyond stream order.  The stage time is
+// *kp.t0 + (step dt) + (stage offset), as the two host-side parts tstep =
+// step index x dt and toff = stage fraction x dt.
 template <int P>
 __global__ void __launch_bounds__(Geom<P, 2, false, false>::THREADS)
-k_kin_volume(const KinParams kp, double tstep, double toff, const double *__restrict__ w, double *__restrict__ rvol,
-             double *__restrict__ tr) {
+k_kin_stage(const KinParams kp, int mode, double tstep, double toff, double dt, const double *__restrict__ win,
+            const double *w0, double *__restrict__ acc, double *out) {
   using G = Geom<P, 2, false, false>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
-  constexpr int P11 = P1 * P1;
-  __shared__ double s_op[4 * P11];
-  __shared__ double s_f[2][EPB][NP];
-  for (int t = threadIdx.x; t < 4 * P11; t += blockDim.x) s_op[t] = kp.ops[t];
-  const double *Dx = s_op, *Dy = s_op + P11, *Dhx = s_op + 2 * P11, *Dhy = s_op + 3 * P11;
+  const OpsLayout L{P1, NP};
+  __shared__ double s_op[4 * P1 * P1 + 3 * P1 + NP];
+  __shared__ double s_f[2][EPB][NP];       // phi, psi; then -a_1
+  __shared__ double s_nb[EPB][4][2][NP];   // the four neighbours' phi, psi
+  __shared__ double s_tr[EPB][NP][6];      // phi, psi, d(phi)/dx, d(phi)/dy, n_x, n_y
+  __shared__ double s_surf[EPB][NFK][2];
+  __shared__ double s_lift[EPB][NFK];
+  for (int t = threadIdx.x; t < L.size(); t += blockDim.x) s_op[t] = kp.ops[t];
+  const double *Dx = s_op + L.Dx(), *Dy = s_op + L.Dy(), *Dhx = s_op + L.Dhx(), *Dhy = s_op + L.Dhy();
+  const double *invM = s_op + L.invM(), *wfx = s_op + L.wfx(), *wfy = s_op + L.wfy();
 
   const int le_raw = threadIdx.x / NP;
   const bool lane = le_raw < EPB;
@@ -121,25 +156,38 @@ k_kin_volume(const KinParams kp, double tstep, double toff, const double *__rest
   const int i = a % P1, j = a / P1;
   const int N = kp.N;
   const long n = (long)(act ? e : 0) * NP + a;
+  const double2 *vt = reinterpret_cast<const double2 *>(kp.vel_tab);
+  // The time factor of the velocity and dt/6, once per CTA: FP64 is this kernel's bound, and a
+  // cosine or a division per thread would cost a fifth of its work.
+  __shared__ double s_c[2];
+  if (threadIdx.x == 0) {
+    s_c[0] = kin_time_factor(kp, (*kp.t0 + tstep) + toff);
+    s_c[1] = dt / 6.0;
+  }
 
-  const double phi = act ? __ldg(w + n) : 0.0, psi = act ? __ldg(w + N + n) : 0.0;
-  const double c = kin_time_factor(kp, (*kp.t0 + tstep) + toff);
-  const double2 U = __ldg(reinterpret_cast<const double2 *>(kp.vel_tab) + n);
-  const double u = U.x * c, v = U.y * c;
-
+  const double phi = act ? __ldg(win + n) : 0.0, psi = act ? __ldg(win + N + n) : 0.0;
+  const double2 U = __ldg(vt + n);
   if (lane) {
     s_f[0][le][a] = phi;
     s_f[1][le][a] = psi;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const long m = (long)(act ? kin_neighbour(kp, e, f) : 0) * NP + a;
+      s_nb[le][f][0][a] = __ldg(win + m);
+      s_nb[le][f][1][a] = __ldg(win + N + m);
+    }
   }
   __syncthreads();
+  const double c = s_c[0], dt6 = s_c[1];
+  const double u = U.x * c, v = U.y * c;
   double gpx = 0.0, gpy = 0.0, gsx = 0.0, gsy = 0.0;
 #pragma unroll
-  for (int c = 0; c < P1; ++c) {
-    const double dx = Dx[i * P1 + c], dy = Dy[j * P1 + c];
-    gpx = fma(dx, s_f[0][le][c + P1 * j], gpx);
-    gsx = fma(dx, s_f[1][le][c + P1 * j], gsx);
-    gpy = fma(dy, s_f[0][le][i + P1 * c], gpy);
-    gsy = fma(dy, s_f[1][le][i + P1 * c], gsy);
+  for (int k = 0; k < P1; ++k) {
+    const double dx = Dx[i * P1 + k], dy = Dy[j * P1 + k];
+    gpx = fma(dx, s_f[0][le][k + P1 * j], gpx);
+    gsx = fma(dx, s_f[1][le][k + P1 * j], gsx);
+    gpy = fma(dy, s_f[0][le][i + P1 * k], gpy);
+    gsy = fma(dy, s_f[1][le][i + P1 * k], gsy);
   }
   const double g2 = gsx * gsx + gsy * gsy;
   double nx = 0.0, ny = 0.0;
@@ -155,113 +203,73 @@ k_kin_volume(const KinParams kp, double tstep, double toff, const double *__rest
   if (lane) {
     s_f[0][le][a] = -a1x;
     s_f[1][le][a] = -a1y;
+    double *t = s_tr[le][a];
+    t[0] = phi;
+    t[1] = psi;
+    t[2] = gpx;
+    t[3] = gpy;
+    t[4] = nx;
+    t[5] = ny;
   }
   __syncthreads();
   double Rphi = 0.0;
 #pragma unroll
-  for (int c = 0; c < P1; ++c) {
-    Rphi = fma(Dhx[i * P1 + c], s_f[0][le][c + P1 * j], Rphi);
-    Rphi = fma(Dhy[j * P1 + c], s_f[1][le][i + P1 * c], Rphi);
+  for (int k = 0; k < P1; ++k) {
+    Rphi = fma(Dhx[i * P1 + k], s_f[0][le][k + P1 * j], Rphi);
+    Rphi = fma(Dhy[j * P1 + k], s_f[1][le][i + P1 * k], Rphi);
   }
   Rphi -= u * gpx + v * gpy;
   const double Rpsi = -(u * gsx + v * gsy);
-  if (act) {
-    rvol[n] = Rphi;
-    rvol[N + n] = Rpsi;
-  }
-  const bool onW = i == 0, onE = i == P, onS = j == 0, onN = j == P;
-  if (act && (onW || onE || onS || onN)) {
-    const long base = (long)e * NFK, stride = (long)kp.E * NFK;
-    auto put = [&](int f, int kk, double gn, double nn, double ua) {
-      const long o = base + f * NK + kk;
-      tr[K_PHI * stride + o] = phi;
-      tr[K_PSI * stride + o] = psi;
-      tr[K_GPHI * stride + o] = gn;
-      tr[K_N * stride + o] = nn;
-      tr[K_U * stride + o] = ua;
-    };
-    if (onW) put(0, j, gpx, nx, u);
-    if (onE) put(1, j, gpx, nx, u);
-    if (onS) put(2, i, gpy, ny, v);
-    if (onN) put(3, i, gpy, ny, v);
-  }
-}
 
-// Periodic neighbour across face f (0 W, 1 E, 2 S, 3 N).
-__device__ __forceinline__ int kin_neighbour(const KinParams &kp, int e, int f) {
-  const int ex = e % kp.nx, ey = e / kp.nx;
-  switch (f) {
-    case 0: return ex > 0 ? e - 1 : e + kp.nx - 1;
-    case 1: return ex < kp.nx - 1 ? e + 1 : e - kp.nx + 1;
-    case 2: return ey > 0 ? e - kp.nx : e + kp.nx * (kp.ny - 1);
-    default: return ey < kp.ny - 1 ? e + kp.nx : e - kp.nx * (kp.ny - 1);
-  }
-}
-
-// Surface kernel: transport and SIP fluxes at the face nodes, lifting of the
-// symmetric term, M^-1, and the right-hand side or an RK4 stage:
-//   K1: acc = L,        out = w0 + dt/2 L
-//   K2: acc += 2 L,     out = w0 + dt/2 L
-//   K3: acc += 2 L,     out = w0 + dt L
-//   K4: out = w0 + dt/6 (acc + L)   (out may be w0: each node is read, then
-//                                    written, by the same thread)
-template <int P>
-__global__ void __launch_bounds__(Geom<P, 2, false, false>::THREADS)
-k_kin_surface(const KinParams kp, int mode, double dt, const double *w0, const double *__restrict__ rvol,
-              const double *__restrict__ tr, double *__restrict__ acc, double *out) {
-  using G = Geom<P, 2, false, false>;
-  constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
-  const OpsLayout L{P1, NP};
-  __shared__ double s_op[4 * P1 * P1 + 3 * P1 + NP];
-  __shared__ double s_surf[EPB][NFK][2];
-  __shared__ double s_lift[EPB][NFK];
-  for (int t = threadIdx.x; t < L.size(); t += blockDim.x) s_op[t] = kp.ops[t];
-  __syncthreads();
-  const double *Dx = s_op + L.Dx(), *Dy = s_op + L.Dy();
-  const double *invM = s_op + L.invM(), *wfx = s_op + L.wfx(), *wfy = s_op + L.wfy();
-
-  const int le_raw = threadIdx.x / NP;
-  const bool lane = le_raw < EPB;
-  const int le = lane ? le_raw : EPB - 1;
-  const int a = threadIdx.x % NP;
-  const int e = blockIdx.x * EPB + le;
-  const bool act = lane && e < kp.E;
-  const long stride = (long)kp.E * NFK;
-
+  // Face nodes: own trace from s_tr, the neighbour's from its nodal values.
   for (int t = a; t < NFK && lane; t += NP) {
     const int f = t / NK, kk = t % NK;
     const bool xf = f < 2;
     const double sg = (f & 1) ? 1.0 : -1.0;
-    double Tm[NT_KIN], Tp[NT_KIN];
+    double flux = 0.0, fpsi = 0.0, lift = 0.0;
     if (act) {
+      const int am = kin_face_node<P>(f, kk), ap = kin_face_node<P>(f ^ 1, kk);
       const int e2 = kin_neighbour(kp, e, f);
-      const long om = (long)e * NFK + t, op = (long)e2 * NFK + (f ^ 1) * NK + kk;
+      const double *tm = s_tr[le][am];
+      const double *nbp = s_nb[le][f][0], *nbs = s_nb[le][f][1];
+      const int i2 = ap % P1, j2 = ap / P1;
+      double qpx = 0.0, qpy = 0.0, qsx = 0.0, qsy = 0.0;  // the neighbour's gradients at its face node
 #pragma unroll
-      for (int q = 0; q < NT_KIN; ++q) {
-        Tm[q] = __ldg(tr + q * stride + om);
-        Tp[q] = __ldg(tr + q * stride + op);
+      for (int k = 0; k < P1; ++k) {
+        const double dx = Dx[i2 * P1 + k], dy = Dy[j2 * P1 + k];
+        qpx = fma(dx, nbp[k + P1 * j2], qpx);
+        qsx = fma(dx, nbs[k + P1 * j2], qsx);
+        qpy = fma(dy, nbp[i2 + P1 * k], qpy);
+        qsy = fma(dy, nbs[i2 + P1 * k], qsy);
       }
-    } else {
-#pragma unroll
-      for (int q = 0; q < NT_KIN; ++q) Tm[q] = Tp[q] = 0.0;
+      const double q2 = qsx * qsx + qsy * qsy;
+      double mx = 0.0, my = 0.0;
+      if (q2 >= 1e-24) {
+        const double r = rsqrt(q2);
+        mx = qsx * r;
+        my = qsy * r;
+      }
+      const double2 Um = __ldg(vt + (long)e * NP + am), Up = __ldg(vt + (long)e2 * NP + ap);
+      const double phm = tm[0], psm = tm[1], php = nbp[ap], psp = nbs[ap];
+      const double unm = (xf ? Um.x : Um.y) * c * sg, unp = (xf ? Up.x : Up.y) * c * sg;
+      const double lam = fmax(fabs(unm), fabs(unp));
+      const double wf = xf ? wfx[kk] : wfy[kk];
+      const double eta = xf ? kp.eta_x : kp.eta_y;
+      const double jump = php - phm;
+      const double gn = 0.5 * ((xf ? qpx : qpy) + (xf ? tm[2] : tm[3])) * sg;
+      const double sharp = 0.5 * (php * (1.0 - php) * (xf ? mx : my) + phm * (1.0 - phm) * (xf ? tm[4] : tm[5])) * sg;
+      const double ahat = kp.Gamma * (kp.eps * (gn + eta * jump) - sharp);
+      flux = wf * (lam - unm) * 0.5 * jump + wf * ahat;
+      fpsi = wf * (lam - unm) * 0.5 * (psp - psm);
+      lift = -wf * 0.5 * kp.Gamma * kp.eps * jump;
     }
-    const double unm = Tm[K_U] * sg, unp = Tp[K_U] * sg;
-    const double lam = fmax(fabs(unm), fabs(unp));
-    const double wf = xf ? wfx[kk] : wfy[kk];
-    const double eta = xf ? kp.eta_x : kp.eta_y;
-    const double jump = Tp[K_PHI] - Tm[K_PHI];
-    const double gn = 0.5 * (Tp[K_GPHI] + Tm[K_GPHI]) * sg;
-    const double sharp =
-        0.5 * (Tp[K_PHI] * (1.0 - Tp[K_PHI]) * Tp[K_N] + Tm[K_PHI] * (1.0 - Tm[K_PHI]) * Tm[K_N]) * sg;
-    const double ahat = kp.Gamma * (kp.eps * (gn + eta * jump) - sharp);
-    s_surf[le][t][0] = wf * (lam - unm) * 0.5 * jump + wf * ahat;
-    s_surf[le][t][1] = wf * (lam - unm) * 0.5 * (Tp[K_PSI] - Tm[K_PSI]);
-    s_lift[le][t] = -wf * 0.5 * kp.Gamma * kp.eps * jump;
+    s_surf[le][t][0] = flux;
+    s_surf[le][t][1] = fpsi;
+    s_lift[le][t] = lift;
   }
   __syncthreads();
   if (!act) return;
 
-  const int i = a % P1, j = a / P1;
   double sp = 0.0, ss = 0.0;
   if (i == 0) { sp += s_surf[le][0 * NK + j][0]; ss += s_surf[le][0 * NK + j][1]; }
   if (i == P) { sp += s_surf[le][1 * NK + j][0]; ss += s_surf[le][1 * NK + j][1]; }
@@ -270,9 +278,7 @@ k_kin_surface(const KinParams kp, int mode, double dt, const double *w0, const d
   sp += s_lift[le][0 * NK + j] * -Dx[0 * P1 + i] + s_lift[le][1 * NK + j] * Dx[P * P1 + i];
   sp += s_lift[le][2 * NK + i] * -Dy[0 * P1 + j] + s_lift[le][3 * NK + i] * Dy[P * P1 + j];
   const double im = invM[a];
-  const long n = (long)e * NP + a;
-  const int N = kp.N;
-  const double Lv[2] = {__ldg(rvol + n) + sp * im, __ldg(rvol + N + n) + ss * im};
+  const double Lv[2] = {Rphi + sp * im, Rpsi + ss * im};
   bool bad = false;
 #pragma unroll
   for (int vv = 0; vv < 2; ++vv) {
@@ -292,7 +298,7 @@ k_kin_surface(const KinParams kp, int mode, double dt, const double *w0, const d
         acc[o] += 2.0 * Lv[vv];
         r = base + dt * Lv[vv];
       } else {
-        r = base + dt / 6.0 * (acc[o] + Lv[vv]);
+        r = base + dt6 * (acc[o] + Lv[vv]);
       }
     }
     bad |= !isfinite(r);
@@ -302,26 +308,16 @@ k_kin_surface(const KinParams kp, int mode, double dt, const double *w0, const d
 }
 
 struct KinKernels {
-  cudaError_t (*volume)(const KinParams &, double tstep, double toff, const double *w, double *rvol, double *tr,
-                        cudaStream_t);
+  cudaError_t (*stage)(const KinParams &, int mode, double tstep, double toff, double dt, const double *win,
+                       const double *w0, double *acc, double *out, cudaStream_t);
   cudaError_t (*velocity_table)(const KinParams &, double *tab, cudaStream_t);
-  cudaError_t (*surface)(const KinParams &, int mode, double dt, const double *w0, const double *rvol,
-                         const double *tr, double *acc, double *out, cudaStream_t);
 };
 
 template <int P>
-cudaError_t launch_kin_volume(const KinParams &kp, double tstep, double toff, const double *w, double *rvol,
-                              double *tr, cudaStream_t s) {
+cudaError_t launch_kin_stage(const KinParams &kp, int mode, double tstep, double toff, double dt, const double *win,
+                             const double *w0, double *acc, double *out, cudaStream_t s) {
   using G = Geom<P, 2, false, false>;
-  k_kin_volume<P><<<(kp.E + G::EPB - 1) / G::EPB, G::THREADS, 0, s>>>(kp, tstep, toff, w, rvol, tr);
-  return cudaGetLastError();
-}
-
-template <int P>
-cudaError_t launch_kin_surface(const KinParams &kp, int mode, double dt, const double *w0, const double *rvol,
-                               const double *tr, double *acc, double *out, cudaStream_t s) {
-  using G = Geom<P, 2, false, false>;
-  k_kin_surface<P><<<(kp.E + G::EPB - 1) / G::EPB, G::THREADS, 0, s>>>(kp, mode, dt, w0, rvol, tr, acc, out);
+  k_kin_stage<P><<<(kp.E + G::EPB - 1) / G::EPB, G::THREADS, 0, s>>>(kp, mode, tstep, toff, dt, win, w0, acc, out);
   return cudaGetLastError();
 }
 

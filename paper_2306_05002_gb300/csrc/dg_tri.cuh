@@ -215,7 +215,7 @@ __device__ __forceinline__ void tri_edge_trace(const double *s_t, const TriLayou
 
 // One stage: the right-hand side L = M^-1 R(win) at time *t0 + tstep + toff,
 // written as L (KIN_RHS) or as one classical RK4 stage (KIN_K1..K4, the same
-// updates as k_kin_surface; out may be w0, each node being read, then written,
+// updates as k_kin_stage; out may be w0, each node being read, then written,
 // by the same thread).
 template <int P>
 __global__ void __launch_bounds__(TriGeom<P>::THREADS)
