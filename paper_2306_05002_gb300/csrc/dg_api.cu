@@ -875,14 +875,18 @@ extern "C" int dg_kernel_costs(const dg_ctx *c, double *flops, double *bytes, in
   // Bytes: the volume kernel reads the state and writes the volume part and
   // the face traces; the surface kernel reads both traces of every face node,
   // the volume part, the stage input and the step start, and writes the stage.
-  const double nt = c->prec == DG_FP64 ? c->ks.nt : c->ks32.nt;
-  const double word = c->prec == DG_FP64 ? 8.0 : 4.0;
-  if (c->prec != DG_FP64) fv += 3 * 2 * d * P1;  // compression term of the reduced energy
-  const double bv = word * (E * Np * (7 + 7) + E * NFK * nt);
-  const double bs = word * (E * NFK * nt * 2 + E * Np * (7 * 4));
+  // FP32-bulk stores traces as padded 12-word records and, in the inviscid
+  // kernels, the state and volume parts as padded 8-word node records.
+  const bool f64 = c->prec == DG_FP64;
+  const double nt = f64 ? c->ks.nt : TRW32;
+  const double nw = f64 || visc ? 7 : SW32;
+  const double word = f64 ? 8.0 : 4.0;
+  if (!f64) fv += 3 * 2 * d * P1;  // compression term of the reduced energy
+  const double bv = word * (E * Np * (nw + nw) + E * NFK * nt);
+  const double bs = word * (E * NFK * nt * 2 + E * Np * (nw * 4));
   // The fused FP32-bulk stage kernel does both; its volume part takes the
   // stage state from registers instead of reading it back.
-  const double bsv = bv + bs - word * E * Np * 7;
+  const double bsv = bv + bs - word * E * Np * nw;
   const int nk = std::min(nmax, c->prec == DG_FP64 ? 2 : 3);
   const double F[3] = {fv * E * Np, fs * E * Np, (fv + fs) * E * Np}, Bb[3] = {bv, bs, bsv};
   for (int k = 0; k < nk; ++k) {
