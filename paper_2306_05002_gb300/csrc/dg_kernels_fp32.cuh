@@ -55,17 +55,21 @@ __host__ inline ParamsF to_float(const Params &p) {
 // Face-trace record of the FP32-bulk kernels: the seven state values (in the
 // order of Var) and what needs the whole element -- d(phi)/d(axis normal to
 // the face), the level-set normal component on that axis and, viscous, the
-// stress components tau . e_axis.  Velocity, pressure, sound speed, B and the
-// mixture viscosity are recomputed from the state by the reader
-// (trace_derive), which is cheaper than moving them: 9 (11) words per face
-// node instead of 14 (17).
+// stress components tau . e_axis.  Viscous kernels: velocity, pressure, sound
+// speed, B and the mixture viscosity are recomputed from the state by the
+// reader (trace_derive).  Inviscid kernels: pressure, sound speed and 1/rho
+// travel in the record's spare words (C_P, C_C, C_IR) and the reader only
+// multiplies (trace_stored).
 enum TraceField32 { C_GPHI = 7, C_N = 8, C_TX = 9, C_TY = 10 };
 constexpr int NT32_INVISCID = 9;
 constexpr int NT32_VISCOUS = 11;
 // The FP32 face traces are stored one 48-byte record per face node ([E * NFK][TRW32] floats, the
 // words in TraceField32 order, the rest padding), so that a record moves in three 128-bit
-// accesses instead of nine or eleven scalar ones.
+// accesses instead of nine or eleven scalar ones.  The inviscid kernels fill the three spare
+// words with the writer's pressure, sound speed and 1/rho (C_P, C_C, C_IR), so the reader skips
+// the closure (two divisions and a square root per side of every face node).
 constexpr int TRW32 = 12;
+enum TraceClosure32 { C_P = 9, C_C = 10, C_IR = 11 };
 // The FP32 internal state and volume parts of the inviscid kernels are stored one 32-byte record
 // per node ([N][SW32] floats: the seven variables and a padding word), moved in two 128-bit
 // accesses; the viscous kernels keep them field-major ([7][N]), where the records did not pay
@@ -116,6 +120,18 @@ __device__ __forceinline__ void trace_derive(const ParamsF &pf, float *T) {
   T[T_C] = sqrtf((Pr + (Pr + Cm) / Gm) * ir);
   T[T_B] = Pr * pf.Bp;
   if (VISC) T[T_MU] = pf.mu1 * phi + pf.mu2 * (1.f - phi);
+}
+
+// The inviscid reader's counterpart of trace_derive: velocity from the stored 1/rho, pressure and
+// sound speed as stored by the writer, B from the pressure.
+template <int DIM>
+__device__ __forceinline__ void trace_stored(const ParamsF &pf, const float *C, float *T) {
+  const float ir = C[C_IR];
+  T[T_U] = T[T_RU] * ir;
+  T[T_V] = DIM == 2 ? T[T_RV] * ir : 0.f;
+  T[T_P] = C[C_P];
+  T[T_C] = C[C_C];
+  T[T_B] = C[C_P] * pf.Bp;
 }
 
 // Volume kernel body for the element tile `blk` (EPB elements) of one problem.
@@ -308,12 +324,13 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   const bool onS = DIM == 2 && j == 0, onN = DIM == 2 && j == P;
   if (act && (onW || onE || onS || onN)) {
     const long base = (long)e * NFK;
+    // the sound speed, with the reader's former operations (trace_derive)
+    const float cs = VISC ? 0.f : sqrtf((Pr + (Pr + fmaf(pf.dC, phi, pf.C2)) / Gm) * ir);
     auto put = [&](int f, int kk, float gn, float nn, float t1, float t2) {
       float4 *rec = reinterpret_cast<float4 *>(tr) + (base + f * NK + kk) * (TRW32 / 4);
       rec[0] = make_float4(q[0], q[1], q[2], q[3]);
       rec[1] = make_float4(q[4], q[5], q[6], gn);
-      if (VISC) rec[2] = make_float4(nn, t1, t2, 0.f);
-      else reinterpret_cast<float *>(rec + 2)[0] = nn;
+      rec[2] = VISC ? make_float4(nn, t1, t2, 0.f) : make_float4(nn, Pr, cs, ir);
     };
     const int kx = DIM == 2 ? j : 0;
     if (onW) put(0, kx, gpx, nx, txx, txy);
@@ -347,6 +364,7 @@ __device__ __forceinline__ void load_trace32(const float *__restrict__ tr, long 
   if (NC > 9) {
     const float4 c = __ldg(rec + 2);
     T[8] = c.x; T[9] = c.y; T[10] = c.z;
+    if (NC > 11) T[11] = c.w;
   } else if (NC > 8) {
     T[8] = __ldg(reinterpret_cast<const float *>(rec + 2));
   }
@@ -372,7 +390,7 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
                                             double *__restrict__ out64, float *rout = nullptr) {
   using G = Geom<P, DIM, VISC, ST, EPBX>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
-  constexpr int NC = VISC ? NT32_VISCOUS : NT32_INVISCID;
+  constexpr int NC = VISC ? NT32_VISCOUS : TRW32;  // words read per trace record
   constexpr int FPT = (NFK + NP - 1) / NP;  // face nodes per thread
   const OpsLayout L{P1, NP};
   __shared__ float s_surf[EPB][NFK][NV];
@@ -435,7 +453,8 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
       Tm[T_TX] = Cm_[fi][C_TX];
       Tm[T_TY] = Cm_[fi][C_TY];
     }
-    trace_derive<DIM, VISC>(pf, Tm);
+    if (VISC) trace_derive<DIM, VISC>(pf, Tm);
+    else trace_stored<DIM>(pf, Cm_[fi], Tm);
     if (!wall) {
 #pragma unroll
       for (int qf = 0; qf < NV; ++qf) Tp[qf] = Cp_[fi][qf];
@@ -444,8 +463,10 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
       if (VISC) {
         Tp[T_TX] = Cp_[fi][C_TX];
         Tp[T_TY] = Cp_[fi][C_TY];
+        trace_derive<DIM, VISC>(pf, Tp);
+      } else {
+        trace_stored<DIM>(pf, Cp_[fi], Tp);
       }
-      trace_derive<DIM, VISC>(pf, Tp);
     } else {
 #pragma unroll
       for (int qf = 0; qf < NT_VISCOUS; ++qf) Tp[qf] = Tm[qf];
