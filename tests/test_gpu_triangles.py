@@ -90,9 +90,9 @@ def test_tri_reinit_is_rejected(dg):
     s.close()
 
 
-def _rider_kothe(dg, orc, n, elem):
+def _rider_kothe(dg, orc, n, elem, p=3):
     import torch
-    wl = W.rider_kothe(n=n, p=3, elem=elem)
+    wl = W.rider_kothe(n=n, p=p, elem=elem)
     pb = orc.Problem(**wl.problem_kwargs())
     if elem == "tri":
         integral = lambda f: orc.tri_integral(pb, f)
@@ -133,3 +133,17 @@ def test_rider_kothe_full_period_on_triangles(orc, dg):
         assert 0.67 < l1_end / quad[n][1] < 1.5, (n, tri, quad)
         assert mass_err < 1e-10, (n, tri)
     assert tri[32][1] < 0.5 * tri[16][1], tri
+
+
+def test_rider_kothe_p1_rows_of_the_paper(orc, dg):
+    """The paper's p = 1 rows of its L1 table at 64^2 and 128^2 DoF (32 x 32 and 64 x 64 cells),
+    on rectangles (mesh (a): 2.22e-2, 8.71e-3) and on triangles (mesh (b): 1.99e-2, 8.23e-3):
+    the drop comes back with an L1 error within a factor 1.5 of the paper's and falling under
+    refinement.  (Results-level: the paper states neither Gamma nor eps; with eps = 0.75 of the
+    element width, as here, the p = 1 rows land within 5-30% of the paper's.)"""
+    paper_p1 = {"quad": (2.22e-2, 8.71e-3), "tri": (1.99e-2, 8.23e-3)}
+    for elem in ("quad", "tri"):
+        l1 = [_rider_kothe(dg, orc, n, elem, p=1)[1] for n in (32, 64)]
+        for got, paper in zip(l1, paper_p1[elem]):
+            assert paper / 1.5 < got < 1.5 * paper, (elem, l1)
+        assert l1[1] < l1[0] / 1.5, (elem, l1)
