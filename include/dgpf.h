@@ -275,7 +275,8 @@ typedef struct {
 /* Create a kinematic-mode context: 2D mesh with periodic boundaries on all
    four sides, order p (1..5 on rectangles, 1..4 on triangles), Allen-Cahn
    Gamma >= 0 and eps >= 0, velocity, interior-penalty constant c_ip (<= 0
-   selects 1).  dg_state_len gives 2 N; dg_destroy releases it; the
+   selects 1), at most 2^26 cells and fewer than 2^31 nodes per field.
+   dg_state_len gives 2 N; dg_destroy releases it; the
    single-problem and batch calls of the full model reject it (DG_ERR_ARG).
    Errors as dg_create.
    Rectangles (DG_ELEM_QUAD): GLL nodes, collocated quadrature, penalty

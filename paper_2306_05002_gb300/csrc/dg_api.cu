@@ -1211,6 +1211,10 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
                 tri ? "dg_kin_create: order p must be in 1..4 on triangles" : "dg_kin_create: order p must be in 1..5");
   if (mesh->nx < 1 || mesh->ny < 1 || (long long)mesh->nx * mesh->ny > (1LL << 26))
     return fail(nullptr, DG_ERR_ARG, "dg_kin_create: need 1 <= nx, ny and a mesh of at most 2^26 elements");
+  // nodes per field must fit the kernels' 32-bit node count
+  const long long nodes = (long long)mesh->nx * mesh->ny * (tri ? 2LL * (p + 1) * (p + 2) / 2 : (p + 1LL) * (p + 1));
+  if (nodes >= (1LL << 31))
+    return fail(nullptr, DG_ERR_ARG, "dg_kin_create: problem too large for one context (2^31 nodes per field)");
   if (!(mesh->x1 > mesh->x0) || !(mesh->y1 > mesh->y0)) return fail(nullptr, DG_ERR_ARG, "dg_kin_create: empty domain");
   for (int f = 0; f < 4; ++f)
     if (mesh->bc[f] != DG_BC_PERIODIC)

@@ -123,6 +123,9 @@ def _kin_args(**over):
     (dict(Gamma=-1.0), -1),
     (dict(elem=2), -1),
     (dict(elem=1, p=5), -7),
+    (dict(nx=1 << 14, ny=(1 << 12) + 1), -1),              # more than 2^26 cells
+    (dict(nx=1 << 13, ny=1 << 13, p=5), -1),               # 2^26 cells of 36 nodes: 2.4e9 nodes
+    (dict(nx=1 << 13, ny=(1 << 13) + 1, p=4, elem=1), -1),  # more than 2^26 cells of triangles
 ])
 def test_kin_create_rejects_invalid_arguments(lib, over, code):
     m, p, G, eps, v = _kin_args(**over)
@@ -138,6 +141,17 @@ def test_kin_calls_reject_other_contexts(lib):
 
 def test_reinit_rejects_null_and_negative_arguments(lib):
     assert lib.dg_reinit(None, None, 1, 0.0, 0.0, None) == -1
+
+
+def test_create_rejects_problems_beyond_the_node_limit(lib):
+    """7 N doubles must be indexable with 32-bit node counts: 16384^2 p5 elements are refused during
+    argument checking, before any device call."""
+    import paper_2306_05002_gb300 as pkg
+    m, eos, o = pkg.make_structs(2, 1 << 14, 1 << 14, 0.0, 1.0, 0.0, 1.0, ("periodic",) * 4, (4.4, 1.4),
+                                 (6e8, 0.0), (1000.0, 1.0))
+    h = ctypes.c_void_p(123)
+    assert lib.dg_create(ctypes.byref(m), 5, ctypes.byref(eos), 1.0, 0.05, ctypes.byref(o), ctypes.byref(h)) == -1
+    assert h.value is None
 
 
 def test_full_model_rejects_triangles(lib):
