@@ -525,7 +525,7 @@ def kinematic_block(dg, steps, n=64):
     wt = 2.0 / (3 * 4 * legendre.Legendre.basis(3)(xi) ** 2)
     M = np.tile(np.outer(wt, wt).ravel() * 0.25 * small.hx * small.hy, small.nx * small.ny)
     ach = kin_flops_per_node_stage(wl.p) * wl.N * 4 / (ms * 1e-3) / 1e12
-    return {"workload": f"Rider-Kothe vortex {n}x{n} quads p=3, T=4, eps=0.75h, Gamma=1, FP64, classical RK4",
+    return {"workload": f"Rider-Kothe vortex {n}x{n} quads p=3, T=4, eps=0.75 h/(p+1), Gamma=1, FP64, classical RK4",
             "nodes": wl.N, "steps": steps, "ms_per_step": ms, "value": 2 * 4 * wl.N / (ms * 1e-3), "unit": UNIT,
             "gpu_launches_per_step": 4,
             "roofline": {"bound": "alu", "kernel": "k_kin_stage", "achieved": ach,
@@ -592,7 +592,7 @@ def triangle_block(dg, steps, n=64):
     M = np.tile(wn * 0.5 * small.hx * small.hy, small.E)
     l1 = float(np.sum(M * np.abs(wend[0] - small.w[0])))
     mass = float(np.sum(M * (wend[0] - small.w[0])) / np.sum(M * small.w[0]))
-    return {"workload": f"Rider-Kothe vortex {n}x{n} cells split into {wl.E} triangles, p=3, T=4, eps=0.75h, "
+    return {"workload": f"Rider-Kothe vortex {n}x{n} cells split into {wl.E} triangles, p=3, T=4, eps=0.75 h/(p+1), "
                         f"Gamma=1, FP64, classical RK4",
             "nodes": wl.N, "steps": steps, "ms_per_step": ms, "value": 2 * 4 * wl.N / (ms * 1e-3), "unit": UNIT,
             "gpu_launches_per_step": 4,

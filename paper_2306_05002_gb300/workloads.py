@@ -402,15 +402,18 @@ def kin_stable_dt(wl: KinWorkload, umax: float) -> float:
 
 
 def rider_kothe(n: int = 16, p: int = 3, T: float = 4.0, R: float = 0.15, center=(0.0, 0.25),
-                eps_h: float = 0.75, Gamma: float = 1.0, vortex=(0.0, 0.0), elem: str = "quad") -> KinWorkload:
+                eps_dof: float = 0.75, Gamma: float = 1.0, vortex=(0.0, 0.0), elem: str = "quad",
+                eps_h: Optional[float] = None) -> KinWorkload:
     """Rider-Kothe vortex (Sec. 4.1): a drop of radius 0.15 centred at (0, 0.25) in the periodic
     square [-0.5, 0.5]^2, stretched by the time-reversing vortex of period T = 4 centred at
     `vortex` (the domain centre; (0.5, 0.5) gives the printed formula, whose vortex sits at the
-    domain corners).  Phase 1 is the drop; psi = R - r grows into it.  eps = 0.75 h (h: element
-    width) and Gamma = |u|max = 1, since the paper leaves both unstated for this test."""
+    domain corners).  Phase 1 is the drop; psi = R - r grows into it.  The paper leaves eps and
+    Gamma unstated for this test: eps = eps_dof h / (p + 1), 0.75 of the node spacing h / (p + 1)
+    (h: cell width; the paper compares orders at matched degrees of freedom), or eps_h h when
+    eps_h is given; Gamma = |u|max = 1."""
     wl = KinWorkload(name=f"rk2d_{n}x{n}p{p}" + ("tri" if elem == "tri" else ""), nx=n, ny=n, p=p, Gamma=Gamma,
                      vel="rider_kothe", T=T, xc=vortex[0], yc=vortex[1], elem=elem)
-    wl.eps = eps_h * wl.hx
+    wl.eps = eps_h * wl.hx if eps_h is not None else eps_dof * wl.hx / (p + 1)
     x, y = _kin_nodes(wl)
     r = np.hypot(x - center[0], y - center[1])
     s = R - r

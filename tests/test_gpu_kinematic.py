@@ -102,19 +102,23 @@ def _rider_kothe(dg, orc, n):
 
 
 def test_rider_kothe_full_period(orc, dg):
-    """16 x 16 and 32 x 32, p = 3 (the paper's 64^2 and 128^2 DoF), vortex centred on the domain:
-    the stretched drop comes back
-    (the error at T is well below the one at T/2), the L1 error falls under refinement and stays
-    within a factor 3 of the paper's p = 3 values (1.75e-2, 4.83e-3; loose, since the paper does
-    not state Gamma and eps for this test), and the phase-field mass error is small and falls
-    under refinement.  It is not round-off: the velocity sampled at the GLL nodes interpolates to
-    a field that is not divergence-free, and the collocated transport term integrates
-    phi div I(u) (exact for a uniform velocity, see the oracle pins)."""
-    res = {n: _rider_kothe(dg, orc, n) for n in (16, 32)}
-    for n, paper in ((16, 1.75e-2), (32, 4.83e-3)):
+    """16 x 16, 32 x 32 and 64 x 64, p = 3 (the paper's 64^2, 128^2 and 256^2 DoF rows), vortex
+    centred on the domain, eps = 0.75 of the node spacing: the stretched drop comes back (the
+    error at T is well below the one at T/2), the L1 error falls under refinement, sits within a
+    factor 2 of the paper's p = 3 values at 128^2 and 256^2 (4.83e-3, 1.23e-3) and below its 64^2
+    value (1.75e-2) -- results-level, since the paper states neither Gamma nor eps for this
+    test -- and the phase-field mass error is small and falls under refinement.  It is not
+    round-off: the velocity sampled at the GLL nodes interpolates to a field that is not
+    divergence-free, and the collocated transport term integrates phi div I(u) (exact for a
+    uniform velocity, see the oracle pins)."""
+    res = {n: _rider_kothe(dg, orc, n) for n in (16, 32, 64)}
+    for n in (16, 32, 64):
         l1_half, l1_end, mass_err = res[n]
-        assert l1_end < 0.5 * l1_half, (n, l1_end, l1_half)
-        assert l1_end < 3 * paper, (n, l1_end)
+        assert l1_end < 0.5 * l1_half, (n, res)
+    assert res[16][1] < 1.75e-2, res
+    for n, paper in ((32, 4.83e-3), (64, 1.23e-3)):
+        assert 0.5 * paper < res[n][1] < 2 * paper, (n, res)
+    assert res[64][1] < res[32][1] < res[16][1], res
     assert res[16][2] < 2e-6, res
-    assert res[32][1] < 0.5 * res[16][1], res
-    assert res[32][2] < 0.25 * res[16][2], res
+    assert res[64][2] < res[32][2] < res[16][2], res
+
