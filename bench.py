@@ -55,6 +55,8 @@ def parse():
                     help="pseudo-time steps of the timed re-initialisation block (0 skips it)")
     ap.add_argument("--rt-paper-steps", type=int, default=10,
                     help="timed steps on the paper's Rayleigh-Taylor domain with the pressure top (0 skips)")
+    ap.add_argument("--slab-steps", type=int, default=1000,
+                    help="steps of the 1D slab block (0 skips it)")
     ap.add_argument("--tri-steps", type=int, default=200,
                     help="timed RK4 steps of the kinematic block on triangles (0 skips it)")
     ap.add_argument("--tri-n", type=int, default=64,
@@ -538,6 +540,39 @@ def kinematic_block(dg, steps, n=64):
                                     "paper_l1_p3_64sq_dof": 1.75e-2}}
 
 
+def slab_block(dg, steps):
+    """The 1D periodic water slab in air (100 elements, p = 3, eps = h, u = 1): `steps` SSP-RK3 steps
+    in one dg_step call (CUDA graphs of 8 steps), FP64 (the configuration's precision) and, for
+    information, FP32-bulk with its relative L2 error in alpha against FP64 after them.  Far too
+    small for a roofline (400 nodes): the step latency is the number to read."""
+    import numpy as np
+    import torch
+    from paper_2306_05002_gb300 import workloads as W
+    wl = W.slab_1d(nx=100, p=3)
+    out = {"workload": "1D periodic water slab in air, 100 elements p=3, eps=h, u=1, SSP-RK3", "nodes": wl.N,
+           "steps": steps}
+    states = {}
+    for prec in ("fp64", "fp32bulk"):
+        s = dg.Solver(wl, precision=prec)
+        w = torch.from_numpy(wl.w.copy()).cuda()
+        s.dg_step(w, wl.dt, 9)
+        w.copy_(torch.from_numpy(wl.w.copy()))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.dg_step(w, wl.dt, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[prec] = {"us_per_step": 1e3 * ms, "value": 21 * wl.N / (ms * 1e-3), "unit": UNIT,
+                     "device_status": s.dg_status_read()}
+        states[prec] = w.cpu().numpy()
+        s.close()
+    a, b = states["fp32bulk"], states["fp64"]
+    out["l2_rel_alpha"] = float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0]))
+    return out
+
+
 def tri_flops_per_stage(p):
     """Algorithmic FP64 flops of one triangle and one RK stage (both fields), 2 per multiply-add:
     phi and its r-, s-derivatives and psi's at the (p+2)^2 volume points (5 dot products of length
@@ -689,6 +724,7 @@ def run_ours(args, rank, world, local_rank):
     adjoint = (adjoint_block(dg, args.adjoint_steps, n=args.adjoint_n)
                if (args.adjoint_steps > 0 and rank == 0) else None)
     rt = rt_block(dg, args.rt_steps) if (args.rt_steps > 0 and rank == 0) else None
+    slab = slab_block(dg, args.slab_steps) if (args.slab_steps > 0 and rank == 0) else None
     kin = kinematic_block(dg, args.kin_steps) if (args.kin_steps > 0 and rank == 0) else None
     tri = triangle_block(dg, args.tri_steps, args.tri_n) if (args.tri_steps > 0 and rank == 0) else None
     ri = reinit_block(dg, args.reinit_iters) if (args.reinit_iters > 0 and rank == 0) else None
@@ -725,6 +761,8 @@ def run_ours(args, rank, world, local_rank):
             line["adjoint"] = adjoint
         if rt:
             line["rayleigh_taylor"] = rt
+        if slab:
+            line["slab_1d"] = slab
         if kin:
             line["kinematic"] = kin
         if tri:
