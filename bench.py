@@ -144,7 +144,8 @@ KERNEL_SOURCES = {"fp64": ["paper_2306_05002_gb300/csrc/dg_kernels_fp64.cuh",
                            "paper_2306_05002_gb300/csrc/dg_common.cuh"],
                   "fp32bulk": ["paper_2306_05002_gb300/csrc/dg_kernels_fp32.cuh",
                                "paper_2306_05002_gb300/csrc/dg_kernels_fp64.cuh",
-                               "paper_2306_05002_gb300/csrc/dg_common.cuh"]}
+                               "paper_2306_05002_gb300/csrc/dg_common.cuh",
+                               "paper_2306_05002_gb300/csrc/dg_pdl.cuh"]}
 
 
 def kernel_source_hash(precision="fp64"):

@@ -37,6 +37,7 @@
 
 #include "dg_common.cuh"
 #include "dg_kernels_fp64.cuh"
+#include "dg_pdl.cuh"
 
 namespace dgpf {
 
@@ -76,16 +77,25 @@ enum TraceClosure32 { C_P = 9, C_C = 10, C_IR = 11 };
 // (256x256 p4 Rayleigh-Taylor step 0.301 -> 0.316 ms), while the inviscid batch gained 11%.
 constexpr int SW32 = 8;
 
-template <bool AOS>
+// Loads of data that an earlier kernel wrote: non-coherent (__ldg) in a kernel
+// launched plainly, coherent (__ldca) in one launched as a programmatic
+// dependent (COH), which overlaps the kernel that writes the data.
+template <bool COH, typename T>
+__device__ __forceinline__ T ld_in(const T *p) {
+  if (COH) return __ldca(p);
+  return __ldg(p);
+}
+
+template <bool AOS, bool COH = false>
 __device__ __forceinline__ void load_node32(const float *__restrict__ w, long n, int N, float *q) {
   if (AOS) {
     const float4 *r = reinterpret_cast<const float4 *>(w) + 2 * n;
-    const float4 a = __ldg(r), b = __ldg(r + 1);
+    const float4 a = ld_in<COH>(r), b = ld_in<COH>(r + 1);
     q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
     q[4] = b.x; q[5] = b.y; q[6] = b.z;
   } else {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) q[v] = __ldg(w + (long)v * N + n);
+    for (int v = 0; v < NV; ++v) q[v] = ld_in<COH>(w + (long)v * N + n);
   }
 }
 
@@ -141,7 +151,7 @@ __device__ __forceinline__ void trace_stored(const ParamsF &pf, const float *C, 
 // s_op: the block's shared copy of the operator table; this body copies the
 // two derivative matrices into it unless ops_ready (the fused kernel's
 // surface part has copied the whole table and synchronised the block).
-template <int P, int DIM, bool VISC, bool ST, int EPBX = 0>
+template <int P, int DIM, bool VISC, bool ST, int EPBX = 0, bool PDL = false>
 __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf, const float *__restrict__ opsf,
                                            float *s_op, bool ops_ready, int blk, const float *__restrict__ w,
                                            float *__restrict__ rvol, float *__restrict__ tr,
@@ -175,13 +185,13 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
     // first stage: convert the FP64 state (the stiffened-gas constant leaves rho E in FP64)
     double d[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) d[v] = act ? __ldg(w64 + (long)v * N + n) : (v == M1 || v == M2 ? 1.0 : 0.0);
+    for (int v = 0; v < NV; ++v) d[v] = act ? ld_in<PDL>(w64 + (long)v * N + n) : (v == M1 || v == M2 ? 1.0 : 0.0);
 #pragma unroll
     for (int v = 0; v < RE; ++v) q[v] = (float)d[v];
     q[RE] = (float)(d[RE] - fma(prm.dC, d[PHI], prm.C2));
     if (act) store_node32<!VISC>(w32out, n, N, q);
   } else if (act) {
-    load_node32<!VISC>(w, n, N, q);
+    load_node32<!VISC, PDL>(w, n, N, q);
   } else {
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = v == M1 || v == M2 ? 1.f : 0.f;
@@ -340,33 +350,41 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   }
 }
 
-template <int P, int DIM, bool VISC, bool ST>
+// PDL (here and in the kernels below): launched as a programmatic dependent of
+// the kernel before (launch_dependent).
+template <int P, int DIM, bool VISC, bool ST, bool PDL>
 __global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
 k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, const float *__restrict__ w,
            float *__restrict__ rvol, float *__restrict__ tr, const double *__restrict__ w64,
            float *__restrict__ w32out) {
-  __shared__ float s_op[2 * Geom<P, DIM, VISC, ST>::P1 * Geom<P, DIM, VISC, ST>::P1];  // Dx, Dy
-  vol32_body<P, DIM, VISC, ST>(prm, pf, opsf, s_op, false, blockIdx.x, w, rvol, tr, w64, w32out);
+  constexpr int P11 = Geom<P, DIM, VISC, ST>::P1 * Geom<P, DIM, VISC, ST>::P1;
+  __shared__ float s_op[2 * P11];  // Dx, Dy
+  if (PDL) {
+    grid_dependents_launch();
+    for (int t = threadIdx.x; t < 2 * P11; t += blockDim.x) s_op[t] = opsf[t];
+    grid_dependency_wait();
+  }
+  vol32_body<P, DIM, VISC, ST, 0, PDL>(prm, pf, opsf, s_op, PDL, blockIdx.x, w, rvol, tr, w64, w32out);
 }
 
 // The NC words of face-trace record o (three 128-bit loads, or two and one word), or, when the
 // record does not exist, zeros with m1 = m1_default (a finite density for the closure).
-template <int NC>
+template <int NC, bool COH = false>
 __device__ __forceinline__ void load_trace32(const float *__restrict__ tr, long o, bool valid, float *T,
                                              float m1_default) {
 #pragma unroll
   for (int qf = 0; qf < NC; ++qf) T[qf] = qf == T_M1 ? m1_default : 0.f;
   if (!valid) return;
   const float4 *rec = reinterpret_cast<const float4 *>(tr) + o * (TRW32 / 4);
-  const float4 a = __ldg(rec), b = __ldg(rec + 1);
+  const float4 a = ld_in<COH>(rec), b = ld_in<COH>(rec + 1);
   T[0] = a.x; T[1] = a.y; T[2] = a.z; T[3] = a.w;
   T[4] = b.x; T[5] = b.y; T[6] = b.z; T[7] = b.w;
   if (NC > 9) {
-    const float4 c = __ldg(rec + 2);
+    const float4 c = ld_in<COH>(rec + 2);
     T[8] = c.x; T[9] = c.y; T[10] = c.z;
     if (NC > 11) T[11] = c.w;
   } else if (NC > 8) {
-    T[8] = __ldg(reinterpret_cast<const float *>(rec + 2));
+    T[8] = ld_in<COH>(reinterpret_cast<const float *>(rec + 2));
   }
 }
 
@@ -382,7 +400,10 @@ __device__ __forceinline__ void load_trace32(const float *__restrict__ tr, long 
 // left in rout, for a volume body that follows in the same kernel.  Every
 // thread of the block returns from this body (none leaves early), so such a
 // body may synchronise the block.
-template <int P, int DIM, bool VISC, bool ST, int EPBX = 0>
+// PDL: the kernel was launched as a programmatic dependent; the operator table
+// is copied before the wait for the kernel before, whose results are then read
+// with coherent loads.
+template <int P, int DIM, bool VISC, bool ST, int EPBX = 0, bool PDL = false>
 __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf, const float *__restrict__ opsf,
                                             float *s_op, int blk, int mode, float dt, const float *__restrict__ w0,
                                             const float *__restrict__ ws, const float *__restrict__ rvol,
@@ -405,33 +426,44 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   const int N = prm.N;
   const long n = (long)(act ? e : 0) * NP + a;
 
+  int e2_[FPT];  // neighbour across the face of each face node (-1: wall)
+  if (PDL) {
+#pragma unroll
+    for (int fi = 0; fi < FPT; ++fi) {
+      const int t = a + fi * NP;
+      e2_[fi] = act && t < NFK ? neighbour(prm, e, t / NK) : -1;
+    }
+    for (int t = threadIdx.x; t < L.size(); t += blockDim.x) s_op[t] = opsf[t];
+    grid_dependency_wait();
+  }
+
   // Every global load of the body is issued first -- the node's own inputs of
   // the update and both traces of its face nodes -- so that their latencies
-  // overlap each other and the copy of the operator table.
+  // overlap each other (and the copy of the operator table).
   float Lv[NV], wsn[NV], w0n[NV];
 #pragma unroll
   for (int vv = 0; vv < NV; ++vv) Lv[vv] = wsn[vv] = w0n[vv] = 0.f;
   if (act) {
-    load_node32<!VISC>(rvol, n, N, Lv);
-    if (mode != MODE_RHS) load_node32<!VISC>(ws, n, N, wsn);
-    if (mode == MODE_S2 || mode == MODE_S3) load_node32<!VISC>(w0, n, N, w0n);
+    load_node32<!VISC, PDL>(rvol, n, N, Lv);
+    if (mode != MODE_RHS) load_node32<!VISC, PDL>(ws, n, N, wsn);
+    if (mode == MODE_S2 || mode == MODE_S3) load_node32<!VISC, PDL>(w0, n, N, w0n);
   }
   float Cm_[FPT][NC], Cp_[FPT][NC];
-  int e2_[FPT];
 #pragma unroll
   for (int fi = 0; fi < FPT; ++fi) {
     const int t = a + fi * NP;
     const bool fv = act && t < NFK;
     const int f = fv ? t / NK : 0, kk = fv ? t % NK : 0;
-    const int e2 = fv ? neighbour(prm, e, f) : -1;
+    const int e2 = PDL ? e2_[fi] : (fv ? neighbour(prm, e, f) : -1);
     e2_[fi] = e2;
     const long om = (long)(act ? e : 0) * NFK + (fv ? t : 0);
     const long op = (long)(e2 >= 0 ? e2 : 0) * NFK + (f ^ 1) * NK + kk;
-    load_trace32<NC>(tr, om, fv, Cm_[fi], 1.f);
-    load_trace32<NC>(tr, op, e2 >= 0, Cp_[fi], 0.f);
+    load_trace32<NC, PDL>(tr, om, fv, Cm_[fi], 1.f);
+    load_trace32<NC, PDL>(tr, op, e2 >= 0, Cp_[fi], 0.f);
   }
 
-  for (int t = threadIdx.x; t < L.size(); t += blockDim.x) s_op[t] = opsf[t];
+  if (!PDL)
+    for (int t = threadIdx.x; t < L.size(); t += blockDim.x) s_op[t] = opsf[t];
   __syncthreads();
   const float *Dx = s_op + L.Dx(), *Dy = s_op + L.Dy();
   const float *invM = s_op + L.invM(), *wfx = s_op + L.wfx(), *wfy = s_op + L.wfy();
@@ -622,13 +654,14 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   }
 }
 
-template <int P, int DIM, bool VISC, bool ST>
+template <int P, int DIM, bool VISC, bool ST, bool PDL>
 __global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
 k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt,
             const float *__restrict__ w0, const float *__restrict__ ws, const float *__restrict__ rvol,
             const float *__restrict__ tr, float *__restrict__ out32, double *__restrict__ out64) {
   __shared__ float s_op[Geom<P, DIM, VISC, ST>::OPS];
-  surf32_body<P, DIM, VISC, ST>(prm, pf, opsf, s_op, blockIdx.x, mode, dt, w0, ws, rvol, tr, out32, out64);
+  if (PDL) grid_dependents_launch();
+  surf32_body<P, DIM, VISC, ST, 0, PDL>(prm, pf, opsf, s_op, blockIdx.x, mode, dt, w0, ws, rvol, tr, out32, out64);
 }
 
 // Fused stage kernel: the surface part of stage s (mode MODE_S1..S3) followed,
@@ -645,7 +678,7 @@ k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, 
 // Residency of the viscous variants: at most 80 registers a thread (65,536 / (THREADS x 80) CTAs
 // per SM), which the surface-tension variant otherwise exceeds, one CTA per SM fewer and 6% slower
 // at p = 4.
-template <int P, int DIM, bool VISC, bool ST>
+template <int P, int DIM, bool VISC, bool ST, bool PDL>
 __global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS,
                                   VISC ? 65536 / (Geom<P, DIM, VISC, ST>::THREADS * 80) : 1)
 k_surfvol32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt,
@@ -654,8 +687,9 @@ k_surfvol32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, 
             float *__restrict__ tr_out) {
   __shared__ float s_op[Geom<P, DIM, VISC, ST>::OPS];  // one table for both parts
   float r[NV];
-  surf32_body<P, DIM, VISC, ST>(prm, pf, opsf, s_op, blockIdx.x, mode, dt, w0, ws, rvol_in, tr_in, out32, nullptr,
-                                r);
+  if (PDL) grid_dependents_launch();
+  surf32_body<P, DIM, VISC, ST, 0, PDL>(prm, pf, opsf, s_op, blockIdx.x, mode, dt, w0, ws, rvol_in, tr_in, out32,
+                                        nullptr, r);
   vol32_body<P, DIM, VISC, ST>(prm, pf, opsf, s_op, true, blockIdx.x, nullptr, rvol_out, tr_out, nullptr, nullptr,
                                r);
 }
@@ -679,12 +713,24 @@ struct KernelSet32 {
   int nt, epb, threads;
 };
 
+// A grid that the device holds at once is launched as a programmatic dependent
+// of the kernel before it: its launch, CTA start and operator-table copy
+// overlap that kernel's tail, which is most of the gain on latency-bound
+// stages (64x64 p3: 4.9 instead of 6.2 us per volume launch back to back).  A
+// grid of several waves gains nothing from an early start, and the early CTAs
+// of the next kernel would take the places where this grid's later waves
+// balance over the SMs, so it is launched plainly (and reads with the
+// non-coherent loads, a few per cent faster on the viscous surface kernels).
 template <int P, int DIM, bool VISC, bool ST>
 cudaError_t launch_volume32(const Params &prm, const ParamsF &pf, const float *opsf, const float *w, float *rvol,
                             float *trace, const double *w64, float *w32out, cudaStream_t s) {
   using G = Geom<P, DIM, VISC, ST>;
   const int blocks = (prm.E + G::EPB - 1) / G::EPB;
-  k_volume32<P, DIM, VISC, ST><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, w, rvol, trace, w64, w32out);
+  static const int resident = resident_blocks(k_volume32<P, DIM, VISC, ST, true>, G::THREADS);
+  if (blocks <= resident)
+    return launch_dependent(k_volume32<P, DIM, VISC, ST, true>, blocks, G::THREADS, s, prm, pf, opsf, w, rvol,
+                            trace, w64, w32out);
+  k_volume32<P, DIM, VISC, ST, false><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, w, rvol, trace, w64, w32out);
   return cudaGetLastError();
 }
 
@@ -694,8 +740,12 @@ cudaError_t launch_surface32(const Params &prm, const ParamsF &pf, const float *
                              double *out64, cudaStream_t s) {
   using G = Geom<P, DIM, VISC, ST>;
   const int blocks = (prm.E + G::EPB - 1) / G::EPB;
-  k_surface32<P, DIM, VISC, ST><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, mode, dt, w0, ws, rvol, trace, out32,
-                                                              out64);
+  static const int resident = resident_blocks(k_surface32<P, DIM, VISC, ST, true>, G::THREADS);
+  if (blocks <= resident)
+    return launch_dependent(k_surface32<P, DIM, VISC, ST, true>, blocks, G::THREADS, s, prm, pf, opsf, mode,
+                            dt, w0, ws, rvol, trace, out32, out64);
+  k_surface32<P, DIM, VISC, ST, false><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, mode, dt, w0, ws, rvol, trace,
+                                                                     out32, out64);
   return cudaGetLastError();
 }
 
@@ -705,8 +755,12 @@ cudaError_t launch_surfvol32(const Params &prm, const ParamsF &pf, const float *
                              float *out32, float *rvol_out, float *tr_out, cudaStream_t s) {
   using G = Geom<P, DIM, VISC, ST>;
   const int blocks = (prm.E + G::EPB - 1) / G::EPB;
-  k_surfvol32<P, DIM, VISC, ST><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, mode, dt, w0, ws, rvol_in, tr_in,
-                                                              out32, rvol_out, tr_out);
+  static const int resident = resident_blocks(k_surfvol32<P, DIM, VISC, ST, true>, G::THREADS);
+  if (blocks <= resident)
+    return launch_dependent(k_surfvol32<P, DIM, VISC, ST, true>, blocks, G::THREADS, s, prm, pf, opsf, mode,
+                            dt, w0, ws, rvol_in, tr_in, out32, rvol_out, tr_out);
+  k_surfvol32<P, DIM, VISC, ST, false><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, mode, dt, w0, ws, rvol_in, tr_in,
+                                                                     out32, rvol_out, tr_out);
   return cudaGetLastError();
 }
 
