@@ -111,23 +111,29 @@ __device__ __forceinline__ void store_node32(float *w, long n, int N, const floa
   }
 }
 
+// The closure's divisions (by rho and by the mixture 1/(gamma-1)) use the
+// approximate reciprocal (__fdividef: within 2 ulp for the magnitudes of a
+// density or of 1/(gamma-1)), far below the FP32 storage error of this path;
+// the IEEE division costs about four times the instructions.
+__device__ __forceinline__ float rcp32(float x) { return __fdividef(1.0f, x); }
+
 // Fill T[T_U], T[T_V], T[T_P], T[T_C], T[T_B] (and T[T_MU]) from the state
 // values T[T_PHI..T_RE], with the operations of the volume body.
 template <int DIM, bool VISC>
 __device__ __forceinline__ void trace_derive(const ParamsF &pf, float *T) {
   const float phi = T[T_PHI];
   const float rho = T[T_M1] + T[T_M2];
-  const float ir = 1.0f / rho;
+  const float ir = rcp32(rho);
   const float u = T[T_RU] * ir;
   const float v = DIM == 2 ? T[T_RV] * ir : 0.f;
   const float k = 0.5f * (u * u + v * v);
-  const float Gm = fmaf(phi, pf.g1 - pf.g2, pf.g2);
-  const float Pr = (T[T_RE] - rho * k) / Gm;
+  const float iG = rcp32(fmaf(phi, pf.g1 - pf.g2, pf.g2));
+  const float Pr = (T[T_RE] - rho * k) * iG;
   const float Cm = fmaf(pf.dC, phi, pf.C2);
   T[T_U] = u;
   T[T_V] = v;
   T[T_P] = Pr;
-  T[T_C] = sqrtf((Pr + (Pr + Cm) / Gm) * ir);
+  T[T_C] = sqrtf((Pr + (Pr + Cm) * iG) * ir);
   T[T_B] = Pr * pf.Bp;
   if (VISC) T[T_MU] = pf.mu1 * phi + pf.mu2 * (1.f - phi);
 }
@@ -198,12 +204,12 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   }
   const float phi = q[PHI], psi = q[PSI];
   const float rho = q[M1] + q[M2];
-  const float ir = 1.0f / rho;
+  const float ir = rcp32(rho);
   const float u = q[RU] * ir;
   const float v = DIM == 2 ? q[RV] * ir : 0.f;
   const float k = 0.5f * (u * u + v * v);
-  const float Gm = fmaf(phi, pf.g1 - pf.g2, pf.g2);
-  const float Pr = (q[RE] - rho * k) / Gm;
+  const float iG = rcp32(fmaf(phi, pf.g1 - pf.g2, pf.g2));
+  const float Pr = (q[RE] - rho * k) * iG;
   const float Bq = Pr * pf.Bp;  // B - (C_1 - C_2)
 
   if (lane) {
@@ -335,7 +341,7 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   if (act && (onW || onE || onS || onN)) {
     const long base = (long)e * NFK;
     // the sound speed, with the reader's former operations (trace_derive)
-    const float cs = VISC ? 0.f : sqrtf((Pr + (Pr + fmaf(pf.dC, phi, pf.C2)) / Gm) * ir);
+    const float cs = VISC ? 0.f : sqrtf((Pr + (Pr + fmaf(pf.dC, phi, pf.C2)) * iG) * ir);
     auto put = [&](int f, int kk, float gn, float nn, float t1, float t2) {
       float4 *rec = reinterpret_cast<float4 *>(tr) + (base + f * NK + kk) * (TRW32 / 4);
       rec[0] = make_float4(q[0], q[1], q[2], q[3]);
@@ -414,8 +420,10 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   constexpr int NC = VISC ? NT32_VISCOUS : TRW32;  // words read per trace record
   constexpr int FPT = (NFK + NP - 1) / NP;  // face nodes per thread
   const OpsLayout L{P1, NP};
-  __shared__ float s_surf[EPB][NFK][NV];
-  __shared__ float s_lift[EPB][NFK][6];
+  // Per face node: the surface integrand of the 7 equations and the 6 lifting
+  // coefficients, each padded to 8 floats (two 128-bit shared accesses).
+  __shared__ float4 s_surf[EPB][NFK][2];
+  __shared__ float4 s_lift[EPB][NFK][2];
 
   const int le_raw = threadIdx.x / NP;
   const bool lane = le_raw < EPB;
@@ -583,10 +591,10 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
       const float tup = tpx * Tp[T_U] + tpy * Tp[T_V];
       S[RE] += wf * (0.5f * (tup - tum) + eta * mua * (kp - km));
     }
-#pragma unroll
-    for (int vv = 0; vv < NV; ++vv) s_surf[le][t][vv] = S[vv];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) s_lift[le][t][c] = lift[c];
+    s_surf[le][t][0] = make_float4(S[0], S[1], S[2], S[3]);
+    s_surf[le][t][1] = make_float4(S[4], S[5], S[6], 0.f);
+    s_lift[le][t][0] = make_float4(lift[0], lift[1], lift[2], lift[3]);
+    s_lift[le][t][1] = make_float4(lift[4], lift[5], 0.f, 0.f);
   }
   __syncthreads();
 
@@ -594,8 +602,9 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
     const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
     float acc[NV] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     auto face_add = [&](int f, int kk) {
-#pragma unroll
-      for (int vv = 0; vv < NV; ++vv) acc[vv] += s_surf[le][f * NK + kk][vv];
+      const float4 x = s_surf[le][f * NK + kk][0], y = s_surf[le][f * NK + kk][1];
+      acc[0] += x.x; acc[1] += x.y; acc[2] += x.z; acc[3] += x.w;
+      acc[4] += y.x; acc[5] += y.y; acc[6] += y.z;
     };
     const int kx = DIM == 2 ? j : 0;
     if (i == 0) face_add(0, kx);
@@ -603,16 +612,21 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
     if (DIM == 2 && j == 0) face_add(2, i);
     if (DIM == 2 && j == P) face_add(3, i);
     {
-      const int slot[6] = {PHI, M1, M2, RU, RV, RE};
-      const float lw = -Dx[0 * P1 + i], le_ = Dx[P * P1 + i];
-#pragma unroll
-      for (int c = 0; c < 6; ++c)
-        acc[slot[c]] += s_lift[le][0 * NK + kx][c] * lw + s_lift[le][1 * NK + kx][c] * le_;
+      // the symmetric SIP term of the four faces, weighted by the boundary row of D
+      auto lift_add = [&](int fn, float wgt) {
+        const float4 x = s_lift[le][fn][0], y = s_lift[le][fn][1];
+        acc[PHI] += x.x * wgt;
+        acc[M1] += x.y * wgt;
+        acc[M2] += x.z * wgt;
+        acc[RU] += x.w * wgt;
+        acc[RV] += y.x * wgt;
+        acc[RE] += y.y * wgt;
+      };
+      lift_add(0 * NK + kx, -Dx[0 * P1 + i]);
+      lift_add(1 * NK + kx, Dx[P * P1 + i]);
       if (DIM == 2) {
-        const float ls = -Dy[0 * P1 + j], ln = Dy[P * P1 + j];
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-          acc[slot[c]] += s_lift[le][2 * NK + i][c] * ls + s_lift[le][3 * NK + i][c] * ln;
+        lift_add(2 * NK + i, -Dy[0 * P1 + j]);
+        lift_add(3 * NK + i, Dy[P * P1 + j]);
       }
     }
     const float im = invM[a];
