@@ -656,7 +656,12 @@ def adjoint_block(dg, steps, every=20, n=128):
     s.dg_step(x, wl.dt, steps)
     target = x[0].clone()
     w0 = torch.from_numpy(wl.w.copy()).cuda()
-    A.forward(s, w0, wl.dt, 2, every)  # warm-up (graph capture)
+    # warm-up: one checkpoint segment forward and back (graph capture; the segment's states and
+    # tapes, ~2.6 GB, come from the caching allocator afterwards -- the first allocation of that
+    # much memory on a freshly started GPU took ~0.65 s)
+    wW, ckW = A.forward(s, w0, wl.dt, every, every)
+    A.backward(s, ckW, torch.zeros_like(wW), wl.dt, every, every)
+    del wW, ckW
     torch.cuda.synchronize()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     e[0].record()
