@@ -240,13 +240,29 @@ def oracle_rate(wl, steps: int, threads: int = 0):
     return 7 * wl.N * 3 * steps / dt, dt
 
 
+def host_cpu():
+    """The host CPU the oracle runs on: model name (lscpu, else the machine type) and core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    import platform
+    return {"model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
 def cpu_baseline(wl, steps: int):
     if steps <= 0:
         _, t1 = oracle_rate(wl, 1)
         steps = max(1, min(200, int(15.0 / max(t1, 1e-3))))
     rate, secs = oracle_rate(wl, steps)
     line = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} SSP-RK3 steps of the same workload ({secs:.1f} s, single-threaded plain C FP64)"}
+            "sample": f"{steps} SSP-RK3 steps of the same workload ({secs:.1f} s, single-threaded plain C FP64)",
+            "host": host_cpu()}
     # the same oracle source built with its element loops parallel (OpenMP), on every host core
     try:
         import oracle
@@ -278,7 +294,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_of(wl, {"l2": "n/a (CPU)"}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} SSP-RK3 steps, one per timed step"},
+                             "sample": f"{args.steps} SSP-RK3 steps, one per timed step", "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
