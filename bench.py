@@ -240,6 +240,39 @@ def oracle_rate(wl, steps: int, threads: int = 0):
     return 7 * wl.N * 3 * steps / dt, dt
 
 
+def oracle_sample(single, omp, omp_steps: int = 1, of: str = ""):
+    """The oracle on a bounded sample of a large workload, as DOF-updates/s: one right-hand side
+    of each problem in `single` on one core, and `omp_steps` SSP-RK3 steps of each problem in
+    `omp` on every host core (the OpenMP build; bit-identical results).  `of` names the sample."""
+    import oracle
+    oracle.lib()  # built (or loaded) before any timing
+    units = secs = 0.0
+    for wl in single:
+        pb = oracle.Problem(**wl.problem_kwargs())
+        t0 = time.perf_counter()
+        oracle.rhs(pb, wl.w)
+        secs += time.perf_counter() - t0
+        units += 7 * wl.N
+    out = {"single_core": {"value": units / secs, "unit": UNIT, "cores": 1,
+                           "sample": f"one right-hand side of {of or 'each problem'} ({secs:.1f} s)"}}
+    try:
+        cores = oracle.lib(openmp=True).orc_threads(os.cpu_count() or 1)
+        units = secs = 0.0
+        for wl in omp:
+            pb = oracle.Problem(**wl.problem_kwargs())
+            t0 = time.perf_counter()
+            oracle.rk3(pb, wl.w, wl.dt, omp_steps, threads=cores)
+            secs += time.perf_counter() - t0
+            units += 7 * wl.N * 3 * omp_steps
+        out["openmp"] = {"value": units / secs, "unit": UNIT, "cores": cores,
+                         "sample": f"{omp_steps} SSP-RK3 step(s) of {len(omp)} problem(s) ({secs:.1f} s)"}
+    except Exception as exc:
+        out["openmp"] = {"unavailable": str(exc)[:200]}
+    out["kind"] = "oracle"
+    out["host"] = host_cpu()
+    return out
+
+
 def host_cpu():
     """The host CPU the oracle runs on: model name (lscpu, else the machine type) and core count."""
     model = None
@@ -410,15 +443,16 @@ def batched_block(dg, steps, nprob=256):
             "one_by_one_fp32bulk": {"value": units / (ms_32 * 1e-3), "ms_per_step": ms_32},
             "one_by_one_fp64": {"value": units / (ms_64 * 1e-3), "ms_per_step": ms_64},
             "speedup_vs_fp64": ms_64 / ms_b, "l2": "working set > L2 (no flush needed)",
-            "tiles": tiles}
+            "tiles": tiles, "cpu_oracle": oracle_sample(wls[:8], wls[:32], of="the first 8 problems")}
 
 
-def rt_block(dg, steps, n=256, paper=False):
+def rt_block(dg, steps, n=256, paper=False, cpu=False):
     """Viscous Rayleigh-Taylor set-up (256 x 256 quads, p = 4, walls, gravity, surface tension,
     seed 3): FP32-bulk and FP64 step times and the FP32-bulk error after the timed steps.
     The state (92 MB FP64, 1.64M nodes) and the workspace exceed L2 together; no flush.
     paper: the paper's domain [0, 1] x [0, 4] on n x 4n quads instead (slip sides, no-slip bottom,
-    the Riemann-invariant pressure top, no surface tension)."""
+    the Riemann-invariant pressure top, no surface tension).  cpu: also the oracle on a bounded
+    sample (one right-hand side on one core, one step on every core)."""
     import numpy as np
     import torch
     from paper_2306_05002_gb300 import workloads as W
@@ -454,6 +488,9 @@ def rt_block(dg, steps, n=256, paper=False):
     a, b = states["fp32bulk"], states["fp64"]
     out["l2_rel_alpha"] = float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0]))
     out["speedup_fp32bulk_vs_fp64"] = out["fp64"]["ms_per_step"] / out["fp32bulk"]["ms_per_step"]
+    if cpu:  # one core: the same set-up on 64 x 64 quads (same per-node work); all cores: the full grid
+        small = W.rayleigh_taylor(n=64, p=4, seed=3)
+        out["cpu_oracle"] = oracle_sample([small], [wl], of="the same set-up on 64x64 quads p=4")
     return out
 
 
@@ -751,7 +788,7 @@ def run_ours(args, rank, world, local_rank):
                if (args.batch_steps > 0 and rank == 0) else None)
     adjoint = (adjoint_block(dg, args.adjoint_steps, n=args.adjoint_n)
                if (args.adjoint_steps > 0 and rank == 0) else None)
-    rt = rt_block(dg, args.rt_steps) if (args.rt_steps > 0 and rank == 0) else None
+    rt = rt_block(dg, args.rt_steps, cpu=True) if (args.rt_steps > 0 and rank == 0) else None
     slab = slab_block(dg, args.slab_steps) if (args.slab_steps > 0 and rank == 0) else None
     kin = kinematic_block(dg, args.kin_steps) if (args.kin_steps > 0 and rank == 0) else None
     tri = triangle_block(dg, args.tri_steps, args.tri_n) if (args.tri_steps > 0 and rank == 0) else None
