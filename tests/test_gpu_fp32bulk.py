@@ -171,6 +171,10 @@ def test_fp32bulk_rayleigh_taylor_physics_tracks_fp64(orc, dg):
     (lambda: W.drop_2d(n=9, p=5, seed=7), 2),         # the 2-step remainder graph alone
     (lambda: W.rayleigh_taylor(n=8, p=4, seed=3), 9),  # walls, viscous, gravity, surface tension
     (lambda: W.slab_1d(nx=40, p=3), 5),
+    # grids of several waves: the plain-launch kernel variants (the cases above fit on the GPU at
+    # once and run as programmatic dependent launches)
+    (lambda: W.drop_2d(n=128, p=3, seed=2), 3),
+    (lambda: W.rayleigh_taylor(n=128, p=4, seed=3), 2),
 ])
 def test_fp32bulk_multi_step_call_matches_single_steps(dg, make, nsteps):
     """n steps in one call keep the FP32 state between steps and fuse the surface part of each
