@@ -30,6 +30,13 @@
  *     asynchronous on that stream unless stated otherwise.  Launch-time
  *     errors are returned; conditions the GPU detects (non-finite values)
  *     are latched in a device status word and reported by dg_status_read.
+ *     The FP32-bulk kernels of a grid that fits on the GPU at once run as
+ *     programmatic dependent launches and let the kernel after them on the
+ *     stream be scheduled early: a caller's kernel launched with
+ *     programmatic stream serialization must call
+ *     cudaGridDependencySynchronize() before it reads their results, as
+ *     CUDA requires of any such launch.  Ordinary launches, copies and
+ *     events on the stream are ordered as usual.
  *   - A context is not thread-safe.  No C++ exception crosses this boundary.
  *   - Failure returns a negative dg_status; dg_last_error gives a message.
  */
