@@ -112,6 +112,13 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout: float = 10.0):
+        """Wait for the first sample (the first nvidia-smi on a freshly started box takes a while to
+        start), so that the samples cover the timed region."""
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.05)
+
     def stop(self):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -345,16 +352,21 @@ def time_path(dg, wl, precision, steps, warmup, flush, stream, local_rank, sampl
     clocks = ClockSampler(local_rank) if sample_clocks else None
     if clocks:
         clocks.start()
+        clocks.wait_first()
         time.sleep(0.3)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for ev in starts + ends:  # create the events (lazily made at their first record) before timing
+        ev.record(stream)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
+    t_enq = time.perf_counter()
     for k in range(steps):
         flush.zero_()
         starts[k].record(stream)
         solver.dg_step(w, wl.dt, 1)
         ends[k].record(stream)
+    enqueue_s = time.perf_counter() - t_enq
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
@@ -363,7 +375,7 @@ def time_path(dg, wl, precision, steps, warmup, flush, stream, local_rank, sampl
     kms = solver.dg_time_kernels(w, nrep=20)
     flops, bytes_ = solver.dg_kernel_costs()
     return dict(solver=solver, w=w, ms=ms, wall=wall, clocks=clk, status=status, kms=kms, flops=flops,
-                bytes=bytes_)
+                bytes=bytes_, enqueue_s=enqueue_s)
 
 
 def accuracy(dg, wl, steps):
@@ -805,7 +817,8 @@ def run_ours(args, rank, world, local_rank):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
                 "data": "synthetic",
                 "config": config_of(wl, {"parallelism": f"replicas x{world}", "precision": args.precision,
-                                         "wall_s_timed_region": main["wall"]}),
+                                         "wall_s_timed_region": main["wall"],
+                                         "host_enqueue_s": main["enqueue_s"]}),
                 "gpu_launches": launches * args.steps,
                 "roofline": roof,
                 "e2e": {"value": units * e2e_steps * world / e2e_max, "unit": UNIT,
