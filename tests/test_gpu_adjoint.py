@@ -27,7 +27,7 @@ def _broken(wl, seed=3, amp=0.05):
     v = prim[2] - 0.2 + 0.05 * rng.uniform(-1, 1, wl.N)
     if wl.dim == 1:
         v = 0.0 * v  # the 1D state keeps rho v = 0
-    return W.conserved(wl, phi, psi, P, u, v)
+    return np.array(W.conserved(wl, phi, psi, P, u, v))  # a writable copy (torch.from_numpy shares it)
 
 
 @pytest.mark.parametrize("maker", [lambda: W.drop_2d(n=3, p=2, seed=2), lambda: W.drop_2d(n=2, p=3, seed=3),
