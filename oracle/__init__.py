@@ -14,6 +14,7 @@ limits of the stiffened-gas closure and convergence rates.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -31,20 +32,28 @@ BC = {"periodic": 0, "noslip": 1, "slip": 2, "pressure": 3}
 NV = 7
 
 
+CFLAGS = ["-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC", "-shared"]
+
+
+def compile_sources(sources, out: str, openmp: bool = False, include_dir: str | None = None) -> str:
+    """Compile C sources of the oracle into the shared library `out` (gcc, FP64, no FMA
+    contraction: every product and sum is rounded on its own, as written)."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc"] + CFLAGS + (["-fopenmp"] if openmp else []) + (["-I" + include_dir] if include_dir else [])
+    subprocess.check_call(cmd + ["-o", tmp] + list(sources) + ["-lm"])
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False, openmp: bool = False) -> str:
-    """Compile the oracle into ``oracle/liboracle.so`` (gcc, FP64, no FMA contraction), or, with
-    ``openmp``, the same source with its element loops parallel into ``oracle/liboracle_omp.so``
-    (used only to time the oracle on all host cores; the tests pin the plain build)."""
+    """Compile the oracle into ``oracle/liboracle.so``, or, with ``openmp``, the same source
+    with its element loops parallel into ``oracle/liboracle_omp.so`` (used only to time the
+    oracle on all host cores; the tests pin the plain build)."""
     out = _LIB_OMP if openmp else _LIB
     if force or not os.path.exists(out) or os.path.getmtime(out) < max(
         os.path.getmtime(_SRC), os.path.getmtime(_SRC_TRI), os.path.getmtime(os.path.join(_HERE, "dg_oracle.h"))
     ):
-        tmp = out + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC", "-shared"]
-            + (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, _SRC_TRI, "-lm"]
-        )
-        os.replace(tmp, out)
+        compile_sources([_SRC, _SRC_TRI], out, openmp=openmp)
     return out
 
 
@@ -140,40 +149,61 @@ class Velocity:
 _libs = {}
 
 
+def _configure(_lib):
+    """Declare the argument types of every exported oracle function on a loaded library."""
+    _lib.orc_threads.argtypes = [ctypes.c_int]
+    _lib.orc_threads.restype = ctypes.c_int
+    dp = ctypes.POINTER(ctypes.c_double)
+    pp = ctypes.POINTER(_Problem)
+    _lib.orc_gll.argtypes = [ctypes.c_int, dp, dp]
+    _lib.orc_lagrange_deriv.argtypes = [ctypes.c_int, dp, dp]
+    _lib.orc_num_nodes.argtypes = [pp]
+    _lib.orc_num_nodes.restype = ctypes.c_long
+    _lib.orc_nodes.argtypes = [pp, dp, dp]
+    _lib.orc_primitives.argtypes = [pp, dp, dp]
+    _lib.orc_rhs.argtypes = [pp, dp, dp, dp, dp]
+    _lib.orc_rk3.argtypes = [pp, dp, ctypes.c_double, ctypes.c_int]
+    _lib.orc_diag.argtypes = [pp, dp, dp]
+    vp = ctypes.POINTER(_Velocity)
+    _lib.orc_velocity_at.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
+    _lib.orc_velocity_at.restype = None
+    _lib.orc_kin_rhs.argtypes = [pp, vp, ctypes.c_double, dp, dp, dp]
+    _lib.orc_kin_rk4.argtypes = [pp, vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    _lib.orc_tri_num_nodes.argtypes = [pp]
+    _lib.orc_tri_num_nodes.restype = ctypes.c_long
+    _lib.orc_tri_nodes.argtypes = [pp, dp, dp]
+    _lib.orc_tri_integral.argtypes = [pp, dp, dp]
+    _lib.orc_tri_mass.argtypes = [pp, ctypes.c_int, dp]
+    _lib.orc_tri_rhs.argtypes = [pp, vp, ctypes.c_double, dp, dp, dp]
+    _lib.orc_tri_rk4.argtypes = [pp, vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    _lib.orc_reinit_sign.argtypes = [pp, dp, dp]
+    _lib.orc_reinit_rhs.argtypes = [pp, dp, dp, ctypes.c_double, dp]
+    _lib.orc_reinit.argtypes = [pp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    return _lib
+
+
 def lib(openmp: bool = False):
     """The plain oracle library, or (``openmp``) its OpenMP build."""
     _lib = _libs.get(openmp)
     if _lib is None:
-        _lib = _libs[openmp] = ctypes.CDLL(build(openmp=openmp))
-        _lib.orc_threads.argtypes = [ctypes.c_int]
-        _lib.orc_threads.restype = ctypes.c_int
-        dp = ctypes.POINTER(ctypes.c_double)
-        pp = ctypes.POINTER(_Problem)
-        _lib.orc_gll.argtypes = [ctypes.c_int, dp, dp]
-        _lib.orc_lagrange_deriv.argtypes = [ctypes.c_int, dp, dp]
-        _lib.orc_num_nodes.argtypes = [pp]
-        _lib.orc_num_nodes.restype = ctypes.c_long
-        _lib.orc_nodes.argtypes = [pp, dp, dp]
-        _lib.orc_primitives.argtypes = [pp, dp, dp]
-        _lib.orc_rhs.argtypes = [pp, dp, dp, dp, dp]
-        _lib.orc_rk3.argtypes = [pp, dp, ctypes.c_double, ctypes.c_int]
-        _lib.orc_diag.argtypes = [pp, dp, dp]
-        vp = ctypes.POINTER(_Velocity)
-        _lib.orc_velocity_at.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
-        _lib.orc_velocity_at.restype = None
-        _lib.orc_kin_rhs.argtypes = [pp, vp, ctypes.c_double, dp, dp, dp]
-        _lib.orc_kin_rk4.argtypes = [pp, vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
-        _lib.orc_tri_num_nodes.argtypes = [pp]
-        _lib.orc_tri_num_nodes.restype = ctypes.c_long
-        _lib.orc_tri_nodes.argtypes = [pp, dp, dp]
-        _lib.orc_tri_integral.argtypes = [pp, dp, dp]
-        _lib.orc_tri_mass.argtypes = [pp, ctypes.c_int, dp]
-        _lib.orc_tri_rhs.argtypes = [pp, vp, ctypes.c_double, dp, dp, dp]
-        _lib.orc_tri_rk4.argtypes = [pp, vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
-        _lib.orc_reinit_sign.argtypes = [pp, dp, dp]
-        _lib.orc_reinit_rhs.argtypes = [pp, dp, dp, ctypes.c_double, dp]
-        _lib.orc_reinit.argtypes = [pp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        _lib = _libs[openmp] = _configure(ctypes.CDLL(build(openmp=openmp)))
     return _lib
+
+
+@contextlib.contextmanager
+def using(path: str):
+    """Route every function of this module through the library at `path` (another build of
+    the oracle sources) for the duration of the block.  The mutation tests use it to run the
+    pins against copies of the oracle with a planted mistake."""
+    saved = _libs.get(False)
+    _libs[False] = _configure(ctypes.CDLL(path))
+    try:
+        yield
+    finally:
+        if saved is None:
+            _libs.pop(False, None)
+        else:
+            _libs[False] = saved
 
 
 def _ptr(a):
