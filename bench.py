@@ -45,6 +45,10 @@ def parse():
                     help="timed steps of the batched ensemble (0 skips the batched block)")
     ap.add_argument("--rt-steps", type=int, default=10,
                     help="timed steps of the 256 x 256, p = 4 Rayleigh-Taylor block (0 skips it)")
+    ap.add_argument("--rt-accuracy-steps", type=int, default=2000,
+                    help="steps of the Rayleigh-Taylor FP32-bulk vs FP64 accuracy run (the workload's 2000)")
+    ap.add_argument("--batch-accuracy-steps", type=int, default=200,
+                    help="steps of the batched accuracy run (the ensemble's 200; sampled problems vs FP64)")
     ap.add_argument("--batch-problems", type=int, default=256,
                     help="ensemble size of the batched block (smaller values for profiling)")
     ap.add_argument("--adjoint-n", type=int, default=128,
@@ -145,6 +149,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# Spin cycles of the gate kernel ahead of each timed step (~5 ms at 2 GHz).
+GATE_CYCLES = 10_000_000
+
+
 # --------------------------------------------------------------------------- roofline helpers
 
 KERNEL_SOURCES = {"fp64": ["paper_2306_05002_gb300/csrc/dg_kernels_fp64.cuh",
@@ -195,11 +203,20 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 BYTES_PER_NODE_STAGE = 168
 
 
+NAMES = {"fp64": ["k_volume", "k_surface"],
+         "fp32bulk": ["k_volume32", "k_surface32", "k_surfvol32", "k_volume32(fp64 state in)",
+                      "k_surface32(fp64 state out)"]}
+
+
 def roofline(precision, names, kms, flops, bytes_, nodes):
-    # the kernel taking most of a step: FP64 runs a volume and a surface kernel per stage;
-    # FP32-bulk runs one volume, two fused and one surface kernel per single-step call
-    per_step = [3, 3] if precision == "fp64" else [1, 1, 2]
-    dom = max(range(len(kms)), key=lambda i: kms[i] * per_step[i])
+    # FP64 runs a volume and a surface kernel per stage (the dominant one is the roofline kernel);
+    # a single-step FP32-bulk call runs the first-stage volume kernel (FP64 state in), two fused
+    # stage kernels and the last-stage surface kernel (FP64 state out): the roofline kernel is the
+    # fused one, which completes a whole stage per launch
+    per_step = [3, 3] if precision == "fp64" else [0, 0, 2, 1, 1]
+    n = min(len(kms), len(per_step), len(names))
+    names, kms, flops, bytes_ = names[:n], kms[:n], flops[:n], bytes_[:n]
+    dom = max(range(n), key=lambda i: kms[i] * per_step[i])
     if precision == "fp64":
         ach = flops[dom] / (kms[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": names[dom], "achieved": ach, "peak": FP64_PEAK_TFLOPS,
@@ -213,7 +230,7 @@ def roofline(precision, names, kms, flops, bytes_, nodes):
         roof = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "per_unit": f"{BYTES_PER_NODE_STAGE} B per node and stage x {nodes} nodes",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured"}
-    roof.update({"kernel_ms": dict(zip(names, kms)),
+    roof.update({"kernel_ms": dict(zip(names, kms)), "launches_per_step": dict(zip(names, per_step)),
                  "kernel_flops_per_launch": dict(zip(names, flops)),
                  "kernel_bytes_per_launch": dict(zip(names, bytes_))})
     return roof
@@ -362,6 +379,10 @@ def time_path(dg, wl, precision, steps, warmup, flush, stream, local_rank, sampl
     wall0 = time.perf_counter()
     t_enq = time.perf_counter()
     for k in range(steps):
+        # a spin kernel of GATE_CYCLES ahead of each step keeps the GPU busy while the host enqueues
+        # the flush, the events and the step, so the events measure the step's device time even
+        # when the host is slow to enqueue (the first seconds of a process on a fresh box)
+        torch.cuda._sleep(GATE_CYCLES)
         flush.zero_()
         starts[k].record(stream)
         solver.dg_step(w, wl.dt, 1)
@@ -378,35 +399,47 @@ def time_path(dg, wl, precision, steps, warmup, flush, stream, local_rank, sampl
                 bytes=bytes_, enqueue_s=enqueue_s)
 
 
+def primitives_host(wl, w):
+    """Pressure and velocity from an FP64 state on the host (stiffened gas, Sec. 2)."""
+    g1, g2 = wl.gamma
+    C1 = g1 * wl.pinf[0] / (g1 - 1.0)
+    C2 = g2 * wl.pinf[1] / (g2 - 1.0)
+    rho = w[2] + w[3]
+    rhoe = w[6] - 0.5 * (w[4] ** 2 + w[5] ** 2) / rho
+    P = (rhoe - (w[0] * C1 + (1 - w[0]) * C2)) / (w[0] / (g1 - 1.0) + (1 - w[0]) / (g2 - 1.0))
+    return P, w[4] / rho, w[5] / rho
+
+
+def l2_errors(wl, w32, w64):
+    """Relative L2 error of alpha (= phi), P and the velocity of an FP32-bulk state against the FP64
+    state of the same run (the FP64 path matches the FP64 oracle to 1e-12 per right-hand side)."""
+    import numpy as np
+    P32, u32, v32 = primitives_host(wl, w32)
+    P64, u64, v64 = primitives_host(wl, w64)
+    l2 = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    vel = float(np.sqrt(np.sum((u32 - u64) ** 2 + (v32 - v64) ** 2) / max(np.sum(u64 ** 2 + v64 ** 2), 1e-300)))
+    return {"l2_rel_alpha": l2(w32[0], w64[0]), "l2_rel_p": l2(P32, P64), "l2_rel_u": vel}
+
+
+def run_steps(dg, wl, precision, steps):
+    """The FP64 state after `steps` SSP-RK3 steps in one dg_step call."""
+    import torch
+    s = dg.Solver(wl, precision=precision)
+    d = torch.from_numpy(wl.w.copy()).cuda()
+    s.dg_step(d, wl.dt, steps)
+    out = d.cpu().numpy()
+    s.close()
+    return out
+
+
 def accuracy(dg, wl, steps):
     """Relative L2 error of phi, P, u of the FP32-bulk path against the FP64 path after `steps`."""
-    import numpy as np
-    import torch
-    out = {}
-    for prec in ("fp64", "fp32bulk"):
-        s = dg.Solver(wl, precision=prec)
-        d = torch.from_numpy(wl.w.copy()).cuda()
-        s.dg_step(d, wl.dt, steps)
-        out[prec] = d.cpu().numpy()
-        s.close()
-    # primitives on the host from the FP64 states (stiffened gas, Sec. 2)
-    def prim(w):
-        g1, g2 = wl.gamma
-        C1 = g1 * wl.pinf[0] / (g1 - 1.0)
-        C2 = g2 * wl.pinf[1] / (g2 - 1.0)
-        rho = w[2] + w[3]
-        rhoe = w[6] - 0.5 * (w[4] ** 2 + w[5] ** 2) / rho
-        P = (rhoe - (w[0] * C1 + (1 - w[0]) * C2)) / (w[0] / (g1 - 1.0) + (1 - w[0]) / (g2 - 1.0))
-        return P, w[4] / rho
-    P64, u64 = prim(out["fp64"])
-    P32, u32 = prim(out["fp32bulk"])
-    l2 = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
-    return {"steps": steps, "reference": "FP64 GPU path (matches the FP64 oracle to 1e-12 per RHS)",
-            "l2_rel_alpha": l2(out["fp32bulk"][0], out["fp64"][0]), "l2_rel_p": l2(P32, P64),
-            "l2_rel_u": l2(u32, u64)}
+    out = {"steps": steps, "reference": "FP64 GPU path (matches the FP64 oracle to 1e-12 per RHS)"}
+    out.update(l2_errors(wl, run_steps(dg, wl, "fp32bulk", steps), run_steps(dg, wl, "fp64", steps)))
+    return out
 
 
-def batched_block(dg, steps, nprob=256):
+def batched_block(dg, steps, nprob=256, acc_steps=200):
     """Batched ensemble of 256 independent drop/bubble problems (meshes 16^2..128^2, p in 2..5,
     seed 4): one batched FP32-bulk step vs the same problems stepped one by one (FP32-bulk and
     FP64).  The working set (several GB) is far larger than L2, so no flush is needed."""
@@ -448,6 +481,28 @@ def batched_block(dg, steps, nprob=256):
 
     ms_32 = one_by_one("fp32bulk", 2)
     ms_64 = one_by_one("fp64", 1)
+
+    # accuracy: the batch after acc_steps steps from the initial states, against single-problem FP64
+    # runs of a sample (the first and last problem of each order)
+    acc = None
+    if acc_steps > 0:
+        bs = dg.BatchSolver(wls)
+        fresh = [torch.from_numpy(wl.w.copy()).cuda() for wl in wls]
+        bs.dg_batch_step(fresh, dts, acc_steps)
+        torch.cuda.synchronize()
+        bs.close()
+        picks = []
+        for p in sorted({wl.p for wl in wls}):
+            idx = [k for k, wl in enumerate(wls) if wl.p == p]
+            picks += sorted({idx[0], idx[-1]})
+        per = []
+        for k in picks:
+            e = l2_errors(wls[k], fresh[k].cpu().numpy(), run_steps(dg, wls[k], "fp64", acc_steps))
+            per.append(dict(problem=wls[k].name, **e))
+        acc = {"steps": acc_steps, "sample": "first and last problem of each order", "problems": per}
+        for key in ("l2_rel_alpha", "l2_rel_p", "l2_rel_u"):
+            acc["max_" + key] = max(e[key] for e in per)
+        del fresh
     return {"workload": f"{nprob} independent 2D periodic drop/bubble problems, N x N quads with N ~ U{{16..128}}, "
                         "p ~ U{2,3,4,5}, R ~ U[0.05,0.2], seeded centres (seed 4), u=(1,0.5), eps=0.75h, own dt",
             "problems": len(wls), "nodes": nodes, "steps": steps,
@@ -455,17 +510,18 @@ def batched_block(dg, steps, nprob=256):
             "one_by_one_fp32bulk": {"value": units / (ms_32 * 1e-3), "ms_per_step": ms_32},
             "one_by_one_fp64": {"value": units / (ms_64 * 1e-3), "ms_per_step": ms_64},
             "speedup_vs_fp64": ms_64 / ms_b, "l2": "working set > L2 (no flush needed)",
-            "tiles": tiles, "cpu_oracle": oracle_sample(wls[:32], wls, of="the first 32 problems")}
+            "tiles": tiles, "accuracy": acc,
+            "cpu_oracle": oracle_sample(wls[:32], wls, of="the first 32 problems")}
 
 
-def rt_block(dg, steps, n=256, paper=False, cpu=False):
+def rt_block(dg, steps, n=256, paper=False, cpu=False, acc_steps=0):
     """Viscous Rayleigh-Taylor set-up (256 x 256 quads, p = 4, walls, gravity, surface tension,
     seed 3): FP32-bulk and FP64 step times and the FP32-bulk error after the timed steps.
     The state (92 MB FP64, 1.64M nodes) and the workspace exceed L2 together; no flush.
     paper: the paper's domain [0, 1] x [0, 4] on n x 4n quads instead (slip sides, no-slip bottom,
     the Riemann-invariant pressure top, no surface tension).  cpu: also the oracle on a bounded
-    sample (one right-hand side on one core, one step on every core)."""
-    import numpy as np
+    sample (one right-hand side on one core, one step on every core).  acc_steps > 0: also the
+    FP32-bulk errors (alpha, P, u) against FP64 after that many steps from the initial state."""
     import torch
     from paper_2306_05002_gb300 import workloads as W
     if paper:
@@ -492,13 +548,16 @@ def rt_block(dg, steps, n=256, paper=False, cpu=False):
         ms = e0.elapsed_time(e1) / steps
         out[prec] = {"ms_per_step": ms, "value": 21 * wl.N / (ms * 1e-3), "unit": UNIT,
                      "device_status": s.dg_status_read()}
-        names = ["k_volume", "k_surface"] if prec == "fp64" else ["k_volume32", "k_surface32", "k_surfvol32"]
+        names = NAMES[prec]
         f, b = s.dg_kernel_costs()
         out[prec]["roofline"] = roofline(prec, names, s.dg_time_kernels(w, nrep=10), f, b, wl.N)
         states[prec] = w.cpu().numpy()
         s.close()
-    a, b = states["fp32bulk"], states["fp64"]
-    out["l2_rel_alpha"] = float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0]))
+    out["accuracy_after_timed_steps"] = l2_errors(wl, states["fp32bulk"], states["fp64"])
+    if acc_steps > 0:
+        acc = {"steps": acc_steps}
+        acc.update(l2_errors(wl, run_steps(dg, wl, "fp32bulk", acc_steps), run_steps(dg, wl, "fp64", acc_steps)))
+        out["accuracy"] = acc
     out["speedup_fp32bulk_vs_fp64"] = out["fp64"]["ms_per_step"] / out["fp32bulk"]["ms_per_step"]
     if cpu:
         out["cpu_oracle"] = oracle_sample([wl], [wl], of="the full grid")
@@ -607,10 +666,9 @@ def kinematic_block(dg, steps, n=64):
 
 def slab_block(dg, steps):
     """The 1D periodic water slab in air (100 elements, p = 3, eps = h, u = 1): `steps` SSP-RK3 steps
-    in one dg_step call (CUDA graphs of 8 steps), FP64 (the configuration's precision) and, for
-    information, FP32-bulk with its relative L2 error in alpha against FP64 after them.  Far too
-    small for a roofline (400 nodes): the step latency is the number to read."""
-    import numpy as np
+    in one dg_step call (CUDA graphs of 8 steps), FP64 (the configuration's precision) and
+    FP32-bulk with its relative L2 errors (alpha, P, u) against FP64 after them.  Far too small for
+    a roofline (400 nodes): the step latency is the number to read."""
     import torch
     from paper_2306_05002_gb300 import workloads as W
     wl = W.slab_1d(nx=100, p=3)
@@ -633,8 +691,7 @@ def slab_block(dg, steps):
                      "device_status": s.dg_status_read()}
         states[prec] = w.cpu().numpy()
         s.close()
-    a, b = states["fp32bulk"], states["fp64"]
-    out["l2_rel_alpha"] = float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0]))
+    out["accuracy"] = l2_errors(wl, states["fp32bulk"], states["fp64"])
     return out
 
 
@@ -775,7 +832,7 @@ def run_ours(args, rank, world, local_rank):
     ref = time_path(dg, wl, other, args.steps, args.warmup, flush, stream, local_rank, False) if other else None
 
     # roofline of the dominant kernel of the timed path
-    names = ["k_volume", "k_surface"] if args.precision == "fp64" else ["k_volume32", "k_surface32", "k_surfvol32"]
+    names = NAMES[args.precision]
     kms, flops, bytes_ = main["kms"], main["flops"], main["bytes"]
     roof = roofline(args.precision, names, kms, flops, bytes_, wl.N)
     roof["traffic"] = profiled_traffic(roof["kernel"], wl.name, args.precision)
@@ -795,11 +852,12 @@ def run_ours(args, rank, world, local_rank):
 
     acc = (accuracy(dg, wl, args.accuracy_steps)
            if (args.precision == "fp32bulk" and args.accuracy_steps > 0 and rank == 0) else None)
-    batched = (batched_block(dg, args.batch_steps, args.batch_problems)
+    batched = (batched_block(dg, args.batch_steps, args.batch_problems, args.batch_accuracy_steps)
                if (args.batch_steps > 0 and rank == 0) else None)
     adjoint = (adjoint_block(dg, args.adjoint_steps, n=args.adjoint_n)
                if (args.adjoint_steps > 0 and rank == 0) else None)
-    rt = rt_block(dg, args.rt_steps, cpu=True) if (args.rt_steps > 0 and rank == 0) else None
+    rt = (rt_block(dg, args.rt_steps, cpu=True, acc_steps=args.rt_accuracy_steps)
+          if (args.rt_steps > 0 and rank == 0) else None)
     slab = slab_block(dg, args.slab_steps) if (args.slab_steps > 0 and rank == 0) else None
     kin = kinematic_block(dg, args.kin_steps) if (args.kin_steps > 0 and rank == 0) else None
     tri = triangle_block(dg, args.tri_steps, args.tri_n) if (args.tri_steps > 0 and rank == 0) else None

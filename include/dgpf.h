@@ -104,7 +104,10 @@ typedef struct {
 /* Options.  prec: DG_FP64 or DG_FP32_BULK.  c_ip: interior-penalty constant,
    eta = c_ip (p+1)^2 / h (<= 0 selects 1).  viscous, gravity,
    surface_tension: enable those terms of Sec. 2.  check_finite: latch
-   DG_ERR_NONFINITE when an output is not finite.  batch_tile (batches
+   DG_ERR_NONFINITE when an output is not finite, and DG_ERR_NONPHYSICAL when
+   a state the kernels read has rho <= 0, a mixture 1/(gamma - 1) <= 0 or
+   P + Pinf_mix <= 0 (the stiffened-gas closure of Sec. 2 has no real sound
+   speed there).  The state is never clipped.  batch_tile (batches
    only): 0 lets the first dg_batch_step tune the tile of every order; 1..4
    fixes tile variant batch_tile - 1 for all orders (see dg_batch_step);
    other values are DG_ERR_ARG. */
@@ -165,7 +168,9 @@ dg_status dg_step_host(dg_ctx *ctx, double *w_host, double dt, int nsteps, void 
 dg_status dg_diag(dg_ctx *ctx, const double *w, double *out, void *stream);
 
 /* Read and clear the device status word (synchronises the stream): DG_OK,
-   DG_ERR_NONFINITE or DG_ERR_NONPHYSICAL. */
+   DG_ERR_NONPHYSICAL (reported first when both were latched: a non-physical
+   state is what makes the values non-finite) or DG_ERR_NONFINITE.  Batch
+   contexts latch nothing and return DG_OK. */
 dg_status dg_status_read(dg_ctx *ctx, void *stream);
 
 /* Message of the last failure on this context (or of the last failed
@@ -177,13 +182,17 @@ const char *dg_last_error(const dg_ctx *ctx);
    the mean duration per launch in milliseconds to ms_out
    (index 0 volume kernel, 1 surface kernel, and for FP32-bulk contexts 2 the
    fused kernel that dg_step runs: the surface part of one stage followed by
-   the volume part of the next); returns the number of kinds written
-   (<= nmax).  Synchronises the stream. */
+   the volume part of the next, 3 the volume kernel of a call's first stage,
+   which reads the FP64 state, and 4 the surface kernel of a call's last
+   stage, which writes it -- into a temporary FP64 array that this call
+   allocates and frees); returns the number of kinds written (<= nmax), or
+   -1.  w is not modified.  Synchronises the stream. */
 int dg_time_kernels(dg_ctx *ctx, const double *w, int nrep, double *ms_out, int nmax, void *stream);
 
 /* Algorithmic FP64-equivalent flop and DRAM byte counts per launch of each
    kernel kind (same indexing as dg_time_kernels), from the formulas of the
-   scheme (not from counters). */
+   scheme (not from counters); returns the number of kinds written (<= nmax),
+   or -1. */
 int dg_kernel_costs(const dg_ctx *ctx, double *flops_out, double *bytes_out, int nmax);
 
 /* Discrete adjoint of the right-hand side: out = (dL/dw)^T lam at the state
@@ -350,15 +359,18 @@ dg_status dg_reinit(dg_ctx *ctx, double *w, int niter, double nu, double dtau, v
    file-scope device array of DG_NOALLOC_SCRATCH_BYTES that every GPU loading
    this library holds until the process exits; a problem whose scratch would
    not fit (about 190,000 nodes at p = 3 in 2D, e.g. 64 x 64 elements fits)
-   is rejected with DG_ERR_ARG before any GPU work.  Other invalid arguments
-   give DG_ERR_ARG / DG_ERR_UNSUPPORTED (opts->prec must be DG_FP64, mesh->elem
-   DG_ELEM_QUAD; the device status word is not reported).
+   is rejected with DG_ERR_ARG before any GPU work.  Every other argument is
+   checked as dg_create checks it, with the same status codes (every boundary
+   kind, viscous, gravity and surface-tension terms are supported); opts->prec
+   DG_FP32_BULK gives DG_ERR_UNSUPPORTED; the device status word is not
+   reported.
    The first call on a device looks up the array's device address on that
    device (it loads the library's module there); make that first call before
    any stream capture.  Every call uses the same array and leaves its contents
-   behind; the call clears what must start at zero itself.  Calls whose work
-   overlaps on the GPU (other streams, other host threads) race on the
-   scratch: serialise them.  Asynchronous on stream. */
+   behind; the call writes its operator table and clears what must start at
+   zero itself.  Calls whose work overlaps on the GPU (other streams, other
+   host threads) race on the scratch: serialise them.  Asynchronous on
+   stream. */
 dg_status dg_rhs_noalloc(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps,
                          const dg_opts *opts, const double *w, double *L, void *stream);
 

@@ -23,6 +23,7 @@
 #include "dg_kin.cuh"
 #include "dg_reinit.cuh"
 #include "dg_tri.cuh"
+#include "dg_host.h"
 #include "dgpf.h"
 
 namespace dgpf {
@@ -63,30 +64,6 @@ bool kernels_fp32(int p, int dim, bool viscous, bool st, KernelSet32 *out) {
     case 4: return kernels_fp32_p4(dim, viscous, st, out);
     case 5: return kernels_fp32_p5(dim, viscous, st, out);
     default: return false;
-  }
-}
-
-// FP64 <-> FP32-bulk internal state (see dg_kernels_fp32.cuh).  The FP64 state is field-major
-// ([7][N]); the FP32 internal state one record of SW32 floats per node (aos: the inviscid kernels)
-// or field-major (the viscous kernels).
-__global__ void k_to32(int N, double C2, double dC, int aos, const double *__restrict__ w, float *__restrict__ w32) {
-  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
-    const double phi = w[n];
-    auto at = [&](int v) -> float & { return aos ? w32[n * SW32 + v] : w32[(long)v * N + n]; };
-#pragma unroll
-    for (int v = 0; v < RE; ++v) at(v) = (float)w[(long)v * N + n];
-    at(RE) = (float)(w[(long)RE * N + n] - fma(dC, phi, C2));
-    if (aos) w32[n * SW32 + NV] = 0.f;
-  }
-}
-
-__global__ void k_to64(int N, double C2, double dC, int aos, const float *__restrict__ w32, double *__restrict__ w) {
-  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
-    auto at = [&](int v) { return aos ? w32[n * SW32 + v] : w32[(long)v * N + n]; };
-    const double phi = (double)at(PHI);
-#pragma unroll
-    for (int v = 0; v < RE; ++v) w[(long)v * N + n] = (double)at(v);
-    w[(long)RE * N + n] = (double)at(RE) + fma(dC, phi, C2);
   }
 }
 
@@ -196,65 +173,11 @@ using namespace dgpf;
 // ---------------------------------------------------------------------------
 namespace {
 
-// GLL nodes by Newton's method on (1 - x^2) P_p'(x), written with the
-// identity (1 - x^2) P_p' = p (P_{p-1} - x P_p) and the Newton step
-// x <- x - (x P_p - P_{p-1}) / ((p+1) P_p); weights 2 / (p (p+1) P_p(x)^2).
+// Vector forms of the shared table builders (dg_host.h).
 void gll_nodes(int p, std::vector<double> &x, std::vector<double> &w) {
   x.assign(p + 1, 0.0);
   w.assign(p + 1, 0.0);
-  for (int i = 0; i <= p; ++i) x[i] = -std::cos(M_PI * i / p);
-  auto legendre = [p](double t, double *Pp, double *Pm) {
-    double a = 1.0, b = t;  // P_0, P_1
-    for (int k = 2; k <= p; ++k) {
-      const double c = ((2.0 * k - 1.0) * t * b - (k - 1.0) * a) / k;
-      a = b;
-      b = c;
-    }
-    *Pp = b;
-    *Pm = a;
-  };
-  for (int it = 0; it < 200; ++it) {
-    double moved = 0.0;
-    for (int i = 1; i < p; ++i) {
-      double Pp, Pm;
-      legendre(x[i], &Pp, &Pm);
-      const double dx = (x[i] * Pp - Pm) / ((p + 1.0) * Pp);
-      x[i] -= dx;
-      moved = std::max(moved, std::fabs(dx));
-    }
-    if (moved < 1e-16) break;
-  }
-  for (int i = 0; i <= p / 2; ++i) {  // exact symmetry about 0
-    const double s = 0.5 * (x[p - i] - x[i]);
-    x[i] = -s;
-    x[p - i] = s;
-  }
-  if (p % 2 == 0) x[p / 2] = 0.0;
-  for (int i = 0; i <= p; ++i) {
-    double Pp, Pm;
-    if (i == 0 || i == p) Pp = 1.0;
-    else legendre(x[i], &Pp, &Pm);
-    w[i] = 2.0 / (p * (p + 1.0) * Pp * Pp);
-  }
-}
-
-// Lagrange derivative matrix D[a][b] = l_b'(x_a) from barycentric weights.
-std::vector<double> lagrange_derivative(const std::vector<double> &x) {
-  const int n = (int)x.size();
-  std::vector<double> lam(n, 1.0), D(n * n, 0.0);
-  for (int j = 0; j < n; ++j)
-    for (int k = 0; k < n; ++k)
-      if (k != j) lam[j] /= (x[j] - x[k]);
-  for (int a = 0; a < n; ++a) {
-    double diag = 0.0;
-    for (int b = 0; b < n; ++b) {
-      if (b == a) continue;
-      D[a * n + b] = (lam[b] / lam[a]) / (x[a] - x[b]);
-      diag -= D[a * n + b];
-    }
-    D[a * n + a] = diag;
-  }
-  return D;
+  gll_nodes_into(p, x.data(), w.data());
 }
 
 thread_local std::string g_create_error = "no error";
@@ -303,9 +226,10 @@ struct dg_ctx {
   AdjKernels adj{};
   bool has_adj = false;
   double *d_trbar = nullptr, *d_lam1 = nullptr, *d_lam2 = nullptr;
-  float *d_opsf = nullptr, *d_ws32 = nullptr, *d_w1_32 = nullptr, *d_w2_32 = nullptr, *d_rvol32 = nullptr,
+  // FP32-bulk: step start (hi and lo parts, double-buffered) and the two inner stage increments
+  float *d_hi32[2] = {}, *d_lo32[2] = {}, *d_dd32[2] = {};
+  float *d_opsf = nullptr, *d_rvol32 = nullptr,
         *d_trace32 = nullptr, *d_rvol32b = nullptr, *d_trace32b = nullptr;
-  int conv_blocks = 1;
   double *d_ops = nullptr, *d_w1 = nullptr, *d_w2 = nullptr, *d_rvol = nullptr, *d_trace = nullptr;
   double *d_hstate = nullptr;  // device copy of a host state (dg_step_host), allocated on first use
   // kinematic mode (dg_kin_create); tri: triangles (one fused kernel per stage)
@@ -382,9 +306,11 @@ static void free_ctx(dg_ctx *c) {
   cudaFree(c->d_lam1);
   cudaFree(c->d_lam2);
   cudaFree(c->d_opsf);
-  cudaFree(c->d_ws32);
-  cudaFree(c->d_w1_32);
-  cudaFree(c->d_w2_32);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(c->d_hi32[k]);
+    cudaFree(c->d_lo32[k]);
+    cudaFree(c->d_dd32[k]);
+  }
   cudaFree(c->d_rvol32);
   cudaFree(c->d_trace32);
   cudaFree(c->d_rvol32b);
@@ -393,113 +319,12 @@ static void free_ctx(dg_ctx *c) {
   delete c;
 }
 
-// Validation shared by dg_create and dg_batch_create: NULL when valid.
-static const char *check_problem(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps,
-                                 dg_status *code) {
-  *code = DG_ERR_ARG;
-  if (!mesh || !eos) return "mesh and eos are required";
-  if (mesh->dim != 1 && mesh->dim != 2) return "dim must be 1 or 2";
-  if (mesh->elem != DG_ELEM_QUAD) {
-    *code = mesh->elem == DG_ELEM_TRI ? DG_ERR_UNSUPPORTED : DG_ERR_ARG;
-    return "the two-phase flow model runs on rectangular elements only (elem = DG_ELEM_QUAD)";
-  }
-  if (p < 1 || p > 5) {
-    *code = DG_ERR_UNSUPPORTED;
-    return "order p must be in 1..5";
-  }
-  if (mesh->nx < 1 || mesh->ny < 1 || (mesh->dim == 1 && mesh->ny != 1)) return "bad element counts (1D needs ny = 1)";
-  if (!(mesh->x1 > mesh->x0) || (mesh->dim == 2 && !(mesh->y1 > mesh->y0))) return "empty domain";
-  for (int f = 0; f < 4; ++f)
-    if (mesh->bc[f] < DG_BC_PERIODIC || mesh->bc[f] > DG_BC_PRESSURE) return "unknown boundary condition";
-  for (int f = 0; f < 4; ++f)
-    if (mesh->bc[f] == DG_BC_PRESSURE && !std::isfinite(mesh->p_bc[f])) return "pressure boundary needs a finite p_bc";
-  if ((mesh->bc[0] == DG_BC_PERIODIC) != (mesh->bc[1] == DG_BC_PERIODIC) ||
-      (mesh->dim == 2 && (mesh->bc[2] == DG_BC_PERIODIC) != (mesh->bc[3] == DG_BC_PERIODIC)))
-    return "periodic sides must be paired";
-  for (int l = 0; l < 2; ++l)
-    if (!(eos->gamma[l] > 1.0) || !(eos->rho0[l] > 0.0) || eos->mu[l] < 0.0) return "need gamma > 1, rho0 > 0, mu >= 0";
-  if (!(Gamma >= 0.0) || !(eps >= 0.0)) return "need Gamma, eps >= 0";
-  const long long Np = mesh->dim == 2 ? (long long)(p + 1) * (p + 1) : p + 1;
-  if ((long long)mesh->nx * mesh->ny * Np * 7 >= (1LL << 31)) return "problem too large for one context";
-  *code = DG_OK;
-  return nullptr;
-}
-
 // Operator table (OpsLayout) for one element size.
 static std::vector<double> build_ops(int dim, int p, double hx, double hy) {
-  const int P1 = p + 1, Np = dim == 2 ? P1 * P1 : P1;
-  const double J = dim == 2 ? 0.25 * hx * hy : 0.5 * hx;
-  std::vector<double> xi, wt;
-  gll_nodes(p, xi, wt);
-  const std::vector<double> D = lagrange_derivative(xi);
-  const OpsLayout L{P1, Np};
-  std::vector<double> ops(L.size(), 0.0);
-  const double rx = 2.0 / hx, ry = 2.0 / hy;
-  for (int a = 0; a < P1; ++a)
-    for (int b = 0; b < P1; ++b) {
-      ops[L.Dx() + a * P1 + b] = rx * D[a * P1 + b];
-      ops[L.Dy() + a * P1 + b] = ry * D[a * P1 + b];
-      const double dh = wt[b] * D[b * P1 + a] / wt[a];
-      ops[L.Dhx() + a * P1 + b] = rx * dh;
-      ops[L.Dhy() + a * P1 + b] = ry * dh;
-    }
-  for (int a = 0; a < P1; ++a) ops[L.wt() + a] = wt[a];
-  for (int a = 0; a < Np; ++a) {
-    const double wa = dim == 2 ? wt[a % P1] * wt[a / P1] : wt[a];
-    ops[L.invM() + a] = 1.0 / (wa * J);
-  }
-  for (int k = 0; k < P1; ++k) {
-    ops[L.wfx() + k] = dim == 2 ? wt[k] * 0.5 * hy : 1.0;
-    ops[L.wfy() + k] = dim == 2 ? wt[k] * 0.5 * hx : 1.0;
-  }
+  const int P1 = p + 1;
+  std::vector<double> ops(OpsLayout{P1, dim == 2 ? P1 * P1 : P1}.size(), 0.0);
+  build_ops_into(dim, p, hx, hy, ops.data());
   return ops;
-}
-
-// Kernel parameters of one problem.  The closure constants are computed with
-// the same expressions as the stiffened-gas formula of Sec. 2 so that the
-// pressure is reproducible.
-static Params make_params(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps, const dg_opts &o,
-                          double hx, double hy) {
-  const int P1 = p + 1, Np = mesh->dim == 2 ? P1 * P1 : P1;
-  Params q{};
-  q.nx = mesh->nx;
-  q.ny = mesh->ny;
-  q.E = mesh->nx * mesh->ny;
-  q.N = q.E * Np;
-  for (int f = 0; f < 4; ++f) {
-    q.bc[f] = mesh->bc[f];
-    q.p_bc[f] = mesh->bc[f] == DG_BC_PRESSURE ? mesh->p_bc[f] : 0.0;
-  }
-  q.C1 = eos->gamma[0] * eos->pinf[0] / (eos->gamma[0] - 1.0);
-  q.C2 = eos->gamma[1] * eos->pinf[1] / (eos->gamma[1] - 1.0);
-  q.g1 = 1.0 / (eos->gamma[0] - 1.0);
-  q.g2 = 1.0 / (eos->gamma[1] - 1.0);
-  q.Bp = eos->gamma[0] / (eos->gamma[0] - 1.0) - eos->gamma[1] / (eos->gamma[1] - 1.0);
-  q.dC = q.C1 - q.C2;
-  q.rho01 = eos->rho0[0];
-  q.rho02 = eos->rho0[1];
-  q.drho0 = eos->rho0[0] - eos->rho0[1];
-  q.mu1 = eos->mu[0];
-  q.mu2 = eos->mu[1];
-  q.sigma = eos->sigma;
-  q.gx = eos->g[0];
-  q.gy = eos->g[1];
-  q.Gamma = Gamma;
-  q.eps = eps;
-  q.eta_x = o.c_ip * P1 * P1 / hx;
-  q.eta_y = o.c_ip * P1 * P1 / hy;
-  q.gravity = o.gravity != 0;
-  q.check_finite = o.check_finite != 0;
-  return q;
-}
-
-static dg_opts normalised_opts(const dg_opts *opts) {
-  dg_opts o{};
-  o.prec = DG_FP64;
-  o.c_ip = 1.0;
-  if (opts) o = *opts;
-  if (o.c_ip <= 0.0) o.c_ip = 1.0;
-  return o;
 }
 
 extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps,
@@ -556,7 +381,6 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
   const size_t sbytes = c->len * sizeof(double);
   const size_t tbytes = (size_t)c->ks.nt * c->E * c->NFK * sizeof(double);
   c->nparts = std::min(1024, (c->N + DIAG_THREADS - 1) / DIAG_THREADS);
-  c->conv_blocks = std::max(1, std::min(152 * 8, (c->N + 255) / 256));
   c->pf = to_float(c->prm);
   std::vector<float> opsf(ops.begin(), ops.end());
   auto alloc32 = [&](float **ptr, size_t n) {
@@ -566,8 +390,9 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
   if (!f64) {
     const size_t n32 = (size_t)SW32 * c->N;  // one padded record per node (inviscid kernels)
     const size_t t32 = (size_t)TRW32 * c->E * c->NFK;  // one padded record per face node
-    alloc32(&c->d_opsf, opsf.size()) && alloc32(&c->d_ws32, n32) && alloc32(&c->d_w1_32, n32) &&
-        alloc32(&c->d_w2_32, n32) && alloc32(&c->d_rvol32, n32) && alloc32(&c->d_trace32, t32) &&
+    alloc32(&c->d_opsf, opsf.size()) && alloc32(&c->d_hi32[0], n32) && alloc32(&c->d_hi32[1], n32) &&
+        alloc32(&c->d_lo32[0], n32) && alloc32(&c->d_lo32[1], n32) && alloc32(&c->d_dd32[0], n32) &&
+        alloc32(&c->d_dd32[1], n32) && alloc32(&c->d_rvol32, n32) && alloc32(&c->d_trace32, t32) &&
         alloc32(&c->d_rvol32b, n32) && alloc32(&c->d_trace32b, t32);
   }
   if (e != cudaSuccess || (e = cudaMalloc(&c->d_ops, ops.size() * sizeof(double))) != cudaSuccess ||
@@ -619,24 +444,17 @@ static dg_status run_stage(dg_ctx *c, int mode, double dt, const double *w0, con
   return DG_OK;
 }
 
-// One FP32-bulk stage.  in64 (optional): read the FP64 state in the volume
-// kernel and write the FP32 internal state to c->d_ws32 on the way.
-static dg_status run_stage32(dg_ctx *c, int mode, float dt, const float *w0, const float *ws, float *out32,
-                             double *out64, cudaStream_t s, const double *in64 = nullptr) {
-  cudaError_t e = c->ks32.volume(c->prm, c->pf, c->d_opsf, ws, c->d_rvol32, c->d_trace32, in64,
-                                 in64 ? c->d_ws32 : nullptr, s);
+// The FP32-bulk right-hand side of the FP64 state w64: the volume kernel splits
+// the state into the internal hi part (the lo part is not needed) and the
+// surface kernel writes L in FP64.
+static dg_status rhs32(dg_ctx *c, const double *w64, double *L, cudaStream_t s) {
+  cudaError_t e = c->ks32.volume(c->prm, c->pf, c->d_opsf, nullptr, c->d_rvol32, c->d_trace32, w64, c->d_hi32[0],
+                                 nullptr, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "volume kernel launch");
-  e = c->ks32.surface(c->prm, c->pf, c->d_opsf, mode, dt, w0, ws, c->d_rvol32, c->d_trace32, out32, out64, s);
+  const StageIO io{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, L, nullptr};
+  e = c->ks32.surface(c->prm, c->pf, c->d_opsf, MODE_RHS, 0.f, io, c->d_rvol32, c->d_trace32, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "surface kernel launch");
   return DG_OK;
-}
-
-static dg_status convert(dg_ctx *c, bool to32, double *w, cudaStream_t s) {
-  const int aos = !c->opts.viscous;  // the node-record layout of the inviscid FP32 kernels
-  if (to32) k_to32<<<c->conv_blocks, 256, 0, s>>>(c->N, c->prm.C2, c->prm.dC, aos, w, c->d_ws32);
-  else k_to64<<<c->conv_blocks, 256, 0, s>>>(c->N, c->prm.C2, c->prm.dC, aos, c->d_ws32, w);
-  const cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "state conversion launch");
 }
 
 extern "C" dg_status dg_rhs(dg_ctx *c, const double *w, double *L, void *stream) {
@@ -646,7 +464,7 @@ extern "C" dg_status dg_rhs(dg_ctx *c, const double *w, double *L, void *stream)
   if (w == L) return fail(c, DG_ERR_ARG, "dg_rhs: w and L must not overlap");
   cudaStream_t s = (cudaStream_t)stream;
   if (c->prec == DG_FP64) return run_stage(c, MODE_RHS, 0.0, w, w, L, s);
-  return run_stage32(c, MODE_RHS, 0.f, c->d_ws32, c->d_ws32, nullptr, L, s, w);
+  return rhs32(c, w, L, s);
 }
 
 // One SSP-RK3 step (Shu-Osher): w1 = w + dt L(w); w2 = 3/4 w + 1/4 (w1 + dt L(w1));
@@ -660,36 +478,43 @@ static dg_status enqueue_step(dg_ctx *c, double *w, double dt, cudaStream_t s) {
 }
 
 // `steps` FP32-bulk steps with the fused stage kernel: 1 + 3 steps launches.
-// The volume part of the first stage reads the FP64 state; the last stage
-// writes it back.  In between the state stays in FP32: converting it to FP64
-// and back at a step boundary returns the same FP32 values (the FP64 sum
-// rhoEt + Cmix(phi) is exact to far below half an FP32 unit of rhoEt), so
-// this is the same computation as `steps` separate calls of one step.
-// Buffers rotate so that no launch writes an array it also reads: the step
-// start alternates between A and B, the second stage is always in C, and the
-// volume part and traces alternate between the two buffers of each pair.
+// The volume part of the first stage reads the FP64 state and splits it into
+// the internal step start (hi, lo); the last stage writes hi + lo back.  In
+// between the state stays in FP32 pairs: splitting hi + lo again at a step
+// boundary returns the same pair, so this is the same computation as `steps`
+// separate calls of one step (up to the FP64 rounding of rho E + Cmix(phi)).
+// Stage 1 writes the increment d1 into D[0], stage 2 reads it and writes d2
+// into D[1], stage 3 adds 2 (d2 + dt L) / 3 to the step start in float-float
+// and writes the new step start into the other buffer of each pair (H, Lo),
+// so that no launch writes an array it also reads; the volume part and the
+// traces alternate between the two buffers of their pairs.
 static dg_status enqueue_steps32(dg_ctx *c, double *w, float dt, int steps, cudaStream_t s) {
-  float *A = c->d_ws32, *B = c->d_w1_32, *C = c->d_w2_32;
+  float *const *H = c->d_hi32, *const *Lo = c->d_lo32, *const *D = c->d_dd32;
   float *rv[2] = {c->d_rvol32, c->d_rvol32b}, *tr[2] = {c->d_trace32, c->d_trace32b};
-  int t = 0;
-  cudaError_t e = c->ks32.volume(c->prm, c->pf, c->d_opsf, A, rv[t], tr[t], w, A, s);
+  int t = 0, a = 0;
+  // a single step adds its last increment to the FP64 state itself: no lo part is needed
+  cudaError_t e = c->ks32.volume(c->prm, c->pf, c->d_opsf, nullptr, rv[t], tr[t], w, H[a], steps > 1 ? Lo[a] : nullptr,
+                                 s);
   if (e != cudaSuccess) return cuda_fail(c, e, "volume kernel launch");
   for (int k = 0; k < steps; ++k) {
+    const bool last = k == steps - 1;
+    const StageIO io[3] = {
+        {H[a], nullptr, nullptr, D[0], nullptr, nullptr, nullptr, nullptr},
+        {H[a], nullptr, D[0], D[1], nullptr, nullptr, nullptr, nullptr},
+        {H[a], Lo[a], D[1], nullptr, last ? nullptr : H[a ^ 1], last ? nullptr : Lo[a ^ 1], last ? w : nullptr,
+         steps == 1 ? w : nullptr}};
     const int mode[3] = {MODE_S1, MODE_S2, MODE_S3};
-    const float *ws[3] = {A, B, C};
-    float *out[3] = {B, C, B};
     for (int st = 0; st < 3; ++st) {
-      if (st == 2 && k == steps - 1) {
-        e = c->ks32.surface(c->prm, c->pf, c->d_opsf, MODE_S3, dt, A, C, rv[t], tr[t], nullptr, w, s);
+      if (st == 2 && last) {
+        e = c->ks32.surface(c->prm, c->pf, c->d_opsf, MODE_S3, dt, io[2], rv[t], tr[t], s);
         if (e != cudaSuccess) return cuda_fail(c, e, "surface kernel launch");
         break;
       }
-      e = c->ks32.surfvol(c->prm, c->pf, c->d_opsf, mode[st], dt, A, ws[st], rv[t], tr[t], out[st], rv[t ^ 1],
-                          tr[t ^ 1], s);
+      e = c->ks32.surfvol(c->prm, c->pf, c->d_opsf, mode[st], dt, io[st], rv[t], tr[t], rv[t ^ 1], tr[t ^ 1], s);
       if (e != cudaSuccess) return cuda_fail(c, e, "fused stage kernel launch");
       t ^= 1;
     }
-    std::swap(A, B);  // the new step start is in B
+    a ^= 1;  // the new step start is in the other buffer of each pair
   }
   return DG_OK;
 }
@@ -812,8 +637,10 @@ extern "C" dg_status dg_status_read(dg_ctx *c, void *stream) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "dg_status_read");
+  // a non-physical state is reported first: it is the cause of the non-finite values it produces
+  if (h & STATUS_NONPHYSICAL)
+    return fail(c, DG_ERR_NONPHYSICAL, "non-physical state on the device (rho <= 0 or P + Pinf <= 0)");
   if (h & STATUS_NONFINITE) return fail(c, DG_ERR_NONFINITE, "non-finite value produced on the device");
-  if (h & STATUS_NONPHYSICAL) return fail(c, DG_ERR_NONPHYSICAL, "non-physical state on the device");
   return DG_OK;
 }
 
@@ -821,7 +648,13 @@ extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_
   if (!c || c->batch || c->kin || !w || !ms_out || nmax < 1 || nrep < 1) return -1;
   cudaStream_t s = (cudaStream_t)stream;
   const bool f64 = c->prec == DG_FP64;
-  const int nk = f64 ? 2 : 3;
+  const int nk = f64 ? 2 : 5;
+  // FP32-bulk kind 4 writes an FP64 state: into a temporary, not the caller's w
+  double *tmp64 = nullptr;
+  if (!f64 && nmax > 4 && cudaMalloc(&tmp64, c->len * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
   // Each kind runs nrep times back to back between two events (as in a step,
   // where the kernels follow each other in a graph): the mean includes the
   // gap between dependent launches but no per-launch event overhead.
@@ -830,19 +663,28 @@ extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_
       if (k == 0) c->ks.volume(c->prm, w, c->d_rvol, c->d_trace, s);
       else c->ks.surface(c->prm, MODE_RHS, 0.0, w, w, c->d_rvol, c->d_trace, c->d_w1, s);
     } else if (k == 0) {  // the kernels of a step as dg_step launches them (FP32 state in, FP32 stage out)
-      c->ks32.volume(c->prm, c->pf, c->d_opsf, c->d_ws32, c->d_rvol32, c->d_trace32, nullptr, nullptr, s);
+      c->ks32.volume(c->prm, c->pf, c->d_opsf, c->d_hi32[0], c->d_rvol32, c->d_trace32, nullptr, nullptr, nullptr, s);
     } else if (k == 1) {
-      c->ks32.surface(c->prm, c->pf, c->d_opsf, MODE_S2, 1e-9f, c->d_ws32, c->d_ws32, c->d_rvol32, c->d_trace32,
-                      c->d_w1_32, nullptr, s);
-    } else {
-      c->ks32.surfvol(c->prm, c->pf, c->d_opsf, MODE_S2, 1e-9f, c->d_ws32, c->d_ws32, c->d_rvol32, c->d_trace32,
-                      c->d_w1_32, c->d_rvol32b, c->d_trace32b, s);
+      const StageIO io{c->d_hi32[0], nullptr, c->d_dd32[0], c->d_dd32[1], nullptr, nullptr, nullptr, nullptr};
+      c->ks32.surface(c->prm, c->pf, c->d_opsf, MODE_S2, 1e-9f, io, c->d_rvol32, c->d_trace32, s);
+    } else if (k == 2) {
+      const StageIO io{c->d_hi32[0], nullptr, c->d_dd32[0], c->d_dd32[1], nullptr, nullptr, nullptr, nullptr};
+      c->ks32.surfvol(c->prm, c->pf, c->d_opsf, MODE_S2, 1e-9f, io, c->d_rvol32, c->d_trace32, c->d_rvol32b,
+                      c->d_trace32b, s);
+    } else if (k == 3) {  // the first stage of a single-step call: reads the FP64 state (hi part only)
+      c->ks32.volume(c->prm, c->pf, c->d_opsf, nullptr, c->d_rvol32b, c->d_trace32b, w, c->d_hi32[1], nullptr, s);
+    } else {  // the last stage of a single-step call: adds the last increment to the FP64 state
+      const StageIO io{nullptr, nullptr, c->d_dd32[0], nullptr, nullptr, nullptr, tmp64, w};
+      c->ks32.surface(c->prm, c->pf, c->d_opsf, MODE_S3, 1e-9f, io, c->d_rvol32, c->d_trace32, s);
     }
   };
-  if (!f64) convert(c, true, const_cast<double *>(w), s);
+  if (!f64) {  // the internal state of w (hi, lo) and a zero increment to time the stage kernels on
+    c->ks32.volume(c->prm, c->pf, c->d_opsf, nullptr, c->d_rvol32, c->d_trace32, w, c->d_hi32[0], c->d_lo32[0], s);
+    cudaMemsetAsync(c->d_dd32[0], 0, (size_t)SW32 * c->N * sizeof(float), s);
+  }
   cudaEvent_t ev[2];
   for (auto &x : ev) cudaEventCreate(&x);
-  for (int k = 0; k < nk; ++k) {
+  for (int k = 0; k < std::min(nk, nmax); ++k) {
     launch(k);  // warm-up
     cudaEventRecord(ev[0], s);
     for (int r = 0; r < nrep; ++r) launch(k);
@@ -853,6 +695,7 @@ extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_
     if (k < nmax) ms_out[k] = (double)t / nrep;
   }
   for (auto &x : ev) cudaEventDestroy(x);
+  cudaFree(tmp64);
   if (cudaGetLastError() != cudaSuccess) return -1;
   return std::min(nmax, nk);
 }
@@ -874,9 +717,10 @@ extern "C" int dg_kernel_costs(const dg_ctx *c, double *flops, double *bytes, in
   double fs = fface * (133 + (visc ? 30 : 0)) + 7 * fface + 12 * 2 * d + 14 + 35;
   // Bytes: the volume kernel reads the state and writes the volume part and
   // the face traces; the surface kernel reads both traces of every face node,
-  // the volume part, the stage input and the step start, and writes the stage.
-  // FP32-bulk stores traces as padded 12-word records and, in the inviscid
-  // kernels, the state and volume parts as padded 8-word node records.
+  // the volume part, the stage input and the step start (FP32-bulk: the step
+  // start and the previous increment), and writes the stage (FP32-bulk: its
+  // increment).  FP32-bulk stores traces as padded 12-word records and, in the
+  // inviscid kernels, the state and volume parts as padded 8-word node records.
   const bool f64 = c->prec == DG_FP64;
   const double nt = f64 ? c->ks.nt : TRW32;
   const double nw = f64 || visc ? 7 : SW32;
@@ -887,8 +731,15 @@ extern "C" int dg_kernel_costs(const dg_ctx *c, double *flops, double *bytes, in
   // The fused FP32-bulk stage kernel does both; its volume part takes the
   // stage state from registers instead of reading it back.
   const double bsv = bv + bs - word * E * Np * nw;
-  const int nk = std::min(nmax, c->prec == DG_FP64 ? 2 : 3);
-  const double F[3] = {fv * E * Np, fs * E * Np, (fv + fs) * E * Np}, Bb[3] = {bv, bs, bsv};
+  // FP32-bulk kinds 3 and 4, a call's first volume kernel (reads the FP64 state, writes hi and lo,
+  // 3 FP64 operations per variable for the split) and last surface kernel (reads the step start's
+  // hi and lo, writes the FP64 state hi + lo: 9 operations of the float-float sum and 2 for the
+  // sum per variable)
+  const double b3 = 8.0 * NV * E * Np + 4.0 * (E * Np * 3 * nw + E * NFK * nt);
+  const double b4 = 4.0 * (E * NFK * nt * 2 + E * Np * 4 * nw) + 8.0 * NV * E * Np;
+  const int nk = std::min(nmax, c->prec == DG_FP64 ? 2 : 5);
+  const double F[5] = {fv * E * Np, fs * E * Np, (fv + fs) * E * Np, (fv + 3 * NV) * E * Np, (fs + 11 * NV) * E * Np};
+  const double Bb[5] = {bv, bs, bsv, b3, b4};
   for (int k = 0; k < nk; ++k) {
     flops[k] = F[k];
     bytes[k] = Bb[k];
@@ -956,7 +807,8 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
   }
 
   // One pool for every FP32 buffer and table: per problem the table, the
-  // internal state, two stages, the volume part and the face traces.
+  // internal state, the two stage increments, the volume parts and the face
+  // traces.
   std::vector<std::vector<float>> tables(n);
   std::vector<size_t> off(n);
   size_t total = 0;
@@ -965,7 +817,7 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
     total += (floats + 63) & ~size_t(63);  // 256-byte aligned slices
     return at;
   };
-  std::vector<size_t> o_ops(n), o_ws(n), o_w1(n), o_w2(n), o_rv(n), o_tr(n), o_rv2(n), o_tr2(n);
+  std::vector<size_t> o_ops(n), o_ws(n), o_d1(n), o_d2(n), o_rv(n), o_tr(n), o_rv2(n), o_tr2(n);
   for (int k = 0; k < n; ++k) {
     const dg_mesh &m = meshes[k];
     const double hx = (m.x1 - m.x0) / m.nx, hy = (m.y1 - m.y0) / m.ny;
@@ -980,8 +832,8 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
     b->len[k] = len;
     o_ops[k] = take(tables[k].size());
     o_ws[k] = take(len32);
-    o_w1[k] = take(len32);
-    o_w2[k] = take(len32);
+    o_d1[k] = take(len32);
+    o_d2[k] = take(len32);
     o_rv[k] = take(len32);
     o_tr[k] = take((size_t)TRW32 * E * NFK);
     o_rv2[k] = take(len32);
@@ -999,8 +851,8 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
     BatchProb &d = b->h[k];
     d.opsf = pool + o_ops[k];
     d.ws = pool + o_ws[k];
-    d.w1 = pool + o_w1[k];
-    d.w2 = pool + o_w2[k];
+    d.d1 = pool + o_d1[k];
+    d.d2 = pool + o_d2[k];
     d.rvol[0] = pool + o_rv[k];
     d.tr[0] = pool + o_tr[k];
     d.rvol[1] = pool + o_rv2[k];

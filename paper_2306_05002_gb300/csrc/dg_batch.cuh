@@ -28,7 +28,7 @@ struct BatchProb {
   Params prm;
   ParamsF pf;
   const float *opsf;                        // FP32 operator table (OpsLayout)
-  float *ws, *w1, *w2;                      // internal FP32 state and the two inner stages
+  float *ws, *d1, *d2;                      // internal FP32 state (step start) and the two inner increments
   float *rvol[2], *tr[2];                   // volume part and face traces, double-buffered (fused stages)
   double *w64;                              // the caller's FP64 state (read at stage 1, written at stage 3)
   float dt;                                 // this problem's step size
@@ -99,6 +99,7 @@ k_volume32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ bl
 
 // Surface part of stage `stage` (1 or 2) fused with the volume part of the
 // next stage; stage s reads buffer s-1 of each pair and writes the other.
+// Stage 1 writes the increment d1, stage 2 reads it and writes d2.
 template <int P, int EPBX, int MINB>
 __global__ void __launch_bounds__(BGeom<P, EPBX>::THREADS, MINB)
 k_surfvol32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ block0, int nprob, int stage) {
@@ -109,14 +110,16 @@ k_surfvol32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ b
   const BatchProb &b = stage_descriptor(probs, block0, nprob, s_raw, s_k, &blk);
   const int in = stage - 1, out = in ^ 1;
   float r[NV];
-  surf32_body<P, 2, false, false, EPBX>(b.prm, b.pf, b.opsf, s_op, blk, stage == 1 ? MODE_S1 : MODE_S2, b.dt,
-                                        b.ws, stage == 1 ? b.ws : b.w1, b.rvol[in], b.tr[in],
-                                        stage == 1 ? b.w1 : b.w2, nullptr, r);
+  StageIO io{b.ws, nullptr, stage == 1 ? nullptr : b.d1, stage == 1 ? b.d1 : b.d2, nullptr, nullptr, nullptr,
+             nullptr};
+  surf32_body<P, 2, false, false, EPBX, false, true>(b.prm, b.pf, b.opsf, s_op, blk, stage == 1 ? MODE_S1 : MODE_S2,
+                                                     b.dt, io, b.rvol[in], b.tr[in], r);
   vol32_body<P, 2, false, false, EPBX>(b.prm, b.pf, b.opsf, s_op, true, blk, nullptr, b.rvol[out], b.tr[out],
                                        nullptr, nullptr, r);
 }
 
-// Surface part of stage 3: writes the caller's FP64 state.
+// Surface part of stage 3: adds the last increment to the caller's FP64 state
+// (the step start) in FP64, in place.
 template <int P, int EPBX, int MINB>
 __global__ void __launch_bounds__(BGeom<P, EPBX>::THREADS, MINB)
 k_surface32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ block0, int nprob) {
@@ -125,8 +128,8 @@ k_surface32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ b
   __shared__ float s_op[BGeom<P, EPBX>::OPS];
   int blk;
   const BatchProb &b = stage_descriptor(probs, block0, nprob, s_raw, s_k, &blk);
-  surf32_body<P, 2, false, false, EPBX>(b.prm, b.pf, b.opsf, s_op, blk, MODE_S3, b.dt, b.ws, b.w2, b.rvol[0],
-                                        b.tr[0], nullptr, b.w64);
+  StageIO io{nullptr, nullptr, b.d2, nullptr, nullptr, nullptr, b.w64, b.w64};
+  surf32_body<P, 2, false, false, EPBX>(b.prm, b.pf, b.opsf, s_op, blk, MODE_S3, b.dt, io, b.rvol[0], b.tr[0]);
 }
 
 template <int P, int EPBX, int MINB>

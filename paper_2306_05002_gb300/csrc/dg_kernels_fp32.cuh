@@ -29,10 +29,22 @@
 // rather than with its offset (P ~ 1e5, psi, phi ~ 1), and keeps a uniform
 // state exactly steady.
 //
-// The first stage of a step can read the FP64 state directly (converting it
-// on load and writing the FP32 internal state), and the last stage can write
-// the FP64 state directly.  With the fused stage kernel (k_surfvol32 below)
-// n steps take 1 + 3n launches.
+// Accumulation.  The step start is carried as a float-float pair (hi, lo),
+// hi + lo holding ~48 significant bits, and the three SSP-RK3 stages as FP32
+// increments over it (Shu-Osher form rewritten for the increments):
+//     d1 = dt L(w0),  d2 = (d1 + dt L(w0 + d1)) / 4,  d3 = 2 (d2 + dt L(w0 + d2)) / 3,
+//     w_{n+1} = w0 + d3,
+// where each right-hand side is evaluated on the FP32 state hi + d (rounded).
+// The increments are small next to the state (the acoustic time step moves a
+// field by a few parts in 1e5 per step), so they keep FP32's relative precision
+// of the change, and w0 + d3 is added in float-float (two-sum): the state does
+// not lose the low bits of each step's change to FP32 rounding, which over
+// thousands of steps otherwise grows to ~1e-5 of the field.
+//
+// The first stage of a step can read the FP64 state directly (splitting it into
+// hi and lo on load and writing the FP32 internal state), and the last stage
+// can write the FP64 state directly (hi + lo).  With the fused stage kernel
+// (k_surfvol32 below) n steps take 1 + 3n launches.
 #pragma once
 
 #include "dg_common.cuh"
@@ -111,6 +123,113 @@ __device__ __forceinline__ void store_node32(float *w, long n, int N, const floa
   }
 }
 
+// Buffers of one stage kernel (each a node-record or field-major FP32 array like
+// the internal state, except out64 and w64in): the step start hi part w0 (all
+// stage modes) and lo part lo (MODE_S3), the previous stage's increment din
+// (MODE_S2, MODE_S3), this stage's increment dout (MODE_S1, MODE_S2), the new
+// step start hi_out / lo_out (MODE_S3 when the step is not the last of the
+// call), and the FP64 output out64 (MODE_RHS: L; MODE_S3 at the end of a call:
+// the state).  w64in (MODE_S3 with out64, when the step start is the FP64 state
+// itself, i.e. the call's only step): the last increment is added to it in FP64
+// (in place when w64in == out64), and w0 and lo are not read.
+struct StageIO {
+  const float *w0, *lo, *din;
+  float *dout, *hi_out, *lo_out;
+  double *out64;
+  const double *w64in;
+};
+
+// (hi, lo) + d in float-float arithmetic: Knuth's two-sum of hi and d, the
+// error added to lo, then a fast two-sum to renormalise (|s| >= |t|).  The
+// intrinsics keep every operation separately rounded (no contraction).
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float d) {
+  const float s = __fadd_rn(hi, d);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+  const float t = __fadd_rn(lo, err);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+// FP64 <-> float-float conversions at the ends of a call, by integer operations
+// on the bit patterns.  On GB300 every conversion instruction (F2F, I2F) and
+// every FP64 add runs on the reduced FP64 pipe, where the split and the sum of
+// seven variables per node cost more than the kernel's FP32 work.
+
+// An integer k in [0, 2^23) as a float, exactly (the float 2^23 + k minus 2^23).
+__device__ __forceinline__ float small_int_to_float(unsigned k) {
+  return __uint_as_float(0x4B000000u | k) - 8388608.0f;
+}
+
+// Split an FP64 value into floats hi + lo: hi is the value rounded to 24
+// significant bits (ties away from zero; the top 24 bits of the significand
+// plus one unit when the dropped 29 bits reach half a unit), lo the remainder
+// (the dropped bits less that unit, in units of the double's last place)
+// rounded once to 24 bits.  Magnitudes below 2^-74 split into zeros (lo would
+// be below the normal floats); 2^126 and above, infinities and NaNs give an
+// infinity or a NaN in hi (the state is then non-physical and is flagged).
+__device__ __forceinline__ void split_ff(double d, float &hi, float &lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned e = (hw >> 20) & 0x7FFu, sign = hw & 0x80000000u;
+  if (e < 949u) {
+    hi = lo = __uint_as_float(sign);
+    return;
+  }
+  if (e > 1148u) {
+    const bool nan = e == 0x7FFu && ((hw & 0xFFFFFu) | lw);
+    hi = __uint_as_float(sign | 0x7F800000u | (nan ? 0x400000u : 0u));
+    lo = 0.f;
+    return;
+  }
+  const unsigned low29 = lw & 0x1FFFFFFFu;
+  const bool up = low29 >= 0x10000000u;
+  const unsigned long long bh = (b & ~0x1FFFFFFFull) + (up ? 0x20000000ull : 0ull);
+  const unsigned hhw = (unsigned)(bh >> 32), hlw = (unsigned)bh;
+  const unsigned he = (hhw >> 20) & 0x7FFu;
+  hi = __uint_as_float(sign | ((he - 896u) << 23) | ((hhw & 0xFFFFFu) << 3) | (hlw >> 29));
+  // |remainder| in units of 2^(e - 1075), below 2^28: two exact pieces, one rounding
+  const unsigned m = up ? 0x20000000u - low29 : low29;
+  const float mag = fmaf(small_int_to_float(m >> 14), 16384.0f, small_int_to_float(m & 0x3FFFu));
+  const float unit = __uint_as_float((e - 948u) << 23);  // 2^(e - 1075), a normal float
+  lo = __uint_as_float(__float_as_uint(mag * unit) ^ ((sign != 0u) != up ? 0x80000000u : 0u));
+}
+
+// The FP64 value of the float pair hi + lo (|lo| at most one unit of hi's last
+// place, as ff_add leaves it): the two significands aligned in units of 2^-29
+// of hi's last place, added or subtracted as integers, renormalised and packed
+// (bits of lo below the double's last place are dropped).  lo zero or below
+// the normal floats contributes nothing; hi zero, subnormal, infinite or NaN
+// is converted on its own (subnormals to zero).
+__device__ __forceinline__ double ff_to_double(float hi, float lo) {
+  const unsigned uh = __float_as_uint(hi), ul = __float_as_uint(lo);
+  const unsigned eh = (uh >> 23) & 0xFFu, el = (ul >> 23) & 0xFFu, sign = uh & 0x80000000u;
+  if (eh == 0u) return __hiloint2double((int)sign, 0);
+  if (eh == 0xFFu) return __hiloint2double((int)(sign | 0x7FF00000u | ((uh & 0x7FFFFFu) ? 0x80000u : 0u)), 0);
+  const unsigned long long H = (unsigned long long)(0x800000u | (uh & 0x7FFFFFu)) << 29;
+  const int s = (int)el - (int)eh + 29;
+  unsigned long long L = 0ull;
+  if (el != 0u && s > -24) {
+    const unsigned Ml = 0x800000u | (ul & 0x7FFFFFu);
+    L = s >= 0 ? (unsigned long long)Ml << s : (unsigned long long)(Ml >> (-s));
+  }
+  unsigned long long M = ((ul ^ uh) & 0x80000000u) ? H - L : H + L;
+  int E = (int)eh;
+  if (M >= (1ull << 53)) {
+    M >>= 1;
+    ++E;
+  } else if (M < (1ull << 52)) {
+    M <<= 1;
+    --E;
+  }
+  const unsigned long long bits = ((unsigned long long)sign << 32) | ((unsigned long long)(E + 896) << 52) |
+                                  (M & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
+// Exact float -> double by the same bit manipulation (subnormals to zero).
+__device__ __forceinline__ double f2d(float f) { return ff_to_double(f, 0.f); }
+
 // The closure's divisions (by rho and by the mixture 1/(gamma-1)) use the
 // approximate reciprocal (__fdividef: within 2 ulp for the magnitudes of a
 // density or of 1/(gamma-1)), far below the FP32 storage error of this path;
@@ -162,7 +281,7 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
                                            float *s_op, bool ops_ready, int blk, const float *__restrict__ w,
                                            float *__restrict__ rvol, float *__restrict__ tr,
                                            const double *__restrict__ w64, float *__restrict__ w32out,
-                                           const float *qin = nullptr) {
+                                           const float *qin = nullptr, float *__restrict__ lo_out = nullptr) {
   using G = Geom<P, DIM, VISC, ST, EPBX>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
   constexpr int P11 = P1 * P1;
@@ -188,13 +307,23 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = act ? qin[v] : (v == M1 || v == M2 ? 1.f : 0.f);
   } else if (w64) {
-    // first stage: convert the FP64 state (the stiffened-gas constant leaves rho E in FP64)
+    // first stage: split the FP64 state into hi + lo (the stiffened-gas constant leaves rho E
+    // in FP64 first)
     double d[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) d[v] = act ? ld_in<PDL>(w64 + (long)v * N + n) : (v == M1 || v == M2 ? 1.0 : 0.0);
+    d[RE] = d[RE] - fma(prm.dC, d[PHI], prm.C2);
+    if (lo_out) {
+      // a call of several steps carries the step start as hi + lo
+      float lo[NV];
 #pragma unroll
-    for (int v = 0; v < RE; ++v) q[v] = (float)d[v];
-    q[RE] = (float)(d[RE] - fma(prm.dC, d[PHI], prm.C2));
+      for (int v = 0; v < NV; ++v) split_ff(d[v], q[v], lo[v]);
+      if (act) store_node32<!VISC>(lo_out, n, N, lo);
+    } else {
+      // a single step adds its last increment to the FP64 state itself: hi alone
+#pragma unroll
+      for (int v = 0; v < NV; ++v) q[v] = __double2float_rn(d[v]);
+    }
     if (act) store_node32<!VISC>(w32out, n, N, q);
   } else if (act) {
     load_node32<!VISC, PDL>(w, n, N, q);
@@ -211,6 +340,10 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   const float iG = rcp32(fmaf(phi, pf.g1 - pf.g2, pf.g2));
   const float Pr = (q[RE] - rho * k) * iG;
   const float Bq = Pr * pf.Bp;  // B - (C_1 - C_2)
+  // Non-physical state: rho <= 0, a mixture 1/(gamma - 1) <= 0, or P + Pinf_mix <= 0, i.e.
+  // rho c^2 = P + (P + Cm) / den <= 0 (Sec. 2 mixture rules).
+  if (prm.check_finite && act && (rho <= 0.f || iG <= 0.f || Pr + (Pr + fmaf(pf.dC, phi, pf.C2)) * iG <= 0.f))
+    atomicOr(prm.status, STATUS_NONPHYSICAL);
 
   if (lane) {
     s_f[0][le][a] = phi;
@@ -362,7 +495,7 @@ template <int P, int DIM, bool VISC, bool ST, bool PDL>
 __global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
 k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, const float *__restrict__ w,
            float *__restrict__ rvol, float *__restrict__ tr, const double *__restrict__ w64,
-           float *__restrict__ w32out) {
+           float *__restrict__ w32out, float *__restrict__ lo_out) {
   constexpr int P11 = Geom<P, DIM, VISC, ST>::P1 * Geom<P, DIM, VISC, ST>::P1;
   __shared__ float s_op[2 * P11];  // Dx, Dy
   if (PDL) {
@@ -370,7 +503,8 @@ k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, c
     for (int t = threadIdx.x; t < 2 * P11; t += blockDim.x) s_op[t] = opsf[t];
     grid_dependency_wait();
   }
-  vol32_body<P, DIM, VISC, ST, 0, PDL>(prm, pf, opsf, s_op, PDL, blockIdx.x, w, rvol, tr, w64, w32out);
+  vol32_body<P, DIM, VISC, ST, 0, PDL>(prm, pf, opsf, s_op, PDL, blockIdx.x, w, rvol, tr, w64, w32out, nullptr,
+                                       lo_out);
 }
 
 // The NC words of face-trace record o (three 128-bit loads, or two and one word), or, when the
@@ -395,26 +529,30 @@ __device__ __forceinline__ void load_trace32(const float *__restrict__ tr, long 
 }
 
 // Surface kernel body of the FP32-bulk path.  mode MODE_RHS writes L for the
-// paper's variables in FP64 (out64, with L(rho E) = L(rhoEt) + (C_1-C_2) L(phi));
-// the stage modes write the FP32 internal state (out32), or, when out64 is
-// given, the FP64 state (last stage of a step).
+// paper's variables in FP64 (io.out64, with L(rho E) = L(rhoEt) + (C_1-C_2) L(phi));
+// the stage modes write the stage increment (MODE_S1, MODE_S2: io.dout) or add
+// the last increment to the step start in float-float (MODE_S3) and write the
+// new step start (io.hi_out, io.lo_out), or, when io.out64 is given, the FP64
+// state (last stage of a call).  See StageIO.
 //
 // s_op: the block's shared copy of the operator table (OpsLayout, Geom::OPS
 // floats), filled by this body.
 //
-// rout != NULL (stage modes): the stage result of the thread's node is also
+// rout != NULL (stage modes): the stage state of the thread's node (step start
+// plus increment, in FP32; for MODE_S3 the new step start's hi part) is also
 // left in rout, for a volume body that follows in the same kernel.  Every
 // thread of the block returns from this body (none leaves early), so such a
 // body may synchronise the block.
 // PDL: the kernel was launched as a programmatic dependent; the operator table
 // is copied before the wait for the kernel before, whose results are then read
 // with coherent loads.
-template <int P, int DIM, bool VISC, bool ST, int EPBX = 0, bool PDL = false>
+// FUSED: the body runs in a fused stage kernel (modes MODE_S1..MODE_S3 with hi_out / lo_out), so the
+// FP64 outputs (MODE_RHS, out64, w64in) are compiled out of it.
+template <int P, int DIM, bool VISC, bool ST, int EPBX = 0, bool PDL = false, bool FUSED = false>
 __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf, const float *__restrict__ opsf,
-                                            float *s_op, int blk, int mode, float dt, const float *__restrict__ w0,
-                                            const float *__restrict__ ws, const float *__restrict__ rvol,
-                                            const float *__restrict__ tr, float *__restrict__ out32,
-                                            double *__restrict__ out64, float *rout = nullptr) {
+                                            float *s_op, int blk, int mode, float dt, const StageIO &io,
+                                            const float *__restrict__ rvol, const float *__restrict__ tr,
+                                            float *rout = nullptr) {
   using G = Geom<P, DIM, VISC, ST, EPBX>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
   constexpr int NC = VISC ? NT32_VISCOUS : TRW32;  // words read per trace record
@@ -448,13 +586,22 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   // Every global load of the body is issued first -- the node's own inputs of
   // the update and both traces of its face nodes -- so that their latencies
   // overlap each other (and the copy of the operator table).
-  float Lv[NV], wsn[NV], w0n[NV];
+  float Lv[NV], w0n[NV], dn[NV], lon[NV];
 #pragma unroll
-  for (int vv = 0; vv < NV; ++vv) Lv[vv] = wsn[vv] = w0n[vv] = 0.f;
+  for (int vv = 0; vv < NV; ++vv) Lv[vv] = w0n[vv] = dn[vv] = lon[vv] = 0.f;
+  double w64n[NV];
+#pragma unroll
+  for (int vv = 0; vv < NV; ++vv) w64n[vv] = 0.0;
+  const bool fp64_start = !FUSED && mode == MODE_S3 && io.w64in != nullptr;
   if (act) {
     load_node32<!VISC, PDL>(rvol, n, N, Lv);
-    if (mode != MODE_RHS) load_node32<!VISC, PDL>(ws, n, N, wsn);
-    if (mode == MODE_S2 || mode == MODE_S3) load_node32<!VISC, PDL>(w0, n, N, w0n);
+    if (mode != MODE_RHS && !fp64_start) load_node32<!VISC, PDL>(io.w0, n, N, w0n);
+    if (mode == MODE_S2 || mode == MODE_S3) load_node32<!VISC, PDL>(io.din, n, N, dn);
+    if (mode == MODE_S3 && !fp64_start) load_node32<!VISC, PDL>(io.lo, n, N, lon);
+    if (fp64_start) {
+#pragma unroll
+      for (int vv = 0; vv < NV; ++vv) w64n[vv] = ld_in<PDL>(io.w64in + (long)vv * N + n);
+    }
   }
   float Cm_[FPT][NC], Cp_[FPT][NC];
 #pragma unroll
@@ -633,31 +780,60 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
 #pragma unroll
     for (int vv = 0; vv < NV; ++vv) Lv[vv] += acc[vv] * im;
     bool bad = false;
-    if (mode == MODE_RHS) {
+    if (!FUSED && mode == MODE_RHS) {
 #pragma unroll
       for (int vv = 0; vv < NV; ++vv) {
-        double r = (double)Lv[vv];
-        if (vv == RE) r = fma(prm.dC, (double)Lv[PHI], r);
+        double r = f2d(Lv[vv]);
+        if (vv == RE) r = fma(prm.dC, f2d(Lv[PHI]), r);
         bad |= !isfinite(r);
-        out64[(long)vv * N + n] = r;
+        io.out64[(long)vv * N + n] = r;
       }
     } else {
       float r[NV];
+      if (fp64_start) {
+        // w_{n+1} = w_n + 2 (d2 + dt L) / 3 in FP64 on the caller's state; the increment of the
+        // reduced energy becomes one of rho E by adding (C_1 - C_2) times that of phi
+        float d[NV];
 #pragma unroll
-      for (int vv = 0; vv < NV; ++vv) {
-        const float st = fmaf(dt, Lv[vv], wsn[vv]);
-        if (mode == MODE_S1) r[vv] = st;
-        else if (mode == MODE_S2) r[vv] = 0.75f * w0n[vv] + 0.25f * st;
-        else r[vv] = (1.f / 3.f) * w0n[vv] + (2.f / 3.f) * st;
-        bad |= !isfinite(r[vv]);
-      }
-      if (out64) {
-        // last stage: hand back the FP64 state, restoring the stiffened-gas constant with the FP32 phi
+        for (int vv = 0; vv < NV; ++vv) {
+          d[vv] = (2.f / 3.f) * fmaf(dt, Lv[vv], dn[vv]);
+          bad |= !isfinite(d[vv]);
+          r[vv] = 0.f;
+        }
 #pragma unroll
-        for (int vv = 0; vv < RE; ++vv) out64[(long)vv * N + n] = (double)r[vv];
-        out64[(long)RE * N + n] = (double)r[RE] + fma(prm.dC, (double)r[PHI], prm.C2);
+        for (int vv = 0; vv < RE; ++vv) io.out64[(long)vv * N + n] = w64n[vv] + f2d(d[vv]);
+        io.out64[(long)RE * N + n] = w64n[RE] + fma(prm.dC, f2d(d[PHI]), f2d(d[RE]));
+      } else if (mode == MODE_S3) {
+        // w_{n+1} = (hi, lo) + 2 (d2 + dt L) / 3, in float-float
+        float lo[NV];
+#pragma unroll
+        for (int vv = 0; vv < NV; ++vv) {
+          r[vv] = w0n[vv];
+          lo[vv] = lon[vv];
+          ff_add(r[vv], lo[vv], (2.f / 3.f) * fmaf(dt, Lv[vv], dn[vv]));
+          bad |= !isfinite(r[vv]);
+        }
+        if (!FUSED && io.out64) {
+          // last stage of a call: hand back the FP64 state hi + lo, restoring the stiffened-gas
+          // constant with the carried phi
+#pragma unroll
+          for (int vv = 0; vv < RE; ++vv) io.out64[(long)vv * N + n] = ff_to_double(r[vv], lo[vv]);
+          const double phi64 = ff_to_double(r[PHI], lo[PHI]);
+          io.out64[(long)RE * N + n] = ff_to_double(r[RE], lo[RE]) + fma(prm.dC, phi64, prm.C2);
+        } else {
+          store_node32<!VISC>(io.hi_out, n, N, r);
+          store_node32<!VISC>(io.lo_out, n, N, lo);
+        }
       } else {
-        store_node32<!VISC>(out32, n, N, r);
+        // d1 = dt L,  d2 = (d1 + dt L) / 4; the stage state is w0 + d
+        float d[NV];
+#pragma unroll
+        for (int vv = 0; vv < NV; ++vv) {
+          d[vv] = mode == MODE_S1 ? dt * Lv[vv] : 0.25f * fmaf(dt, Lv[vv], dn[vv]);
+          r[vv] = w0n[vv] + d[vv];
+          bad |= !isfinite(r[vv]);
+        }
+        store_node32<!VISC>(io.dout, n, N, d);
       }
       if (rout) {
 #pragma unroll
@@ -670,12 +846,11 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
 
 template <int P, int DIM, bool VISC, bool ST, bool PDL>
 __global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
-k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt,
-            const float *__restrict__ w0, const float *__restrict__ ws, const float *__restrict__ rvol,
-            const float *__restrict__ tr, float *__restrict__ out32, double *__restrict__ out64) {
+k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt, const StageIO io,
+            const float *__restrict__ rvol, const float *__restrict__ tr) {
   __shared__ float s_op[Geom<P, DIM, VISC, ST>::OPS];
   if (PDL) grid_dependents_launch();
-  surf32_body<P, DIM, VISC, ST, 0, PDL>(prm, pf, opsf, s_op, blockIdx.x, mode, dt, w0, ws, rvol, tr, out32, out64);
+  surf32_body<P, DIM, VISC, ST, 0, PDL>(prm, pf, opsf, s_op, blockIdx.x, mode, dt, io, rvol, tr);
 }
 
 // Fused stage kernel: the surface part of stage s (mode MODE_S1..S3) followed,
@@ -695,35 +870,27 @@ k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, 
 template <int P, int DIM, bool VISC, bool ST, bool PDL>
 __global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS,
                                   VISC ? 65536 / (Geom<P, DIM, VISC, ST>::THREADS * 80) : 1)
-k_surfvol32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt,
-            const float *__restrict__ w0, const float *__restrict__ ws, const float *__restrict__ rvol_in,
-            const float *__restrict__ tr_in, float *__restrict__ out32, float *__restrict__ rvol_out,
+k_surfvol32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt, const StageIO io,
+            const float *__restrict__ rvol_in, const float *__restrict__ tr_in, float *__restrict__ rvol_out,
             float *__restrict__ tr_out) {
   __shared__ float s_op[Geom<P, DIM, VISC, ST>::OPS];  // one table for both parts
   float r[NV];
   if (PDL) grid_dependents_launch();
-  surf32_body<P, DIM, VISC, ST, 0, PDL>(prm, pf, opsf, s_op, blockIdx.x, mode, dt, w0, ws, rvol_in, tr_in, out32,
-                                        nullptr, r);
+  surf32_body<P, DIM, VISC, ST, 0, PDL, true>(prm, pf, opsf, s_op, blockIdx.x, mode, dt, io, rvol_in, tr_in, r);
   vol32_body<P, DIM, VISC, ST>(prm, pf, opsf, s_op, true, blockIdx.x, nullptr, rvol_out, tr_out, nullptr, nullptr,
                                r);
 }
 
-// FP64 <-> FP32 internal state.  The stiffened-gas constant is removed from
-// rho E in FP64 with the FP64 phase field on entry, and restored with the
-// FP32 phase field on exit, so the pressure carried by the internal state is
-// the FP64 pressure and is handed back unchanged.
-__global__ void k_to32(int N, double C2, double dC, int aos, const double *__restrict__ w, float *__restrict__ w32);
-__global__ void k_to64(int N, double C2, double dC, int aos, const float *__restrict__ w32, double *__restrict__ w);
-
+// Launch interface of one FP32-bulk kernel family.  volume: the volume part of a
+// stage on the FP32 state w, or, with w64, on the FP64 state, which it splits
+// into the internal state's hi (w32out) and lo (lo_out, may be NULL) parts.
 struct KernelSet32 {
   cudaError_t (*volume)(const Params &, const ParamsF &, const float *opsf, const float *w, float *rvol,
-                        float *trace, const double *w64, float *w32out, cudaStream_t);
-  cudaError_t (*surface)(const Params &, const ParamsF &, const float *opsf, int mode, float dt, const float *w0,
-                         const float *ws, const float *rvol, const float *trace, float *out32, double *out64,
-                         cudaStream_t);
-  cudaError_t (*surfvol)(const Params &, const ParamsF &, const float *opsf, int mode, float dt, const float *w0,
-                         const float *ws, const float *rvol_in, const float *tr_in, float *out32, float *rvol_out,
-                         float *tr_out, cudaStream_t);
+                        float *trace, const double *w64, float *w32out, float *lo_out, cudaStream_t);
+  cudaError_t (*surface)(const Params &, const ParamsF &, const float *opsf, int mode, float dt, const StageIO &io,
+                         const float *rvol, const float *trace, cudaStream_t);
+  cudaError_t (*surfvol)(const Params &, const ParamsF &, const float *opsf, int mode, float dt, const StageIO &io,
+                         const float *rvol_in, const float *tr_in, float *rvol_out, float *tr_out, cudaStream_t);
   int nt, epb, threads;
 };
 
@@ -737,44 +904,43 @@ struct KernelSet32 {
 // non-coherent loads, a few per cent faster on the viscous surface kernels).
 template <int P, int DIM, bool VISC, bool ST>
 cudaError_t launch_volume32(const Params &prm, const ParamsF &pf, const float *opsf, const float *w, float *rvol,
-                            float *trace, const double *w64, float *w32out, cudaStream_t s) {
+                            float *trace, const double *w64, float *w32out, float *lo_out, cudaStream_t s) {
   using G = Geom<P, DIM, VISC, ST>;
   const int blocks = (prm.E + G::EPB - 1) / G::EPB;
   static const int resident = resident_blocks(k_volume32<P, DIM, VISC, ST, true>, G::THREADS);
   if (blocks <= resident)
     return launch_dependent(k_volume32<P, DIM, VISC, ST, true>, blocks, G::THREADS, s, prm, pf, opsf, w, rvol,
-                            trace, w64, w32out);
-  k_volume32<P, DIM, VISC, ST, false><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, w, rvol, trace, w64, w32out);
+                            trace, w64, w32out, lo_out);
+  k_volume32<P, DIM, VISC, ST, false><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, w, rvol, trace, w64, w32out,
+                                                                    lo_out);
   return cudaGetLastError();
 }
 
 template <int P, int DIM, bool VISC, bool ST>
 cudaError_t launch_surface32(const Params &prm, const ParamsF &pf, const float *opsf, int mode, float dt,
-                             const float *w0, const float *ws, const float *rvol, const float *trace, float *out32,
-                             double *out64, cudaStream_t s) {
+                             const StageIO &io, const float *rvol, const float *trace, cudaStream_t s) {
   using G = Geom<P, DIM, VISC, ST>;
   const int blocks = (prm.E + G::EPB - 1) / G::EPB;
   static const int resident = resident_blocks(k_surface32<P, DIM, VISC, ST, true>, G::THREADS);
   if (blocks <= resident)
     return launch_dependent(k_surface32<P, DIM, VISC, ST, true>, blocks, G::THREADS, s, prm, pf, opsf, mode,
-                            dt, w0, ws, rvol, trace, out32, out64);
-  k_surface32<P, DIM, VISC, ST, false><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, mode, dt, w0, ws, rvol, trace,
-                                                                     out32, out64);
+                            dt, io, rvol, trace);
+  k_surface32<P, DIM, VISC, ST, false><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, mode, dt, io, rvol, trace);
   return cudaGetLastError();
 }
 
 template <int P, int DIM, bool VISC, bool ST>
 cudaError_t launch_surfvol32(const Params &prm, const ParamsF &pf, const float *opsf, int mode, float dt,
-                             const float *w0, const float *ws, const float *rvol_in, const float *tr_in,
-                             float *out32, float *rvol_out, float *tr_out, cudaStream_t s) {
+                             const StageIO &io, const float *rvol_in, const float *tr_in, float *rvol_out,
+                             float *tr_out, cudaStream_t s) {
   using G = Geom<P, DIM, VISC, ST>;
   const int blocks = (prm.E + G::EPB - 1) / G::EPB;
   static const int resident = resident_blocks(k_surfvol32<P, DIM, VISC, ST, true>, G::THREADS);
   if (blocks <= resident)
     return launch_dependent(k_surfvol32<P, DIM, VISC, ST, true>, blocks, G::THREADS, s, prm, pf, opsf, mode,
-                            dt, w0, ws, rvol_in, tr_in, out32, rvol_out, tr_out);
-  k_surfvol32<P, DIM, VISC, ST, false><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, mode, dt, w0, ws, rvol_in, tr_in,
-                                                                     out32, rvol_out, tr_out);
+                            dt, io, rvol_in, tr_in, rvol_out, tr_out);
+  k_surfvol32<P, DIM, VISC, ST, false><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, mode, dt, io, rvol_in, tr_in,
+                                                                     rvol_out, tr_out);
   return cudaGetLastError();
 }
 

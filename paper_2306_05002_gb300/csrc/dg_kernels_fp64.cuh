@@ -115,6 +115,10 @@ k_volume(const Params prm, const double *__restrict__ w, double *__restrict__ rv
   const double Pr = sg_pressure(prm, phi, rho, q[RU], DIM == 2 ? q[RV] : 0.0, q[RE], &Cm, &den);
   const double B = fma(Pr, prm.Bp, prm.dC);
   const double k = 0.5 * (u * u + v * v);
+  // Non-physical state: rho <= 0, a mixture 1/(gamma - 1) <= 0, or P + Pinf_mix <= 0, i.e.
+  // P (1 + den) + Cm <= 0 with Pinf_mix = Cm / (1 + den) (Sec. 2 mixture rules).
+  if (prm.check_finite && act && (rho <= 0.0 || den <= 0.0 || fma(Pr, den + 1.0, Cm) <= 0.0))
+    atomicOr(prm.status, STATUS_NONPHYSICAL);
 
   if (lane) {
     s_f[0][le][a] = phi;

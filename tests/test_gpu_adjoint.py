@@ -1,12 +1,14 @@
 """Discrete adjoint (FP64 path): dg_rhs_vjp and dg_adjoint_step against finite differences,
-and the gradient of an interface functional with respect to level-set parameters against
-central differences of the GPU forward map and of the oracle's forward map.
+the gradient of an interface functional with respect to level-set parameters against central
+differences of the GPU forward map and of the oracle's forward map (relative 1e-6), and the
+same gradient through torch.autograd with the DGTrajectory function.
 
 The right-hand side has kinks (lambda = max of the one-sided wave speeds at every face), so a
 finite difference is only as good as the number of kinks its step straddles.  Column by
 column on a tiny mesh (few faces) a step of 1e-6 of the variable's scale straddles none and
 keeps round-off at ~1e-7 (tolerance 1e-5); a directional difference on a large mesh needs
-1e-9 (tolerance 2e-6)."""
+1e-9 (tolerance 2e-6).  The parameter gradients use Richardson-extrapolated central
+differences (steps h and h/2, truncation O(h^4)) in the 16 level-set coefficients."""
 import numpy as np
 import pytest
 
@@ -149,6 +151,19 @@ def _objective(orc, wl, wN, target):
     return 0.5 * np.sum(M * (wN[0] - target) ** 2), M
 
 
+def _richardson(J, theta, k, h=1e-5):
+    """dJ/dtheta_k by Richardson-extrapolated central differences (steps h and h/2)."""
+    def d(step):
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += step
+        tm[k] -= step
+        return (J(tp) - J(tm)) / (2 * step)
+    return (4.0 * d(0.5 * h) - d(h)) / 3.0
+
+
+GRAD_RTOL = 1e-6
+
+
 def test_level_set_parameter_gradient(orc, dg):
     """dJ/dtheta by the adjoint (checkpointed trajectory) against central differences of J
     through the GPU forward map; J = 1/2 int (alpha_N - alpha*)^2, alpha* from other parameters."""
@@ -175,18 +190,13 @@ def test_level_set_parameter_gradient(orc, dg):
     np.testing.assert_array_equal(lam0, lam0_recompute)
     modes = W.level_set_modes(base, base.meta["cx"], base.meta["cy"])
     grad = -(modes @ lam0[1])          # psi0 = ... - theta . modes
-    fd = np.zeros(16)
-    for k in range(16):
-        h = 1e-5
-        tp, tm = theta.copy(), theta.copy()
-        tp[k] += h
-        tm[k] -= h
-        Jp = _objective(orc, base, run(W.adjoint_drop(n=n, p=3, nsteps=steps, theta=tp)), target)[0]
-        Jm = _objective(orc, base, run(W.adjoint_drop(n=n, p=3, nsteps=steps, theta=tm)), target)[0]
-        fd[k] = (Jp - Jm) / (2 * h)
+
+    def Jof(th):
+        return _objective(orc, base, run(W.adjoint_drop(n=n, p=3, nsteps=steps, theta=th)), target)[0]
+    fd = np.array([_richardson(Jof, theta, k) for k in range(16)])
     s.close()
     assert J > 0
-    np.testing.assert_allclose(grad, fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
+    np.testing.assert_allclose(grad, fd, rtol=GRAD_RTOL, atol=GRAD_RTOL * np.abs(fd).max())
 
 
 def test_level_set_parameter_gradient_against_oracle(orc, dg):
@@ -210,18 +220,65 @@ def test_level_set_parameter_gradient_against_oracle(orc, dg):
     s.close()
     modes = W.level_set_modes(base, base.meta["cx"], base.meta["cy"])
     grad = -(modes @ lam0[1])
-    fd = np.zeros(16)
-    for k in range(16):
-        h = 1e-5
-        tp, tm = theta.copy(), theta.copy()
-        tp[k] += h
-        tm[k] -= h
-        Jp = _objective(orc, base, orc.rk3(pb, W.adjoint_drop(n=n, p=2, nsteps=steps, theta=tp).w, dt, steps),
-                        target)[0]
-        Jm = _objective(orc, base, orc.rk3(pb, W.adjoint_drop(n=n, p=2, nsteps=steps, theta=tm).w, dt, steps),
-                        target)[0]
-        fd[k] = (Jp - Jm) / (2 * h)
-    np.testing.assert_allclose(grad, fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
+
+    def Jof(th):
+        return _objective(orc, base, orc.rk3(pb, W.adjoint_drop(n=n, p=2, nsteps=steps, theta=th).w, dt, steps),
+                          target)[0]
+    fd = np.array([_richardson(Jof, theta, k) for k in range(16)])
+    np.testing.assert_allclose(grad, fd, rtol=GRAD_RTOL, atol=GRAD_RTOL * np.abs(fd).max())
+
+
+def test_dgtrajectory_autograd_gradient(orc, dg):
+    """DGTrajectory, the torch.autograd.Function over checkpointed SSP-RK3 trajectories: the
+    initial level set is built in torch from the 16 coefficients theta (psi0 = psi_circle -
+    theta . modes), J = 1/2 int (alpha_N - alpha*)^2 is formed in torch, and torch.autograd.grad
+    returns dJ/dtheta -- against Richardson central differences of J through the GPU forward map.
+    The gradient with respect to the whole initial state equals the checkpointed adjoint sweep."""
+    import torch
+    from paper_2306_05002_gb300 import adjoint as A
+    from paper_2306_05002_gb300.adjoint import DGTrajectory
+    n, steps, every = 12, 24, 5
+    base = W.adjoint_drop(n=n, p=3, nsteps=steps)
+    theta_np = np.array(base.meta["theta"])
+    modes_np = W.level_set_modes(base, base.meta["cx"], base.meta["cy"])
+    s = dg.Solver(base)
+    dt = base.dt
+    tgt = W.adjoint_drop(n=n, p=3, nsteps=steps, theta=np.random.default_rng(51).normal(0, 0.01, 16))
+    xt = torch.from_numpy(tgt.w.copy()).cuda()
+    s.dg_step(xt, dt, steps)
+    target = xt[0].clone()
+    M = torch.from_numpy(mass_weights(orc, base)).cuda()
+    w_base = torch.from_numpy(base.w.copy()).cuda()
+    modes = torch.from_numpy(modes_np).cuda()
+    psi_circle = w_base[1] + torch.from_numpy(theta_np).cuda() @ modes
+
+    def initial_state(theta):
+        return torch.cat([w_base[:1], (psi_circle - theta @ modes)[None], w_base[2:]]).contiguous()
+
+    theta = torch.tensor(theta_np, dtype=torch.float64, device="cuda", requires_grad=True)
+    w0 = initial_state(theta)
+    wN = DGTrajectory.apply(w0, s, dt, steps, every)
+    J = 0.5 * (M * (wN[0] - target) ** 2).sum()
+    (g_theta,) = torch.autograd.grad(J, theta)
+    g_theta = g_theta.cpu().numpy()
+
+    # the state gradient through autograd equals the checkpointed adjoint sweep bit for bit
+    w0_leaf = initial_state(torch.from_numpy(theta_np).cuda()).requires_grad_(True)
+    wN2 = DGTrajectory.apply(w0_leaf, s, dt, steps, every)
+    (g_w0,) = torch.autograd.grad(0.5 * (M * (wN2[0] - target) ** 2).sum(), w0_leaf)
+    lamN = torch.zeros_like(wN2)
+    lamN[0] = M * (wN2[0].detach() - target)
+    _, ckpt = A.forward(s, w0_leaf.detach(), dt, steps, every)
+    assert torch.equal(g_w0, A.backward(s, ckpt, lamN, dt, steps, every))
+
+    def Jof(th):
+        with torch.no_grad():
+            x = initial_state(torch.from_numpy(th).cuda())
+            s.dg_step(x, dt, steps)
+            return float(0.5 * (M * (x[0] - target) ** 2).sum())
+    fd = np.array([_richardson(Jof, theta_np, k) for k in range(16)])
+    s.close()
+    np.testing.assert_allclose(g_theta, fd, rtol=GRAD_RTOL, atol=GRAD_RTOL * np.abs(fd).max())
 
 
 def test_adjoint_rejects_pressure_boundary(dg):

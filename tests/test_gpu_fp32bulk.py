@@ -129,6 +129,32 @@ def test_fp32bulk_500_steps_accuracy(orc, dg):
     assert e_u <= 1e-3, e_u
 
 
+def test_fp32bulk_slab_1000_steps_accuracy(orc, dg):
+    """The 1D slab workload (100 elements, p = 3), all of its 1000 steps: phi and P within 1e-5
+    (relative L2) of FP64.  With the acoustic time step a field changes by a few parts in 1e5 per
+    step, so an FP32 state rounded at every stage drifts by ~1e-5 over 1000 steps; the carried
+    float-float step start keeps the change's low bits."""
+    wl = W.slab_1d(nx=100, p=3)
+    w64 = _run(dg, wl, "fp64", 1000)
+    w32 = _run(dg, wl, "fp32bulk", 1000)
+    pb = problem(orc, wl)
+    e_phi = _l2(w32[0], w64[0])
+    e_P = _l2(orc.primitives(pb, w32)[3], orc.primitives(pb, w64)[3])
+    assert e_phi <= 1e-5 and e_P <= 1e-5, (e_phi, e_P)
+
+
+def test_fp32bulk_rayleigh_taylor_2000_steps_accuracy(orc, dg):
+    """The Rayleigh-Taylor set-up (walls, viscous stress, gravity, surface tension) on 64 x 64,
+    p = 4, for the workload's 2000 steps: phi and P within 1e-5 (relative L2) of FP64."""
+    wl = W.rayleigh_taylor(n=64, p=4, seed=3)
+    w64 = _run(dg, wl, "fp64", 2000)
+    w32 = _run(dg, wl, "fp32bulk", 2000)
+    pb = problem(orc, wl)
+    e_phi = _l2(w32[0], w64[0])
+    e_P = _l2(orc.primitives(pb, w32)[3], orc.primitives(pb, w64)[3])
+    assert e_phi <= 1e-5 and e_P <= 1e-5, (e_phi, e_P)
+
+
 def test_fp32bulk_short_run_against_oracle(orc, dg):
     wl = W.drop_2d(n=16, p=3, seed=2)
     w32 = _run(dg, wl, "fp32bulk", 20)
@@ -176,11 +202,15 @@ def test_fp32bulk_rayleigh_taylor_physics_tracks_fp64(orc, dg):
     (lambda: W.drop_2d(n=128, p=3, seed=2), 3),
     (lambda: W.rayleigh_taylor(n=128, p=4, seed=3), 2),
 ])
-def test_fp32bulk_multi_step_call_matches_single_steps(dg, make, nsteps):
-    """n steps in one call keep the FP32 state between steps and fuse the surface part of each
-    stage with the volume part of the next; n calls of one step convert to FP64 and back at every
-    step boundary.  The round trip is exact, so both agree to FP32 rounding (the fused kernel may
-    contract a few operations differently): max |a - b| <= 1e-6 max |b| per variable."""
+def test_fp32bulk_multi_step_call_matches_single_steps(orc, dg, make, nsteps):
+    """n steps in one call keep the FP32 step start (hi, lo) between steps and fuse the surface part
+    of each stage with the volume part of the next; n calls of one step write the FP64 state and
+    split it again at every step boundary.  hi + lo survives that round trip except for the FP64
+    rounding of rho E + Cmix(phi), which can move hi by one FP32 unit where lo sits at half a unit;
+    the right-hand side reads hi, so the two agree to FP32 rounding plus the effect of one unit of
+    the stored pressure on the pressure gradient: per variable
+    max |a - b| <= 1e-6 max |b| + 3 n dt 4 eps32 max|P| (2/h) max_i sum_c |D_ic| (momentum, times
+    max|u| for the energy)."""
     import torch
     wl = make()
     s = dg.Solver(wl, precision="fp32bulk")
@@ -193,7 +223,13 @@ def test_fp32bulk_multi_step_call_matches_single_steps(dg, make, nsteps):
     s.close()
     a, b = a.cpu().numpy(), b.cpu().numpy()
     assert not np.array_equal(b, wl.w)
+    prim = orc.primitives(problem(orc, wl), b)
+    xi, _ = orc.gll(wl.p)
+    D = orc.lagrange_deriv(wl.p, xi)
+    dP = 4 * np.finfo(np.float32).eps * np.abs(prim[3]).max() * (2.0 / min(wl.hx, wl.hy)) * np.abs(D).sum(axis=1).max()
+    umax = np.max(np.hypot(prim[1], prim[2]))
+    extra = {4: dP, 5: dP, 6: dP * umax}
     for v in range(7):
         sc = np.abs(b[v]).max()
-        assert np.abs(a[v] - b[v]).max() <= 1e-6 * max(sc, 1e-30), (v, np.abs(a[v] - b[v]).max(), sc)
-
+        tol = 1e-6 * max(sc, 1e-30) + 3 * nsteps * wl.dt * extra.get(v, 0.0)
+        assert np.abs(a[v] - b[v]).max() <= tol, (v, np.abs(a[v] - b[v]).max(), sc, tol)
