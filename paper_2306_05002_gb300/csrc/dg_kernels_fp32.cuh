@@ -72,15 +72,16 @@ __host__ inline ParamsF to_float(const Params &p) {
 // speed, B and the mixture viscosity are recomputed from the state by the
 // reader (trace_derive).  Inviscid kernels: pressure, sound speed and 1/rho
 // travel in the record's spare words (C_P, C_C, C_IR) and the reader only
-// multiplies (trace_stored).
+// multiplies (trace_stored).  (Viscous records of 64 bytes carrying P, c and
+// 1/rho as well were measured slower at 256x256 p4: the kernels are close
+// enough to the memory bound that the extra 16 bytes per record cost more than
+// the closure they save.)
 enum TraceField32 { C_GPHI = 7, C_N = 8, C_TX = 9, C_TY = 10 };
 constexpr int NT32_INVISCID = 9;
 constexpr int NT32_VISCOUS = 11;
 // The FP32 face traces are stored one 48-byte record per face node ([E * NFK][TRW32] floats, the
 // words in TraceField32 order, the rest padding), so that a record moves in three 128-bit
-// accesses instead of nine or eleven scalar ones.  The inviscid kernels fill the three spare
-// words with the writer's pressure, sound speed and 1/rho (C_P, C_C, C_IR), so the reader skips
-// the closure (two divisions and a square root per side of every face node).
+// accesses instead of nine or eleven scalar ones.
 constexpr int TRW32 = 12;
 enum TraceClosure32 { C_P = 9, C_C = 10, C_IR = 11 };
 // The FP32 internal state and volume parts of the inviscid kernels are stored one 32-byte record
@@ -269,6 +270,39 @@ __device__ __forceinline__ void trace_stored(const ParamsF &pf, const float *C, 
   T[T_B] = C[C_P] * pf.Bp;
 }
 
+// Element lines in shared memory.  Every field a contraction reads is stored
+// per element by rows (the x-lines, i fastest) and, for the y-derivatives, by
+// columns (the y-lines, j fastest), so that a thread reads a whole line in the
+// widest aligned loads the line length allows (P + 1 = 4: one 128-bit load;
+// P + 1 = 2 or 6: 64-bit loads; odd lengths: one load per node) instead of one
+// load per node.  (Padding odd lines to 16 bytes was measured slower at
+// p = 4: the padded stride makes shared-memory bank conflicts.)
+template <int P1>
+__device__ __forceinline__ void load_line(const float *row, float *v) {
+  if (P1 % 4 == 0) {
+    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+    for (int k = 0; k < P1 / 4; ++k) {
+      const float4 x = r4[k];
+      v[4 * k] = x.x;
+      v[4 * k + 1] = x.y;
+      v[4 * k + 2] = x.z;
+      v[4 * k + 3] = x.w;
+    }
+  } else if (P1 % 2 == 0) {
+    const float2 *r2 = reinterpret_cast<const float2 *>(row);
+#pragma unroll
+    for (int k = 0; k < P1 / 2; ++k) {
+      const float2 x = r2[k];
+      v[2 * k] = x.x;
+      v[2 * k + 1] = x.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < P1; ++k) v[k] = row[k];
+  }
+}
+
 // Volume kernel body for the element tile `blk` (EPB elements) of one problem.
 // opsf: FP32 operator table (OpsLayout).  w64 != NULL: read the FP64 state and
 // write the FP32 internal state to w32out (first stage of a step).  qin !=
@@ -286,7 +320,16 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
   constexpr int P11 = P1 * P1;
   constexpr int NS = 12;
-  __shared__ float s_f[NS][EPB][NP];
+  constexpr int LS = P1;
+  constexpr int NLY = DIM == 2 ? P1 : 1;  // lines per element in each orientation
+  // Even line lengths: y-lines from a column copy in vector loads, the node's rows of D held in
+  // registers.  Odd ones: y-lines read across the rows one node at a time and D read where used,
+  // which the 80-register viscous kernels need (p = 4: the column copies and held rows cost 7%).
+  constexpr bool COLS = DIM == 2 && P1 % 2 == 0;
+  // rows (x-lines) of six fields per element and, when COLS, their columns (y-lines); without COLS
+  // the y-flux components take six more row slots
+  __shared__ __align__(16) float s_row[COLS || DIM == 1 ? 6 : 12][EPB][NLY][LS];
+  __shared__ __align__(16) float s_col[COLS ? 6 : 1][EPB][COLS ? P1 : 1][LS];
 
   if (!ops_ready)
     for (int t = threadIdx.x; t < 2 * P11; t += blockDim.x) s_op[t] = opsf[t];
@@ -346,36 +389,77 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
     atomicOr(prm.status, STATUS_NONPHYSICAL);
 
   if (lane) {
-    s_f[0][le][a] = phi;
-    s_f[1][le][a] = psi;
-    s_f[2][le][a] = u;
-    s_f[3][le][a] = v;
+    s_row[0][le][j][i] = phi;
+    s_row[1][le][j][i] = psi;
+    s_row[2][le][j][i] = u;
+    if (VISC) s_row[3][le][j][i] = v;
+    if (COLS) {
+      s_col[0][le][i][j] = phi;
+      s_col[1][le][i][j] = psi;
+      s_col[3][le][i][j] = v;
+      if (VISC) s_col[2][le][i][j] = u;
+    } else if (DIM == 2) {
+      s_row[3][le][j][i] = v;
+    }
   }
-  __syncthreads();
+  __syncthreads();  // also orders the operator table's copy (above, or in the caller) before its reads
+  // the node's rows of the two derivative matrices (held in registers when COLS)
+  float dxr[P1], dyr[P1];
+  if (COLS) {
+#pragma unroll
+    for (int c = 0; c < P1; ++c) {
+      dxr[c] = Dx[i * P1 + c];
+      dyr[c] = Dy[j * P1 + c];
+    }
+  }
+  auto DX = [&](int c) { return COLS ? dxr[c] : Dx[i * P1 + c]; };
+  auto DY = [&](int c) { return COLS ? dyr[c] : Dy[j * P1 + c]; };
+  auto s_fy = [&](int eq) -> float * { return &s_row[COLS || DIM == 1 ? 0 : 6 + eq][le][0][0]; };
+  // the y-line of field slot f through the node
+  auto yline = [&](int f, float *lv) {
+    if (COLS) {
+      load_line<P1>(&s_col[f][le][i][0], lv);
+    } else {
+#pragma unroll
+      for (int c = 0; c < P1; ++c) lv[c] = s_row[f][le][c][i];
+    }
+  };
 
   float gpx = 0.f, gpy = 0.f, gsx = 0.f, gsy = 0.f, gux = 0.f, guy = 0.f, gvx = 0.f, gvy = 0.f, comp = 0.f;
+  {
+    float lp[P1], lq[P1];
+    load_line<P1>(&s_row[0][le][j][0], lp);  // phi along x
+    load_line<P1>(&s_row[2][le][j][0], lq);  // u along x
 #pragma unroll
-  for (int c = 0; c < P1; ++c) {
-    const float dx = Dx[i * P1 + c];
-    const int ax = c + P1 * j;
-    const float phc = s_f[0][le][ax], uc = s_f[2][le][ax];
-    gpx = fmaf(dx, phc - phi, gpx);
-    gsx = fmaf(dx, s_f[1][le][ax] - psi, gsx);
-    comp = fmaf(dx * fmaf(pf.dC, phc, pf.C2), uc - u, comp);
+    for (int c = 0; c < P1; ++c) {
+      gpx = fmaf(DX(c), lp[c] - phi, gpx);
+      comp = fmaf(DX(c) * fmaf(pf.dC, lp[c], pf.C2), lq[c] - u, comp);
+      if (VISC) gux = fmaf(DX(c), lq[c] - u, gux);
+    }
+    load_line<P1>(&s_row[1][le][j][0], lp);  // psi along x
+#pragma unroll
+    for (int c = 0; c < P1; ++c) gsx = fmaf(DX(c), lp[c] - psi, gsx);
     if (VISC) {
-      gux = fmaf(dx, uc - u, gux);
-      gvx = fmaf(dx, s_f[3][le][ax] - v, gvx);
+      load_line<P1>(&s_row[3][le][j][0], lp);  // v along x
+#pragma unroll
+      for (int c = 0; c < P1; ++c) gvx = fmaf(DX(c), lp[c] - v, gvx);
     }
     if (DIM == 2) {
-      const float dy = Dy[j * P1 + c];
-      const int ay = i + P1 * c;
-      const float phy = s_f[0][le][ay], vc = s_f[3][le][ay];
-      gpy = fmaf(dy, phy - phi, gpy);
-      gsy = fmaf(dy, s_f[1][le][ay] - psi, gsy);
-      comp = fmaf(dy * fmaf(pf.dC, phy, pf.C2), vc - v, comp);
+      yline(0, lp);  // phi along y
+      yline(3, lq);  // v along y
+#pragma unroll
+      for (int c = 0; c < P1; ++c) {
+        gpy = fmaf(DY(c), lp[c] - phi, gpy);
+        comp = fmaf(DY(c) * fmaf(pf.dC, lp[c], pf.C2), lq[c] - v, comp);
+        if (VISC) gvy = fmaf(DY(c), lq[c] - v, gvy);
+      }
+      yline(1, lp);  // psi along y
+#pragma unroll
+      for (int c = 0; c < P1; ++c) gsy = fmaf(DY(c), lp[c] - psi, gsy);
       if (VISC) {
-        guy = fmaf(dy, s_f[2][le][ay] - u, guy);
-        gvy = fmaf(dy, vc - v, gvy);
+        yline(2, lp);  // u along y
+#pragma unroll
+        for (int c = 0; c < P1; ++c) guy = fmaf(DY(c), lp[c] - u, guy);
       }
     }
   }
@@ -406,15 +490,19 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   float kappa = 0.f;
   if (ST) {
     if (lane) {
-      s_f[4][le][a] = nx;
-      s_f[5][le][a] = ny;
+      s_row[4][le][j][i] = nx;
+      if (COLS) s_col[4][le][i][j] = ny;
+      else if (DIM == 2) s_row[5][le][j][i] = ny;
     }
     __syncthreads();
-    float dv = 0.f;
+    float dv = 0.f, lp[P1];
+    load_line<P1>(&s_row[4][le][j][0], lp);
 #pragma unroll
-    for (int c = 0; c < P1; ++c) {
-      dv = fmaf(Dx[i * P1 + c], s_f[4][le][c + P1 * j] - nx, dv);
-      if (DIM == 2) dv = fmaf(Dy[j * P1 + c], s_f[5][le][i + P1 * c] - ny, dv);
+    for (int c = 0; c < P1; ++c) dv = fmaf(DX(c), lp[c] - nx, dv);
+    if (DIM == 2) {
+      yline(COLS ? 4 : 5, lp);
+#pragma unroll
+      for (int c = 0; c < P1; ++c) dv = fmaf(DY(c), lp[c] - ny, dv);
     }
     kappa = -dv;
   }
@@ -434,9 +522,15 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   F[10] = (q[RE] + Pr) * u - cE * a1x - (txx * u + txy * v);
   F[11] = (q[RE] + Pr) * v - cE * a1y - (txy * u + tyy * v);
   __syncthreads();
+  // (odd line lengths: the y-components in slots 6..11 of the row layout, s_row and s_col being
+  // one array there -- see below)
   if (lane) {
 #pragma unroll
-    for (int s = 0; s < NS; ++s) s_f[s][le][a] = F[s];
+    for (int eq = 0; eq < 6; ++eq) {
+      s_row[eq][le][j][i] = F[2 * eq];
+      if (COLS) s_col[eq][le][i][j] = F[2 * eq + 1];
+      else if (DIM == 2) s_fy(eq)[j * P1 + i] = F[2 * eq + 1];
+    }
   }
   __syncthreads();
 
@@ -444,12 +538,18 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   float R[NV];
 #pragma unroll
   for (int eq = 0; eq < 6; ++eq) {
-    float acc = 0.f;
+    float acc = 0.f, lp[P1];
     const float fx = F[2 * eq], fy = F[2 * eq + 1];
+    load_line<P1>(&s_row[eq][le][j][0], lp);
 #pragma unroll
-    for (int c = 0; c < P1; ++c) {
-      acc = fmaf(Dx[i * P1 + c], s_f[2 * eq][le][c + P1 * j] - fx, acc);
-      if (DIM == 2) acc = fmaf(Dy[j * P1 + c], s_f[2 * eq + 1][le][i + P1 * c] - fy, acc);
+    for (int c = 0; c < P1; ++c) acc = fmaf(DX(c), lp[c] - fx, acc);
+    if (COLS) {
+      load_line<P1>(&s_col[eq][le][i][0], lp);
+#pragma unroll
+      for (int c = 0; c < P1; ++c) acc = fmaf(DY(c), lp[c] - fy, acc);
+    } else if (DIM == 2) {
+#pragma unroll
+      for (int c = 0; c < P1; ++c) acc = fmaf(DY(c), s_fy(eq)[c * P1 + i] - fy, acc);
     }
     R[eq == 0 ? PHI : eq + 1] = -acc;
   }
@@ -507,24 +607,22 @@ k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, c
                                        lo_out);
 }
 
-// The NC words of face-trace record o (three 128-bit loads, or two and one word), or, when the
-// record does not exist, zeros with m1 = m1_default (a finite density for the closure).
-template <int NC, bool COH = false>
+// The NC words of face-trace record o (records of RW floats, 128-bit loads), or, when the record
+// does not exist, zeros with m1 = m1_default (a finite density for the closure).
+template <int NC, int RW, bool COH = false>
 __device__ __forceinline__ void load_trace32(const float *__restrict__ tr, long o, bool valid, float *T,
                                              float m1_default) {
 #pragma unroll
   for (int qf = 0; qf < NC; ++qf) T[qf] = qf == T_M1 ? m1_default : 0.f;
   if (!valid) return;
-  const float4 *rec = reinterpret_cast<const float4 *>(tr) + o * (TRW32 / 4);
-  const float4 a = ld_in<COH>(rec), b = ld_in<COH>(rec + 1);
-  T[0] = a.x; T[1] = a.y; T[2] = a.z; T[3] = a.w;
-  T[4] = b.x; T[5] = b.y; T[6] = b.z; T[7] = b.w;
-  if (NC > 9) {
-    const float4 c = ld_in<COH>(rec + 2);
-    T[8] = c.x; T[9] = c.y; T[10] = c.z;
-    if (NC > 11) T[11] = c.w;
-  } else if (NC > 8) {
-    T[8] = ld_in<COH>(reinterpret_cast<const float *>(rec + 2));
+  const float4 *rec = reinterpret_cast<const float4 *>(tr) + o * (RW / 4);
+#pragma unroll
+  for (int k = 0; k < (NC + 3) / 4; ++k) {
+    const float4 x = ld_in<COH>(rec + k);
+    if (4 * k + 0 < NC) T[4 * k + 0] = x.x;
+    if (4 * k + 1 < NC) T[4 * k + 1] = x.y;
+    if (4 * k + 2 < NC) T[4 * k + 2] = x.z;
+    if (4 * k + 3 < NC) T[4 * k + 3] = x.w;
   }
 }
 
@@ -555,7 +653,8 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
                                             float *rout = nullptr) {
   using G = Geom<P, DIM, VISC, ST, EPBX>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
-  constexpr int NC = VISC ? NT32_VISCOUS : TRW32;  // words read per trace record
+  constexpr int RW = TRW32;                          // floats per trace record
+  constexpr int NC = VISC ? NT32_VISCOUS : TRW32;    // words read per trace record
   constexpr int FPT = (NFK + NP - 1) / NP;  // face nodes per thread
   const OpsLayout L{P1, NP};
   // Per face node: the surface integrand of the 7 equations and the 6 lifting
@@ -613,8 +712,8 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
     e2_[fi] = e2;
     const long om = (long)(act ? e : 0) * NFK + (fv ? t : 0);
     const long op = (long)(e2 >= 0 ? e2 : 0) * NFK + (f ^ 1) * NK + kk;
-    load_trace32<NC, PDL>(tr, om, fv, Cm_[fi], 1.f);
-    load_trace32<NC, PDL>(tr, op, e2 >= 0, Cp_[fi], 0.f);
+    load_trace32<NC, RW, PDL>(tr, om, fv, Cm_[fi], 1.f);
+    load_trace32<NC, RW, PDL>(tr, op, e2 >= 0, Cp_[fi], 0.f);
   }
 
   if (!PDL)
