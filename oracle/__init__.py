@@ -67,7 +67,7 @@ class _Problem(ctypes.Structure):
         ("sigma", ctypes.c_double), ("g", ctypes.c_double * 2),
         ("Gamma", ctypes.c_double), ("eps", ctypes.c_double), ("c_ip", ctypes.c_double),
         ("viscous", ctypes.c_int), ("gravity", ctypes.c_int), ("surface_tension", ctypes.c_int),
-        ("p_bc", ctypes.c_double * 4),
+        ("p_bc", ctypes.c_double * 4), ("grad_lift", ctypes.c_int),
     ]
 
 
@@ -96,6 +96,7 @@ class Problem:
     gravity: bool = False
     surface_tension: bool = False
     p_bc: tuple = (0.0, 0.0, 0.0, 0.0)
+    grad_lift: bool = False
 
     @property
     def Np(self) -> int:
@@ -118,6 +119,7 @@ class Problem:
         s.viscous, s.gravity, s.surface_tension = int(self.viscous), int(self.gravity), int(self.surface_tension)
         for i in range(4):
             s.p_bc[i] = self.p_bc[i]
+        s.grad_lift = int(self.grad_lift)
         return s
 
 
@@ -161,6 +163,7 @@ def _configure(_lib):
     _lib.orc_num_nodes.restype = ctypes.c_long
     _lib.orc_nodes.argtypes = [pp, dp, dp]
     _lib.orc_primitives.argtypes = [pp, dp, dp]
+    _lib.orc_gradients.argtypes = [pp, dp, dp, dp]
     _lib.orc_rhs.argtypes = [pp, dp, dp, dp, dp]
     _lib.orc_rk3.argtypes = [pp, dp, ctypes.c_double, ctypes.c_int]
     _lib.orc_diag.argtypes = [pp, dp, dp]
@@ -249,6 +252,15 @@ def primitives(pb: Problem, w):
     s = pb._c()
     _check(lib().orc_primitives(ctypes.byref(s), _ptr(w), _ptr(out)), "primitives")
     return out
+
+
+def gradients(pb: Problem, f):
+    """Gradient (gx, gy) of the nodal field f: broken, or BR1-lifted when pb.grad_lift."""
+    f = np.ascontiguousarray(f, dtype=np.float64).reshape(pb.N)
+    gx, gy = np.zeros(pb.N), np.zeros(pb.N)
+    s = pb._c()
+    _check(lib().orc_gradients(ctypes.byref(s), _ptr(f), _ptr(gx), _ptr(gy)), "gradients")
+    return gx, gy
 
 
 def rhs(pb: Problem, w, want_scale: bool = False, want_parts: bool = False):

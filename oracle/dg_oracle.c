@@ -46,6 +46,12 @@
  *       C_m1 = rho_1^(0), C_m2 = -rho_2^(0), C_rhou = (rho_1^(0)-rho_2^(0)) u,
  *       C_rhoE = B + (rho_1^(0)-rho_2^(0)) k,  B = rho_1 H_1 - rho_2 H_2;
  *   - n = 0 where |grad psi| < 1e-12;
+ *   - gradients of phi and psi: broken (element-local) by default; with the
+ *     option grad_lift, BR1-lifted (the broken gradient plus M^-1 times the
+ *     face integrals of l ({f} - f-) m, the central trace), and those lifted
+ *     gradients give a_1, the normal, the SIP flux's {grad phi} and the CSF
+ *     delta; the non-conservative transport -u.grad(phi), -u.grad(psi) keeps
+ *     the broken gradient (its face flux already carries the jump);
  *   - viscous flux: {tau}.m + eta {mu} (u+ - u-) for momentum and
  *     {tau.u}.m + eta {mu} (k+ - k-) for energy (no symmetric term);
  *   - walls: ghost state equal to the own state with the velocity (no-slip)
@@ -334,6 +340,7 @@ int orc_primitives(const orc_problem *pr, const double *w, double *prim) {
 typedef struct {
   prim_t q;
   double gphi[2], gpsi[2], gu[2], gv[2];
+  double bphi[2], bpsi[2];  /* broken gradients of phi and psi (the transport term's) */
   double n[2];          /* interface normal from the level set */
   double a1[2], a1m[2]; /* a_1 and the magnitude of its two parts */
   double tau[2][2];     /* viscous stress */
@@ -371,6 +378,49 @@ static int neighbour(const geo_t *g, int e, int f) {
       if (ey < g->ny - 1) return e + g->nx;
       return bc[3] == ORC_BC_PERIODIC ? e - g->nx * (g->ny - 1) : -1;
   }
+}
+
+/* BR1 lifting of the face jumps of the nodal field f into the gradient (gx, gy):
+   at every face node a of element e, M_a^-1 int_face l_a ({f} - f-) m, i.e.
+   w_f / (w_a J) (f+ - f-) / 2 times the outward normal m, with f+ the
+   neighbour's value at the coincident node (the own value at a wall, where
+   nothing is added). */
+static void lift_jumps(const geo_t *g, const double *f, double *gx, double *gy) {
+  const int nf = g->dim == 2 ? 4 : 2, nk = g->dim == 2 ? g->P1 : 1;
+  for (int e = 0; e < g->E; ++e)
+    for (int fc = 0; fc < nf; ++fc) {
+      int e2 = neighbour(g, e, fc);
+      if (e2 < 0) continue;
+      const double *m = face_m[fc];
+      double Jf = g->dim == 2 ? 0.5 * (fc < 2 ? g->hy : g->hx) : 1.0;
+      for (int k = 0; k < nk; ++k) {
+        int a = face_node(g, fc, k);
+        long nm = (long)e * g->Np + a, np_ = (long)e2 * g->Np + face_node(g, fc ^ 1, k);
+        double wf = (g->dim == 2 ? g->wt[k] : 1.0) * Jf;
+        double lift = wf / (node_weight(g, a) * g->J) * 0.5 * (f[np_] - f[nm]);
+        gx[nm] += lift * m[0];
+        if (gy) gy[nm] += lift * m[1];
+      }
+    }
+}
+
+int orc_gradients(const orc_problem *pr, const double *f, double *gx, double *gy) {
+  geo_t g;
+  if (geo_init(&g, pr)) return -1;
+  for (int e = 0; e < g.E; ++e)
+    for (int a = 0; a < g.Np; ++a) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int b = 0; b < g.Np; ++b) {
+        double gr[2];
+        grad_basis(&g, b, a, gr);
+        s0 += f[(long)e * g.Np + b] * gr[0];
+        s1 += f[(long)e * g.Np + b] * gr[1];
+      }
+      gx[(long)e * g.Np + a] = s0;
+      gy[(long)e * g.Np + a] = s1;
+    }
+  if (pr->grad_lift) lift_jumps(&g, f, gx, gy);
+  return 0;
 }
 
 /* Accumulate a contribution to R and its magnitude to the rounding scale. */
@@ -435,6 +485,35 @@ int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double
         }
       }
     }
+  }
+
+  /* 2b. Broken gradients kept for the transport term; with grad_lift, the
+         gradients of phi and psi become BR1-lifted (central traces). */
+  for (long n = 0; n < N; ++n)
+    for (int d = 0; d < 2; ++d) {
+      nd[n].bphi[d] = nd[n].gphi[d];
+      nd[n].bpsi[d] = nd[n].gpsi[d];
+    }
+  if (pr->grad_lift) {
+    double *f = (double *)malloc(sizeof(double) * N), *gx = (double *)malloc(sizeof(double) * N),
+           *gy = (double *)malloc(sizeof(double) * N);
+    if (!f || !gx || !gy) {
+      free(f); free(gx); free(gy); free(nd); free(R); free(A);
+      return -2;
+    }
+    for (int fld = 0; fld < 2; ++fld) {
+      for (long n = 0; n < N; ++n) {
+        f[n] = fld == 0 ? nd[n].q.phi : nd[n].q.psi;
+        gx[n] = gy[n] = 0.0;
+      }
+      lift_jumps(&g, f, gx, gy);
+      for (long n = 0; n < N; ++n) {
+        double *gr = fld == 0 ? nd[n].gphi : nd[n].gpsi;
+        gr[0] += gx[n];
+        gr[1] += gy[n];
+      }
+    }
+    free(f); free(gx); free(gy);
   }
 
   /* 3. Normal from the level set, a_1, viscous stress. */
@@ -540,10 +619,10 @@ int orc_rhs(const orc_problem *pr, const double *w, double *L, double *S, double
       const node_t *t = &nd[n];
       const prim_t *q = &t->q;
       double wa = node_weight(&g, a) * g.J;
-      double tphi = q->u * t->gphi[0] + q->v * t->gphi[1];
-      double tpsi = q->u * t->gpsi[0] + q->v * t->gpsi[1];
-      add(&vol, ORC_PHI, n, -wa * tphi, wa * (fabs(q->u * t->gphi[0]) + fabs(q->v * t->gphi[1])));
-      add(&vol, ORC_PSI, n, -wa * tpsi, wa * (fabs(q->u * t->gpsi[0]) + fabs(q->v * t->gpsi[1])));
+      double tphi = q->u * t->bphi[0] + q->v * t->bphi[1];
+      double tpsi = q->u * t->bpsi[0] + q->v * t->bpsi[1];
+      add(&vol, ORC_PHI, n, -wa * tphi, wa * (fabs(q->u * t->bphi[0]) + fabs(q->v * t->bphi[1])));
+      add(&vol, ORC_PSI, n, -wa * tpsi, wa * (fabs(q->u * t->bpsi[0]) + fabs(q->v * t->bpsi[1])));
       if (pr->gravity) {
         add(&src, ORC_RU, n, wa * q->rho * pr->g[0], wa * q->rho * pr->g[0]);
         add(&src, ORC_RV, n, wa * q->rho * pr->g[1], wa * q->rho * pr->g[1]);

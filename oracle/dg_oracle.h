@@ -38,6 +38,7 @@ typedef struct {
   double c_ip;        /* interior-penalty constant: eta = c_ip (p+1)^2 / h */
   int viscous, gravity, surface_tension;
   double p_bc[4];     /* exterior pressure of ORC_BC_PRESSURE sides */
+  int grad_lift;      /* 1: BR1-lifted gradients of phi and psi (see orc_gradients) */
 } orc_problem;
 
 /* GLL nodes xi[0..p] (ascending) and weights wt[0..p] on [-1, 1]. */
@@ -50,6 +51,14 @@ long orc_num_nodes(const orc_problem *pr);
 int orc_nodes(const orc_problem *pr, double *x, double *y);
 /* Primitive variables at every node: prim[q * N + n], q = rho, u, v, P, c, B. */
 int orc_primitives(const orc_problem *pr, const double *w, double *prim);
+/*
+ * Gradient of the nodal field f (N values) at every node: the broken
+ * (element-local) gradient, plus, when pr->grad_lift is set, the BR1 lifting of
+ * the face jumps: q = grad_h f + M^-1 sum over faces of int l (f^ - f-) m with
+ * the central trace f^ = {f} (at walls and pressure boundaries the exterior
+ * value is the own, so nothing is lifted there).
+ */
+int orc_gradients(const orc_problem *pr, const double *f, double *gx, double *gy);
 /*
  * L = M^-1 R(w).  S (nullable) receives the sum of absolute values of every
  * contribution to R, also scaled by M^-1, which sets the rounding scale for

@@ -56,6 +56,7 @@ class Workload:
     gravity: bool = False
     surface_tension: bool = False
     p_bc: tuple = (0.0, 0.0, 0.0, 0.0)  # exterior pressure of "pressure" sides
+    grad_lift: bool = False            # BR1-lifted gradients of phi and psi
     w: Optional[np.ndarray] = None   # (7, N) float64
     dt: float = 0.0
     nsteps: int = 0
@@ -84,7 +85,7 @@ class Workload:
     def problem_kwargs(self) -> dict:
         """Fields shared by the oracle's and the library's problem descriptions."""
         keys = ["dim", "nx", "ny", "p", "x0", "x1", "y0", "y1", "bc", "gamma", "pinf", "rho0", "mu",
-                "sigma", "g", "Gamma", "eps", "c_ip", "viscous", "gravity", "surface_tension", "p_bc"]
+                "sigma", "g", "Gamma", "eps", "c_ip", "viscous", "gravity", "surface_tension", "p_bc", "grad_lift"]
         return {k: getattr(self, k) for k in keys}
 
 

@@ -103,6 +103,12 @@ MUTATIONS = [
     ("dg_oracle.c", "w[i] = w[i] / 3.0 + 2.0 / 3.0 * (w2[i] + dt * L[i]);",
      "w[i] = w[i] / 3.0 + 2.0 / 3.0 * (w2[i] + 0.5 * dt * L[i]);", "wrong third SSP-RK3 stage"),
     ("dg_oracle.c", "out[v] += wJ * wn[v];", "out[v] += wn[v];", "diagnostic integrals without quadrature weights"),
+    # BR1-lifted gradients (option grad_lift)
+    ("dg_oracle.c", "double lift = wf / (node_weight(g, a) * g->J) * 0.5 * (f[np_] - f[nm]);",
+     "double lift = wf / (node_weight(g, a) * g->J) * (f[np_] - f[nm]);", "lifting with the full jump"),
+    ("dg_oracle.c", "gx[nm] += lift * m[0];", "gx[nm] -= lift * m[0];", "lifting against the outward normal"),
+    ("dg_oracle.c", "double tphi = q->u * t->bphi[0] + q->v * t->bphi[1];",
+     "double tphi = q->u * t->gphi[0] + q->v * t->gphi[1];", "transport of phi on the lifted gradient"),
     # kinematic mode (Sec. 4.1)
     ("dg_oracle.c", "k->a1[d] = Gam * (eps * k->gphi[d] - s * k->n[d]);", "k->a1[d] = Gam * (eps * k->gphi[d] + s * k->n[d]);",
      "kinematic sharpening term with the wrong sign"),
@@ -134,7 +140,8 @@ MUTATIONS = [
 ]
 
 # The pin modules, cheapest first (a mutant is usually caught by an early one).
-PIN_MODULES = ["test_oracle_operators", "test_oracle_closure", "test_oracle_walls", "test_oracle_invariants",
+PIN_MODULES = ["test_oracle_operators", "test_oracle_closure", "test_oracle_walls", "test_oracle_lifting",
+               "test_oracle_invariants",
                "test_oracle_pressure_bc", "test_oracle_reinit", "test_oracle_kinematic", "test_oracle_triangles",
                "test_oracle_convergence"]
 
