@@ -110,13 +110,22 @@ typedef struct {
    speed there).  The state is never clipped.  batch_tile (batches
    only): 0 lets the first dg_batch_step tune the tile of every order; 1..4
    fixes tile variant batch_tile - 1 for all orders (see dg_batch_step);
-   other values are DG_ERR_ARG. */
+   other values are DG_ERR_ARG.  grad_lift: 0 (the default) takes the
+   gradients of phi and psi element by element (broken gradients); 1 takes
+   them BR1-lifted, the broken gradient plus M^-1 times the face integrals of
+   l ({f} - f-) m (central traces; nothing is lifted at walls and pressure
+   boundaries), for a_1, the level-set normal, the SIP flux's {grad phi} and
+   the CSF delta -- the non-conservative transport keeps the broken gradient.
+   Sec. 3 leaves the gradient discretisation open.  The lifted gradients are
+   built by the FP64 kernels: FP32-bulk and batch contexts reject grad_lift = 1
+   with DG_ERR_UNSUPPORTED, and such a context has no discrete adjoint. */
 typedef struct {
   int prec;
   double c_ip;
   int viscous, gravity, surface_tension;
   int check_finite;
   int batch_tile;
+  int grad_lift;
 } dg_opts;
 
 typedef struct dg_ctx dg_ctx;

@@ -56,7 +56,7 @@ class dg_eos(ctypes.Structure):
 class dg_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("c_ip", ctypes.c_double), ("viscous", ctypes.c_int),
                 ("gravity", ctypes.c_int), ("surface_tension", ctypes.c_int), ("check_finite", ctypes.c_int),
-                ("batch_tile", ctypes.c_int)]
+                ("batch_tile", ctypes.c_int), ("grad_lift", ctypes.c_int)]
 
 
 class dg_velocity(ctypes.Structure):
@@ -161,7 +161,7 @@ def _stream(stream=None):
 
 def make_structs(dim, nx, ny, x0, x1, y0, y1, bc, gamma, pinf, rho0, mu=(0.0, 0.0), sigma=0.0, g=(0.0, 0.0),
                  precision="fp64", c_ip=1.0, viscous=False, gravity=False, surface_tension=False,
-                 check_finite=True, p_bc=(0.0, 0.0, 0.0, 0.0), **_ignored):
+                 check_finite=True, p_bc=(0.0, 0.0, 0.0, 0.0), grad_lift=False, **_ignored):
     m = dg_mesh()
     m.dim, m.nx, m.ny = dim, nx, ny
     m.x0, m.x1, m.y0, m.y1 = x0, x1, y0, y1
@@ -176,6 +176,7 @@ def make_structs(dim, nx, ny, x0, x1, y0, y1, bc, gamma, pinf, rho0, mu=(0.0, 0.
     o.prec = PREC[precision] if isinstance(precision, str) else int(precision)
     o.c_ip, o.viscous, o.gravity, o.surface_tension = c_ip, int(viscous), int(gravity), int(surface_tension)
     o.check_finite = int(check_finite)
+    o.grad_lift = int(grad_lift)
     return m, e, o
 
 

@@ -337,6 +337,9 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
   const dg_opts o = normalised_opts(opts);
   if (o.prec != DG_FP64 && o.prec != DG_FP32_BULK)
     return fail(nullptr, DG_ERR_ARG, "dg_create: precision must be DG_FP64 or DG_FP32_BULK");
+  if (o.grad_lift != 0 && o.grad_lift != 1) return fail(nullptr, DG_ERR_ARG, "dg_create: grad_lift must be 0 or 1");
+  if (o.grad_lift && o.prec != DG_FP64)
+    return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_create: lifted gradients (grad_lift) are built by the FP64 kernels");
   const long long E = (long long)mesh->nx * mesh->ny;
   const int P1 = p + 1;
   const int Np = mesh->dim == 2 ? P1 * P1 : P1;
@@ -370,7 +373,7 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
   // The discrete adjoint covers the FP64 inviscid equations without surface tension.
   bool pressure_bc = false;
   for (int f = 0; f < 4; ++f) pressure_bc |= mesh->bc[f] == DG_BC_PRESSURE;
-  c->has_adj = c->prec == DG_FP64 && !o.viscous && !o.surface_tension && !pressure_bc &&
+  c->has_adj = c->prec == DG_FP64 && !o.viscous && !o.surface_tension && !pressure_bc && !o.grad_lift &&
                adj_kernels(p, c->dim, &c->adj);
   const std::vector<double> ops = build_ops(c->dim, p, c->hx, c->hy);
   c->prm = make_params(mesh, p, eos, Gamma, eps, o, c->hx, c->hy);
@@ -760,8 +763,9 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
   const dg_opts o = normalised_opts(opts);
   if (o.prec != DG_FP32_BULK)
     return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_batch_create: the batched form runs the FP32-bulk path only");
-  if (o.viscous || o.surface_tension)
-    return fail(nullptr, DG_ERR_UNSUPPORTED, "dg_batch_create: viscous and surface-tension terms are not batched");
+  if (o.viscous || o.surface_tension || o.grad_lift)
+    return fail(nullptr, DG_ERR_UNSUPPORTED,
+                "dg_batch_create: viscous and surface-tension terms and lifted gradients are not batched");
   if (o.batch_tile < 0 || o.batch_tile > NVAR)
     return fail(nullptr, DG_ERR_ARG, "dg_batch_create: batch_tile must be 0 (tune) or 1..4");
   for (int k = 0; k < n; ++k) {

@@ -45,6 +45,7 @@ struct Params {
   double Gamma, eps;
   double eta_x, eta_y;       // interior penalty on faces normal to x and to y
   int gravity, check_finite;
+  int grad_lift;             // BR1-lifted gradients of phi and psi (dg_opts.grad_lift)
   const double *ops;         // operator tables, see OpsLayout
   unsigned *status;          // latched device status bits
 };

@@ -183,6 +183,7 @@ inline Params make_params(const dg_mesh *mesh, int p, const dg_eos *eos, double 
   q.eta_y = o.c_ip * P1 * P1 / hy;
   q.gravity = o.gravity != 0;
   q.check_finite = o.check_finite != 0;
+  q.grad_lift = o.grad_lift != 0;
   return q;
 }
 

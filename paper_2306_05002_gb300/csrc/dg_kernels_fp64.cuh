@@ -154,6 +154,31 @@ k_volume(const Params prm, const double *__restrict__ w, double *__restrict__ rv
     }
   }
 
+  // The transport term keeps the broken gradients; with grad_lift the gradients of phi and psi
+  // become BR1-lifted: at a face node, M^-1 w_f (f+ - f-) / 2 along the outward normal, f+ the
+  // neighbour's value at the coincident node (none at walls and pressure boundaries).
+  const double bpx = gpx, bpy = gpy, bsx = gsx, bsy = gsy;
+  if (prm.grad_lift && act && (i == 0 || i == P || (DIM == 2 && (j == 0 || j == P)))) {
+    const OpsLayout Lo{P1, NP};
+    const double im = __ldg(prm.ops + Lo.invM() + a);
+    auto lift = [&](int f, int kk, double &gx_phi, double &gx_psi, double sgn) {
+      const int e2 = neighbour(prm, e, f);
+      if (e2 < 0) return;
+      const int f2 = f ^ 1;
+      const int a2 = f2 == 0 ? P1 * kk : f2 == 1 ? P + P1 * kk : f2 == 2 ? kk : kk + P1 * P;
+      const long n2 = (long)e2 * NP + a2;
+      const double wf = DIM == 2 ? __ldg(prm.ops + (f < 2 ? Lo.wfx() : Lo.wfy()) + kk) : 1.0;
+      const double c = sgn * 0.5 * im * wf;
+      gx_phi += c * (__ldg(w + (long)PHI * N + n2) - phi);
+      gx_psi += c * (__ldg(w + (long)PSI * N + n2) - psi);
+    };
+    const int kx = DIM == 2 ? j : 0;
+    if (i == 0) lift(0, kx, gpx, gsx, -1.0);
+    if (i == P) lift(1, kx, gpx, gsx, 1.0);
+    if (DIM == 2 && j == 0) lift(2, i, gpy, gsy, -1.0);
+    if (DIM == 2 && j == P) lift(3, i, gpy, gsy, 1.0);
+  }
+
   // Interface normal from the level set (zero where |grad psi| < 1e-12).
   const double g2 = gsx * gsx + gsy * gsy;
   double nx = 0.0, ny = 0.0;
@@ -227,9 +252,9 @@ k_volume(const Params prm, const double *__restrict__ w, double *__restrict__ rv
     }
     R[eq == 0 ? PHI : eq + 1] = acc;
   }
-  // Non-conservative transport of phi and psi (Sec. 3: treated as a source).
-  R[PHI] -= u * gpx + v * gpy;
-  R[PSI] = -(u * gsx + v * gsy);
+  // Non-conservative transport of phi and psi (Sec. 3: treated as a source), broken gradients.
+  R[PHI] -= u * bpx + v * bpy;
+  R[PSI] = -(u * bsx + v * bsy);
   if (prm.gravity) {
     R[RU] += rho * prm.gx;
     R[RV] += rho * prm.gy;

@@ -76,6 +76,7 @@ extern "C" dg_status dg_rhs_noalloc(const dg_mesh *mesh, int p, const dg_eos *eo
   if (check_problem(mesh, p, eos, Gamma, eps, &code)) return code;
   const dg_opts o = normalised_opts(opts);
   if (o.prec != DG_FP64) return o.prec == DG_FP32_BULK ? DG_ERR_UNSUPPORTED : DG_ERR_ARG;
+  if (o.grad_lift != 0 && o.grad_lift != 1) return DG_ERR_ARG;
   KernelSet ks;
   if (!kernels_fp64(p, mesh->dim, o.viscous != 0, o.surface_tension != 0, &ks)) return DG_ERR_UNSUPPORTED;
 

@@ -4,7 +4,7 @@ that already holds all device memory).  Its scratch is a fixed file-scope device
 every call, so these tests check that its output matches dg_rhs (the context-based entry point)
 on calls in a row -- each call must not be affected by what the one before left in the shared
 array -- over every kernel family it reaches (orders 1 to 5, 1D and 2D, viscous stress, gravity,
-surface tension, walls, the pressure boundary), and that a problem too large for the array, or
+surface tension, walls, the pressure boundary, lifted gradients), and that a problem too large for the array, or
 one it does not cover, is refused before any GPU work.
 
 This file is collected last on purpose: if it fails, a run that stops at the first failure has
@@ -46,7 +46,20 @@ CASES = {
     "rayleigh_taylor_8x8_p4": lambda: W.rayleigh_taylor(n=8, p=4, seed=3),
     # the paper's Rayleigh-Taylor domain: slip sides, no-slip bottom, pressure top
     "rt_paper_4x12_p4": lambda: W.rayleigh_taylor_paper(nx=4, ny=12, p=4),
+    # BR1-lifted gradients on a state that jumps at every face
+    "drop_lifted_8x8_p3": lambda: _jumping(W.drop_2d(n=8, p=3, seed=5), lift=True),
 }
+
+
+def _jumping(wl, lift):
+    """The workload with its phase field and level set perturbed node by node (seeded)."""
+    rng = np.random.default_rng(9)
+    w = np.array(wl.w)
+    w[0] = np.clip(w[0] + 0.05 * rng.uniform(-1, 1, wl.N), 0.0, 1.0)
+    w[1] = w[1] + 0.05 * rng.uniform(-1, 1, wl.N)
+    wl.w = W.conserved(wl, w[0], w[1], 1e5, 1.0, 0.5)
+    wl.grad_lift = lift
+    return wl
 
 
 def _noalloc_vs_rhs(pkg, f, wl, stream):
