@@ -154,8 +154,10 @@ dg_status dg_rhs(dg_ctx *ctx, const double *w, double *L, void *stream);
 
 /* Advance w (device, in place) by nsteps steps of the three-stage SSP
    Runge-Kutta method (Shu-Osher form) with step dt > 0.  nsteps = 0 is a
-   no-op.  The step sequence is captured once in a CUDA graph per (w, dt)
-   pair and replayed; the first call for a new pair pays the capture. */
+   no-op.  The step sequence is captured once in a CUDA graph per state array
+   w and replayed; the first call for a new w pays the capture.  The graphs
+   read the step size from device memory (set on stream when dt changes), so a
+   caller that varies dt from call to call pays no capture for it. */
 dg_status dg_step(dg_ctx *ctx, double *w, double dt, int nsteps, void *stream);
 
 /* dg_step on a HOST state w_host (dg_state_len doubles); returns when
@@ -235,6 +237,21 @@ size_t dg_tape_len(const dg_ctx *ctx);
 dg_status dg_step_tape(dg_ctx *ctx, double *w, double dt, double *tape, void *stream);
 dg_status dg_adjoint_step_tape(dg_ctx *ctx, const double *w_n, const double *tape, const double *lam_np1,
                                double *lam_n, double dt, void *stream);
+
+/* One checkpoint segment of a reverse sweep in a single call: from the
+   segment's checkpoint w_start (device, dg_state_len doubles), replay m taped
+   SSP-RK3 steps of size dt, keeping each step's start in states (device,
+   (m + 1) * dg_state_len doubles; states[j] = w_j, states[m] = the segment's
+   end) and its tape in tapes (device, m * dg_tape_len doubles), then run the m
+   reverse steps, lam <- (d w_{j+1} / d w_j)^T lam from j = m - 1 down to 0, in
+   place on lam (device, dg_state_len doubles).  The sequence is captured in a
+   CUDA graph on the first call for a given (m, dt, states, tapes, lam) and
+   replayed (the context keeps two such graphs), so a sweep's launches do not
+   depend on the caller's issue rate.  Same availability as dg_rhs_vjp.
+   Asynchronous on stream.  No Sec. of the paper corresponds: this is the
+   checkpointed driver of the discrete adjoint. */
+dg_status dg_adjoint_segment(dg_ctx *ctx, const double *w_start, int m, double dt, double *states, double *tapes,
+                             double *lam, void *stream);
 
 /* Batched ensemble: n independent 2D problems (each with its own mesh, order
    p[k] in 1..5, closure eos[k], Gamma[k], eps[k]) advanced together by the

@@ -32,8 +32,8 @@ PREC = {"fp64": 0, "fp32bulk": 1}
 EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_step_host", "dg_diag",
            "dg_status_read", "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc", "dg_batch_create",
            "dg_batch_step", "dg_rhs_vjp", "dg_adjoint_step", "dg_tape_len", "dg_step_tape",
-           "dg_adjoint_step_tape", "dg_batch_tiles", "dg_kin_create", "dg_kin_rhs", "dg_kin_step", "dg_kin_nodes",
-           "dg_reinit"]
+           "dg_adjoint_step_tape", "dg_adjoint_segment", "dg_batch_tiles", "dg_kin_create", "dg_kin_rhs",
+           "dg_kin_step", "dg_kin_nodes", "dg_reinit"]
 
 
 class DGError(RuntimeError):
@@ -135,6 +135,8 @@ def load(path: str | None = None):
     lib.dg_step_tape.restype = ctypes.c_int
     lib.dg_adjoint_step_tape.argtypes = [vp, dp, dp, dp, dp, ctypes.c_double, vp]
     lib.dg_adjoint_step_tape.restype = ctypes.c_int
+    lib.dg_adjoint_segment.argtypes = [vp, dp, ctypes.c_int, ctypes.c_double, dp, dp, dp, vp]
+    lib.dg_adjoint_segment.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -265,6 +267,14 @@ class Solver:
         _check(self.ctx, load().dg_adjoint_step_tape(self.ctx, _ptr(w_n), _ptr(tape), _ptr(lam_np1), _ptr(lam_n),
                                                      float(dt), _stream(stream)), "dg_adjoint_step_tape")
         return lam_n
+
+    def dg_adjoint_segment(self, w_start, m: int, dt: float, states, tapes, lam, stream=None):
+        """One checkpoint segment of a reverse sweep: m taped steps from w_start (states: (m + 1)
+        state rows, tapes: m tape rows, both contiguous float64 CUDA buffers), then lam <- the
+        transpose of the segment's Jacobian applied to lam, in place."""
+        _check(self.ctx, load().dg_adjoint_segment(self.ctx, _ptr(w_start), int(m), float(dt), _ptr(states),
+                                                   _ptr(tapes), _ptr(lam), _stream(stream)), "dg_adjoint_segment")
+        return lam
 
     def dg_reinit(self, w, niter: int = 50, nu: float = 0.0, dtau: float = 0.0, stream=None):
         """Re-initialise the level set of w in place (end of Sec. 3; nu, dtau <= 0: defaults)."""

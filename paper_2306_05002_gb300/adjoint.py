@@ -2,9 +2,10 @@
 
 Checkpointing (revolve-style, one level): the forward sweep keeps the state every
 `every` steps; the reverse sweep replays each segment from its checkpoint (storing
-the segment's states) and runs ``dg_adjoint_step`` back through it.  Every step and
-every adjoint step runs in the library's kernels; this module only orders the calls
-and keeps the checkpoints (device memory).
+the segment's states and tapes) and runs the adjoint steps back through it, one
+``dg_adjoint_segment`` call per segment.  Every step and every adjoint step runs in
+the library's kernels; this module only orders the calls and keeps the checkpoints
+(device memory).
 """
 from __future__ import annotations
 
@@ -29,34 +30,34 @@ def forward(solver, w0, dt: float, nsteps: int, every: int = 20):
 def backward(solver, ckpt, lam_N, dt: float, nsteps: int, every: int = 20, tape: bool = True):
     """lam_0 = (d w_N / d w_0)^T lam_N by segment replay and adjoint steps.
 
-    tape=True replays each segment with dg_step_tape (the stages and face traces of every
-    step are kept) and reverses with dg_adjoint_step_tape; tape=False keeps only the states
-    and lets dg_adjoint_step recompute the stages."""
+    tape=True runs each checkpoint segment through dg_adjoint_segment (one call, one captured
+    graph per segment length: the replay with dg_step_tape keeping every step's start and tape,
+    then dg_adjoint_step_tape back through them); tape=False keeps only the states and lets
+    dg_adjoint_step recompute the stages, one call per step."""
     lam = lam_N.clone()
-    work = torch.empty_like(lam)
     starts = sorted(s for s in ckpt if s < nsteps)
-    seg_states, tapes = [], []
-    tl = solver.dg_tape_len() if tape else 0
+    if tape:
+        m_max = min(every, nsteps)
+        states = torch.empty((m_max + 1,) + tuple(lam.shape), dtype=lam.dtype, device=lam.device)
+        tapes = torch.empty((m_max, solver.dg_tape_len()), dtype=lam.dtype, device=lam.device)
+        for s0 in reversed(starts):
+            m = min(s0 + every, nsteps) - s0
+            solver.dg_adjoint_segment(ckpt[s0], m, dt, states, tapes, lam)
+        return lam
+    work = torch.empty_like(lam)
+    seg_states = []
     for s0 in reversed(starts):
-        s1 = min(s0 + every, nsteps)
-        m = s1 - s0
+        m = min(s0 + every, nsteps) - s0
         while len(seg_states) < m:
             seg_states.append(torch.empty_like(lam))
-            if tape:
-                tapes.append(torch.empty(tl, dtype=lam.dtype, device=lam.device))
-        # replay the segment from its checkpoint, keeping w_{s0}, ..., w_{s1-1} (and the tapes)
+        # replay the segment from its checkpoint, keeping w_{s0}, ..., w_{s1-1}
         work.copy_(ckpt[s0])
         for j in range(m):
             seg_states[j].copy_(work)
-            if tape:
-                solver.dg_step_tape(work, dt, tapes[j])
-            elif j < m - 1:
+            if j < m - 1:
                 solver.dg_step(work, dt, 1)
         for j in reversed(range(m)):
-            if tape:
-                solver.dg_adjoint_step_tape(seg_states[j], tapes[j], lam, dt, lam_n=lam)
-            else:
-                solver.dg_adjoint_step(seg_states[j], lam, dt, lam_n=lam)
+            solver.dg_adjoint_step(seg_states[j], lam, dt, lam_n=lam)
     return lam
 
 

@@ -67,6 +67,9 @@ bool kernels_fp32(int p, int dim, bool viscous, bool st, KernelSet32 *out) {
   }
 }
 
+// One value into device memory, in stream order (the step size of the captured dg_step graphs).
+__global__ void k_set_double(double *dst, double v) { *dst = v; }
+
 bool adj_kernels_p1(int, AdjKernels *);
 bool adj_kernels_p2(int, AdjKernels *);
 bool adj_kernels_p3(int, AdjKernels *);
@@ -248,8 +251,17 @@ struct dg_ctx {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t g1 = nullptr, gk = nullptr;
   cudaGraphExec_t grem[8] = {};  // FP32-bulk: graphs of 1..7 steps, captured on first use
+  // dg_adjoint_segment: captured segment sweeps, keyed by (steps, dt, states, tapes, lam)
+  struct SegGraph {
+    cudaGraphExec_t exec = nullptr;
+    int m = 0;
+    double dt = 0.0;
+    const double *states = nullptr, *tapes = nullptr, *lam = nullptr;
+  } seg[2];
   const double *g_w = nullptr;
   double g_dt = 0.0;
+  double *d_dt = nullptr;      // the step size the captured dg_step graphs read
+  double dt_set = 0.0;         // the value last written there (0: none)
   std::string err = "no error";
 };
 
@@ -277,9 +289,17 @@ static void free_graphs(dg_ctx *c) {
   c->g_w = nullptr;
 }
 
+static void free_seg_graphs(dg_ctx *c) {
+  for (auto &g : c->seg) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = dg_ctx::SegGraph{};
+  }
+}
+
 static void free_ctx(dg_ctx *c) {
   if (!c) return;
   free_graphs(c);
+  free_seg_graphs(c);
   if (c->batch) {
     for (auto &g : c->batch->groups) {
       cudaFree(g.d_probs);
@@ -302,6 +322,7 @@ static void free_ctx(dg_ctx *c) {
   cudaFree(c->d_part);
   cudaFree(c->d_diag);
   cudaFree(c->d_status);
+  cudaFree(c->d_dt);
   cudaFree(c->d_trbar);
   cudaFree(c->d_lam1);
   cudaFree(c->d_lam2);
@@ -408,6 +429,7 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
                       (e = cudaMalloc(&c->d_lam1, sbytes)) != cudaSuccess ||
                       (e = cudaMalloc(&c->d_lam2, sbytes)) != cudaSuccess)) ||
       (e = cudaMalloc(&c->d_diag, DIAG_N * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_dt, sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&c->d_status, sizeof(unsigned))) != cudaSuccess) {
     free_ctx(c);
     cudaGetLastError();
@@ -439,10 +461,11 @@ extern "C" size_t dg_state_len(const dg_ctx *c) { return c ? c->len : 0; }
 extern "C" const char *dg_last_error(const dg_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 
 static dg_status run_stage(dg_ctx *c, int mode, double dt, const double *w0, const double *ws, double *out,
-                           cudaStream_t s) {
-  cudaError_t e = c->ks.volume(c->prm, ws, c->d_rvol, c->d_trace, s);
+                           cudaStream_t s, const Params *prm = nullptr) {
+  const Params &q = prm ? *prm : c->prm;
+  cudaError_t e = c->ks.volume(q, ws, c->d_rvol, c->d_trace, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "volume kernel launch");
-  e = c->ks.surface(c->prm, mode, dt, w0, ws, c->d_rvol, c->d_trace, out, s);
+  e = c->ks.surface(q, mode, dt, w0, ws, c->d_rvol, c->d_trace, out, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "surface kernel launch");
   return DG_OK;
 }
@@ -473,11 +496,14 @@ extern "C" dg_status dg_rhs(dg_ctx *c, const double *w, double *L, void *stream)
 // One SSP-RK3 step (Shu-Osher): w1 = w + dt L(w); w2 = 3/4 w + 1/4 (w1 + dt L(w1));
 // w <- 1/3 w + 2/3 (w2 + dt L(w2)).  The last stage writes w in place (each
 // node's w0 value is read by the thread that overwrites it).
+// The captured sequences read dt from c->d_dt at run time, so a new dt needs no new capture.
 static dg_status enqueue_step(dg_ctx *c, double *w, double dt, cudaStream_t s) {
   dg_status r;
-  if ((r = run_stage(c, MODE_S1, dt, w, w, c->d_w1, s)) != DG_OK) return r;
-  if ((r = run_stage(c, MODE_S2, dt, w, c->d_w1, c->d_w2, s)) != DG_OK) return r;
-  return run_stage(c, MODE_S3, dt, w, c->d_w2, w, s);
+  Params q = c->prm;
+  q.dt_dev = c->d_dt;
+  if ((r = run_stage(c, MODE_S1, dt, w, w, c->d_w1, s, &q)) != DG_OK) return r;
+  if ((r = run_stage(c, MODE_S2, dt, w, c->d_w1, c->d_w2, s, &q)) != DG_OK) return r;
+  return run_stage(c, MODE_S3, dt, w, c->d_w2, w, s, &q);
 }
 
 // `steps` FP32-bulk steps with the fused stage kernel: 1 + 3 steps launches.
@@ -502,10 +528,10 @@ static dg_status enqueue_steps32(dg_ctx *c, double *w, float dt, int steps, cuda
   for (int k = 0; k < steps; ++k) {
     const bool last = k == steps - 1;
     const StageIO io[3] = {
-        {H[a], nullptr, nullptr, D[0], nullptr, nullptr, nullptr, nullptr},
-        {H[a], nullptr, D[0], D[1], nullptr, nullptr, nullptr, nullptr},
+        {H[a], nullptr, nullptr, D[0], nullptr, nullptr, nullptr, nullptr, c->d_dt},
+        {H[a], nullptr, D[0], D[1], nullptr, nullptr, nullptr, nullptr, c->d_dt},
         {H[a], Lo[a], D[1], nullptr, last ? nullptr : H[a ^ 1], last ? nullptr : Lo[a ^ 1], last ? w : nullptr,
-         steps == 1 ? w : nullptr}};
+         steps == 1 ? w : nullptr, c->d_dt}};
     const int mode[3] = {MODE_S1, MODE_S2, MODE_S3};
     for (int st = 0; st < 3; ++st) {
       if (st == 2 && last) {
@@ -548,16 +574,20 @@ extern "C" dg_status dg_step(dg_ctx *c, double *w, double dt, int nsteps, void *
   if (!w) return fail(c, DG_ERR_ARG, "dg_step: null state");
   if (!(dt > 0.0) || nsteps < 0) return fail(c, DG_ERR_ARG, "dg_step: need dt > 0 and nsteps >= 0");
   if (nsteps == 0) return DG_OK;
-  if (c->g_w != w || c->g_dt != dt || !c->g1) {
+  if (c->g_w != w || !c->g1) {
     free_graphs(c);
     dg_status r;
     if ((r = capture(c, w, dt, 1, &c->g1)) != DG_OK) return r;
     if ((r = capture(c, w, dt, GRAPH_UNROLL, &c->gk)) != DG_OK) return r;
     c->g_w = w;
-    c->g_dt = dt;
   }
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
+  if (dt != c->dt_set) {  // the graphs read the step size from device memory
+    k_set_double<<<1, 1, 0, s>>>(c->d_dt, dt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "dg_step: set dt");
+    c->dt_set = dt;
+  }
   for (int k = 0; k < nsteps / GRAPH_UNROLL; ++k)
     if ((e = cudaGraphLaunch(c->gk, s)) != cudaSuccess) return cuda_fail(c, e, "dg_step: graph launch");
   const int rem = nsteps % GRAPH_UNROLL;
@@ -1482,4 +1512,68 @@ extern "C" dg_status dg_adjoint_step_tape(dg_ctx *c, const double *w_n, const do
   if (e == cudaSuccess) e = vjp(w1, tr[1], c->d_lam2, c->d_lam1, 0.25, c->d_lam2, 0.25 * dt, 0.0, nullptr, 0.0, nullptr);
   if (e == cudaSuccess) e = vjp(w_n, tr[0], c->d_lam1, lam_n, 1.0, c->d_lam1, dt, 1.0 / 3.0, lam_np1, 0.75, c->d_lam2);
   return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_adjoint_step_tape: kernel launch");
+}
+
+// One checkpoint segment of a reverse sweep: replay m taped steps from
+// states[0] (each step's start kept in states[j]), then m adjoint steps back
+// through them, lam updated in place.  The whole sequence is one CUDA graph,
+// captured on the first call for (m, dt, states, tapes, lam) and replayed.
+static dg_status enqueue_segment(dg_ctx *c, int m, double dt, double *states, double *tapes, double *lam,
+                                 cudaStream_t s) {
+  const size_t len = c->len, tl = dg_tape_len(c);
+  for (int j = 0; j < m; ++j) {
+    cudaError_t e = cudaMemcpyAsync(states + (j + 1) * len, states + j * len, len * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_adjoint_segment: copy");
+    const dg_status r = dg_step_tape(c, states + (j + 1) * len, dt, tapes + j * tl, s);
+    if (r != DG_OK) return r;
+  }
+  for (int j = m - 1; j >= 0; --j) {
+    const dg_status r = dg_adjoint_step_tape(c, states + j * len, tapes + j * tl, lam, lam, dt, s);
+    if (r != DG_OK) return r;
+  }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_adjoint_segment(dg_ctx *c, const double *w_start, int m, double dt, double *states,
+                                        double *tapes, double *lam, void *stream) {
+  if (!c) return DG_ERR_ARG;
+  dg_status r = adj_check(c, "dg_adjoint_segment");
+  if (r != DG_OK) return r;
+  if (!w_start || !states || !tapes || !lam) return fail(c, DG_ERR_ARG, "dg_adjoint_segment: null array");
+  if (m < 1 || !(dt > 0.0)) return fail(c, DG_ERR_ARG, "dg_adjoint_segment: need m >= 1 and dt > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(states, w_start, c->len * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_adjoint_segment: copy");
+  dg_ctx::SegGraph *g = nullptr;
+  for (auto &x : c->seg)
+    if (x.exec && x.m == m && x.dt == dt && x.states == states && x.tapes == tapes && x.lam == lam) g = &x;
+  if (!g) {
+    g = !c->seg[0].exec ? &c->seg[0] : !c->seg[1].exec ? &c->seg[1] : &c->seg[0];
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    *g = dg_ctx::SegGraph{};
+    cudaGraph_t graph = nullptr;
+    if ((e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(c, e, "dg_adjoint_segment: begin capture");
+    r = enqueue_segment(c, m, dt, states, tapes, lam, c->cap);
+    e = cudaStreamEndCapture(c->cap, &graph);
+    if (r != DG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return r;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_adjoint_segment: end capture");
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g->exec = nullptr;
+      return cuda_fail(c, e, "dg_adjoint_segment: instantiate");
+    }
+    g->m = m;
+    g->dt = dt;
+    g->states = states;
+    g->tapes = tapes;
+    g->lam = lam;
+  }
+  if ((e = cudaGraphLaunch(g->exec, s)) != cudaSuccess) return cuda_fail(c, e, "dg_adjoint_segment: graph launch");
+  return DG_OK;
 }

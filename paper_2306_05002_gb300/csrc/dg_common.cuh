@@ -48,6 +48,7 @@ struct Params {
   int grad_lift;             // BR1-lifted gradients of phi and psi (dg_opts.grad_lift)
   const double *ops;         // operator tables, see OpsLayout
   unsigned *status;          // latched device status bits
+  const double *dt_dev;      // step size read at run time (captured step sequences), else NULL
 };
 
 // Layout of the per-context operator table (device memory, doubles):

@@ -138,6 +138,7 @@ struct StageIO {
   float *dout, *hi_out, *lo_out;
   double *out64;
   const double *w64in;
+  const double *dt_dev;  // step size read at run time (captured step sequences), else NULL
 };
 
 // (hi, lo) + d in float-float arithmetic: Knuth's two-sum of hi and d, the
@@ -721,6 +722,7 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   __syncthreads();
   const float *Dx = s_op + L.Dx(), *Dy = s_op + L.Dy();
   const float *invM = s_op + L.invM(), *wfx = s_op + L.wfx(), *wfy = s_op + L.wfy();
+  if (io.dt_dev) dt = (float)ld_in<PDL>(io.dt_dev);
 
 #pragma unroll
   for (int fi = 0; fi < FPT; ++fi) {

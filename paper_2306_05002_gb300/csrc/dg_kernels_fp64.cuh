@@ -462,6 +462,7 @@ k_surface(const Params prm, int mode, double dt, const double *__restrict__ w0, 
   const double im = invM[a];
   const long n = (long)e * NP + a;
   const int N = prm.N;
+  if (prm.dt_dev) dt = __ldg(prm.dt_dev);
   bool bad = false;
 #pragma unroll
   for (int vv = 0; vv < NV; ++vv) {

@@ -290,3 +290,23 @@ def test_nonfinite_flag(dg):
     assert s.dg_status_read() == -5
     assert s.dg_status_read() == 0  # cleared
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32bulk"])
+def test_step_size_changes_between_calls(dg, precision):
+    """The captured step graphs read dt from device memory: calls with alternating step sizes on one
+    context give exactly what fresh contexts give for each sequence of step sizes."""
+    import torch
+    wl = W.drop_2d(n=8, p=3, seed=3)
+    dts = [wl.dt, 0.5 * wl.dt, wl.dt, 0.25 * wl.dt]
+    s = dg.Solver(wl, precision=precision)
+    a = torch.from_numpy(wl.w.copy()).cuda()
+    for k, dt in enumerate(dts):
+        s.dg_step(a, dt, 1 + k % 3)  # single steps and multi-step graphs
+    s.close()
+    b = torch.from_numpy(wl.w.copy()).cuda()
+    for k, dt in enumerate(dts):
+        f = dg.Solver(wl, precision=precision)
+        f.dg_step(b, dt, 1 + k % 3)
+        f.close()
+    assert torch.equal(a, b)
