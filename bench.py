@@ -192,8 +192,30 @@ def peaks():
         return {}
 
 
-# FP64 ALU peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 FMA peak: measured on the GPU by the library's FMA-chain probe (dg_peak_flops) at the start
+# of the run; before that (or if the probe fails), the figure from unit counts and clock:
+# 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9 / 1e12
+MEASURED_PIPES = {}
+
+
+def fp64_peak():
+    return MEASURED_PIPES.get("fp64_tflops", FP64_PEAK_DERIVED)
+
+
+def fp64_peak_source():
+    if "fp64_tflops" in MEASURED_PIPES:
+        return "measured: dg_peak_flops FP64 FMA chains on this GPU (every resident thread, 8 chains), of measured"
+    return "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (ncu: 2 DFMA/clk/SM)"
+
+
+def measure_pipes(dg):
+    """FP64 and FP32 FMA rates of this GPU (best of three probe runs each)."""
+    try:
+        MEASURED_PIPES["fp64_tflops"] = max(dg.peak_flops("fp64") for _ in range(3))
+        MEASURED_PIPES["fp32_tflops"] = max(dg.peak_flops("fp32") for _ in range(3))
+    except Exception as exc:  # report the derived figure instead
+        MEASURED_PIPES["error"] = str(exc)[:200]
 
 
 # Per-unit algorithmic figures.  FP32-bulk (HBM-bound): 168 B per node and RK stage -- read the
@@ -219,10 +241,9 @@ def roofline(precision, names, kms, flops, bytes_, nodes):
     dom = max(range(n), key=lambda i: kms[i] * per_step[i])
     if precision == "fp64":
         ach = flops[dom] / (kms[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": names[dom], "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "per_unit": "dg_kernel_costs flops per launch",
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (ncu: 2 DFMA/clk/SM)"}
+        roof = {"bound": "alu", "kernel": names[dom], "achieved": ach, "peak": fp64_peak(),
+                "unit": "TFLOP/s", "frac": ach / fp64_peak(),
+                "per_unit": "dg_kernel_costs flops per launch", "peak_source": fp64_peak_source()}
     else:
         dom = names.index("k_surfvol32")
         hbm = peaks().get("hbm_gbs", 6800.0)
@@ -610,7 +631,7 @@ def reinit_block(dg, iters, n=64):
             "ms_per_iteration": per_iter, "ms_total": ms, "gpu_launches": 1 + 6 * iters,
             "device_status": status,
             "roofline": {"bound": "alu", "kernel": "k_ri_volume + k_ri_surface", "achieved": ach,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                         "peak": fp64_peak(), "unit": "TFLOP/s", "frac": ach / fp64_peak(),
                          "per_unit": f"{reinit_flops_per_node_stage(wl.p)} flops per node and stage x {wl.N} nodes",
                          "duration": "call time / iterations / 3 stages (gaps included)"}}
 
@@ -655,7 +676,7 @@ def kinematic_block(dg, steps, n=64):
             "nodes": wl.N, "steps": steps, "ms_per_step": ms, "value": 2 * 4 * wl.N / (ms * 1e-3), "unit": UNIT,
             "gpu_launches_per_step": 4,
             "roofline": {"bound": "alu", "kernel": "k_kin_stage", "achieved": ach,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                         "peak": fp64_peak(), "unit": "TFLOP/s", "frac": ach / fp64_peak(),
                          "per_unit": f"{kin_flops_per_node_stage(wl.p)} flops per node and stage x {wl.N} nodes",
                          "duration": "step time / 4 (one kernel per stage in a graph; gaps included)"},
             "full_period_16x16p3": {"steps": small.nsteps, "wall_s": wall,
@@ -753,8 +774,8 @@ def triangle_block(dg, steps, n=64):
                         f"Gamma=1, FP64, classical RK4",
             "nodes": wl.N, "steps": steps, "ms_per_step": ms, "value": 2 * 4 * wl.N / (ms * 1e-3), "unit": UNIT,
             "gpu_launches_per_step": 4,
-            "roofline": {"bound": "alu", "kernel": "k_tri_stage", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+            "roofline": {"bound": "alu", "kernel": "k_tri_stage", "achieved": ach, "peak": fp64_peak(),
+                         "unit": "TFLOP/s", "frac": ach / fp64_peak(),
                          "per_unit": f"{tri_flops_per_stage(wl.p)} flops per triangle and stage x {wl.E} triangles",
                          "duration": "step time / 4 (graph of back-to-back stage kernels; gaps included)"},
             "full_period_16x16p3": {"steps": small.nsteps, "wall_s": wall, "l1_phi": l1,
@@ -822,6 +843,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     wl = workload(2 + rank)
+    measure_pipes(dg)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     other = "fp64" if args.precision == "fp32bulk" else None
@@ -881,7 +903,8 @@ def run_ours(args, rank, world, local_rank):
                 "roofline": roof,
                 "e2e": {"value": units * e2e_steps * world / e2e_max, "unit": UNIT,
                         "h2d_bytes_per_step": 8 * 7 * wl.N, "d2h_bytes_per_step": 8 * 7 * wl.N},
-                "clocks": main["clocks"], "device_status": main["status"]}
+                "clocks": main["clocks"], "device_status": main["status"],
+                "pipe_peaks": dict(MEASURED_PIPES, fp64_derived_tflops=FP64_PEAK_DERIVED)}
         if ref:
             line["fp64"] = {"value": units * args.steps * world / (ref_ms * 1e-3), "unit": UNIT,
                             "ms_per_step": ref_ms / args.steps, "kernel_ms": dict(zip(["k_volume", "k_surface"],

@@ -370,6 +370,13 @@ dg_status dg_kin_step(dg_ctx *ctx, double *w, double t0, double dt, int nsteps, 
    gives DG_ERR_UNSUPPORTED.  Asynchronous on stream. */
 dg_status dg_reinit(dg_ctx *ctx, double *w, int niter, double nu, double dtau, void *stream);
 
+/* Measured multiply-add rate of the current GPU in TFLOP/s (2 flops per FMA):
+   kind 0 FP64, kind 1 FP32; every resident thread runs 8 independent FMA
+   chains for iters rounds, timed with CUDA events on stream (synchronises
+   it).  The roofline denominators of the FP64 kernels.  No Sec. of the paper
+   corresponds.  DG_ERR_ARG for a bad kind, iters < 1 or a NULL output. */
+dg_status dg_peak_flops(int kind, int iters, double *tflops, void *stream);
+
 /* Size of the fixed device scratch used by dg_rhs_noalloc (32 MiB per GPU). */
 #define DG_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 

@@ -33,7 +33,7 @@ EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_s
            "dg_status_read", "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc", "dg_batch_create",
            "dg_batch_step", "dg_rhs_vjp", "dg_adjoint_step", "dg_tape_len", "dg_step_tape",
            "dg_adjoint_step_tape", "dg_adjoint_segment", "dg_batch_tiles", "dg_kin_create", "dg_kin_rhs",
-           "dg_kin_step", "dg_kin_nodes", "dg_reinit"]
+           "dg_kin_step", "dg_kin_nodes", "dg_reinit", "dg_peak_flops"]
 
 
 class DGError(RuntimeError):
@@ -137,8 +137,19 @@ def load(path: str | None = None):
     lib.dg_adjoint_step_tape.restype = ctypes.c_int
     lib.dg_adjoint_segment.argtypes = [vp, dp, ctypes.c_int, ctypes.c_double, dp, dp, dp, vp]
     lib.dg_adjoint_segment.restype = ctypes.c_int
+    lib.dg_peak_flops.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
+    lib.dg_peak_flops.restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+def peak_flops(kind: str = "fp64", iters: int = 0, stream=None) -> float:
+    """Measured FMA rate of the current GPU in TFLOP/s (dg_peak_flops): kind "fp64" or "fp32"."""
+    k = {"fp64": 0, "fp32": 1}[kind]
+    out = ctypes.c_double()
+    n = iters or (20000 if k == 0 else 400000)
+    _check(None, load().dg_peak_flops(k, n, ctypes.byref(out), _stream(stream)), "dg_peak_flops")
+    return out.value
 
 
 def _check(ctx, status, what):

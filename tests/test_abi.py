@@ -208,3 +208,12 @@ def test_noalloc_rejects_triangles_before_gpu_work(lib):
     m.elem = 2
     assert f(ctypes.byref(m), 3, ctypes.byref(eos), 1.0, 0.05, ctypes.byref(o), 16, 4096, None) == -1
 
+
+
+def test_peak_probe_rejects_invalid_arguments(lib):
+    """Checked before any GPU work."""
+    import ctypes
+    out = ctypes.c_double()
+    assert lib.dg_peak_flops(2, 100, ctypes.byref(out), None) == -1
+    assert lib.dg_peak_flops(0, 0, ctypes.byref(out), None) == -1
+    assert lib.dg_peak_flops(0, 100, None, None) == -1

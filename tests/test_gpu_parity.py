@@ -310,3 +310,12 @@ def test_step_size_changes_between_calls(dg, precision):
         f.dg_step(b, dt, 1 + k % 3)
         f.close()
     assert torch.equal(a, b)
+
+
+def test_peak_flops_probe(dg):
+    """The FMA-chain probe behind the FP64 rooflines: positive, FP64 within the range GB300-class
+    parts have (0.1 to 100 TFLOP/s) and FP32 well above FP64 (the reduced FP64 pipe)."""
+    f64 = dg.peak_flops("fp64")
+    f32 = dg.peak_flops("fp32")
+    assert 0.1 < f64 < 100.0, f64
+    assert f32 > 10.0 * f64, (f32, f64)
