@@ -398,8 +398,9 @@ dg_status dg_peak_flops(int kind, int iters, double *tflops, void *stream);
    DG_FP32_BULK gives DG_ERR_UNSUPPORTED; the device status word is not
    reported.
    The first call on a device looks up the array's device address on that
-   device (it loads the library's module there); make that first call before
-   any stream capture.  Every call uses the same array and leaves its contents
+   device (loading the library's module there if needed).  The operator table
+   reaches the device as a kernel argument, not by a copy from host memory.
+   Every call uses the same array and leaves its contents
    behind; the call writes its operator table and clears what must start at
    zero itself.  Calls whose work overlaps on the GPU (other streams, other
    host threads) race on the scratch: serialise them.  Asynchronous on

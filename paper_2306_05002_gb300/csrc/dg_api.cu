@@ -509,9 +509,10 @@ static dg_status enqueue_step(dg_ctx *c, double *w, double dt, cudaStream_t s) {
 // `steps` FP32-bulk steps with the fused stage kernel: 1 + 3 steps launches.
 // The volume part of the first stage reads the FP64 state and splits it into
 // the internal step start (hi, lo); the last stage writes hi + lo back.  In
-// between the state stays in FP32 pairs: splitting hi + lo again at a step
-// boundary returns the same pair, so this is the same computation as `steps`
-// separate calls of one step (up to the FP64 rounding of rho E + Cmix(phi)).
+// between the state stays in FP32 pairs, whose sum keeps ~48 bits: a call of
+// several steps differs from as many single-step calls (which add the last
+// increment to the FP64 state in FP64) only by that rounding of each step's
+// sum, far below the FP32 rounding of the increments themselves.
 // Stage 1 writes the increment d1 into D[0], stage 2 reads it and writes d2
 // into D[1], stage 3 adds 2 (d2 + dt L) / 3 to the step start in float-float
 // and writes the new step start into the other buffer of each pair (H, Lo),
