@@ -180,6 +180,68 @@ def test_fp32bulk_conversion_round_trip_keeps_pressure(orc, dg):
 
 
 
+def _split_merge_model(d):
+    """What a call of several FP32-bulk steps hands back for an FP64 value d when every increment
+    is exactly zero, written from the definitions: hi = d rounded to 24 significant bits (ties away
+    from zero, at the 29th bit below the double's last place), lo = d - hi rounded to nearest float,
+    result hi + lo (exact in FP64); magnitudes below 2^-74 (lo would not be a normal float) give a
+    signed zero."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    b = d.view(np.uint64)
+    e = (b >> np.uint64(52)) & np.uint64(0x7FF)
+    low29 = b & np.uint64(0x1FFFFFFF)
+    up = low29 >= np.uint64(1 << 28)
+    bh = (b & ~np.uint64(0x1FFFFFFF)) + np.where(up, np.uint64(1 << 29), np.uint64(0))
+    hi = bh.view(np.float64)
+    assert np.array_equal(hi.astype(np.float32).astype(np.float64), hi)
+    lo = (d - hi).astype(np.float32).astype(np.float64)
+    out = hi + lo
+    return np.where(e < 949, np.copysign(0.0, d), out)
+
+
+def test_fp32bulk_fp64_state_split_and_merge(dg):
+    """The integer-arithmetic split of the FP64 state into float pairs and the merge back (first and
+    last launch of a call of several steps), on a state whose fields span many binades (psi from
+    1e-30, below the split's 2^-74 floor, to 1e2; partial densities from 1e-3 to 1e3; phi with exact
+    0 and 1): with a step size below the smallest float every FP32 increment is exactly zero, so the
+    call must hand back, bit for bit, the model's hi + lo for phi, psi, m_l and rho u; rho E, whose
+    stiffened-gas constant is taken off and put back in FP64, to a few ulps of rho E and Cmix."""
+    import torch
+    wl = W.drop_2d(n=8, p=3, seed=2)
+    rng = np.random.default_rng(11)
+    N = wl.N
+    phi = rng.uniform(0.0, 1.0, N)
+    phi[::17] = 0.0
+    phi[5::17] = 1.0
+    psi = rng.choice([-1.0, 1.0], N) * 10.0 ** rng.uniform(-30, 2, N)
+    m1 = 10.0 ** rng.uniform(-3, 3, N)
+    m2 = 10.0 ** rng.uniform(-3, 3, N)
+    rho = m1 + m2
+    u, v = rng.uniform(-10, 10, N), rng.uniform(-10, 10, N)
+    P = 10.0 ** rng.uniform(0, 6, N)
+    C = [wl.gamma[l] * wl.pinf[l] / (wl.gamma[l] - 1) for l in range(2)]
+    Cmix = phi * C[0] + (1 - phi) * C[1]
+    G = phi / (wl.gamma[0] - 1) + (1 - phi) / (wl.gamma[1] - 1)
+    rE = 0.5 * rho * (u * u + v * v) + Cmix + P * G
+    w = np.stack([phi, psi, m1, m2, rho * u, rho * v, rE])
+    s = dg.Solver(wl, precision="fp32bulk")
+    d = torch.from_numpy(w.copy()).cuda()
+    s.dg_step(d, 1e-300, 3)
+    got = d.cpu().numpy()
+    assert s.dg_status_read() == 0
+    s.close()
+    for k in range(6):
+        want = _split_merge_model(w[k])
+        assert np.array_equal(got[k].view(np.uint64), want.view(np.uint64)), (k, np.abs(got[k] - want).max())
+    assert np.any(got[1] == 0.0) and np.any(got[1] != 0.0)
+    # rho E: Cmix(phi) taken off in FP64, the rest split and merged, Cmix(phi out) put back
+    dC, C2 = C[0] - C[1], C[1]
+    red = rE - (dC * phi + C2)
+    want = _split_merge_model(red) + (dC * got[0] + C2)
+    tol = 8 * np.finfo(np.float64).eps * (np.abs(rE) + abs(C[0]) + abs(C[1])) + 2.0 ** -47 * np.abs(red)
+    assert np.all(np.abs(got[6] - want) <= tol), np.max(np.abs(got[6] - want) / tol)
+
+
 def test_fp32bulk_rayleigh_taylor_physics_tracks_fp64(orc, dg):
     """Walls, viscous stress, gravity and surface tension in the FP32-bulk path: 20 steps of a
     32 x 32, p = 4 Rayleigh-Taylor set-up stay within 1e-5 (relative L2) of the FP64 path in
