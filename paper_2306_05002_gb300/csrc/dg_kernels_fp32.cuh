@@ -965,12 +965,13 @@ k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, 
 // part to the other in registers.  The volume part and the traces go to the
 // other buffer of a pair (rvol_out, tr_out), because neighbouring blocks of
 // the same launch may still read rvol_in and tr_in.
-// Residency of the viscous variants: at most 80 registers a thread (65,536 / (THREADS x 80) CTAs
-// per SM), which the surface-tension variant otherwise exceeds, one CTA per SM fewer and 6% slower
-// at p = 4.
+// Residency of the viscous variants: at most 72 registers a thread (65,536 / (THREADS x 72) CTAs
+// per SM: 7 of 128 threads).  Uncapped, the surface-tension variant needs 90 and runs 6% slower at
+// p = 4 (one CTA per SM fewer); at 72 it spills a few words and runs 2% faster than at 80, and at
+// 64 (more spills) no faster than at 80.
 template <int P, int DIM, bool VISC, bool ST, bool PDL>
 __global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS,
-                                  VISC ? 65536 / (Geom<P, DIM, VISC, ST>::THREADS * 80) : 1)
+                                  VISC ? 65536 / (Geom<P, DIM, VISC, ST>::THREADS * 72) : 1)
 k_surfvol32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt, const StageIO io,
             const float *__restrict__ rvol_in, const float *__restrict__ tr_in, float *__restrict__ rvol_out,
             float *__restrict__ tr_out) {
