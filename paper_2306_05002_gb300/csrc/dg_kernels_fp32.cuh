@@ -658,10 +658,12 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   constexpr int NC = VISC ? NT32_VISCOUS : TRW32;    // words read per trace record
   constexpr int FPT = (NFK + NP - 1) / NP;  // face nodes per thread
   const OpsLayout L{P1, NP};
-  // Per face node: the surface integrand of the 7 equations and the 6 lifting
-  // coefficients, each padded to 8 floats (two 128-bit shared accesses).
-  __shared__ float4 s_surf[EPB][NFK][2];
-  __shared__ float4 s_lift[EPB][NFK][2];
+  // Per face node: the surface integrand of the 7 equations (padded to 8 floats)
+  // and the 6 lifting coefficients, in planes of consecutive face nodes, so that
+  // the face nodes' 128- and 64-bit accesses are consecutive in shared memory.
+  __shared__ float4 s_surf[2][EPB][NFK];
+  __shared__ float4 s_lift0[EPB][NFK];
+  __shared__ float2 s_lift1[EPB][NFK];
 
   const int le_raw = threadIdx.x / NP;
   const bool lane = le_raw < EPB;
@@ -839,10 +841,10 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
       const float tup = tpx * Tp[T_U] + tpy * Tp[T_V];
       S[RE] += wf * (0.5f * (tup - tum) + eta * mua * (kp - km));
     }
-    s_surf[le][t][0] = make_float4(S[0], S[1], S[2], S[3]);
-    s_surf[le][t][1] = make_float4(S[4], S[5], S[6], 0.f);
-    s_lift[le][t][0] = make_float4(lift[0], lift[1], lift[2], lift[3]);
-    s_lift[le][t][1] = make_float4(lift[4], lift[5], 0.f, 0.f);
+    s_surf[0][le][t] = make_float4(S[0], S[1], S[2], S[3]);
+    s_surf[1][le][t] = make_float4(S[4], S[5], S[6], 0.f);
+    s_lift0[le][t] = make_float4(lift[0], lift[1], lift[2], lift[3]);
+    s_lift1[le][t] = make_float2(lift[4], lift[5]);
   }
   __syncthreads();
 
@@ -850,7 +852,7 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
     const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
     float acc[NV] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     auto face_add = [&](int f, int kk) {
-      const float4 x = s_surf[le][f * NK + kk][0], y = s_surf[le][f * NK + kk][1];
+      const float4 x = s_surf[0][le][f * NK + kk], y = s_surf[1][le][f * NK + kk];
       acc[0] += x.x; acc[1] += x.y; acc[2] += x.z; acc[3] += x.w;
       acc[4] += y.x; acc[5] += y.y; acc[6] += y.z;
     };
@@ -862,7 +864,8 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
     {
       // the symmetric SIP term of the four faces, weighted by the boundary row of D
       auto lift_add = [&](int fn, float wgt) {
-        const float4 x = s_lift[le][fn][0], y = s_lift[le][fn][1];
+        const float4 x = s_lift0[le][fn];
+        const float2 y = s_lift1[le][fn];
         acc[PHI] += x.x * wgt;
         acc[M1] += x.y * wgt;
         acc[M2] += x.z * wgt;
