@@ -215,6 +215,7 @@ class Solver:
         self.N = self.len // 7
 
     def close(self):
+        self._adjoint_workspace = None
         if getattr(self, "ctx", None):
             load().dg_destroy(self.ctx)
             self.ctx = None

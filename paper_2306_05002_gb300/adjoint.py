@@ -34,16 +34,27 @@ def backward(solver, ckpt, lam_N, dt: float, nsteps: int, every: int = 20, tape:
     graph per segment length: the replay with dg_step_tape keeping every step's start and tape,
     then dg_adjoint_step_tape back through them); tape=False keeps only the states and lets
     dg_adjoint_step recompute the stages, one call per step."""
-    lam = lam_N.clone()
     starts = sorted(s for s in ckpt if s < nsteps)
     if tape:
+        # The segment graphs are captured with the addresses of the states, tapes and adjoint
+        # buffers, so these live on the solver and are reused by every sweep of the same shape
+        # (new buffers in each sweep would mean a new capture in each sweep).
         m_max = min(every, nsteps)
-        states = torch.empty((m_max + 1,) + tuple(lam.shape), dtype=lam.dtype, device=lam.device)
-        tapes = torch.empty((m_max, solver.dg_tape_len()), dtype=lam.dtype, device=lam.device)
+        key = (m_max, tuple(lam_N.shape), lam_N.dtype, lam_N.device)
+        ws = getattr(solver, "_adjoint_workspace", None)
+        if ws is None or ws[0] != key:
+            ws = (key,
+                  torch.empty((m_max + 1,) + tuple(lam_N.shape), dtype=lam_N.dtype, device=lam_N.device),
+                  torch.empty((m_max, solver.dg_tape_len()), dtype=lam_N.dtype, device=lam_N.device),
+                  torch.empty_like(lam_N))
+            solver._adjoint_workspace = ws
+        _, states, tapes, lam = ws
+        lam.copy_(lam_N)
         for s0 in reversed(starts):
             m = min(s0 + every, nsteps) - s0
             solver.dg_adjoint_segment(ckpt[s0], m, dt, states, tapes, lam)
-        return lam
+        return lam.clone()
+    lam = lam_N.clone()
     work = torch.empty_like(lam)
     seg_states = []
     for s0 in reversed(starts):

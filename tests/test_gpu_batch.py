@@ -148,3 +148,27 @@ def test_full_ensemble_sampled_problems_match_single_runs(dg):
             scale = max(np.abs(ref[v]).max(), 1e-300)
             assert np.abs(got[v] - ref[v]).max() <= TOL_STAGE * 3 * 2 * scale, (wls[k].name, v)
     bs.close()
+
+
+def test_order5_ensemble_problems_stay_finite(dg):
+    """The order-5 bubbles among the ensemble's first 13 problems (seed 4), 300 steps at their own
+    step size, batched and one by one in FP64 and FP32-bulk: finite, and no status raised.  (At
+    the acoustic limit that suits p <= 4 these problems overflow within 200 steps in either
+    precision; order 5 takes 0.9 of it.)"""
+    import torch
+    wls = [wl for wl in W.ensemble(n=13, seed=4) if wl.p == 5 and wl.nx <= 60]
+    assert len(wls) >= 2
+    for prec in ("fp64", "fp32bulk"):
+        for wl in wls:
+            s = dg.Solver(wl, precision=prec)
+            d = torch.from_numpy(wl.w.copy()).cuda()
+            s.dg_step(d, wl.dt, 300)
+            assert bool(torch.isfinite(d).all()), (prec, wl.name)
+            assert s.dg_status_read() == 0, (prec, wl.name)
+            s.close()
+    bs = dg.BatchSolver(wls)
+    states = [torch.from_numpy(wl.w.copy()).cuda() for wl in wls]
+    bs.dg_batch_step(states, [wl.dt for wl in wls], 300)
+    torch.cuda.synchronize()
+    assert all(bool(torch.isfinite(st).all()) for st in states)
+    bs.close()
