@@ -384,7 +384,9 @@ def time_path(dg, wl, precision, steps, warmup, flush, stream, local_rank, sampl
     import torch
     solver = dg.Solver(wl, precision=precision)
     w = torch.from_numpy(wl.w.copy()).cuda()
-    for _ in range(warmup):
+    for _ in range(warmup):  # the timed steps' operations, so that none is a first use when timed
+        torch.cuda._sleep(GATE_CYCLES)
+        flush.zero_()
         solver.dg_step(w, wl.dt, 1)
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank) if sample_clocks else None
