@@ -57,7 +57,8 @@ typedef enum {
   DG_ERR_TIMEOUT = -4,      /* a bounded device wait expired */
   DG_ERR_NONFINITE = -5,    /* the device saw a non-finite value */
   DG_ERR_NONPHYSICAL = -6,  /* the device saw rho <= 0 or P + Pinf <= 0 */
-  DG_ERR_UNSUPPORTED = -7   /* valid request the library does not implement */
+  DG_ERR_UNSUPPORTED = -7,  /* valid request the library does not implement */
+  DG_ERR_BOUNDS = -8        /* bounds-checked build only: a kernel index left its array */
 } dg_status;
 
 enum { DG_BC_PERIODIC = 0, DG_BC_NOSLIP = 1, DG_BC_SLIP = 2, DG_BC_PRESSURE = 3 };
@@ -179,10 +180,32 @@ dg_status dg_step_host(dg_ctx *ctx, double *w_host, double dt, int nsteps, void 
 dg_status dg_diag(dg_ctx *ctx, const double *w, double *out, void *stream);
 
 /* Read and clear the device status word (synchronises the stream): DG_OK,
-   DG_ERR_NONPHYSICAL (reported first when both were latched: a non-physical
-   state is what makes the values non-finite) or DG_ERR_NONFINITE.  Batch
-   contexts latch nothing and return DG_OK. */
+   DG_ERR_BOUNDS (bounds-checked build only, reported first: a kernel index
+   left its array), DG_ERR_NONPHYSICAL (reported before DG_ERR_NONFINITE when
+   both were latched: a non-physical state is what makes the values
+   non-finite) or DG_ERR_NONFINITE.  Batch contexts latch no value checks, so
+   they return DG_OK or, in the bounds-checked build, DG_ERR_BOUNDS. */
 dg_status dg_status_read(dg_ctx *ctx, void *stream);
+
+/* Whether this library is the bounds-checked build (1) or the normal one (0).
+   The bounds-checked build (compiled with DG_CHECK; libdgpf_check.so) checks
+   the index of every global access of the two-phase model's kernels (FP64,
+   FP32-bulk and batched: node, face-record and neighbour indices) against its
+   array's extent; a failed check skips the access and latches a status bit,
+   which dg_status_read reports as DG_ERR_BOUNDS.  failures (HOST, may be
+   NULL) receives the number of such reports so far in this process, counting
+   bits still latched when a context is destroyed (0 in the normal build).
+   The kinematic, re-initialisation, triangle and adjoint kernels and
+   dg_rhs_noalloc are not checked.  The normal build compiles the checks out. */
+int dg_check_build(long long *failures);
+
+/* Self-test of the bounds-checked build: runs the FP64 volume kernel of a
+   small problem with a node count one short of the mesh's (every array keeps
+   its true size, so no access leaves its allocation) and returns 1 when the
+   last node's index check caught it (latched and skipped), 0 when it did not,
+   DG_ERR_CUDA on a CUDA failure and DG_ERR_UNSUPPORTED in the normal build.
+   Synchronises stream; the planted failure is not counted by dg_check_build. */
+int dg_check_selftest(void *stream);
 
 /* Message of the last failure on this context (or of the last failed
    dg_create when ctx is NULL).  Never NULL. */

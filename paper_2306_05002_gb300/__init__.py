@@ -21,10 +21,13 @@ from . import workloads  # noqa: F401  (numpy-only input generators)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdgpf.so")
+# The bounds-checked build (same sources with -DDG_CHECK), loaded instead of LIB_PATH when the
+# environment sets DGPF_CHECKED=1.
+LIB_CHECK_PATH = os.path.join(_HERE, "libdgpf_check.so")
 
 DG_OK = 0
 STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_CUDA", -3: "DG_ERR_OOM", -4: "DG_ERR_TIMEOUT",
-          -5: "DG_ERR_NONFINITE", -6: "DG_ERR_NONPHYSICAL", -7: "DG_ERR_UNSUPPORTED"}
+          -5: "DG_ERR_NONFINITE", -6: "DG_ERR_NONPHYSICAL", -7: "DG_ERR_UNSUPPORTED", -8: "DG_ERR_BOUNDS"}
 BC = {"periodic": 0, "noslip": 1, "slip": 2, "pressure": 3}
 PREC = {"fp64": 0, "fp32bulk": 1}
 
@@ -33,7 +36,8 @@ EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_s
            "dg_status_read", "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc", "dg_batch_create",
            "dg_batch_step", "dg_rhs_vjp", "dg_adjoint_step", "dg_tape_len", "dg_step_tape",
            "dg_adjoint_step_tape", "dg_adjoint_segment", "dg_batch_tiles", "dg_kin_create", "dg_kin_rhs",
-           "dg_kin_step", "dg_kin_nodes", "dg_reinit", "dg_peak_flops"]
+           "dg_kin_step", "dg_kin_nodes", "dg_reinit", "dg_peak_flops", "dg_check_build",
+           "dg_check_selftest"]
 
 
 class DGError(RuntimeError):
@@ -70,13 +74,14 @@ _lib = None
 
 
 def load(path: str | None = None):
-    """Load libdgpf.so (built by ``paper_2306_05002_gb300.build``); raises if it is missing."""
+    """Load libdgpf.so (built by ``paper_2306_05002_gb300.build``), or libdgpf_check.so when the
+    environment sets DGPF_CHECKED=1; raises if the library is missing."""
     global _lib
     if _lib is not None:
         return _lib
-    path = path or LIB_PATH
+    path = path or (LIB_CHECK_PATH if os.environ.get("DGPF_CHECKED") == "1" else LIB_PATH)
     if not os.path.exists(path):
-        raise RuntimeError(f"libdgpf.so not found at {path}: build it with "
+        raise RuntimeError(f"{os.path.basename(path)} not found at {path}: build it with "
                            "`python -c 'import __graft_entry__ as g; g.build()'`")
     lib = ctypes.CDLL(path)
     vp, dp, sz = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t
@@ -139,8 +144,19 @@ def load(path: str | None = None):
     lib.dg_adjoint_segment.restype = ctypes.c_int
     lib.dg_peak_flops.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
     lib.dg_peak_flops.restype = ctypes.c_int
+    lib.dg_check_build.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+    lib.dg_check_build.restype = ctypes.c_int
+    lib.dg_check_selftest.argtypes = [vp]
+    lib.dg_check_selftest.restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+def check_build():
+    """(is_checked_build, bounds failures reported so far in this process): dg_check_build."""
+    n = ctypes.c_longlong()
+    flag = load().dg_check_build(ctypes.byref(n))
+    return bool(flag), n.value
 
 
 def peak_flops(kind: str = "fp64", iters: int = 0, stream=None) -> float:

@@ -2,7 +2,10 @@
 
 Each translation unit compiles in its own nvcc process (in parallel), then one
 link step produces ``paper_2306_05002_gb300/libdgpf.so``.  The library depends
-on the CUDA runtime only (no torch C++ ABI).
+on the CUDA runtime only (no torch C++ ABI).  ``build(check=True)`` builds the
+bounds-checked variant ``libdgpf_check.so`` (the same sources with -DDG_CHECK:
+every global access of the two-phase kernels checks its index) in its own
+object directory.
 """
 from __future__ import annotations
 
@@ -18,6 +21,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgpf.so")
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(HERE, "libdgpf_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,15 +44,17 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None, check: bool = False) -> str:
+    build_dir, lib = (BUILD_CHECK, LIB_CHECK) if check else (BUILD, LIB)
+    os.makedirs(build_dir, exist_ok=True)
+    headers = (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+               glob.glob(os.path.join(ROOT, "include", "*.h")))
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-                    "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
+                    "-I" + os.path.join(ROOT, "include"), "-I" + CSRC] + (["-DDG_CHECK"] if check else [])
     objs = []
     cmds = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             cmds.append([nvcc()] + flags + ["-c", src, "-o", obj])
@@ -61,12 +68,12 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
 
     with ThreadPoolExecutor(max_workers=jobs or min(16, os.cpu_count() or 4)) as ex:
         list(ex.map(run, cmds))
-    if force or cmds or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or cmds or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, check="--check" in sys.argv))

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -184,6 +185,11 @@ void gll_nodes(int p, std::vector<double> &x, std::vector<double> &w) {
 }
 
 thread_local std::string g_create_error = "no error";
+
+#ifdef DG_CHECK
+// Bounds failures seen by dg_status_read or found latched by dg_destroy (bounds-checked build).
+std::atomic<long long> g_bounds_failures{0};
+#endif
 
 }  // namespace
 
@@ -453,7 +459,70 @@ extern "C" dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, do
 extern "C" void dg_destroy(dg_ctx *c) {
   if (!c) return;
   cudaDeviceSynchronize();
+#ifdef DG_CHECK
+  // a bounds failure nobody read is counted before the word goes away
+  unsigned h = 0;
+  if (c->d_status && cudaMemcpy(&h, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost) == cudaSuccess &&
+      (h & STATUS_BOUNDS))
+    ++g_bounds_failures;
+#endif
   free_ctx(c);
+}
+
+// Self-test of the bounds-checked build: the FP64 volume kernel of a 2 x 2, p = 2 periodic problem
+// runs with a node count one short of the mesh's.  Every array keeps its true size, so no access
+// leaves its allocation (the field offsets v (N - 1) + n stay below 7 N); only the last node's
+// index fails its check, which must latch STATUS_BOUNDS and skip that node.
+extern "C" int dg_check_selftest(void *stream) {
+#ifndef DG_CHECK
+  (void)stream;
+  return DG_ERR_UNSUPPORTED;
+#else
+  dg_mesh m{};
+  m.dim = 2;
+  m.nx = m.ny = 2;
+  m.x1 = m.y1 = 1.0;
+  dg_eos eos{};
+  eos.gamma[0] = 1.4;
+  eos.gamma[1] = 4.4;
+  eos.pinf[1] = 6e8;
+  eos.rho0[0] = 1.0;
+  eos.rho0[1] = 1000.0;
+  dg_ctx *c = nullptr;
+  if (dg_create(&m, 2, &eos, 1.0, 0.1, nullptr, &c) != DG_OK) return DG_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  // air at rest at P = 1e5 (phi = 1, m1 = 1, rho E = P / (gamma - 1))
+  std::vector<double> h(c->len, 0.0);
+  const size_t N = (size_t)c->N;
+  for (size_t n = 0; n < N; ++n) {
+    h[PHI * N + n] = 1.0;
+    h[M1 * N + n] = 1.0;
+    h[RE * N + n] = 1e5 / 0.4;
+  }
+  Params q = c->prm;
+  q.N -= 1;
+  q.check_finite = 0;
+  unsigned word = 0;
+  cudaError_t e = cudaMemcpyAsync(c->d_w1, h.data(), c->len * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = c->ks.volume(q, c->d_w1, c->d_rvol, c->d_trace, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&word, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), s);  // planted: not a failure
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dg_destroy(c);
+  if (e != cudaSuccess) return DG_ERR_CUDA;
+  return (word & STATUS_BOUNDS) ? 1 : 0;
+#endif
+}
+
+extern "C" int dg_check_build(long long *failures) {
+#ifdef DG_CHECK
+  if (failures) *failures = g_bounds_failures.load();
+  return 1;
+#else
+  if (failures) *failures = 0;
+  return 0;
+#endif
 }
 
 extern "C" size_t dg_state_len(const dg_ctx *c) { return c ? c->len : 0; }
@@ -664,13 +733,19 @@ extern "C" dg_status dg_diag(dg_ctx *c, const double *w, double *out, void *stre
 
 extern "C" dg_status dg_status_read(dg_ctx *c, void *stream) {
   if (!c) return DG_ERR_ARG;
-  if (c->batch) return DG_OK;  // the batched kernels latch no status
+  if (!c->d_status) return DG_OK;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned h = 0;
   cudaError_t e = cudaMemcpyAsync(&h, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "dg_status_read");
+  if (h & STATUS_BOUNDS) {  // only the bounds-checked build sets it: a library bug, reported first
+#ifdef DG_CHECK
+    ++g_bounds_failures;
+#endif
+    return fail(c, DG_ERR_BOUNDS, "a kernel index left its array (bounds-checked build)");
+  }
   // a non-physical state is reported first: it is the cause of the non-finite values it produces
   if (h & STATUS_NONPHYSICAL)
     return fail(c, DG_ERR_NONPHYSICAL, "non-physical state on the device (rho <= 0 or P + Pinf <= 0)");
@@ -915,6 +990,11 @@ extern "C" dg_status dg_batch_create(int n, const dg_mesh *meshes, const int *p,
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  // the status word: the batched kernels latch no value checks (check_finite is off), only the
+  // index checks of the bounds-checked build
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
+  for (int k = 0; k < n && e == cudaSuccess; ++k) b->h[k].prm.status = c->d_status;
   for (auto &g : b->groups) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);

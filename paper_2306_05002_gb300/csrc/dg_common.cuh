@@ -31,6 +31,24 @@ constexpr int NT_VISCOUS = 17;
 
 constexpr unsigned STATUS_NONFINITE = 1u;
 constexpr unsigned STATUS_NONPHYSICAL = 2u;
+constexpr unsigned STATUS_BOUNDS = 4u;  // bounds-checked build: an index left its array
+
+// Index check of the bounds-checked build (compiled with -DDG_CHECK), the
+// stand-in for a memory checker: i in [0, n) passes; a failed check latches
+// STATUS_BOUNDS in the status word (when there is one) and the caller skips
+// the access.  In the normal build it is the constant true.
+__device__ __forceinline__ bool in_bounds(unsigned *status, long long i, long long n) {
+#ifdef DG_CHECK
+  if (i >= 0 && i < n) return true;
+  if (status) atomicOr(status, STATUS_BOUNDS);
+  return false;
+#else
+  (void)status;
+  (void)i;
+  (void)n;
+  return true;
+#endif
+}
 
 // Everything the kernels need about one problem, passed by value.
 struct Params {

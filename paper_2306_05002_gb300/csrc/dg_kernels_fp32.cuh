@@ -325,7 +325,7 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   constexpr int NLY = DIM == 2 ? P1 : 1;  // lines per element in each orientation
   // Even line lengths: y-lines from a column copy in vector loads, the node's rows of D held in
   // registers.  Odd ones: y-lines read across the rows one node at a time and D read where used,
-  // which the 80-register viscous kernels need (p = 4: the column copies and held rows cost 7%).
+  // which the register-capped viscous kernels need (p = 4: the column copies and held rows cost 7%).
   constexpr bool COLS = DIM == 2 && P1 % 2 == 0;
   // rows (x-lines) of six fields per element and, when COLS, their columns (y-lines); without COLS
   // the y-flux components take six more row slots
@@ -341,9 +341,9 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
   const int le = lane ? le_raw : EPB - 1;
   const int a = threadIdx.x % NP;
   const int e = blk * EPB + le;
-  const bool act = lane && e < prm.E;
-  const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
   const int N = prm.N;
+  const bool act = lane && e < prm.E && in_bounds(prm.status, (long long)e * NP + a, N);
+  const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
   const long n = (long)(act ? e : 0) * NP + a;
 
   float q[NV];
@@ -577,6 +577,7 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
     // the sound speed, with the reader's former operations (trace_derive)
     const float cs = VISC ? 0.f : sqrtf((Pr + (Pr + fmaf(pf.dC, phi, pf.C2)) * iG) * ir);
     auto put = [&](int f, int kk, float gn, float nn, float t1, float t2) {
+      if (!in_bounds(prm.status, base + f * NK + kk, (long long)prm.E * NFK)) return;
       float4 *rec = reinterpret_cast<float4 *>(tr) + (base + f * NK + kk) * (TRW32 / 4);
       rec[0] = make_float4(q[0], q[1], q[2], q[3]);
       rec[1] = make_float4(q[4], q[5], q[6], gn);
@@ -670,8 +671,8 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   const int le = lane ? le_raw : EPB - 1;
   const int a = threadIdx.x % NP;
   const int e = blk * EPB + le;
-  const bool act = lane && e < prm.E;
   const int N = prm.N;
+  const bool act = lane && e < prm.E && in_bounds(prm.status, (long long)e * NP + a, N);
   const long n = (long)(act ? e : 0) * NP + a;
 
   int e2_[FPT];  // neighbour across the face of each face node (-1: wall)
@@ -715,8 +716,9 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
     e2_[fi] = e2;
     const long om = (long)(act ? e : 0) * NFK + (fv ? t : 0);
     const long op = (long)(e2 >= 0 ? e2 : 0) * NFK + (f ^ 1) * NK + kk;
-    load_trace32<NC, RW, PDL>(tr, om, fv, Cm_[fi], 1.f);
-    load_trace32<NC, RW, PDL>(tr, op, e2 >= 0, Cp_[fi], 0.f);
+    const long long ntr = (long long)prm.E * NFK;
+    load_trace32<NC, RW, PDL>(tr, om, fv && in_bounds(prm.status, om, ntr), Cm_[fi], 1.f);
+    load_trace32<NC, RW, PDL>(tr, op, e2 >= 0 && in_bounds(prm.status, op, ntr), Cp_[fi], 0.f);
   }
 
   if (!PDL)

@@ -98,9 +98,9 @@ k_volume(const Params prm, const double *__restrict__ w, double *__restrict__ rv
   const int le = lane ? le_raw : EPB - 1;  // padding lanes mirror the last element, write nothing
   const int a = threadIdx.x % NP;
   const int e = blockIdx.x * EPB + le;
-  const bool act = lane && e < prm.E;
-  const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
   const int N = prm.N;
+  const bool act = lane && e < prm.E && in_bounds(prm.status, (long long)e * NP + a, N);
+  const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
   const long n = (long)(act ? e : 0) * NP + a;
 
   double q[NV];
@@ -167,6 +167,7 @@ k_volume(const Params prm, const double *__restrict__ w, double *__restrict__ rv
       const int f2 = f ^ 1;
       const int a2 = f2 == 0 ? P1 * kk : f2 == 1 ? P + P1 * kk : f2 == 2 ? kk : kk + P1 * P;
       const long n2 = (long)e2 * NP + a2;
+      if (!in_bounds(prm.status, n2, N)) return;
       const double wf = DIM == 2 ? __ldg(prm.ops + (f < 2 ? Lo.wfx() : Lo.wfy()) + kk) : 1.0;
       const double c = sgn * 0.5 * im * wf;
       gx_phi += c * (__ldg(w + (long)PHI * N + n2) - phi);
@@ -283,6 +284,7 @@ k_volume(const Params prm, const double *__restrict__ w, double *__restrict__ rv
     const long stride = (long)prm.E * NFK;
     auto put = [&](int f, int kk, double gn, double nn, double t1, double t2) {
       const long o = base + f * NK + kk;
+      if (!in_bounds(prm.status, o, stride)) return;
 #pragma unroll
       for (int qf = 0; qf < T_GPHI; ++qf) tr[qf * stride + o] = tx[qf];
       tr[T_GPHI * stride + o] = gn;
@@ -335,12 +337,14 @@ k_surface(const Params prm, int mode, double dt, const double *__restrict__ w0, 
     const double sg = (f & 1) ? 1.0 : -1.0;  // m = sg * e_axis
     double Tm[NT], Tp[NT];
     const long om = (long)(act ? e : 0) * NFK + t;
+    const bool okm = act && in_bounds(prm.status, om, stride);
 #pragma unroll
-    for (int qf = 0; qf < NT; ++qf) Tm[qf] = act ? __ldg(tr + qf * stride + om) : (qf == T_M1 ? 1.0 : 0.0);
+    for (int qf = 0; qf < NT; ++qf) Tm[qf] = okm ? __ldg(tr + qf * stride + om) : (qf == T_M1 ? 1.0 : 0.0);
     if (!wall) {
       const long op = (long)e2 * NFK + (f ^ 1) * NK + kk;
+      const bool okp = in_bounds(prm.status, op, stride);
 #pragma unroll
-      for (int qf = 0; qf < NT; ++qf) Tp[qf] = __ldg(tr + qf * stride + op);
+      for (int qf = 0; qf < NT; ++qf) Tp[qf] = okp ? __ldg(tr + qf * stride + op) : Tm[qf];
     } else {
 #pragma unroll
       for (int qf = 0; qf < NT; ++qf) Tp[qf] = Tm[qf];
@@ -434,7 +438,7 @@ k_surface(const Params prm, int mode, double dt, const double *__restrict__ w0, 
 
   // Phase 2: gather onto the element's nodes, lift the symmetric term along
   // the normal lines, apply M^-1, add the volume part, write L or the stage.
-  if (!act) return;
+  if (!act || !in_bounds(prm.status, (long long)e * NP + a, prm.N)) return;
   const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
   double acc[NV] = {0, 0, 0, 0, 0, 0, 0};
   auto face_add = [&](int f, int kk) {

@@ -36,3 +36,22 @@ def dg():
     import paper_2306_05002_gb300 as pkg
     pkg.load()  # raises if the extension is missing
     return pkg
+
+
+@pytest.fixture(autouse=True)
+def _bounds_checked_build(request):
+    """Under DGPF_CHECKED=1 (the GPU tests run on the bounds-checked library, see
+    tests/test_gpu_checked.py): every GPU test must run on that library and leave the count of
+    bounds failures where it found it.  A no-op otherwise."""
+    if os.environ.get("DGPF_CHECKED") != "1" or request.node.get_closest_marker("gpu") is None:
+        yield
+        return
+    import gc
+
+    import paper_2306_05002_gb300 as pkg
+    checked, before = pkg.check_build()
+    assert checked, "DGPF_CHECKED=1 but the loaded library is not the bounds-checked build"
+    yield
+    gc.collect()  # contexts a test dropped are destroyed here, and bits they still hold counted
+    _, after = pkg.check_build()
+    assert after == before, f"{after - before} bounds failure(s) in the bounds-checked build"
