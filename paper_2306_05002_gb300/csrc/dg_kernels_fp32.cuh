@@ -970,13 +970,16 @@ k_surface32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, 
 // part to the other in registers.  The volume part and the traces go to the
 // other buffer of a pair (rvol_out, tr_out), because neighbouring blocks of
 // the same launch may still read rvol_in and tr_in.
-// Residency of the viscous variants: at most 72 registers a thread (65,536 / (THREADS x 72) CTAs
-// per SM: 7 of 128 threads).  Uncapped, the surface-tension variant needs 90 and runs 6% slower at
-// p = 4 (one CTA per SM fewer); at 72 it spills a few words and runs 2% faster than at 80, and at
-// 64 (more spills) no faster than at 80.
+// Residency of the viscous variants and of every variant at p >= 4: at most 72 registers a thread
+// (65,536 / (THREADS x 72) CTAs per SM: 7 of 128 threads at p = 4).  Uncapped, the viscous
+// surface-tension variant needs 90 and runs 6% slower at p = 4 than at 80; at 72 it spills a few
+// words and runs 2% faster than at 80, and at 64 (more spills) no faster than at 80.  The inviscid
+// p = 4 variants fit 72 without spills and run 18% faster than uncapped (86 vs 105 us at 256 x 256).
+// Below p = 4 the inviscid grids of the single-problem workloads are one partial wave, where
+// residency does not bind.
 template <int P, int DIM, bool VISC, bool ST, bool PDL>
 __global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS,
-                                  VISC ? 65536 / (Geom<P, DIM, VISC, ST>::THREADS * 72) : 1)
+                                  (VISC || P >= 4) ? 65536 / (Geom<P, DIM, VISC, ST>::THREADS * 72) : 1)
 k_surfvol32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, int mode, float dt, const StageIO io,
             const float *__restrict__ rvol_in, const float *__restrict__ tr_in, float *__restrict__ rvol_out,
             float *__restrict__ tr_out) {
