@@ -149,8 +149,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# Spin cycles of the gate kernel ahead of each timed step (~5 ms at 2 GHz).
-GATE_CYCLES = 10_000_000
+# Spin cycles of the gate kernel ahead of each timed step (~19 ms at 2.07 GHz): longer than the
+# host takes to enqueue the flush, the events and the step even in the first process on a fresh
+# box (~5 ms per step there), so the GPU never waits for the host inside the event interval.
+GATE_CYCLES = 40_000_000
 
 
 # --------------------------------------------------------------------------- roofline helpers
@@ -404,7 +406,7 @@ def time_path(dg, wl, precision, steps, warmup, flush, stream, local_rank, sampl
     for k in range(steps):
         # a spin kernel of GATE_CYCLES ahead of each step keeps the GPU busy while the host enqueues
         # the flush, the events and the step, so the events measure the step's device time even
-        # when the host is slow to enqueue (the first seconds of a process on a fresh box)
+        # when the host is slow to enqueue (the first process on a fresh box)
         torch.cuda._sleep(GATE_CYCLES)
         flush.zero_()
         starts[k].record(stream)
