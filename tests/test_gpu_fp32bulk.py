@@ -164,6 +164,18 @@ def test_fp32bulk_short_run_against_oracle(orc, dg):
     assert _l2(orc.primitives(pb, w32)[3], orc.primitives(pb, wr)[3]) <= 1e-6
 
 
+def test_fp32bulk_rayleigh_taylor_full_size_10_steps_against_oracle(orc, dg):
+    """Config 3 at full size, 10 steps in one call, against the oracle's SSP-RK3 (OpenMP build,
+    bit-identical to the plain one): phi and P within 1e-6 (relative L2), as the short drop run."""
+    import os
+    wl = W.rayleigh_taylor(n=256, p=4, seed=3)
+    w32 = _run(dg, wl, "fp32bulk", 10)
+    pb = problem(orc, wl)
+    wr = orc.rk3(pb, wl.w, wl.dt, 10, threads=os.cpu_count() or 1)
+    assert _l2(w32[0], wr[0]) <= 1e-6
+    assert _l2(orc.primitives(pb, w32)[3], orc.primitives(pb, wr)[3]) <= 1e-6
+
+
 def test_fp32bulk_conversion_round_trip_keeps_pressure(orc, dg):
     """nsteps = 0 is a no-op; one step with a tiny dt changes P by ~FP32 round-off only."""
     import torch

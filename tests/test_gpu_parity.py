@@ -224,6 +224,23 @@ def test_step_full_size_drop(orc, dg):
     _assert_steps_close(orc, wl, 3, w, w_ref)
 
 
+def test_step_full_size_rayleigh_taylor_10_steps(orc, dg):
+    """Config 3 at full size (256 x 256, p = 4, viscous, gravity, surface tension, no-slip walls):
+    10 SSP-RK3 steps against the oracle's (its OpenMP build on every host core, bit-identical to
+    the plain one), within the multi-step bound."""
+    import os
+    import torch
+    wl = W.rayleigh_taylor(n=256, p=4, seed=3)
+    w_ref = orc.rk3(problem(orc, wl), wl.w, wl.dt, 10, threads=os.cpu_count() or 1)
+    solver = dg.Solver(wl)
+    d = torch.from_numpy(wl.w.copy()).cuda()
+    solver.dg_step(d, wl.dt, 10)
+    w = d.cpu().numpy()
+    assert solver.dg_status_read() == 0
+    solver.close()
+    _assert_steps_close(orc, wl, 10, w, w_ref)
+
+
 def test_step_rayleigh_taylor_small(orc, dg):
     wl = W.rayleigh_taylor(n=8, p=4, seed=3)
     w, w_ref = _step_both(orc, dg, wl, 5)
