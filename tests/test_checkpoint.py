@@ -83,3 +83,26 @@ def test_resume_continues_the_run(dg, tmp_path, precision):
     else:
         for v in range(7):
             assert np.abs(x[v] - y[v]).max() <= 1e-12 * np.abs(x[v]).max() + 1e-300, v
+
+
+@pytest.mark.gpu
+def test_command_line_save_and_resume(dg, tmp_path):
+    """`python -m paper_2306_05002_gb300 ... --save` then `--resume ... --save`: 4 + 6 steps give the
+    state of 10 steps in one run, bit for bit (FP64), and the clock adds up."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    run = lambda *a: subprocess.run([sys.executable, "-m", "paper_2306_05002_gb300", *a], cwd=root,
+                                    capture_output=True, text=True, timeout=300)
+    a, b = os.path.join(tmp_path, "a.npz"), os.path.join(tmp_path, "b.npz")
+    base = ["drop", "--n", "8", "--p", "3", "--precision", "fp64"]
+    r1 = run(*base, "--steps", "4", "--save", a)
+    r2 = run("--resume", a, "--steps", "6", "--precision", "fp64", "--save", a)
+    r3 = run(*base, "--steps", "10", "--save", b)
+    for r in (r1, r2, r3):
+        assert r.returncode == 0, r.stderr[-2000:]
+    assert json.loads(r2.stdout.splitlines()[-1])["step"] == 10
+    _, sa, ta, na, _ = C.load(a)
+    _, sb, tb, nb, _ = C.load(b)
+    assert np.array_equal(sa, sb) and na == nb == 10 and abs(ta - tb) <= 1e-15 * tb
