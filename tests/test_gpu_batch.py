@@ -53,6 +53,46 @@ def test_batch_matches_oracle(orc, dg, nsteps):
         assert _l2(P_got, P_ref) <= 1e-6, (wl.name, _l2(P_got, P_ref))
 
 
+@pytest.mark.parametrize("nsteps", [1, 3])
+def test_batch_with_walls_pressure_top_and_gravity_matches_oracle(orc, dg, nsteps):
+    """A batch whose problems have walls and gravity (inviscid): the paper's Rayleigh-Taylor domain
+    (slip sides, no-slip bottom, the pressure top), a no-slip box with a perturbed interface, and a
+    periodic drop (g = 0), against the oracle's SSP-RK3: phi, psi, m_l, rho E and P within 1e-6
+    (relative L2) as above, the momenta within the FP32 storage bound of the pressure gradient."""
+    import torch
+    a = W.rayleigh_taylor_paper(nx=4, ny=12, p=4)
+    b = W.rayleigh_taylor(n=6, p=3, seed=5)
+    for wl in (a, b):
+        wl.viscous = wl.surface_tension = False
+        wl.gravity = True
+    c = W.drop_2d(n=6, p=2, seed=3)
+    wls = [a, b, c]
+    bs = dg.BatchSolver(wls)
+    states = [torch.from_numpy(wl.w.copy()).cuda() for wl in wls]
+    bs.dg_batch_step(states, [wl.dt for wl in wls], nsteps)
+    torch.cuda.synchronize()
+    bs.close()
+    for wl, st in zip(wls, states):
+        pb = problem(orc, wl)
+        ref = orc.rk3(pb, wl.w, wl.dt, nsteps)
+        got = st.cpu().numpy()
+        for v in (0, 1, 2, 3, 6):
+            assert _l2(got[v], ref[v]) <= 1e-6, (wl.name, v, _l2(got[v], ref[v]))
+        # the momenta of fluids at rest under gravity: what moves them is the hydrostatic imbalance, so
+        # the FP32 storage error of P (4 eps32 max|P|) through the pressure gradient, (2/h) max_i
+        # sum_c |D_ic| per stage, bounds the difference (the bound of the multi-step FP32-bulk test)
+        xi, _ = orc.gll(wl.p)
+        D = orc.lagrange_deriv(wl.p, xi)
+        h = min(wl.hx, wl.hy)
+        P_max = np.abs(orc.primitives(pb, ref)[3]).max()
+        extra = 3 * nsteps * wl.dt * 4 * np.finfo(np.float32).eps * P_max * (2.0 / h) * np.abs(D).sum(axis=1).max()
+        for v in (4, 5):
+            tol = 1e-6 * np.abs(ref[v]).max() + extra
+            assert np.abs(got[v] - ref[v]).max() <= tol, (wl.name, v, np.abs(got[v] - ref[v]).max(), tol)
+        P_got, P_ref = orc.primitives(pb, got)[3], orc.primitives(pb, ref)[3]
+        assert _l2(P_got, P_ref) <= 1e-6, (wl.name, _l2(P_got, P_ref))
+
+
 @pytest.mark.parametrize("nsteps", [1, 9])
 def test_batch_equals_single_problem_runs(dg, nsteps):
     import torch
