@@ -30,14 +30,14 @@ def _l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("nsteps", [1, 4])
-def test_batch_matches_oracle(orc, dg, nsteps):
-    """Each problem of a batch of orders 2..5 (meshes of 4 to 9 elements a side, drops and
-    bubbles) after `nsteps` batched steps against the oracle's SSP-RK3 steps of the same problem:
-    relative L2 error of every stored variable and of the pressure <= 1e-6."""
+@pytest.mark.parametrize("nsteps,orders", [(1, (2, 3, 4, 5)), (4, (2, 3, 4, 5)), (3, (1,))])
+def test_batch_matches_oracle(orc, dg, nsteps, orders):
+    """Each problem of a batch of orders 2..5, or of order 1 (meshes of 4 to 9 elements a side,
+    drops and bubbles) after `nsteps` batched steps against the oracle's SSP-RK3 steps of the same
+    problem: relative L2 error of every stored variable and of the pressure <= 1e-6."""
     import torch
-    wls = W.ensemble(n=8, seed=11, nmin=4, nmax=9, orders=(2, 3, 4, 5))
-    assert {wl.p for wl in wls} == {2, 3, 4, 5}
+    wls = W.ensemble(n=8, seed=11, nmin=4, nmax=9, orders=orders)
+    assert {wl.p for wl in wls} == set(orders)
     bs = dg.BatchSolver(wls)
     states = [torch.from_numpy(wl.w.copy()).cuda() for wl in wls]
     bs.dg_batch_step(states, [wl.dt for wl in wls], nsteps)

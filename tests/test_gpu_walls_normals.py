@@ -6,6 +6,7 @@ FP32-bulk path (2e-6 of S plus the FP32 storage bound), and the device's non-phy
 * plane Poiseuille flow between no-slip walls (viscous, gravity);
 * a constant level-set patch (|grad psi| = 0: n = 0) with exact pure-phase regions
   (phi = 0 and phi = 1 exactly, where phi (1 - phi) = 0);
+* 1D: a slab between a no-slip wall and the Riemann-invariant pressure boundary;
 * the FP32 normal cut-off: FP32 kernels set n = 0 where |grad psi| < 1e-4 (below that the
   direction of a distance-like psi stored in FP32 is noise), the oracle and the FP64 kernels
   where |grad psi| < 1e-12.  On a level set that is not a distance the two differ by the
@@ -63,8 +64,22 @@ def _degenerate_normals(p=3):
     return wl
 
 
+def _slab_1d_walls(p=3):
+    """1D: a water slab in air between a no-slip wall (x = 0) and the pressure boundary (x = 1,
+    P_b = 1.2e5 against P = 1e5 inside), with a flow toward the pressure side."""
+    wl = W.Workload(name="slab1d_walls", dim=1, nx=9, ny=1, p=p, bc=("noslip", "pressure", "periodic", "periodic"),
+                    p_bc=(0.0, 1.2e5, 0.0, 0.0), Gamma=1.0)
+    wl.eps = wl.hx
+    x, _ = W.node_coords(wl)
+    s = 0.2 - np.abs(x - 0.55)
+    u = 0.5 * np.sin(np.pi * x)
+    wl.w = W.conserved(wl, W.tanh_profile(s, wl.eps), s, 1e5 + 50.0 * x, u, 0.0)
+    return wl
+
+
 CASES = {"slip_channel": _slip_channel_crossing_flow, "poiseuille_p3": lambda: _poiseuille(3),
-         "poiseuille_p2": lambda: _poiseuille(2), "degenerate_normals": _degenerate_normals}
+         "poiseuille_p2": lambda: _poiseuille(2), "degenerate_normals": _degenerate_normals,
+         "slab_1d_walls_p3": lambda: _slab_1d_walls(3), "slab_1d_walls_p5": lambda: _slab_1d_walls(5)}
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
