@@ -836,6 +836,37 @@ def adjoint_block(dg, steps, every=20, n=128):
             "adjoint_over_forward": tb / tf, "repetitions_ms": {"forward": tfs, "backward": tbs}, "finite": ok}
 
 
+def summary(line):
+    """A short digest of the line, one entry per configuration (3 significant digits): the figures
+    a reader of the line's last few hundred characters needs."""
+    r3 = lambda x: float(f"{x:.3g}") if isinstance(x, (int, float)) and x == x else x
+    acc3 = lambda a: None if not a else [r3(a.get(k, a.get("max_" + k))) for k in ("l2_rel_alpha", "l2_rel_p", "l2_rel_u")]
+    out = {"acc_order": "l2_rel alpha, P, u vs the FP64 path",
+           "config2": {"us_per_step": r3(1e3 * line["ms_per_step"]), "value": r3(line["value"]),
+                       "frac": r3(line["roofline"]["frac"]), "e2e": r3(line["e2e"]["value"]),
+                       "acc_500": acc3(line.get("accuracy"))}}
+    if "fp64" in line:
+        out["config2"]["fp64_us_per_step"] = r3(1e3 * line["fp64"]["ms_per_step"])
+    if "slab_1d" in line:
+        sl = line["slab_1d"]
+        out["config1"] = {"fp64_us_per_step": r3(sl["fp64"]["us_per_step"]),
+                          "fp32bulk_us_per_step": r3(sl["fp32bulk"]["us_per_step"]), "acc_1000": acc3(sl["accuracy"])}
+    if "rayleigh_taylor" in line:
+        rt = line["rayleigh_taylor"]
+        out["config3"] = {"ms_per_step": r3(rt["fp32bulk"]["ms_per_step"]), "value": r3(rt["fp32bulk"]["value"]),
+                          "frac": r3(rt["fp32bulk"]["roofline"]["frac"]),
+                          "fp64_ms_per_step": r3(rt["fp64"]["ms_per_step"]), "acc_2000": acc3(rt.get("accuracy"))}
+    if "batched" in line:
+        b = line["batched"]
+        out["config4"] = {"ms_per_step": r3(b["ms_per_step"]), "value": r3(b["value"]),
+                          "speedup_vs_fp64": r3(b["speedup_vs_fp64"]), "acc_200_max": acc3(b.get("accuracy"))}
+    if "adjoint" in line:
+        a = line["adjoint"]
+        out["config5"] = {"adjoint_over_forward": r3(a["adjoint_over_forward"]), "forward_ms": r3(a["forward_ms"]),
+                          "backward_ms": r3(a["backward_ms"])}
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2306_05002_gb300 as dg
@@ -939,6 +970,7 @@ def run_ours(args, rank, world, local_rank):
             line["rayleigh_taylor_paper_domain"] = rtp
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
+        line["summary"] = summary(line)  # last key: a short digest of every block
         print(json.dumps(line), flush=True)
     main["solver"].close()
     if ref:

@@ -21,3 +21,19 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["config"]["workload"].startswith("2D periodic drop advection 64x64 quads p=3")
+
+
+def test_summary_digest_of_a_line():
+    """The line's last key digests every block present, in a few hundred characters."""
+    import bench
+    line = {"ms_per_step": 0.0234, "value": 5.89e10, "roofline": {"frac": 0.303}, "e2e": {"value": 1.75e10},
+            "accuracy": {"l2_rel_alpha": 4.8e-9, "l2_rel_p": 4.9e-7, "l2_rel_u": 3e-5},
+            "adjoint": {"adjoint_over_forward": 2.72, "forward_ms": 124.5, "backward_ms": 338.7},
+            "batched": {"ms_per_step": 7.8, "value": 9.5e10, "speedup_vs_fp64": 13.0,
+                        "accuracy": {"max_l2_rel_alpha": 1.5e-8, "max_l2_rel_p": float("nan"), "max_l2_rel_u": 2e-5}}}
+    s = bench.summary(line)
+    assert s["config2"]["us_per_step"] == 23.4 and s["config2"]["acc_500"] == [4.8e-9, 4.9e-7, 3e-5]
+    assert s["config5"]["adjoint_over_forward"] == 2.72
+    assert s["config4"]["acc_200_max"][1] != s["config4"]["acc_200_max"][1]  # a NaN stays a NaN
+    assert "config3" not in s and "config1" not in s
+    assert len(json.dumps(s)) < 1000
