@@ -59,6 +59,8 @@ def parse():
                     help="pseudo-time steps of the timed re-initialisation block (0 skips it)")
     ap.add_argument("--rt-paper-steps", type=int, default=10,
                     help="timed steps on the paper's Rayleigh-Taylor domain with the pressure top (0 skips)")
+    ap.add_argument("--rb-steps", type=int, default=100,
+                    help="timed steps of the rising-bubble block (20 x 40 quads, p = 4; 0 skips it)")
     ap.add_argument("--slab-steps", type=int, default=1000,
                     help="steps of the 1D slab block (0 skips it)")
     ap.add_argument("--tri-steps", type=int, default=200,
@@ -557,17 +559,23 @@ def batched_block(dg, steps, nprob=256, acc_steps=200):
             "cpu_oracle": oracle_sample(wls[:32], wls, of="the first 32 problems")}
 
 
-def rt_block(dg, steps, n=256, paper=False, cpu=False, acc_steps=0):
+def rt_block(dg, steps, n=256, paper=False, cpu=False, acc_steps=0, bubble=False):
     """Viscous Rayleigh-Taylor set-up (256 x 256 quads, p = 4, walls, gravity, surface tension,
     seed 3): FP32-bulk and FP64 step times and the FP32-bulk error after the timed steps.
     The state (92 MB FP64, 1.64M nodes) and the workspace exceed L2 together; no flush.
     paper: the paper's domain [0, 1] x [0, 4] on n x 4n quads instead (slip sides, no-slip bottom,
     the Riemann-invariant pressure top, no surface tension).  cpu: also the oracle on a bounded
     sample (one right-hand side on one core, one step on every core).  acc_steps > 0: also the
-    FP32-bulk errors (alpha, P, u) against FP64 after that many steps from the initial state."""
+    FP32-bulk errors (alpha, P, u) against FP64 after that many steps from the initial state.
+    bubble: the paper's rising bubble (case 1) on n x 2n quads instead."""
     import torch
     from paper_2306_05002_gb300 import workloads as W
-    if paper:
+    if bubble:
+        wl = W.rising_bubble(nx=n, ny=2 * n, p=4, case=1)
+        desc = (f"2D rising bubble (the paper's case 1: R=0.25 at (0,0.5) in [-0.5,0.5]x[0,2], density and "
+                f"viscosity ratio 10, Re=35, Eo=10) on {n}x{2 * n} quads p=4, slip sides, no-slip bottom, "
+                "Riemann-invariant pressure top")
+    elif paper:
         wl = W.rayleigh_taylor_paper(nx=n, ny=4 * n, p=4)
         desc = (f"2D viscous Rayleigh-Taylor, the paper's domain [0,1]x[0,4] on {n}x{4 * n} quads p=4, slip sides, "
                 "no-slip bottom, Riemann-invariant pressure top, g=-9.81, density ratio 3, Re=3000")
@@ -879,6 +887,10 @@ def summary(line):
         b = line["batched"]
         out["config4"] = {"ms_per_step": r3(b["ms_per_step"]), "value": r3(b["value"]),
                           "speedup_vs_fp64": r3(b["speedup_vs_fp64"]), "acc_200_max": acc3(b.get("accuracy"))}
+    if "rising_bubble" in line:
+        rb = line["rising_bubble"]
+        out["rising_bubble"] = {"ms_per_step": r3(rb["fp32bulk"]["ms_per_step"]),
+                                "fp64_ms_per_step": r3(rb["fp64"]["ms_per_step"]), "acc": acc3(rb.get("accuracy"))}
     if "adjoint" in line:
         a = line["adjoint"]
         out["config5"] = {"adjoint_over_forward": r3(a["adjoint_over_forward"]), "forward_ms": r3(a["forward_ms"]),
@@ -943,6 +955,8 @@ def run_ours(args, rank, world, local_rank):
     tri = triangle_block(dg, args.tri_steps, args.tri_n) if (args.tri_steps > 0 and rank == 0) else None
     ri = reinit_block(dg, args.reinit_iters) if (args.reinit_iters > 0 and rank == 0) else None
     rtp = rt_block(dg, args.rt_paper_steps, n=64, paper=True) if (args.rt_paper_steps > 0 and rank == 0) else None
+    rb = (rt_block(dg, args.rb_steps, n=20, bubble=True, acc_steps=1000)
+          if (args.rb_steps > 0 and rank == 0) else None)
 
     ms_max, e2e_max, ref_ms = reduce_max([main["ms"], e2e_t, ref["ms"] if ref else 0.0], "cuda")
 
@@ -987,6 +1001,8 @@ def run_ours(args, rank, world, local_rank):
             line["reinit"] = ri
         if rtp:
             line["rayleigh_taylor_paper_domain"] = rtp
+        if rb:
+            line["rising_bubble"] = rb
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
         line["summary"] = summary(line)  # last key: a short digest of every block

@@ -275,6 +275,51 @@ def rayleigh_taylor_paper(nx: int = 10, ny: int = 40, p: int = 4, P_top: float =
     return wl
 
 
+def _trapezoid(f, x):
+    """Trapezoidal rule along the last axis (numpy's name for it changed between versions)."""
+    return np.sum(0.5 * (f[..., 1:] + f[..., :-1]) * np.diff(x, axis=-1), axis=-1)
+
+
+def rising_bubble(nx: int = 10, ny: int = 20, p: int = 4, case: int = 1, P_top: float = 1e5,
+                  eps_h: float = 0.75, nquad: int = 4000) -> Workload:
+    """The paper's rising bubble (Sec. 4.2): a circular bubble of the light phase 2, radius
+    R = 0.25, centred at (0, 0.5) in [-0.5, 0.5] x [0, 2], rising in the heavy phase 1 under
+    gravity; no-slip bottom, slip sides and the Riemann-invariant top boundary at rest at P_top.
+    Case 1: rho_1/rho_2 = mu_1/mu_2 = 10, Eo = 4 rho_1 |g| R^2 / sigma = 10; case 2:
+    rho_1/rho_2 = 1000, mu_1/mu_2 = 100, Eo = 125; both Re = rho_1 d^(3/2) |g|^(1/2) / mu_1 = 35 with
+    d = 2R.  rho_1 = 1000 and |g| = 0.98 fix the dimensional values (the paper states only the
+    ratios and the numbers).  Liquid-liquid closure as in `rayleigh_taylor` (both phases gamma =
+    4.4, Pinf = 6e8); Gamma = sqrt(|g| d / 2), the rule that gives `rayleigh_taylor`'s 2.21;
+    eps = 0.75 h.  The pressure is hydrostatic: P_top plus |g| times the column integral of the
+    density above each node (trapezoidal rule with `nquad` points)."""
+    g, R, d = 0.98, 0.25, 0.5
+    rho1 = 1000.0
+    rho2, mu_ratio, Eo = (rho1 / 10.0, 10.0, 10.0) if case == 1 else (rho1 / 1000.0, 100.0, 125.0)
+    mu1 = rho1 * d ** 1.5 * np.sqrt(g) / 35.0
+    sigma = 4.0 * rho1 * g * R * R / Eo
+    wl = Workload(name=f"rb{case}_{nx}x{ny}p{p}", dim=2, nx=nx, ny=ny, p=p, x0=-0.5, x1=0.5, y0=0.0, y1=2.0,
+                  bc=("slip", "slip", "noslip", "pressure"), p_bc=(0.0, 0.0, 0.0, P_top),
+                  gamma=(4.4, 4.4), pinf=(6e8, 6e8), rho0=(rho1, rho2), mu=(mu1, mu1 / mu_ratio),
+                  sigma=sigma, g=(0.0, -g), Gamma=float(np.sqrt(g * d / 2.0)), viscous=True, gravity=True,
+                  surface_tension=True)
+    wl.eps = eps_h * min(wl.hx, wl.hy)
+    x, y = node_coords(wl)
+    s = np.hypot(x, y - 0.5) - R                  # grows into the heavy outer phase 1
+    phi = tanh_profile(s, wl.eps)
+    # hydrostatic pressure: P(x, y) = P_top + g int_y^2 rho(x, y') dy', rho = rho2 + (rho1 - rho2) phi
+    t = np.linspace(0.0, 1.0, nquad)
+    P = np.empty(wl.N)
+    for k0 in range(0, wl.N, 2048):
+        xs, ys = x[k0:k0 + 2048, None], y[k0:k0 + 2048, None]
+        yy = ys + (2.0 - ys) * t[None, :]
+        rho = rho2 + (rho1 - rho2) * tanh_profile(np.hypot(xs, yy - 0.5) - R, wl.eps)
+        P[k0:k0 + 2048] = P_top + g * _trapezoid(rho, yy)
+    wl.w = conserved(wl, phi, s, P, 0.0, 0.0)
+    wl.dt = stable_dt(wl, 0.0, P_top)
+    wl.meta = dict(P_top=P_top, case=case)
+    return wl
+
+
 def resized(wl_fn, **kw) -> Workload:
     """Convenience: build a workload with overridden sizes (used for small parity cases)."""
     return wl_fn(**kw)

@@ -164,6 +164,21 @@ def test_fp32bulk_short_run_against_oracle(orc, dg):
     assert _l2(orc.primitives(pb, w32)[3], orc.primitives(pb, wr)[3]) <= 1e-6
 
 
+@pytest.mark.parametrize("case", [1, 2])
+def test_rhs32_rising_bubble(orc, dg, case):
+    _rhs32(orc, dg, W.rising_bubble(nx=4, ny=8, p=4, case=case))
+
+
+def test_fp32bulk_rising_bubble_tracks_fp64(orc, dg):
+    """The rising bubble on 10 x 20 quads, p = 4, 200 steps: phi and P within 1e-5 (relative L2)
+    of the FP64 path."""
+    wl = W.rising_bubble(nx=10, ny=20, p=4)
+    w32, w64 = _run(dg, wl, "fp32bulk", 200), _run(dg, wl, "fp64", 200)
+    pb = problem(orc, wl)
+    assert _l2(w32[0], w64[0]) <= 1e-5
+    assert _l2(orc.primitives(pb, w32)[3], orc.primitives(pb, w64)[3]) <= 1e-5
+
+
 def test_fp32bulk_rayleigh_taylor_full_size_10_steps_against_oracle(orc, dg):
     """Config 3 at full size, 10 steps in one call, against the oracle's SSP-RK3 (OpenMP build,
     bit-identical to the plain one): phi and P within 1e-6 (relative L2), as the short drop run."""

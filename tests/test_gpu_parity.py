@@ -241,6 +241,19 @@ def test_step_full_size_rayleigh_taylor_10_steps(orc, dg):
     _assert_steps_close(orc, wl, 10, w, w_ref)
 
 
+@pytest.mark.parametrize("case", [1, 2])
+def test_rhs_rising_bubble(orc, dg, case):
+    """The paper's rising bubble (slip sides, no-slip bottom, pressure top, viscous, gravity,
+    surface tension; both cases) on 4 x 8 quads, p = 4."""
+    _assert_parity(*_rhs_both(orc, dg, W.rising_bubble(nx=4, ny=8, p=4, case=case)))
+
+
+def test_step_rising_bubble(orc, dg):
+    wl = W.rising_bubble(nx=4, ny=8, p=4)
+    w, w_ref = _step_both(orc, dg, wl, 5)
+    _assert_steps_close(orc, wl, 5, w, w_ref)
+
+
 def test_step_rayleigh_taylor_small(orc, dg):
     wl = W.rayleigh_taylor(n=8, p=4, seed=3)
     w, w_ref = _step_both(orc, dg, wl, 5)
