@@ -122,3 +122,34 @@ def test_rider_kothe_full_period(orc, dg):
     assert res[16][2] < 2e-6, res
     assert res[64][2] < res[32][2] < res[16][2], res
 
+
+
+def _droplet_l1(dg, orc, n, p, eps):
+    import torch
+    wl = W.kin_drop(n=n, p=p, eps=eps)
+    xi, wt = orc.gll(wl.p)
+    M = np.tile(np.outer(wt, wt).ravel() * 0.25 * wl.hx * wl.hy, wl.nx * wl.ny)
+    s = dg.KinematicSolver(wl)
+    w = torch.from_numpy(wl.w.copy()).cuda()
+    s.dg_kin_step(w, 0.0, wl.dt, wl.nsteps)  # one period: the exact solution is the initial one
+    out = w.cpu().numpy()
+    assert s.dg_status_read() == 0
+    s.close()
+    return float(np.sum(M * np.abs(out[0] - wl.w[0])))
+
+
+def test_droplet_advection_convergence(orc, dg):
+    """The linear advection of a droplet (Sec. 4.1: R = 0.15, u = (1, 0), one period).  With the
+    paper's eps = 0.05 the L1 error falls under refinement for p = 1, 2, 3 and with p at a fixed
+    mesh, but the level set's cone tip at the drop centre, where phi (1 - phi) is still 0.045
+    (the drop is 3 eps in radius) and the discrete normal is O(1) wrong within an element, adds
+    an O(h^2) error; with eps = 0.02 (phi (1 - phi) = 5.5e-4 there) p = 3 converges at the optimal
+    rate p + 1."""
+    paper = {(p, n): _droplet_l1(dg, orc, n, p, 0.05) for p in (1, 2, 3) for n in (10, 20, 40)}
+    for p in (1, 2, 3):
+        assert paper[(p, 40)] < paper[(p, 20)] < paper[(p, 10)], paper
+    for n in (10, 20, 40):
+        assert paper[(3, n)] < paper[(2, n)] < paper[(1, n)], paper
+    thin = [_droplet_l1(dg, orc, n, 3, 0.02) for n in (20, 40, 80)]
+    rates = [np.log2(a / b) for a, b in zip(thin, thin[1:])]
+    assert min(rates) > 3.5, (thin, rates)
