@@ -11,7 +11,7 @@
 Workloads (``workloads.py``): ``slab`` (1D periodic water slab in air), ``drop`` (2D periodic
 water drop in air, seeded centre), ``rt`` (2D viscous Rayleigh-Taylor with walls, gravity and
 surface tension), ``rtpaper`` (the paper's Rayleigh-Taylor domain with slip sides and the pressure
-top), ``rk`` (the kinematic Rider-Kothe vortex, phi and psi only, classical RK4, on rectangles or,
+top), ``bubble`` (the paper's rising bubble, ``--case 1`` or ``2``), ``rk`` (the kinematic Rider-Kothe vortex, phi and psi only, classical RK4, on rectangles or,
 with ``--elem tri``, triangles; prints phi's min/max and mean instead of ``dg_diag``).  The state is
 built on the host (or read from a checkpoint with ``--resume``), moved to the GPU once, stepped
 with ``dg_step`` in one call and read back; the line printed holds the wall time of the call and
@@ -26,7 +26,8 @@ import time
 
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2306_05002_gb300")
-    ap.add_argument("workload", nargs="?", default="drop", choices=["slab", "drop", "rt", "rtpaper", "rk"])
+    ap.add_argument("workload", nargs="?", default="drop", choices=["slab", "drop", "rt", "rtpaper", "bubble", "rk"])
+    ap.add_argument("--case", type=int, default=1, choices=[1, 2], help="rising-bubble case (bubble only)")
     ap.add_argument("--n", type=int, default=None, help="elements per direction")
     ap.add_argument("--p", type=int, default=None, help="polynomial order")
     ap.add_argument("--steps", type=int, default=10)
@@ -65,6 +66,10 @@ def main(argv=None):
             if args.n is not None:
                 kw["nx"], kw["ny"] = args.n, 4 * args.n
             wl = W.rayleigh_taylor_paper(**kw)
+        elif args.workload == "bubble":
+            if args.n is not None:
+                kw["nx"], kw["ny"] = args.n, 2 * args.n
+            wl = W.rising_bubble(case=args.case, **kw)
         else:
             if args.n is not None:
                 kw["n"] = args.n
