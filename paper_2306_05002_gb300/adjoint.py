@@ -85,3 +85,21 @@ class DGTrajectory(torch.autograd.Function):
     def backward(ctx, grad_wN):
         lam0 = backward(ctx.solver, ctx.ckpt, grad_wN.contiguous(), ctx.dt, ctx.nsteps, ctx.every)
         return lam0, None, None, None, None
+
+
+class DGRHS(torch.autograd.Function):
+    """L = M^-1 R(w), one right-hand side, as a differentiable torch op: backward is the library's
+    hand-written reverse mode, dg_rhs_vjp (FP64 contexts without viscous / surface terms or a
+    pressure boundary)."""
+
+    @staticmethod
+    def forward(ctx, w, solver):
+        ctx.solver = solver
+        w = w.detach().contiguous()
+        ctx.save_for_backward(w)
+        return solver.dg_rhs(w)
+
+    @staticmethod
+    def backward(ctx, grad_L):
+        (w,) = ctx.saved_tensors
+        return ctx.solver.dg_rhs_vjp(w, grad_L.contiguous()), None

@@ -281,6 +281,30 @@ def test_dgtrajectory_autograd_gradient(orc, dg):
     np.testing.assert_allclose(g_theta, fd, rtol=GRAD_RTOL, atol=GRAD_RTOL * np.abs(fd).max())
 
 
+def test_dgrhs_autograd(dg):
+    """DGRHS, the torch.autograd.Function of one right-hand side: its gradient is dg_rhs_vjp bit for
+    bit, and <grad, v> matches a central difference of <lam, L(w)> along v (h = 1e-9, 2e-6)."""
+    import torch
+    from paper_2306_05002_gb300.adjoint import DGRHS
+    wl = W.drop_2d(n=8, p=3, seed=2)
+    s = dg.Solver(wl)
+    w0 = torch.from_numpy(_broken(wl)).cuda()
+    g = torch.Generator(device="cpu").manual_seed(4)
+    lam = torch.randn(w0.shape, generator=g, dtype=torch.float64).cuda()
+    lam /= s.dg_rhs(w0).abs().amax(dim=1, keepdim=True)
+    w = w0.clone().requires_grad_(True)
+    J = (lam * DGRHS.apply(w, s)).sum()
+    (grad,) = torch.autograd.grad(J, w)
+    assert torch.equal(grad, s.dg_rhs_vjp(w0, lam))
+    vdir = torch.randn(w0.shape, generator=g, dtype=torch.float64).cuda() * w0.abs().amax(dim=1, keepdim=True)
+    h = 1e-9
+    with torch.no_grad():
+        lhs = float(((lam * s.dg_rhs(w0 + h * vdir)).sum() - (lam * s.dg_rhs(w0 - h * vdir)).sum()) / (2 * h))
+    rhs = float((grad * vdir).sum())
+    s.close()
+    assert abs(lhs - rhs) <= 2e-6 * max(abs(lhs), abs(rhs)), (lhs, rhs)
+
+
 def test_adjoint_rejects_pressure_boundary(dg):
     """The discrete adjoint covers periodic and wall boundaries; a pressure boundary is refused."""
     import torch
