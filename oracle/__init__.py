@@ -170,6 +170,9 @@ def _configure(_lib):
     vp = ctypes.POINTER(_Velocity)
     _lib.orc_velocity_at.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
     _lib.orc_velocity_at.restype = None
+    _lib.orc_stream_at.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    _lib.orc_stream_at.restype = ctypes.c_double
+    _lib.orc_kin_velocity.argtypes = [pp, vp, ctypes.c_double, dp, dp]
     _lib.orc_kin_rhs.argtypes = [pp, vp, ctypes.c_double, dp, dp, dp]
     _lib.orc_kin_rk4.argtypes = [pp, vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
     _lib.orc_tri_num_nodes.argtypes = [pp]
@@ -315,6 +318,21 @@ def velocity_at(vel: Velocity, x: float, y: float, t: float):
     c = vel._c()
     lib().orc_velocity_at(ctypes.byref(c), float(x), float(y), float(t), ctypes.byref(u), ctypes.byref(v))
     return u.value, v.value
+
+
+def stream_at(vel: Velocity, x: float, y: float, t: float) -> float:
+    """Stream function of the prescribed velocity: u = dPsi/dy, v = -dPsi/dx."""
+    c = vel._c()
+    return lib().orc_stream_at(ctypes.byref(c), float(x), float(y), float(t))
+
+
+def kin_velocity(pb: Problem, vel: Velocity, t: float):
+    """The nodal velocity (u, v) the kinematic scheme uses at time t, shape (2, N)."""
+    out = np.zeros((2, pb.N))
+    s, c = pb._c(), vel._c()
+    _check(lib().orc_kin_velocity(ctypes.byref(s), ctypes.byref(c), float(t), _ptr(out[0]), _ptr(out[1])),
+           "kin_velocity")
+    return out
 
 
 def kin_rhs(pb: Problem, vel: Velocity, t: float, w, want_scale: bool = False):

@@ -63,11 +63,13 @@
  *     pressure (rho E from the stiffened-gas relation), and the
  *     Lax-Friedrichs flux between the two states carries it in; gradients and
  *     a_1 are treated as at a wall;
- *   - kinematic mode: the velocity is the analytical field sampled at the
- *     nodes, and the characteristic speed of the transport flux is the
- *     advection speed alone, lambda = max(|u-.m|, |u+.m|) (there is no sound
- *     speed in the kinematic system); everything else is the phi and psi
- *     rows of the full scheme;
+ *   - kinematic mode: a uniform velocity is taken as given, the Rider-Kothe
+ *     vortex as the discrete curl of its stream function interpolated at the
+ *     nodes (discretely divergence-free, normal component continuous across
+ *     faces, so the phase field's mass is conserved to round-off), and the
+ *     characteristic speed of the transport flux is the advection speed alone,
+ *     lambda = max(|u-.m|, |u+.m|) (there is no sound speed in the kinematic
+ *     system); everything else is the phi and psi rows of the full scheme;
  *   - re-initialisation: the equation is taken as
  *       d(psi)/d(tau) = S (1 - |grad psi|) + div(nu grad psi),
  *     the sign with which |grad psi| relaxes to 1 (as printed, with
@@ -880,6 +882,48 @@ void orc_velocity_at(const orc_velocity *vel, double x, double y, double t, doub
   }
 }
 
+double orc_stream_at(const orc_velocity *vel, double x, double y, double t) {
+  if (vel->kind == ORC_VEL_RIDER_KOTHE) {
+    double X = x - vel->xc + 0.5, Y = y - vel->yc + 0.5;
+    double sx = sin(M_PI * X), sy = sin(M_PI * Y);
+    return sx * sx * sy * sy * cos(M_PI * t / vel->T) / M_PI;
+  }
+  return vel->u0 * y - vel->v0 * x;
+}
+
+int orc_kin_velocity(const orc_problem *pr, const orc_velocity *vel, double t, double *u, double *v) {
+  geo_t g;
+  if (geo_init(&g, pr) || pr->dim != 2 || !vel) return -1;
+  const long N = g.N;
+  const int Np = g.Np;
+  double *x = (double *)malloc(sizeof(double) * N), *y = (double *)malloc(sizeof(double) * N);
+  double *psi = (double *)malloc(sizeof(double) * N);
+  if (!x || !y || !psi) {
+    free(x); free(y); free(psi);
+    return -2;
+  }
+  orc_nodes(pr, x, y);
+  if (vel->kind != ORC_VEL_RIDER_KOTHE) {
+    for (long n = 0; n < N; ++n) orc_velocity_at(vel, x[n], y[n], t, &u[n], &v[n]);
+  } else {
+    for (long n = 0; n < N; ++n) psi[n] = orc_stream_at(vel, x[n], y[n], t);
+    for (int e = 0; e < g.E; ++e)
+      for (int a = 0; a < Np; ++a) {
+        double ua = 0.0, va = 0.0;
+        for (int b = 0; b < Np; ++b) {
+          double gr[2];
+          grad_basis(&g, b, a, gr);
+          ua += psi[(long)e * Np + b] * gr[1];
+          va -= psi[(long)e * Np + b] * gr[0];
+        }
+        u[(long)e * Np + a] = ua;
+        v[(long)e * Np + a] = va;
+      }
+  }
+  free(x); free(y); free(psi);
+  return 0;
+}
+
 typedef struct {
   double phi, psi, u, v;
   double gphi[2], gpsi[2], n[2], a1[2], a1m[2];
@@ -895,22 +939,24 @@ int orc_kin_rhs(const orc_problem *pr, const orc_velocity *vel, double t, const 
   const int Np = g.Np, P1 = g.P1;
   const double Gam = pr->Gamma, eps = pr->eps;
   knode_t *nd = (knode_t *)calloc((size_t)N, sizeof(knode_t));
-  double *x = (double *)malloc(sizeof(double) * N), *y = (double *)malloc(sizeof(double) * N);
   double *R = (double *)calloc((size_t)2 * N, sizeof(double));
   double *A = (double *)calloc((size_t)2 * N, sizeof(double));
-  if (!nd || !x || !y || !R || !A) {
-    free(nd); free(x); free(y); free(R); free(A);
+  double *vu = (double *)malloc(sizeof(double) * N), *vv = (double *)malloc(sizeof(double) * N);
+  if (!nd || !R || !A || !vu || !vv || orc_kin_velocity(pr, vel, t, vu, vv)) {
+    free(nd); free(R); free(A); free(vu); free(vv);
     return -2;
   }
   acc_t ac = {R, A, NULL, N};
-  orc_nodes(pr, x, y);
 
-  /* 1. Nodal values and the prescribed velocity. */
+  /* 1. Nodal values and the nodal velocity of the scheme (orc_kin_velocity). */
   for (long n = 0; n < N; ++n) {
     nd[n].phi = w[n];
     nd[n].psi = w[N + n];
-    orc_velocity_at(vel, x[n], y[n], t, &nd[n].u, &nd[n].v);
+    nd[n].u = vu[n];
+    nd[n].v = vv[n];
   }
+  free(vu);
+  free(vv);
   /* 2. Broken gradients of phi and psi. */
   for (int e = 0; e < g.E; ++e)
     for (int a = 0; a < Np; ++a) {
@@ -1007,7 +1053,7 @@ int orc_kin_rhs(const orc_problem *pr, const orc_velocity *vel, double t, const 
         if (S) S[v * N + n] = A[v * N + n] * Minv;
       }
     }
-  free(nd); free(x); free(y); free(R); free(A);
+  free(nd); free(R); free(A);
   return 0;
 }
 

@@ -97,6 +97,14 @@ typedef struct {
 
 /* Velocity at (x, y) and time t. */
 void orc_velocity_at(const orc_velocity *vel, double x, double y, double t, double *u, double *v);
+/* Stream function Psi at (x, y) and time t: u = dPsi/dy, v = -dPsi/dx
+   (Rider-Kothe: sin^2(pi X) sin^2(pi Y) cos(pi t / T) / pi; uniform: u0 y - v0 x). */
+double orc_stream_at(const orc_velocity *vel, double x, double y, double t);
+/* The nodal velocity of the kinematic scheme at time t (u, v: N values each): a uniform field as
+   given; the Rider-Kothe vortex as the discrete curl of its stream function interpolated at each
+   element's nodes, (dPsi_h/dy, -dPsi_h/dx) with the element's derivative matrices, so that its
+   discrete divergence vanishes and its normal component is continuous across faces. */
+int orc_kin_velocity(const orc_problem *pr, const orc_velocity *vel, double t, double *u, double *v);
 /* L = M^-1 R(w) of the kinematic system at time t; S (nullable) as in orc_rhs. */
 int orc_kin_rhs(const orc_problem *pr, const orc_velocity *vel, double t, const double *w, double *L,
                 double *S);

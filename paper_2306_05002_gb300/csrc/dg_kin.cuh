@@ -9,8 +9,11 @@
 // non-conservative transport -u . grad f at the nodes, the transport flux
 // (lambda - m.u-) [[f]] with lambda = max(|u-.m|, |u+.m|) -- the advection
 // speed alone, as the kinematic system has no sound speed -- and the SIP flux
-// of a_1 with its lifted symmetric term.  The velocity is the analytical field
-// sampled at each node.  Time integration is the classical four-stage
+// of a_1 with its lifted symmetric term.  The nodal velocity is a uniform field
+// as given, or, for the Rider-Kothe vortex, the discrete curl of its stream
+// function interpolated at each element's nodes (discretely divergence-free,
+// normal components continuous across faces: the phase field's mass is then
+// conserved to round-off).  Time integration is the classical four-stage
 // Runge-Kutta method; each stage is one launch (k_kin_stage), which also
 // evaluates the neighbours' face traces from their nodal values.  Periodic
 // meshes only.
@@ -77,7 +80,16 @@ __device__ __forceinline__ double kin_time_factor(const KinParams &kp, double t)
   return kp.vel == VEL_RIDER_KOTHE ? cos(CUDART_PI * t / kp.T) : 1.0;
 }
 
-// U at every node of the rectangles, [N][2].
+// Spatial factor of the Rider-Kothe stream function, u = d(Psi)/dy and v = -d(Psi)/dx:
+// Psi = sin^2(pi X) sin^2(pi Y) / pi.
+__device__ __forceinline__ double kin_stream_factor(const KinParams &kp, double x, double y) {
+  const double sx = sin(CUDART_PI * (x - kp.xc + 0.5)), sy = sin(CUDART_PI * (y - kp.yc + 0.5));
+  return sx * sx * sy * sy / CUDART_PI;
+}
+
+// U at every node of the rectangles, [N][2]: a uniform field as given; the vortex as the
+// discrete curl of its stream function at the element's nodes, U = sum_c Dy[j][c] Psi(i, c),
+// V = -sum_c Dx[i][c] Psi(c, j) (Dx, Dy: the (2/h) D rows of the operator table).
 template <int P>
 __global__ void k_kin_velocity_table(const KinParams kp, double *__restrict__ tab) {
   constexpr int P1 = P + 1, NP = P1 * P1;
@@ -87,7 +99,20 @@ __global__ void k_kin_velocity_table(const KinParams kp, double *__restrict__ ta
   const int ex = e % kp.nx, ey = e / kp.nx;
   const double x = kp.x0 + kp.hx * (ex + 0.5 * (__ldg(kp.xi + i) + 1.0));
   const double y = kp.y0 + kp.hy * (ey + 0.5 * (__ldg(kp.xi + j) + 1.0));
-  kin_velocity_factor(kp, x, y, &tab[2 * n], &tab[2 * n + 1]);
+  if (kp.vel != VEL_RIDER_KOTHE) {
+    kin_velocity_factor(kp, x, y, &tab[2 * n], &tab[2 * n + 1]);
+    return;
+  }
+  const OpsLayout L{P1, NP};
+  double U = 0.0, V = 0.0;
+  for (int c = 0; c < P1; ++c) {
+    const double xc = kp.x0 + kp.hx * (ex + 0.5 * (__ldg(kp.xi + c) + 1.0));
+    const double yc = kp.y0 + kp.hy * (ey + 0.5 * (__ldg(kp.xi + c) + 1.0));
+    U = fma(__ldg(kp.ops + L.Dy() + j * P1 + c), kin_stream_factor(kp, x, yc), U);
+    V = fma(-__ldg(kp.ops + L.Dx() + i * P1 + c), kin_stream_factor(kp, xc, y), V);
+  }
+  tab[2 * n] = U;
+  tab[2 * n + 1] = V;
 }
 
 template <int P>

@@ -8,7 +8,10 @@ mathematics fixes rather than against the oracle's own formulas:
 * a pure phase stays put, a constant level set stays put (to the rounding of D's row sums);
 * for a uniform velocity the discrete phase-field mass is conserved to round-off (the
   non-conservative transport integrates to the single-valued upwind flux, and every
-  a_1 term sums to zero over a periodic domain);
+  a_1 term sums to zero over a periodic domain), and so for the vortex, whose nodal velocity
+  is the discrete curl of its stream function: that velocity reproduces the printed field
+  (finite differences of the stream function), is discretely divergence-free with continuous
+  normal components across faces, and converges to the analytical field at order p;
 * with Gamma = 0 the phase field is transported exactly like the level set;
 * with u = 0 and a constant level set the operator is the SIP diffusion alone:
   M L is symmetric, negative semi-definite, with the constants as its null space;
@@ -90,6 +93,67 @@ def test_uniform_velocity_conserves_phase_field_mass(orc, p):
     M = _weights(orc, pb)
     assert abs(np.sum(M * L[0])) <= 1e-13 * np.sum(M * S[0])
     assert abs(np.sum(M * L[1])) <= 1e-13 * np.sum(M * S[1])
+
+
+@pytest.mark.parametrize("centre", [(0.5, 0.5), (0.0, 0.0), (0.2, -0.1)])
+def test_stream_function_gives_the_vortex(orc, centre):
+    """u = dPsi/dy and v = -dPsi/dx (central differences of the stream function) reproduce the
+    Rider-Kothe field of orc_velocity_at."""
+    vel = orc.Velocity("rider_kothe", T=4.0, xc=centre[0], yc=centre[1])
+    h = 1e-5
+    for x, y, t in np.random.default_rng(8).uniform([-0.5, -0.5, 0.0], [0.5, 0.5, 4.0], (20, 3)):
+        u = (orc.stream_at(vel, x, y + h, t) - orc.stream_at(vel, x, y - h, t)) / (2 * h)
+        v = -(orc.stream_at(vel, x + h, y, t) - orc.stream_at(vel, x - h, y, t)) / (2 * h)
+        assert np.allclose((u, v), orc.velocity_at(vel, x, y, t), rtol=0, atol=1e-9)
+
+
+def _element_derivatives(orc, pb, f):
+    """d f/dx and d f/dy of nodal values f with each element's derivative matrices (node
+    a = i + (p+1) j), by numpy's matrix products rather than the oracle's basis gradients."""
+    xi, _ = orc.gll(pb.p)
+    D = orc.lagrange_deriv(pb.p, xi)
+    P1 = pb.p + 1
+    hx, hy = (pb.x1 - pb.x0) / pb.nx, (pb.y1 - pb.y0) / pb.ny
+    F = f.reshape(-1, P1, P1)                       # [element][j][i]
+    fx = np.einsum("ic,ejc->eji", D, F) * (2 / hx)
+    fy = np.einsum("jc,eci->eji", D, F) * (2 / hy)
+    return fx.reshape(-1), fy.reshape(-1)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_nodal_vortex_velocity(orc, p):
+    """The scheme's nodal Rider-Kothe velocity: discretely divergence-free in every element, its
+    normal component continuous across every face, and converging to the analytical field at
+    order p (the derivative of a degree-p interpolant)."""
+    vel = orc.Velocity("rider_kothe", T=4.0)
+    errs = []
+    for n in (6, 12):
+        pb = _pb(orc, n, p)
+        u, v = orc.kin_velocity(pb, vel, 0.7)
+        ux, _ = _element_derivatives(orc, pb, u)
+        _, vy = _element_derivatives(orc, pb, v)
+        assert np.abs(ux + vy).max() <= 1e-12 * np.abs(ux).max()
+        P1 = p + 1
+        U, V = u.reshape(n, n, P1, P1), v.reshape(n, n, P1, P1)    # [ey][ex][j][i]
+        assert np.abs(U[:, :, :, -1] - np.roll(U, -1, axis=1)[:, :, :, 0]).max() <= 1e-13   # E | W
+        assert np.abs(V[:, :, -1, :] - np.roll(V, -1, axis=0)[:, :, 0, :]).max() <= 1e-13   # N | S
+        x, y = orc.nodes(pb)
+        exact = np.array([orc.velocity_at(vel, a, b, 0.7) for a, b in zip(x, y)]).T
+        errs.append(max(np.abs(u - exact[0]).max(), np.abs(v - exact[1]).max()))
+    assert np.log2(errs[0] / errs[1]) > p - 0.5, errs
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_vortex_conserves_phase_field_mass(orc, p):
+    """With the discretely divergence-free vortex the phase field's mass is conserved to
+    round-off, as for a uniform velocity."""
+    pb = _pb(orc, 5, p, ny=4)
+    vel = orc.Velocity("rider_kothe", T=4.0, xc=0.1, yc=-0.2)
+    w = _smooth(orc, pb, seed=p)
+    M = _weights(orc, pb)
+    for t in (0.3, 1.7):
+        L, S = orc.kin_rhs(pb, vel, t, w, want_scale=True)
+        assert abs(np.sum(M * L[0])) <= 1e-13 * np.sum(M * S[0])
 
 
 def test_phase_field_without_a1_is_transported_like_the_level_set(orc):

@@ -117,6 +117,12 @@ MUTATIONS = [
     ("dg_oracle.c", "for (size_t i = 0; i < len; ++i) { acc[i] += 2.0 * k[i]; ws[i] = w[i] + dt * k[i]; }\n    if (rc == 0) rc = orc_kin_rhs",
      "for (size_t i = 0; i < len; ++i) { acc[i] += k[i]; ws[i] = w[i] + dt * k[i]; }\n    if (rc == 0) rc = orc_kin_rhs",
      "RK4 weight of the third stage"),
+    ("dg_oracle.c", "va -= psi[(long)e * Np + b] * gr[0];", "va += psi[(long)e * Np + b] * gr[0];",
+     "vortex velocity from the stream function with the wrong sign of v"),
+    ("dg_oracle.c", "ua += psi[(long)e * Np + b] * gr[1];", "ua += psi[(long)e * Np + b] * gr[0];",
+     "vortex velocity from the wrong derivative of the stream function"),
+    ("dg_oracle.c", "return sx * sx * sy * sy * cos(M_PI * t / vel->T) / M_PI;",
+     "return sx * sx * sy * sy * cos(M_PI * t / vel->T);", "stream function without its 1/pi"),
     # re-initialisation (end of Sec. 3)
     ("dg_oracle.c", "R[nk] += wk * S[nk] * (1.0 - gm);", "R[nk] += wk * S[nk] * (gm - 1.0);",
      "re-initialisation source with the printed (growing) sign"),
