@@ -266,6 +266,28 @@ def test_surface_tension_net_force_on_half_drop(orc):
     assert abs(np.sum(M * L[4])) < 1e-6 * 2 * sigma
 
 
+def test_laplace_pressure_jump_balances_surface_tension(orc):
+    """A drop at rest (phase 1 inside, radius R) whose pressure carries the Laplace jump across the
+    smeared interface, P = P0 + (sigma / R) phi: the pressure gradient and the CSF force
+    sigma kappa n delta (kappa = -div n = 1/r) cancel up to the variation of 1/r across the
+    interface, so the momentum rate is a small fraction of the CSF force alone and shrinks with
+    eps / R (with a wrong sign of kappa or of n the two would add up instead)."""
+    sigma, R = 0.07, 0.2
+    ratios = []
+    for n, eps in ((24, 0.02), (24, 0.01), (48, 0.005)):
+        wl = W.Workload(name="lap", dim=2, nx=n, ny=n, p=3, gamma=(1.4, 1.4), pinf=(0.0, 0.0),
+                        rho0=(1.0, 1.0), sigma=sigma, surface_tension=True, Gamma=0.0, eps=eps)
+        x, y = W.node_coords(wl)
+        s = R - np.hypot(x - 0.5, y - 0.5)
+        phi = W.tanh_profile(s, eps)
+        M = mass_weights(orc, wl)
+        norm = lambda L: np.sqrt(np.sum(M * (L[4] ** 2 + L[5] ** 2)))
+        csf = norm(orc.rhs(problem(orc, wl), W.conserved(wl, phi, s, 1e5, 0.0, 0.0)))
+        bal = norm(orc.rhs(problem(orc, wl), W.conserved(wl, phi, s, 1e5 + sigma / R * phi, 0.0, 0.0)))
+        ratios.append(bal / csf)
+    assert ratios[1] < 0.1 and ratios[2] < ratios[1] < ratios[0], ratios
+
+
 # --------------------------------------------------------------------------- broken (discontinuous) data
 
 def _broken(wl, w, seed=11, amp=0.05):
