@@ -156,7 +156,9 @@ dg_status dg_rhs(dg_ctx *ctx, const double *w, double *L, void *stream);
 /* Advance w (device, in place) by nsteps steps of the three-stage SSP
    Runge-Kutta method (Shu-Osher form) with step dt > 0.  nsteps = 0 is a
    no-op.  The step sequence is captured once in a CUDA graph per state array
-   w and replayed; the first call for a new w pays the capture.  The graphs
+   w and replayed; the context keeps the graphs of the two state arrays used
+   most recently (a caller alternating two buffers captures once per buffer),
+   and the first call for any other w pays a capture.  The graphs
    read the step size from device memory (set on stream when dt changes), so a
    caller that varies dt from call to call pays no capture for it. */
 dg_status dg_step(dg_ctx *ctx, double *w, double dt, int nsteps, void *stream);

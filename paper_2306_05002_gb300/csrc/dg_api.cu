@@ -255,8 +255,17 @@ struct dg_ctx {
   unsigned *d_status = nullptr;
   int nparts = 0;
   cudaStream_t cap = nullptr;
-  cudaGraphExec_t g1 = nullptr, gk = nullptr;
-  cudaGraphExec_t grem[8] = {};  // FP32-bulk: graphs of 1..7 steps, captured on first use
+  cudaGraphExec_t g1 = nullptr, gk = nullptr;  // dg_batch_step, dg_kin_step
+  // dg_step: the captured step graphs of the two state arrays used most recently (one step,
+  // GRAPH_UNROLL steps, and for FP32-bulk the remainders of 2..7 steps, captured on first use), so
+  // that a caller alternating two buffers captures once per buffer
+  struct StepGraphs {
+    const double *w = nullptr;
+    cudaGraphExec_t g1 = nullptr, gk = nullptr;
+    cudaGraphExec_t grem[8] = {};
+    unsigned long long used = 0;
+  } sg[2];
+  unsigned long long sg_clock = 0;
   // dg_adjoint_segment: captured segment sweeps, keyed by (steps, dt, states, tapes, lam)
   struct SegGraph {
     cudaGraphExec_t exec = nullptr;
@@ -272,7 +281,8 @@ struct dg_ctx {
 };
 
 static const int GRAPH_UNROLL = 8;
-static_assert(GRAPH_UNROLL <= (int)(sizeof(dg_ctx::grem) / sizeof(cudaGraphExec_t)), "remainder graph slots");
+static_assert(GRAPH_UNROLL <= (int)(sizeof(dg_ctx::StepGraphs::grem) / sizeof(cudaGraphExec_t)),
+              "remainder graph slots");
 
 static dg_status fail(dg_ctx *c, dg_status s, const std::string &msg) {
   if (c) c->err = msg;
@@ -284,15 +294,20 @@ static dg_status cuda_fail(dg_ctx *c, cudaError_t e, const char *what) {
   return fail(c, DG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+static void free_step_graphs(dg_ctx::StepGraphs *G) {
+  if (G->g1) cudaGraphExecDestroy(G->g1);
+  if (G->gk) cudaGraphExecDestroy(G->gk);
+  for (auto &g : G->grem)
+    if (g) cudaGraphExecDestroy(g);
+  *G = dg_ctx::StepGraphs{};
+}
+
 static void free_graphs(dg_ctx *c) {
   if (c->g1) cudaGraphExecDestroy(c->g1);
   if (c->gk) cudaGraphExecDestroy(c->gk);
   c->g1 = c->gk = nullptr;
-  for (auto &g : c->grem) {
-    if (g) cudaGraphExecDestroy(g);
-    g = nullptr;
-  }
   c->g_w = nullptr;
+  for (auto &G : c->sg) free_step_graphs(&G);
 }
 
 static void free_seg_graphs(dg_ctx *c) {
@@ -644,13 +659,20 @@ extern "C" dg_status dg_step(dg_ctx *c, double *w, double dt, int nsteps, void *
   if (!w) return fail(c, DG_ERR_ARG, "dg_step: null state");
   if (!(dt > 0.0) || nsteps < 0) return fail(c, DG_ERR_ARG, "dg_step: need dt > 0 and nsteps >= 0");
   if (nsteps == 0) return DG_OK;
-  if (c->g_w != w || !c->g1) {
-    free_graphs(c);
+  dg_ctx::StepGraphs *G = nullptr;
+  for (auto &x : c->sg)
+    if (x.g1 && x.w == w) G = &x;
+  if (!G) {  // capture for this state array, in a free slot or over the least recently used one
+    G = !c->sg[0].g1 ? &c->sg[0] : !c->sg[1].g1 ? &c->sg[1] : c->sg[0].used <= c->sg[1].used ? &c->sg[0] : &c->sg[1];
+    free_step_graphs(G);
     dg_status r;
-    if ((r = capture(c, w, dt, 1, &c->g1)) != DG_OK) return r;
-    if ((r = capture(c, w, dt, GRAPH_UNROLL, &c->gk)) != DG_OK) return r;
-    c->g_w = w;
+    if ((r = capture(c, w, dt, 1, &G->g1)) != DG_OK || (r = capture(c, w, dt, GRAPH_UNROLL, &G->gk)) != DG_OK) {
+      free_step_graphs(G);
+      return r;
+    }
+    G->w = w;
   }
+  G->used = ++c->sg_clock;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   if (dt != c->dt_set) {  // the graphs read the step size from device memory
@@ -659,18 +681,18 @@ extern "C" dg_status dg_step(dg_ctx *c, double *w, double dt, int nsteps, void *
     c->dt_set = dt;
   }
   for (int k = 0; k < nsteps / GRAPH_UNROLL; ++k)
-    if ((e = cudaGraphLaunch(c->gk, s)) != cudaSuccess) return cuda_fail(c, e, "dg_step: graph launch");
+    if ((e = cudaGraphLaunch(G->gk, s)) != cudaSuccess) return cuda_fail(c, e, "dg_step: graph launch");
   const int rem = nsteps % GRAPH_UNROLL;
   if (c->prec != DG_FP64 && rem > 1) {  // FP32-bulk: the remainder as one graph (fewer launches)
-    if (!c->grem[rem]) {
+    if (!G->grem[rem]) {
       dg_status r;
-      if ((r = capture(c, w, dt, rem, &c->grem[rem])) != DG_OK) return r;
+      if ((r = capture(c, w, dt, rem, &G->grem[rem])) != DG_OK) return r;
     }
-    if ((e = cudaGraphLaunch(c->grem[rem], s)) != cudaSuccess) return cuda_fail(c, e, "dg_step: graph launch");
+    if ((e = cudaGraphLaunch(G->grem[rem], s)) != cudaSuccess) return cuda_fail(c, e, "dg_step: graph launch");
     return DG_OK;
   }
   for (int k = 0; k < rem; ++k)
-    if ((e = cudaGraphLaunch(c->g1, s)) != cudaSuccess) return cuda_fail(c, e, "dg_step: graph launch");
+    if ((e = cudaGraphLaunch(G->g1, s)) != cudaSuccess) return cuda_fail(c, e, "dg_step: graph launch");
   return DG_OK;
 }
 

@@ -260,6 +260,30 @@ def test_step_rayleigh_taylor_small(orc, dg):
     _assert_steps_close(orc, wl, 5, w, w_ref)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32bulk"])
+def test_step_graphs_of_several_state_arrays(dg, precision):
+    """A context keeps the step graphs of the two state arrays used most recently: stepping three
+    buffers in turn (the third evicts the least recently used graphs, which are captured again
+    later) gives, for each buffer, exactly what a context of its own gives."""
+    import torch
+    wls = [W.drop_2d(n=6, p=3, seed=k) for k in (1, 2, 3)]
+    s = dg.Solver(wls[0], precision=precision)
+    bufs = [torch.from_numpy(wl.w.copy()).cuda() for wl in wls]
+    dt = wls[0].dt
+    for order in ((0, 1), (0, 1), (2, 0), (1, 2), (0,)):
+        for k in order:
+            s.dg_step(bufs[k], dt, 3)
+    counts = [4, 3, 2]  # calls of 3 steps per buffer
+    s.close()
+    for k in range(3):
+        ref_s = dg.Solver(wls[0], precision=precision)
+        ref = torch.from_numpy(wls[k].w.copy()).cuda()
+        for _ in range(counts[k]):
+            ref_s.dg_step(ref, dt, 3)
+        ref_s.close()
+        assert torch.equal(bufs[k], ref), k
+
+
 def test_step_zero_is_noop(dg):
     import torch
     wl = W.drop_2d(n=4, p=2, seed=1)
