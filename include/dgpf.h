@@ -371,9 +371,9 @@ dg_status dg_kin_nodes(const dg_mesh *mesh, int p, double *x, double *y);
 dg_status dg_kin_rhs(dg_ctx *ctx, const double *w, double t, double *L, void *stream);
 
 /* Advance w (device, in place) from time t0 by nsteps classical RK4 steps of
-   size dt > 0.  Captured once in a CUDA graph per (w, dt) pair (the graph reads
-   the start time from device memory, so t0 may change freely).  Asynchronous
-   on stream. */
+   size dt > 0.  Captured once in a CUDA graph per state array w (the graphs
+   read the start time and the step size from device memory, so t0 and dt
+   may change freely).  Asynchronous on stream. */
 dg_status dg_kin_step(dg_ctx *ctx, double *w, double t0, double dt, int nsteps, void *stream);
 
 /* Level-set re-initialisation (end of Sec. 3): replace the level set psi of

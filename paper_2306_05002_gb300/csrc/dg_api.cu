@@ -274,8 +274,7 @@ struct dg_ctx {
     const double *states = nullptr, *tapes = nullptr, *lam = nullptr;
   } seg[2];
   const double *g_w = nullptr;
-  double g_dt = 0.0;
-  double *d_dt = nullptr;      // the step size the captured dg_step graphs read
+  double *d_dt = nullptr;      // the step size the captured dg_step / dg_kin_step graphs read
   double dt_set = 0.0;         // the value last written there (0: none)
   std::string err = "no error";
 };
@@ -1280,6 +1279,8 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
     c->tri_grid = (int)std::max(1L, std::min(groups, (long)std::max(1, sms) * std::max(1, per_sm)));
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->d_kt0, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_dt, sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->d_dt, 0, sizeof(double));  // dg_kin_rhs: stage time t0 exactly
   if (e == cudaSuccess) e = cudaMalloc(&c->d_kxi, xi.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_ops, ops.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
@@ -1297,6 +1298,7 @@ extern "C" dg_status dg_kin_create(const dg_mesh *mesh, int p, double Gamma, dou
   k.ops = c->d_ops;
   k.xi = c->d_kxi;
   k.t0 = c->d_kt0;
+  k.dt = c->d_dt;
   k.status = c->d_status;
   k.vel_tab = c->d_ktv;
   e = tri ? c->tk.velocity_table(k, c->d_ktv, c->cap) : c->kk.velocity_table(k, c->d_ktv, c->cap);
@@ -1362,40 +1364,40 @@ extern "C" dg_status dg_kin_rhs(dg_ctx *c, const double *w, double t, double *L,
   k_kin_set_time<<<1, 1, 0, s>>>(c->d_kt0, t);
   cudaError_t e = cudaGetLastError();
   if (c->tri) {
-    if (e == cudaSuccess) e = c->tk.stage(c->kp, KIN_RHS, 0.0, 0.0, 0.0, w, nullptr, nullptr, L, c->tri_grid, s);
+    if (e == cudaSuccess) e = c->tk.stage(c->kp, KIN_RHS, 0, 0.0, w, nullptr, nullptr, L, c->tri_grid, s);
     return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_kin_rhs: launch");
   }
-  if (e == cudaSuccess) e = c->kk.stage(c->kp, KIN_RHS, 0.0, 0.0, 0.0, w, nullptr, nullptr, L, s);
+  if (e == cudaSuccess) e = c->kk.stage(c->kp, KIN_RHS, 0, 0.0, w, nullptr, nullptr, L, s);
   return e == cudaSuccess ? DG_OK : cuda_fail(c, e, "dg_kin_rhs: launch");
 }
 
 // One classical RK4 step of the captured sequence: step k of the graph, stage
-// inputs w -> A -> B -> A, the last stage writes w in place.
-static dg_status enqueue_kin_step(dg_ctx *c, double *w, double dt, int k, cudaStream_t s) {
+// inputs w -> A -> B -> A, the last stage writes w in place.  The kernels read
+// the step size from device memory (c->d_dt) and form the stage times there.
+static dg_status enqueue_kin_step(dg_ctx *c, double *w, int k, cudaStream_t s) {
   double *A = c->d_kwsA, *B = c->d_kwsB;
-  const double tstep = k * dt;
-  const double toff[4] = {0.0, 0.5 * dt, 0.5 * dt, dt};
+  const double frac[4] = {0.0, 0.5, 0.5, 1.0};
   const double *in[4] = {w, A, B, A};
   double *out[4] = {A, B, A, w};
   const int mode[4] = {KIN_K1, KIN_K2, KIN_K3, KIN_K4};
   for (int st = 0; st < 4; ++st) {
     cudaError_t e;
     if (c->tri) {
-      e = c->tk.stage(c->kp, mode[st], tstep, toff[st], dt, in[st], w, c->d_kacc, out[st], c->tri_grid, s);
+      e = c->tk.stage(c->kp, mode[st], k, frac[st], in[st], w, c->d_kacc, out[st], c->tri_grid, s);
     } else {
-      e = c->kk.stage(c->kp, mode[st], tstep, toff[st], dt, in[st], w, c->d_kacc, out[st], s);
+      e = c->kk.stage(c->kp, mode[st], k, frac[st], in[st], w, c->d_kacc, out[st], s);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "dg_kin_step: launch");
   }
   return DG_OK;
 }
 
-static dg_status capture_kin(dg_ctx *c, double *w, double dt, int steps, cudaGraphExec_t *exec) {
+static dg_status capture_kin(dg_ctx *c, double *w, int steps, cudaGraphExec_t *exec) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(c, e, "dg_kin_step: begin capture");
   dg_status r = DG_OK;
-  for (int k = 0; k < steps && r == DG_OK; ++k) r = enqueue_kin_step(c, w, dt, k, c->cap);
+  for (int k = 0; k < steps && r == DG_OK; ++k) r = enqueue_kin_step(c, w, k, c->cap);
   e = cudaStreamEndCapture(c->cap, &g);
   if (r != DG_OK) {
     if (g) cudaGraphDestroy(g);
@@ -1413,15 +1415,19 @@ extern "C" dg_status dg_kin_step(dg_ctx *c, double *w, double t0, double dt, int
   if (!w) return fail(c, DG_ERR_ARG, "dg_kin_step: null state");
   if (!(dt > 0.0) || nsteps < 0) return fail(c, DG_ERR_ARG, "dg_kin_step: need dt > 0 and nsteps >= 0");
   if (nsteps == 0) return DG_OK;
-  if (c->g_w != w || c->g_dt != dt || !c->g1) {
+  if (c->g_w != w || !c->g1) {  // the graphs read dt and the start time from device memory
     free_graphs(c);
-    if ((r = capture_kin(c, w, dt, 1, &c->g1)) != DG_OK) return r;
-    if ((r = capture_kin(c, w, dt, GRAPH_UNROLL, &c->gk)) != DG_OK) return r;
+    if ((r = capture_kin(c, w, 1, &c->g1)) != DG_OK) return r;
+    if ((r = capture_kin(c, w, GRAPH_UNROLL, &c->gk)) != DG_OK) return r;
     c->g_w = w;
-    c->g_dt = dt;
   }
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
+  if (dt != c->dt_set) {
+    k_set_double<<<1, 1, 0, s>>>(c->d_dt, dt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "dg_kin_step: set dt");
+    c->dt_set = dt;
+  }
   int done = 0;
   while (done < nsteps && e == cudaSuccess) {
     const bool big = nsteps - done >= GRAPH_UNROLL;

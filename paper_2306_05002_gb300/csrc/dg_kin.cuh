@@ -54,6 +54,7 @@ struct KinParams {
   const double *ops;       // operator table (OpsLayout)
   const double *xi;        // GLL nodes on [-1, 1]
   const double *t0;        // device: time at the start of the captured step sequence
+  const double *dt;        // device: the step size of the captured step sequences
   int check_finite;
   unsigned *status;
 };
@@ -152,13 +153,16 @@ __device__ __forceinline__ int kin_face_node(int f, int kk) {
 //   K4: out = w0 + dt/6 (acc + L)   (out may be w0: each node is read, then
 //                                    written, by the same thread)
 // Neighbour values come from the stage input, which no stage writes, so the
-// stages need no synchronisation beyond stream order.  The stage time is
-// *kp.t0 + (step dt) + (stage offset), as the two host-side parts tstep =
-// step index x dt and toff = stage fraction x dt.
+// stages need no synchronisation beyond stream order.  The step size is read
+// from device memory (*kp.dt), so captured step sequences serve any dt; the
+// stage time is *kp.t0 + (kstep dt) + (frac dt), kstep the step's index in the
+// captured sequence and frac the stage's fraction of the step (0, 1/2, 1/2, 1).
 template <int P>
 __global__ void __launch_bounds__(Geom<P, 2, false, false>::THREADS)
-k_kin_stage(const KinParams kp, int mode, double tstep, double toff, double dt, const double *__restrict__ win,
+k_kin_stage(const KinParams kp, int mode, int kstep, double frac, const double *__restrict__ win,
             const double *w0, double *__restrict__ acc, double *out) {
+  const double dt = __ldg(kp.dt);
+  const double tstep = kstep * dt, toff = frac * dt;
   using G = Geom<P, 2, false, false>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
   const OpsLayout L{P1, NP};
@@ -333,16 +337,16 @@ k_kin_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
 }
 
 struct KinKernels {
-  cudaError_t (*stage)(const KinParams &, int mode, double tstep, double toff, double dt, const double *win,
-                       const double *w0, double *acc, double *out, cudaStream_t);
+  cudaError_t (*stage)(const KinParams &, int mode, int kstep, double frac, const double *win, const double *w0,
+                       double *acc, double *out, cudaStream_t);
   cudaError_t (*velocity_table)(const KinParams &, double *tab, cudaStream_t);
 };
 
 template <int P>
-cudaError_t launch_kin_stage(const KinParams &kp, int mode, double tstep, double toff, double dt, const double *win,
+cudaError_t launch_kin_stage(const KinParams &kp, int mode, int kstep, double frac, const double *win,
                              const double *w0, double *acc, double *out, cudaStream_t s) {
   using G = Geom<P, 2, false, false>;
-  k_kin_stage<P><<<(kp.E + G::EPB - 1) / G::EPB, G::THREADS, 0, s>>>(kp, mode, tstep, toff, dt, win, w0, acc, out);
+  k_kin_stage<P><<<(kp.E + G::EPB - 1) / G::EPB, G::THREADS, 0, s>>>(kp, mode, kstep, frac, win, w0, acc, out);
   return cudaGetLastError();
 }
 

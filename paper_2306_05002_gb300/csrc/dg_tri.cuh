@@ -213,14 +213,16 @@ __device__ __forceinline__ void tri_edge_trace(const double *s_t, const TriLayou
   o->n_m = g2 < 1e-24 ? 0.0 : sgn * gs * rsqrt(g2);  // n = 0 where |grad psi| < 1e-12
 }
 
-// One stage: the right-hand side L = M^-1 R(win) at time *t0 + tstep + toff,
+// One stage: the right-hand side L = M^-1 R(win) at time *t0 + kstep dt + frac dt,
 // written as L (KIN_RHS) or as one classical RK4 stage (KIN_K1..K4, the same
 // updates as k_kin_stage; out may be w0, each node being read, then written,
 // by the same thread).
 template <int P>
 __global__ void __launch_bounds__(TriGeom<P>::THREADS)
-k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, const double *__restrict__ win,
+k_tri_stage(const KinParams kp, int mode, int kstep, double frac, const double *__restrict__ win,
             const double *w0, double *__restrict__ acc, double *out) {
+  const double dt = __ldg(kp.dt);  // step size and stage time as in k_kin_stage
+  const double tstep = kstep * dt, toff = frac * dt;
   using G = TriGeom<P>;
   constexpr TriLayout L = G::L;
   constexpr int NP = G::NP, NQ1 = G::NQ1, NQV = G::NQV, NQE = G::NQE, EPB = G::EPB;
@@ -384,8 +386,8 @@ k_tri_stage(const KinParams kp, int mode, double tstep, double toff, double dt, 
 }
 
 struct TriKernels {
-  cudaError_t (*stage)(const KinParams &, int mode, double tstep, double toff, double dt, const double *win,
-                       const double *w0, double *acc, double *out, int grid, cudaStream_t);
+  cudaError_t (*stage)(const KinParams &, int mode, int kstep, double frac, const double *win, const double *w0,
+                       double *acc, double *out, int grid, cudaStream_t);
   cudaError_t (*velocity_table)(const KinParams &, double *tab, cudaStream_t);
   const void *fn;  // the stage kernel, for the occupancy query
   int threads;
@@ -393,9 +395,9 @@ struct TriKernels {
 };
 
 template <int P>
-cudaError_t launch_tri_stage(const KinParams &kp, int mode, double tstep, double toff, double dt, const double *win,
+cudaError_t launch_tri_stage(const KinParams &kp, int mode, int kstep, double frac, const double *win,
                              const double *w0, double *acc, double *out, int grid, cudaStream_t s) {
-  k_tri_stage<P><<<grid, TriGeom<P>::THREADS, 0, s>>>(kp, mode, tstep, toff, dt, win, w0, acc, out);
+  k_tri_stage<P><<<grid, TriGeom<P>::THREADS, 0, s>>>(kp, mode, kstep, frac, win, w0, acc, out);
   return cudaGetLastError();
 }
 
