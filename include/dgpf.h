@@ -136,7 +136,8 @@ typedef struct dg_ctx dg_ctx;
    opts may be NULL (FP64, c_ip = 1, no viscous/gravity/surface terms).
    Allocates all device memory the context will use on the current device
    (except the staging buffer of dg_step_host, allocated on its first staged
-   call).
+   call, and the device copy of a page-locked host state, allocated on the
+   first FP32-bulk single step of one).
    On success *out receives the context; on failure *out is NULL. */
 dg_status dg_create(const dg_mesh *mesh, int p, const dg_eos *eos, double Gamma, double eps,
                     const dg_opts *opts, dg_ctx **out);
@@ -168,7 +169,11 @@ dg_status dg_step(dg_ctx *ctx, double *w, double dt, int nsteps, void *stream);
    with a page-locked, device-mapped w_host (cudaHostAlloc / cudaHostRegister
    memory, e.g. a pinned torch tensor) read and write it in place from the
    kernels over the host link: the first stage reads the FP64 state, the last
-   stage writes it.  Otherwise the state is copied to a device staging buffer
+   stage writes it (a single step also leaves a device copy of the state it
+   read, dg_state_len doubles allocated on first use and kept until
+   dg_destroy, and adds its last increment to that copy, so the state
+   crosses the link once each way; DG_ERR_OOM if that allocation fails).
+   dg_step given such a pointer does the same.  Otherwise the state is copied to a device staging buffer
    (dg_state_len doubles, allocated on the first such call and kept until
    dg_destroy; DG_ERR_OOM if that fails), stepped and copied back, all on
    stream; pageable memory works but is staged by the driver.  No Sec. of the

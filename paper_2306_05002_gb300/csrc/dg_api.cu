@@ -241,6 +241,7 @@ struct dg_ctx {
         *d_trace32 = nullptr, *d_rvol32b = nullptr, *d_trace32b = nullptr;
   double *d_ops = nullptr, *d_w1 = nullptr, *d_w2 = nullptr, *d_rvol = nullptr, *d_trace = nullptr;
   double *d_hstate = nullptr;  // device copy of a host state (dg_step_host), allocated on first use
+  double *d_copy64 = nullptr;  // FP32-bulk single steps on a page-locked host state (enqueue_steps32)
   // kinematic mode (dg_kin_create); tri: triangles (one fused kernel per stage)
   bool kin = false, tri = false;
   KinParams kp{};
@@ -333,6 +334,7 @@ static void free_ctx(dg_ctx *c) {
   }
   cudaFree(c->d_ops);
   cudaFree(c->d_hstate);
+  cudaFree(c->d_copy64);
   for (double *q : {c->d_kacc, c->d_kwsA, c->d_kwsB, c->d_kt0, c->d_kxi, c->d_ktv}) cudaFree(q);
   for (double *q : {c->d_riS, c->d_ri1, c->d_ri2, c->d_rirvol, c->d_ritr}) cudaFree(q);
   cudaFree(c->d_w1);
@@ -558,7 +560,7 @@ static dg_status run_stage(dg_ctx *c, int mode, double dt, const double *w0, con
 // surface kernel writes L in FP64.
 static dg_status rhs32(dg_ctx *c, const double *w64, double *L, cudaStream_t s) {
   cudaError_t e = c->ks32.volume(c->prm, c->pf, c->d_opsf, nullptr, c->d_rvol32, c->d_trace32, w64, c->d_hi32[0],
-                                 nullptr, s);
+                                 nullptr, nullptr, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "volume kernel launch");
   const StageIO io{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, L, nullptr};
   e = c->ks32.surface(c->prm, c->pf, c->d_opsf, MODE_RHS, 0.f, io, c->d_rvol32, c->d_trace32, s);
@@ -601,13 +603,18 @@ static dg_status enqueue_step(dg_ctx *c, double *w, double dt, cudaStream_t s) {
 // and writes the new step start into the other buffer of each pair (H, Lo),
 // so that no launch writes an array it also reads; the volume part and the
 // traces alternate between the two buffers of their pairs.
-static dg_status enqueue_steps32(dg_ctx *c, double *w, float dt, int steps, cudaStream_t s) {
+// copy64 != NULL (a single step on a state in host memory): the first launch also copies the
+// FP64 state it reads into copy64 (device memory), and the last adds its increment to that copy,
+// so that the state crosses the host link once each way.
+static dg_status enqueue_steps32(dg_ctx *c, double *w, float dt, int steps, cudaStream_t s,
+                                 double *copy64 = nullptr) {
   float *const *H = c->d_hi32, *const *Lo = c->d_lo32, *const *D = c->d_dd32;
   float *rv[2] = {c->d_rvol32, c->d_rvol32b}, *tr[2] = {c->d_trace32, c->d_trace32b};
   int t = 0, a = 0;
+  if (steps != 1) copy64 = nullptr;
   // a single step adds its last increment to the FP64 state itself: no lo part is needed
   cudaError_t e = c->ks32.volume(c->prm, c->pf, c->d_opsf, nullptr, rv[t], tr[t], w, H[a], steps > 1 ? Lo[a] : nullptr,
-                                 s);
+                                 copy64, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "volume kernel launch");
   for (int k = 0; k < steps; ++k) {
     const bool last = k == steps - 1;
@@ -615,7 +622,7 @@ static dg_status enqueue_steps32(dg_ctx *c, double *w, float dt, int steps, cuda
         {H[a], nullptr, nullptr, D[0], nullptr, nullptr, nullptr, nullptr, c->d_dt},
         {H[a], nullptr, D[0], D[1], nullptr, nullptr, nullptr, nullptr, c->d_dt},
         {H[a], Lo[a], D[1], nullptr, last ? nullptr : H[a ^ 1], last ? nullptr : Lo[a ^ 1], last ? w : nullptr,
-         steps == 1 ? w : nullptr, c->d_dt}};
+         steps == 1 ? (copy64 ? copy64 : w) : nullptr, c->d_dt}};
     const int mode[3] = {MODE_S1, MODE_S2, MODE_S3};
     for (int st = 0; st < 3; ++st) {
       if (st == 2 && last) {
@@ -633,11 +640,30 @@ static dg_status enqueue_steps32(dg_ctx *c, double *w, float dt, int steps, cuda
 }
 
 static dg_status capture(dg_ctx *c, double *w, double dt, int steps, cudaGraphExec_t *exec) {
+  double *copy64 = nullptr;
+  if (c->prec != DG_FP64 && steps == 1) {
+    // a state in page-locked host memory, read and written in place over the host link
+    cudaPointerAttributes at{};
+    const bool host = cudaPointerGetAttributes(&at, w) == cudaSuccess && at.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    if (host) {
+      if (!c->d_copy64) {
+        cudaError_t e = cudaMalloc(&c->d_copy64, c->len * sizeof(double));
+        if (e != cudaSuccess) {
+          c->d_copy64 = nullptr;
+          cudaGetLastError();
+          return fail(c, e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA,
+                      std::string("dg_step: device copy of a host state: ") + cudaGetErrorString(e));
+        }
+      }
+      copy64 = c->d_copy64;
+    }
+  }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(c, e, "dg_step: begin capture");
   dg_status r = DG_OK;
-  if (c->prec != DG_FP64) r = enqueue_steps32(c, w, (float)dt, steps, c->cap);
+  if (c->prec != DG_FP64) r = enqueue_steps32(c, w, (float)dt, steps, c->cap, copy64);
   else
     for (int s = 0; s < steps && r == DG_OK; ++s) r = enqueue_step(c, w, dt, c->cap);
   e = cudaStreamEndCapture(c->cap, &g);
@@ -793,7 +819,8 @@ extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_
       if (k == 0) c->ks.volume(c->prm, w, c->d_rvol, c->d_trace, s);
       else c->ks.surface(c->prm, MODE_RHS, 0.0, w, w, c->d_rvol, c->d_trace, c->d_w1, s);
     } else if (k == 0) {  // the kernels of a step as dg_step launches them (FP32 state in, FP32 stage out)
-      c->ks32.volume(c->prm, c->pf, c->d_opsf, c->d_hi32[0], c->d_rvol32, c->d_trace32, nullptr, nullptr, nullptr, s);
+      c->ks32.volume(c->prm, c->pf, c->d_opsf, c->d_hi32[0], c->d_rvol32, c->d_trace32, nullptr, nullptr, nullptr,
+                     nullptr, s);
     } else if (k == 1) {
       const StageIO io{c->d_hi32[0], nullptr, c->d_dd32[0], c->d_dd32[1], nullptr, nullptr, nullptr, nullptr};
       c->ks32.surface(c->prm, c->pf, c->d_opsf, MODE_S2, 1e-9f, io, c->d_rvol32, c->d_trace32, s);
@@ -802,14 +829,16 @@ extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_
       c->ks32.surfvol(c->prm, c->pf, c->d_opsf, MODE_S2, 1e-9f, io, c->d_rvol32, c->d_trace32, c->d_rvol32b,
                       c->d_trace32b, s);
     } else if (k == 3) {  // the first stage of a single-step call: reads the FP64 state (hi part only)
-      c->ks32.volume(c->prm, c->pf, c->d_opsf, nullptr, c->d_rvol32b, c->d_trace32b, w, c->d_hi32[1], nullptr, s);
+      c->ks32.volume(c->prm, c->pf, c->d_opsf, nullptr, c->d_rvol32b, c->d_trace32b, w, c->d_hi32[1], nullptr,
+                     nullptr, s);
     } else {  // the last stage of a single-step call: adds the last increment to the FP64 state
       const StageIO io{nullptr, nullptr, c->d_dd32[0], nullptr, nullptr, nullptr, tmp64, w};
       c->ks32.surface(c->prm, c->pf, c->d_opsf, MODE_S3, 1e-9f, io, c->d_rvol32, c->d_trace32, s);
     }
   };
   if (!f64) {  // the internal state of w (hi, lo) and a zero increment to time the stage kernels on
-    c->ks32.volume(c->prm, c->pf, c->d_opsf, nullptr, c->d_rvol32, c->d_trace32, w, c->d_hi32[0], c->d_lo32[0], s);
+    c->ks32.volume(c->prm, c->pf, c->d_opsf, nullptr, c->d_rvol32, c->d_trace32, w, c->d_hi32[0], c->d_lo32[0],
+                   nullptr, s);
     cudaMemsetAsync(c->d_dd32[0], 0, (size_t)SW32 * c->N * sizeof(float), s);
   }
   cudaEvent_t ev[2];

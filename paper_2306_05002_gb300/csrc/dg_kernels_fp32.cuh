@@ -306,7 +306,8 @@ __device__ __forceinline__ void load_line(const float *row, float *v) {
 
 // Volume kernel body for the element tile `blk` (EPB elements) of one problem.
 // opsf: FP32 operator table (OpsLayout).  w64 != NULL: read the FP64 state and
-// write the FP32 internal state to w32out (first stage of a step).  qin !=
+// write the FP32 internal state to w32out (first stage of a step), and, when
+// w64copy != NULL, the FP64 values as read into w64copy.  qin !=
 // NULL: the thread's node state is already in registers (fused kernel).
 // s_op: the block's shared copy of the operator table; this body copies the
 // two derivative matrices into it unless ops_ready (the fused kernel's
@@ -316,7 +317,8 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
                                            float *s_op, bool ops_ready, int blk, const float *__restrict__ w,
                                            float *__restrict__ rvol, float *__restrict__ tr,
                                            const double *__restrict__ w64, float *__restrict__ w32out,
-                                           const float *qin = nullptr, float *__restrict__ lo_out = nullptr) {
+                                           const float *qin = nullptr, float *__restrict__ lo_out = nullptr,
+                                           double *__restrict__ w64copy = nullptr) {
   using G = Geom<P, DIM, VISC, ST, EPBX>;
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
   constexpr int P11 = P1 * P1;
@@ -356,6 +358,12 @@ __device__ __forceinline__ void vol32_body(const Params &prm, const ParamsF &pf,
     double d[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) d[v] = act ? ld_in<PDL>(w64 + (long)v * N + n) : (v == M1 || v == M2 ? 1.0 : 0.0);
+    if (w64copy && act) {
+      // a device copy of a state in host memory, for the last stage to add to (one read over the
+      // host link per call instead of two)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) w64copy[(long)v * N + n] = d[v];
+    }
     d[RE] = d[RE] - fma(prm.dC, d[PHI], prm.C2);
     if (lo_out) {
       // a call of several steps carries the step start as hi + lo
@@ -597,7 +605,7 @@ template <int P, int DIM, bool VISC, bool ST, bool PDL>
 __global__ void __launch_bounds__(Geom<P, DIM, VISC, ST>::THREADS)
 k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, const float *__restrict__ w,
            float *__restrict__ rvol, float *__restrict__ tr, const double *__restrict__ w64,
-           float *__restrict__ w32out, float *__restrict__ lo_out) {
+           float *__restrict__ w32out, float *__restrict__ lo_out, double *__restrict__ w64copy) {
   constexpr int P11 = Geom<P, DIM, VISC, ST>::P1 * Geom<P, DIM, VISC, ST>::P1;
   __shared__ float s_op[2 * P11];  // Dx, Dy
   if (PDL) {
@@ -606,7 +614,7 @@ k_volume32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, c
     grid_dependency_wait();
   }
   vol32_body<P, DIM, VISC, ST, 0, PDL>(prm, pf, opsf, s_op, PDL, blockIdx.x, w, rvol, tr, w64, w32out, nullptr,
-                                       lo_out);
+                                       lo_out, w64copy);
 }
 
 // The NC words of face-trace record o (records of RW floats, 128-bit loads), or, when the record
@@ -993,10 +1001,12 @@ k_surfvol32(const Params prm, const ParamsF pf, const float *__restrict__ opsf, 
 
 // Launch interface of one FP32-bulk kernel family.  volume: the volume part of a
 // stage on the FP32 state w, or, with w64, on the FP64 state, which it splits
-// into the internal state's hi (w32out) and lo (lo_out, may be NULL) parts.
+// into the internal state's hi (w32out) and lo (lo_out, may be NULL) parts and
+// copies into w64copy (may be NULL).
 struct KernelSet32 {
   cudaError_t (*volume)(const Params &, const ParamsF &, const float *opsf, const float *w, float *rvol,
-                        float *trace, const double *w64, float *w32out, float *lo_out, cudaStream_t);
+                        float *trace, const double *w64, float *w32out, float *lo_out, double *w64copy,
+                        cudaStream_t);
   cudaError_t (*surface)(const Params &, const ParamsF &, const float *opsf, int mode, float dt, const StageIO &io,
                          const float *rvol, const float *trace, cudaStream_t);
   cudaError_t (*surfvol)(const Params &, const ParamsF &, const float *opsf, int mode, float dt, const StageIO &io,
@@ -1014,15 +1024,16 @@ struct KernelSet32 {
 // non-coherent loads, a few per cent faster on the viscous surface kernels).
 template <int P, int DIM, bool VISC, bool ST>
 cudaError_t launch_volume32(const Params &prm, const ParamsF &pf, const float *opsf, const float *w, float *rvol,
-                            float *trace, const double *w64, float *w32out, float *lo_out, cudaStream_t s) {
+                            float *trace, const double *w64, float *w32out, float *lo_out, double *w64copy,
+                            cudaStream_t s) {
   using G = Geom<P, DIM, VISC, ST>;
   const int blocks = (prm.E + G::EPB - 1) / G::EPB;
   static const int resident = resident_blocks(k_volume32<P, DIM, VISC, ST, true>, G::THREADS);
   if (blocks <= resident)
     return launch_dependent(k_volume32<P, DIM, VISC, ST, true>, blocks, G::THREADS, s, prm, pf, opsf, w, rvol,
-                            trace, w64, w32out, lo_out);
+                            trace, w64, w32out, lo_out, w64copy);
   k_volume32<P, DIM, VISC, ST, false><<<blocks, G::THREADS, 0, s>>>(prm, pf, opsf, w, rvol, trace, w64, w32out,
-                                                                    lo_out);
+                                                                    lo_out, w64copy);
   return cudaGetLastError();
 }
 

@@ -294,26 +294,29 @@ def test_step_zero_is_noop(dg):
     s.close()
 
 
-@pytest.mark.parametrize("precision,pinned", [("fp64", False), ("fp64", True), ("fp32bulk", True)])
-def test_step_host_buffer_round_trip(orc, dg, precision, pinned):
+@pytest.mark.parametrize("precision,pinned,maker", [
+    ("fp64", False, "drop"), ("fp64", True, "drop"), ("fp32bulk", False, "drop"), ("fp32bulk", True, "drop"),
+    ("fp32bulk", True, "rt")])
+def test_step_host_buffer_round_trip(orc, dg, precision, pinned, maker):
     """dg_step_host (a CPU tensor, pageable or pinned) gives exactly dg_step on a device copy, and
-    the FP64 result matches the oracle."""
+    the FP64 result matches the oracle.  Single-step calls come first: on a pinned state the
+    FP32-bulk single step reads the state over the host link once, keeps a device copy and adds its
+    last increment to that copy (the same FP64 arithmetic as on a device state)."""
     import torch
-    wl = W.drop_2d(n=5, p=3, seed=2)
+    wl = W.drop_2d(n=5, p=3, seed=2) if maker == "drop" else W.rayleigh_taylor(n=6, p=4)
     s = dg.Solver(wl, precision=precision)
     h = torch.from_numpy(wl.w.copy())
     if pinned:
         h = h.pin_memory()
     d = torch.from_numpy(wl.w.copy()).cuda()
-    s.dg_step(h, wl.dt, 2)
-    s.dg_step(d, wl.dt, 2)
-    s.dg_step(h, wl.dt, 3)  # the staging buffer is reused
-    s.dg_step(d, wl.dt, 3)
+    for k in (1, 1, 2, 3):  # the staging buffer and the device copy are reused
+        s.dg_step(h, wl.dt, k)
+        s.dg_step(d, wl.dt, k)
+        assert np.array_equal(h.numpy(), d.cpu().numpy()), k
     assert s.dg_status_read() == 0
     s.close()
-    assert np.array_equal(h.numpy(), d.cpu().numpy())
     if precision == "fp64":
-        _assert_steps_close(orc, wl, 5, h.numpy(), orc.rk3(problem(orc, wl), wl.w, wl.dt, 5))
+        _assert_steps_close(orc, wl, 7, h.numpy(), orc.rk3(problem(orc, wl), wl.w, wl.dt, 7))
 
 
 # ----------------------------------------------------------------------------- diagnostics
