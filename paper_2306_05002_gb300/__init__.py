@@ -182,10 +182,22 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+_raw_stream = None
+
+
 def _stream(stream=None):
+    """The CUDA stream handle of `stream`, or of torch's current stream on the current device.  The
+    current stream's handle is read with torch's raw-handle query where it exists: building a
+    torch Stream object per call costs microseconds of host time on every library call."""
+    global _raw_stream
+    if stream is not None:
+        return ctypes.c_void_p(stream.cuda_stream)
     import torch
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return ctypes.c_void_p(s.cuda_stream)
+    if _raw_stream is None:
+        _raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", False)
+    if _raw_stream:
+        return ctypes.c_void_p(_raw_stream(torch.cuda.current_device()))
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
 def make_structs(dim, nx, ny, x0, x1, y0, y1, bc, gamma, pinf, rho0, mu=(0.0, 0.0), sigma=0.0, g=(0.0, 0.0),

@@ -294,6 +294,19 @@ def test_step_zero_is_noop(dg):
     s.close()
 
 
+def test_stream_handle_is_torch_current_stream(dg):
+    """The binding passes torch's current stream (the default one, or one made current with
+    torch.cuda.stream) to the library."""
+    import torch
+    from paper_2306_05002_gb300 import _stream
+    assert _stream().value == (torch.cuda.current_stream().cuda_stream or None)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        assert _stream().value == s.cuda_stream
+    assert _stream(s).value == s.cuda_stream
+    assert _stream().value == (torch.cuda.current_stream().cuda_stream or None)
+
+
 @pytest.mark.parametrize("precision,pinned,maker", [
     ("fp64", False, "drop"), ("fp64", True, "drop"), ("fp32bulk", False, "drop"), ("fp32bulk", True, "drop"),
     ("fp32bulk", True, "rt")])
