@@ -963,7 +963,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         units = 7 * wl.N * 3
         value = weak_scaling_value(units, args.steps, world, ms_max)
-        launches = 6 if args.precision == "fp64" else 4  # kernels of one single-step dg_step call
+        launches = main["solver"].dg_step_launches(1)  # kernels of one single-step dg_step call
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",

@@ -230,6 +230,14 @@ const char *dg_last_error(const dg_ctx *ctx);
    -1.  w is not modified.  Synchronises the stream. */
 int dg_time_kernels(dg_ctx *ctx, const double *w, int nrep, double *ms_out, int nmax, void *stream);
 
+/* Number of kernel launches one dg_step call of nsteps >= 0 steps makes on
+   this context (the kernels of its graphs; the step-size update when dt
+   changes is not counted): FP64 6 per step (a volume and a surface kernel per
+   stage); FP32-bulk 1 + 3 nsteps (the first stage's volume kernel, then per
+   stage one fused surface + next-volume kernel, the last stage's surface
+   kernel alone).  -1 for a NULL, batch or kinematic context or nsteps < 0. */
+int dg_step_launches(const dg_ctx *ctx, int nsteps);
+
 /* Algorithmic FP64-equivalent flop and DRAM byte counts per launch of each
    kernel kind (same indexing as dg_time_kernels), from the formulas of the
    scheme (not from counters); returns the number of kinds written (<= nmax),

@@ -33,7 +33,8 @@ PREC = {"fp64": 0, "fp32bulk": 1}
 
 # Every exported symbol of include/dgpf.h.
 EXPORTS = ["dg_create", "dg_destroy", "dg_state_len", "dg_rhs", "dg_step", "dg_step_host", "dg_diag",
-           "dg_status_read", "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_rhs_noalloc", "dg_batch_create",
+           "dg_status_read", "dg_last_error", "dg_time_kernels", "dg_kernel_costs", "dg_step_launches",
+           "dg_rhs_noalloc", "dg_batch_create",
            "dg_batch_step", "dg_rhs_vjp", "dg_adjoint_step", "dg_tape_len", "dg_step_tape",
            "dg_adjoint_step_tape", "dg_adjoint_segment", "dg_batch_tiles", "dg_kin_create", "dg_kin_rhs",
            "dg_kin_step", "dg_kin_nodes", "dg_reinit", "dg_peak_flops", "dg_check_build",
@@ -109,6 +110,8 @@ def load(path: str | None = None):
     lib.dg_kernel_costs.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.c_int]
     lib.dg_kernel_costs.restype = ctypes.c_int
+    lib.dg_step_launches.argtypes = [vp, ctypes.c_int]
+    lib.dg_step_launches.restype = ctypes.c_int
     lib.dg_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(dg_mesh), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(dg_eos), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(dg_opts), ctypes.POINTER(vp)]
@@ -336,6 +339,13 @@ class Solver:
         if n < 0:
             raise DGError(-2, "dg_time_kernels failed")
         return list(out)[:n]
+
+    def dg_step_launches(self, nsteps: int = 1) -> int:
+        """Kernel launches of one dg_step call of nsteps steps (dg_step_launches)."""
+        n = load().dg_step_launches(self.ctx, int(nsteps))
+        if n < 0:
+            raise DGError(-1, "dg_step_launches failed")
+        return n
 
     def dg_kernel_costs(self):
         f = (ctypes.c_double * 8)()

@@ -859,6 +859,12 @@ extern "C" int dg_time_kernels(dg_ctx *c, const double *w, int nrep, double *ms_
   return std::min(nmax, nk);
 }
 
+extern "C" int dg_step_launches(const dg_ctx *c, int nsteps) {
+  if (!c || c->batch || c->kin || nsteps < 0) return -1;
+  if (nsteps == 0) return 0;
+  return c->prec == DG_FP64 ? 6 * nsteps : 1 + 3 * nsteps;  // enqueue_step, enqueue_steps32
+}
+
 extern "C" int dg_kernel_costs(const dg_ctx *c, double *flops, double *bytes, int nmax) {
   if (!c || c->batch || c->kin || !flops || !bytes || nmax < 1) return -1;
   // Algorithmic counts from the formulas of the scheme (an FMA counts 2, a

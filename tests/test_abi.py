@@ -77,6 +77,7 @@ def test_null_context_is_safe(lib):
     assert lib.dg_step(None, None, 1.0, 1, None) == -1
     assert lib.dg_step_host(None, None, 1.0, 1, None) == -1
     assert lib.dg_batch_tiles(None, None, None, None, None, None, 4) == -1
+    assert lib.dg_step_launches(None, 1) == -1
     lib.dg_destroy(None)
     assert isinstance(lib.dg_last_error(None), bytes)
 

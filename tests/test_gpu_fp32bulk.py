@@ -323,3 +323,13 @@ def test_fp32bulk_multi_step_call_matches_single_steps(orc, dg, make, nsteps):
         sc = np.abs(b[v]).max()
         tol = 1e-6 * max(sc, 1e-30) + 3 * nsteps * wl.dt * extra.get(v, 0.0)
         assert np.abs(a[v] - b[v]).max() <= tol, (v, np.abs(a[v] - b[v]).max(), sc, tol)
+
+
+def test_step_launch_counts(dg):
+    """dg_step_launches: FP64 six launches a step, FP32-bulk 1 + 3 n (inviscid and viscous)."""
+    for wl in (W.rayleigh_taylor(n=6, p=4), W.drop_2d(n=6, p=3)):
+        s64, s32 = dg.Solver(wl), dg.Solver(wl, precision="fp32bulk")
+        assert [s64.dg_step_launches(n) for n in (0, 1, 4)] == [0, 6, 24]
+        assert [s32.dg_step_launches(n) for n in (0, 1, 4)] == [0, 4, 13]
+        s64.close()
+        s32.close()
