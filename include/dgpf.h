@@ -196,14 +196,16 @@ dg_status dg_status_read(dg_ctx *ctx, void *stream);
 
 /* Whether this library is the bounds-checked build (1) or the normal one (0).
    The bounds-checked build (compiled with DG_CHECK; libdgpf_check.so) checks
-   the index of every global access of the two-phase model's kernels (FP64,
-   FP32-bulk and batched: node, face-record and neighbour indices) against its
-   array's extent; a failed check skips the access and latches a status bit,
-   which dg_status_read reports as DG_ERR_BOUNDS.  failures (HOST, may be
-   NULL) receives the number of such reports so far in this process, counting
-   bits still latched when a context is destroyed (0 in the normal build).
-   The kinematic, re-initialisation, triangle and adjoint kernels and
-   dg_rhs_noalloc are not checked.  The normal build compiles the checks out. */
+   the index of every global access of the library's kernels on a context
+   (the two-phase model's FP64, FP32-bulk and batched kernels, the adjoint,
+   kinematic, triangle and re-initialisation kernels: node, face-record,
+   velocity-table and neighbour indices) against its array's extent; a failed
+   check skips the access and latches a status bit, which dg_status_read
+   reports as DG_ERR_BOUNDS.  failures (HOST, may be NULL) receives the number
+   of such reports so far in this process, counting bits still latched when a
+   context is destroyed (0 in the normal build).  dg_rhs_noalloc has no
+   context to report through: its kernels check, but nothing counts them.
+   The normal build compiles the checks out. */
 int dg_check_build(long long *failures);
 
 /* Self-test of the bounds-checked build: runs the FP64 volume kernel of a

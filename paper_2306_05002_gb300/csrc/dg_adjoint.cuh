@@ -90,10 +90,16 @@ k_adj_face(const Params prm, const double *__restrict__ lam, const double *__res
   if (le >= EPB || e >= prm.E) return;
   const long stride = (long)prm.E * NFK;
   const int N = prm.N;
+  // the element's nodes (face seeds) and its face records
+  if (!in_bounds(prm.status, (long long)e * NP + NP - 1, N) || !in_bounds(prm.status, (long long)e * NFK + NFK - 1, stride))
+    return;
 
   for (int t = a; t < NFK; t += NP) {
     const int f = t / NK, kk = t % NK;
     const int e2 = neighbour(prm, e, f);
+    if (e2 >= 0 && (!in_bounds(prm.status, (long long)e2 * NP + NP - 1, N) ||
+                    !in_bounds(prm.status, (long long)e2 * NFK + NFK - 1, stride)))
+      continue;
     const bool wall = e2 < 0;
     const bool xf = f < 2;
     const double sg = (f & 1) ? 1.0 : -1.0;
@@ -271,9 +277,9 @@ k_adj_volume(const Params prm, const double *__restrict__ w, const double *__res
   const int le = lane ? le_raw : EPB - 1;
   const int a = threadIdx.x % NP;
   const int e = blockIdx.x * EPB + le;
-  const bool act = lane && e < prm.E;
-  const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
   const int N = prm.N;
+  const bool act = lane && e < prm.E && in_bounds(prm.status, (long long)e * NP + a, N);
+  const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
   const long n = (long)(act ? e : 0) * NP + a;
 
   // ---- forward recomputation (as k_volume)
@@ -366,6 +372,7 @@ k_adj_volume(const Params prm, const double *__restrict__ w, const double *__res
     const long stride = (long)prm.E * NFK;
     auto take = [&](int f, int kk, bool xaxis) {
       const long o = (long)e * NFK + f * NK + kk;
+      if (!in_bounds(prm.status, o, stride)) return;
       double T[NT_INVISCID];
 #pragma unroll
       for (int qf = 0; qf < NT_INVISCID; ++qf) T[qf] = __ldg(trbar + qf * stride + o);

@@ -1507,6 +1507,7 @@ extern "C" dg_status dg_reinit(dg_ctx *c, double *w, int niter, double nu, doubl
     rp.eta_y = c->prm.eta_y;
   }
   rp.ops = c->d_ops;
+  rp.status = c->d_status;
   const double h = c->dim == 2 ? std::min(c->hx, c->hy) : c->hx;
   const double q = 2.0 * c->p + 1.0;
   rp.nu = nu > 0.0 ? nu : h / (2.0 * (c->p + 1));

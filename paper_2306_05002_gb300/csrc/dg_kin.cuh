@@ -181,9 +181,9 @@ k_kin_stage(const KinParams kp, int mode, int kstep, double frac, const double *
   const int le = lane ? le_raw : EPB - 1;
   const int a = threadIdx.x % NP;
   const int e = blockIdx.x * EPB + le;
-  const bool act = lane && e < kp.E;
-  const int i = a % P1, j = a / P1;
   const int N = kp.N;
+  const bool act = lane && e < kp.E && in_bounds(kp.status, (long long)e * NP + a, N);
+  const int i = a % P1, j = a / P1;
   const long n = (long)(act ? e : 0) * NP + a;
   const double2 *vt = reinterpret_cast<const double2 *>(kp.vel_tab);
   // The time factor of the velocity and dt/6, once per CTA: FP64 is this kernel's bound, and a
@@ -202,8 +202,9 @@ k_kin_stage(const KinParams kp, int mode, int kstep, double frac, const double *
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const long m = (long)(act ? kin_neighbour(kp, e, f) : 0) * NP + a;
-      s_nb[le][f][0][a] = __ldg(win + m);
-      s_nb[le][f][1][a] = __ldg(win + N + m);
+      const bool ok = in_bounds(kp.status, m, N);
+      s_nb[le][f][0][a] = ok ? __ldg(win + m) : 0.0;
+      s_nb[le][f][1][a] = ok ? __ldg(win + N + m) : 0.0;
     }
   }
   __syncthreads();
@@ -278,7 +279,9 @@ k_kin_stage(const KinParams kp, int mode, int kstep, double frac, const double *
         mx = qsx * r;
         my = qsy * r;
       }
-      const double2 Um = __ldg(vt + (long)e * NP + am), Up = __ldg(vt + (long)e2 * NP + ap);
+      const long om = (long)e * NP + am, op = (long)e2 * NP + ap;
+      const double2 Um = in_bounds(kp.status, om, N) ? __ldg(vt + om) : make_double2(0.0, 0.0);
+      const double2 Up = in_bounds(kp.status, op, N) ? __ldg(vt + op) : make_double2(0.0, 0.0);
       const double phm = tm[0], psm = tm[1], php = nbp[ap], psp = nbs[ap];
       const double unm = (xf ? Um.x : Um.y) * c * sg, unp = (xf ? Up.x : Up.y) * c * sg;
       const double lam = fmax(fabs(unm), fabs(unp));

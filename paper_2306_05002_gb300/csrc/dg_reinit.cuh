@@ -21,6 +21,7 @@ struct ReinitParams {
   double eps, nu;
   double eta_x, eta_y;
   const double *ops;  // operator table (OpsLayout)
+  unsigned *status;   // the context's status word (the bounds-checked build latches STATUS_BOUNDS)
 };
 
 __device__ __forceinline__ int ri_neighbour(const ReinitParams &rp, int e, int f) {
@@ -62,7 +63,7 @@ k_ri_sign(const ReinitParams rp, double *w, double *S) {
   const int le = lane ? le_raw : EPB - 1;
   const int a = threadIdx.x % NP;
   const int e = blockIdx.x * EPB + le;
-  const bool act = lane && e < rp.E;
+  const bool act = lane && e < rp.E && in_bounds(rp.status, (long long)e * NP + a, rp.N);
   const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
   const long n = (long)(act ? e : 0) * NP + a;
   const double p0 = act ? w[n] - 0.5 : 0.0;
@@ -95,7 +96,7 @@ k_ri_volume(const ReinitParams rp, const double *__restrict__ psi, const double 
   const int le = lane ? le_raw : EPB - 1;
   const int a = threadIdx.x % NP;
   const int e = blockIdx.x * EPB + le;
-  const bool act = lane && e < rp.E;
+  const bool act = lane && e < rp.E && in_bounds(rp.status, (long long)e * NP + a, rp.N);
   const int i = a % P1, j = DIM == 2 ? a / P1 : 0;
   const long n = (long)(act ? e : 0) * NP + a;
   const double ps = act ? __ldg(psi + n) : 0.0;
@@ -120,6 +121,7 @@ k_ri_volume(const ReinitParams rp, const double *__restrict__ psi, const double 
   if (act && (onW || onE || onS || onN)) {
     const long base = (long)e * NFK, stride = (long)rp.E * NFK;
     auto put = [&](int f, int kk, double gn) {
+      if (!in_bounds(rp.status, base + f * NK + kk, stride)) return;
       tr[base + f * NK + kk] = ps;
       tr[stride + base + f * NK + kk] = gn;
     };
@@ -153,15 +155,15 @@ k_ri_surface(const ReinitParams rp, int mode, double dtau, const double *w0, con
   const int le = lane ? le_raw : EPB - 1;
   const int a = threadIdx.x % NP;
   const int e = blockIdx.x * EPB + le;
-  const bool act = lane && e < rp.E;
+  const bool act = lane && e < rp.E && in_bounds(rp.status, (long long)e * NP + a, rp.N);
   const long stride = (long)rp.E * NFK;
   for (int t = a; t < NFK && lane; t += NP) {
     const int f = t / NK, kk = t % NK;
     const int e2 = act ? ri_neighbour(rp, e, f) : -1;
     double flux = 0.0, lift = 0.0;
-    if (e2 >= 0) {
+    const long om = (long)(act ? e : 0) * NFK + t, op = (long)(e2 >= 0 ? e2 : 0) * NFK + (f ^ 1) * NK + kk;
+    if (e2 >= 0 && in_bounds(rp.status, om, stride) && in_bounds(rp.status, op, stride)) {
       const double sg = (f & 1) ? 1.0 : -1.0;
-      const long om = (long)e * NFK + t, op = (long)e2 * NFK + (f ^ 1) * NK + kk;
       const double jump = __ldg(tr + op) - __ldg(tr + om);
       const double gn = 0.5 * (__ldg(tr + stride + op) + __ldg(tr + stride + om)) * sg;
       const double wf = f < 2 ? wfx[kk] : wfy[kk];

@@ -248,8 +248,10 @@ k_tri_stage(const KinParams kp, int mode, int kstep, double frac, const double *
       if (e < kp.E) {
         int f2, src = e;
         if (slot > 0) src = tri_neighbour(kp, e, slot - 1, &f2);
-        a = win[(long)src * NP + n];
-        b = win[N + (long)src * NP + n];
+        if (in_bounds(kp.status, (long)src * NP + n, N)) {
+          a = win[(long)src * NP + n];
+          b = win[N + (long)src * NP + n];
+        }
       }
       double *dst = slot == 0 ? s_w[le][0] : s_nb[le][slot - 1][0];
       dst[n] = a;
@@ -265,7 +267,10 @@ k_tri_stage(const KinParams kp, int mode, int kstep, double frac, const double *
         TriPoint o;
         tri_eval_point<NP, false>(kp, g, s_w[le][0], s_w[le][1], s_t + L.bv() + q * NP, s_t + L.brv() + q * NP,
                            s_t + L.bsv() + q * NP, &o);
-        const double2 U = __ldg(reinterpret_cast<const double2 *>(kp.vel_tab) + (long)e * NPT + q);
+        const long ov = (long)e * NPT + q;
+        const double2 U = in_bounds(kp.status, ov, (long long)kp.E * NPT)
+                              ? __ldg(reinterpret_cast<const double2 *>(kp.vel_tab) + ov)
+                              : make_double2(0.0, 0.0);
         const double u = U.x * c, v = U.y * c;
         const double wq = s_t[L.wv() + q] * g.det;
         cv[0] = -wq * (u * o.gp[0] + v * o.gp[1]);
@@ -291,7 +296,10 @@ k_tri_stage(const KinParams kp, int mode, int kstep, double frac, const double *
         tri_edge_trace<P>(s_t, L, e & 1, f, fk, s_w[le][0], s_w[le][1], g.hl[f], 1.0, &om);
         tri_edge_trace<P>(s_t, L, e2 & 1, f2, fk2, s_nb[le][f][0], s_nb[le][f][1], g2.hl[f2], -1.0, &op);
         const double2 *vt = reinterpret_cast<const double2 *>(kp.vel_tab);
-        const double2 U = __ldg(vt + (long)e * NPT + NQV + fk), U2 = __ldg(vt + (long)e2 * NPT + NQV + fk2);
+        const long vm = (long)e * NPT + NQV + fk, vp = (long)e2 * NPT + NQV + fk2;
+        const long long nt = (long long)kp.E * NPT;
+        const double2 U = in_bounds(kp.status, vm, nt) ? __ldg(vt + vm) : make_double2(0.0, 0.0);
+        const double2 U2 = in_bounds(kp.status, vp, nt) ? __ldg(vt + vp) : make_double2(0.0, 0.0);
         const double m0 = g.m0[f], m1 = g.m1[f];
         const double unm = U.x * c * m0 + U.y * c * m1, unp = U2.x * c * m0 + U2.y * c * m1;
         const double lam = fmax(fabs(unm), fabs(unp));
@@ -350,7 +358,7 @@ k_tri_stage(const KinParams kp, int mode, int kstep, double frac, const double *
     // 5. L = M^-1 R / det and the stage update.
     for (int it = threadIdx.x; it < EPB * NP; it += blockDim.x) {
       const int le = it / NP, n = it % NP, e = e0 + le;
-      if (e >= kp.E) continue;
+      if (e >= kp.E || !in_bounds(kp.status, (long)e * NP + n, N)) continue;
       const double idet = kp.tc[e & 1].idet;
 #pragma unroll
       for (int vv = 0; vv < 2; ++vv) {

@@ -4,10 +4,10 @@ check is latched and the access skipped), the stand-in for a memory checker on t
 
 * its self-test: an inconsistent node count planted on the device (no access leaves its
   allocation) is caught;
-* the GPU parity suites of the full model (FP64, FP32-bulk, batched, walls and normals, lifted
-  gradients, checkpoints, the allocation-free entry) run again in a child process on the checked
-  library, each test also required to leave the process's count of bounds failures unchanged
-  (tests/conftest.py)."""
+* the GPU suites (FP64, FP32-bulk, batched, walls and normals, lifted gradients, checkpoints, the
+  adjoint, the kinematic mode on rectangles and triangles, the re-initialisation, the
+  allocation-free entry) run again in a child process on the checked library, each test also
+  required to leave the process's count of bounds failures unchanged (tests/conftest.py)."""
 import os
 import subprocess
 import sys
@@ -19,7 +19,8 @@ pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SUITES = ["tests/test_gpu_parity.py", "tests/test_gpu_fp32bulk.py", "tests/test_gpu_batch.py",
           "tests/test_gpu_walls_normals.py", "tests/test_gpu_lifting.py", "tests/test_checkpoint.py",
-          "tests/test_zz_no_alloc.py"]
+          "tests/test_gpu_adjoint.py", "tests/test_gpu_kinematic.py", "tests/test_gpu_triangles.py",
+          "tests/test_gpu_reinit.py", "tests/test_zz_no_alloc.py"]
 
 
 def _checked_lib_path():
@@ -45,3 +46,6 @@ def test_gpu_suites_on_the_checked_build(dg):
     cmd = [sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu", "-p", "no:cacheprovider"] + SUITES
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=1500)
     assert r.returncode == 0, r.stdout[-4000:] + r.stderr[-2000:]
+    import re
+    m = re.search(r"(\d+) passed", r.stdout)
+    assert m and int(m.group(1)) >= 150 and " failed" not in r.stdout, r.stdout[-2000:]
