@@ -48,4 +48,5 @@ def test_gpu_suites_on_the_checked_build(dg):
     assert r.returncode == 0, r.stdout[-4000:] + r.stderr[-2000:]
     import re
     m = re.search(r"(\d+) passed", r.stdout)
-    assert m and int(m.group(1)) >= 150 and " failed" not in r.stdout, r.stdout[-2000:]
+    # the suites hold 195 GPU tests: all of them ran, none failed or was skipped
+    assert m and int(m.group(1)) >= 190 and " failed" not in r.stdout and " skipped" not in r.stdout, r.stdout[-2000:]
