@@ -555,8 +555,22 @@ def batched_block(dg, steps, nprob=256, acc_steps=200):
             "one_by_one_fp32bulk": {"value": units / (ms_32 * 1e-3), "ms_per_step": ms_32},
             "one_by_one_fp64": {"value": units / (ms_64 * 1e-3), "ms_per_step": ms_64},
             "speedup_vs_fp64": ms_64 / ms_b, "l2": "working set > L2 (no flush needed)",
+            "roofline": batch_roofline(nodes, ms_b),
             "tiles": tiles, "accuracy": acc,
             "cpu_oracle": oracle_sample(wls[:32], wls, of="the first 32 problems")}
+
+
+def batch_roofline(nodes, ms_step):
+    """Step-level HBM roofline of the batched form: 168 B per node and RK stage (the per-unit figure
+    of the single-problem path) over the whole step's duration, launch gaps and all orders' kernels
+    included -- a lower bound on the fraction the kernels reach while they run."""
+    hbm = peaks().get("hbm_gbs", 6800.0)
+    ach = BYTES_PER_NODE_STAGE * nodes * 3 / (ms_step * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "whole batched step (volume, fused and surface kernels of every order)",
+            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "per_unit": f"{BYTES_PER_NODE_STAGE} B per node and stage x 3 stages x {nodes} nodes",
+            "duration": "step time (CUDA events over the batched steps)",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured"}
 
 
 def rt_block(dg, steps, n=256, paper=False, cpu=False, acc_steps=0, bubble=False):
@@ -886,6 +900,7 @@ def summary(line):
     if "batched" in line:
         b = line["batched"]
         out["config4"] = {"ms_per_step": r3(b["ms_per_step"]), "value": r3(b["value"]),
+                          "frac": r3(b["roofline"]["frac"]) if "roofline" in b else None,
                           "speedup_vs_fp64": r3(b["speedup_vs_fp64"]), "acc_200_max": acc3(b.get("accuracy"))}
     if "rising_bubble" in line:
         rb = line["rising_bubble"]
