@@ -112,7 +112,7 @@ k_surfvol32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ b
   float r[NV];
   StageIO io{b.ws, nullptr, stage == 1 ? nullptr : b.d1, stage == 1 ? b.d1 : b.d2, nullptr, nullptr, nullptr,
              nullptr};
-  surf32_body<P, 2, false, false, EPBX, false, true>(b.prm, b.pf, b.opsf, s_op, blk, stage == 1 ? MODE_S1 : MODE_S2,
+  surf32_body<P, 2, false, false, EPBX, false, true, 1>(b.prm, b.pf, b.opsf, s_op, blk, stage == 1 ? MODE_S1 : MODE_S2,
                                                      b.dt, io, b.rvol[in], b.tr[in], r);
   vol32_body<P, 2, false, false, EPBX>(b.prm, b.pf, b.opsf, s_op, true, blk, nullptr, b.rvol[out], b.tr[out],
                                        nullptr, nullptr, r);
@@ -129,7 +129,8 @@ k_surface32_batch(const BatchProb *__restrict__ probs, const int *__restrict__ b
   int blk;
   const BatchProb &b = stage_descriptor(probs, block0, nprob, s_raw, s_k, &blk);
   StageIO io{nullptr, nullptr, b.d2, nullptr, nullptr, nullptr, b.w64, b.w64};
-  surf32_body<P, 2, false, false, EPBX>(b.prm, b.pf, b.opsf, s_op, blk, MODE_S3, b.dt, io, b.rvol[0], b.tr[0]);
+  surf32_body<P, 2, false, false, EPBX, false, false, 1>(b.prm, b.pf, b.opsf, s_op, blk, MODE_S3, b.dt, io, b.rvol[0],
+                                                        b.tr[0]);
 }
 
 template <int P, int EPBX, int MINB>

@@ -656,7 +656,9 @@ __device__ __forceinline__ void load_trace32(const float *__restrict__ tr, long 
 // with coherent loads.
 // FUSED: the body runs in a fused stage kernel (modes MODE_S1..MODE_S3 with hi_out / lo_out), so the
 // FP64 outputs (MODE_RHS, out64, w64in) are compiled out of it.
-template <int P, int DIM, bool VISC, bool ST, int EPBX = 0, bool PDL = false, bool FUSED = false>
+// FMAP: how face nodes are given to threads (below): 1 block-level, 0 element-level, -1 the default
+// (block-level in 2D at p = 1, 4, 5).
+template <int P, int DIM, bool VISC, bool ST, int EPBX = 0, bool PDL = false, bool FUSED = false, int FMAP = -1>
 __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf, const float *__restrict__ opsf,
                                             float *s_op, int blk, int mode, float dt, const StageIO &io,
                                             const float *__restrict__ rvol, const float *__restrict__ tr,
@@ -665,7 +667,19 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   constexpr int P1 = G::P1, NP = G::NP, EPB = G::EPB, NFK = G::NFK, NK = G::NK;
   constexpr int RW = TRW32;                          // floats per trace record
   constexpr int NC = VISC ? NT32_VISCOUS : TRW32;    // words read per trace record
-  constexpr int FPT = (NFK + NP - 1) / NP;  // face nodes per thread
+  // Face nodes to threads.  Block-level: the block's EPB * NFK face nodes go to consecutive threads
+  // (face node g = tid + fi * THREADS: element g / NFK, its face node g % NFK), so that the face
+  // phase occupies as few warps as it can -- at p = 5 (120 face nodes, 192 threads) four warps
+  // instead of all six, at p = 2 (84 face nodes, 64 threads) one warp for the second pass instead
+  // of both: the batched ensemble's step 7.86 -> 7.61 ms, 64 x 64 p1 16.5 -> 15.7 us, the p = 4
+  // surface kernels 4% faster, outputs bit-identical.  Element-level: the threads of an element
+  // take its own face nodes (face node a + fi * NP), which stays faster for the 1D slab (8.7 vs
+  // 9.8 us a step: its face nodes then spread over both warps of a block) and for single problems
+  // at p = 2 (128 x 128: 12.4 vs 14.4 us per fused launch).  At p = 3 (NFK = NP, EPB * NP threads)
+  // the two give the same assignment.
+  constexpr bool BMAP = FMAP >= 0 ? FMAP == 1 : (DIM == 2 && P != 2 && P != 3);
+  constexpr int NFC = EPB * NFK;
+  constexpr int FPT = BMAP ? (NFC + G::THREADS - 1) / G::THREADS : (NFK + NP - 1) / NP;  // per thread
   const OpsLayout L{P1, NP};
   // Per face node: the surface integrand of the 7 equations (padded to 8 floats)
   // and the 6 lifting coefficients, in planes of consecutive face nodes, so that
@@ -684,11 +698,26 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   const long n = (long)(act ? e : 0) * NP + a;
 
   int e2_[FPT];  // neighbour across the face of each face node (-1: wall)
+  // block-level: face node fi of the thread -- its element's slot fle in the block, index t within the
+  // element (NFK: none), element fe; true when the face node exists
+  auto face_of = [&](int fi, int &fle, int &t, int &fe) {
+    const int g = threadIdx.x + fi * G::THREADS;
+    fle = g < NFC ? g / NFK : 0;
+    t = g < NFC ? g % NFK : NFK;
+    fe = blk * EPB + fle;
+    return g < NFC && fe < prm.E;
+  };
   if (PDL) {
 #pragma unroll
     for (int fi = 0; fi < FPT; ++fi) {
-      const int t = a + fi * NP;
-      e2_[fi] = act && t < NFK ? neighbour(prm, e, t / NK) : -1;
+      if constexpr (BMAP) {
+        int fle, t, fe;
+        const bool fv = face_of(fi, fle, t, fe);
+        e2_[fi] = fv ? neighbour(prm, fe, t / NK) : -1;
+      } else {
+        const int t = a + fi * NP;
+        e2_[fi] = act && t < NFK ? neighbour(prm, e, t / NK) : -1;
+      }
     }
     for (int t = threadIdx.x; t < L.size(); t += blockDim.x) s_op[t] = opsf[t];
     grid_dependency_wait();
@@ -717,12 +746,20 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
   float Cm_[FPT][NC], Cp_[FPT][NC];
 #pragma unroll
   for (int fi = 0; fi < FPT; ++fi) {
-    const int t = a + fi * NP;
-    const bool fv = act && t < NFK;
+    int t, fe;
+    bool fv;
+    if constexpr (BMAP) {
+      int fle;
+      fv = face_of(fi, fle, t, fe);
+    } else {
+      t = a + fi * NP;
+      fv = act && t < NFK;
+      fe = e;
+    }
     const int f = fv ? t / NK : 0, kk = fv ? t % NK : 0;
-    const int e2 = PDL ? e2_[fi] : (fv ? neighbour(prm, e, f) : -1);
+    const int e2 = PDL ? e2_[fi] : (fv ? neighbour(prm, fe, f) : -1);
     e2_[fi] = e2;
-    const long om = (long)(act ? e : 0) * NFK + (fv ? t : 0);
+    const long om = (long)(BMAP ? (fv ? fe : 0) : (act ? e : 0)) * NFK + (fv ? t : 0);
     const long op = (long)(e2 >= 0 ? e2 : 0) * NFK + (f ^ 1) * NK + kk;
     const long long ntr = (long long)prm.E * NFK;
     load_trace32<NC, RW, PDL>(tr, om, fv && in_bounds(prm.status, om, ntr), Cm_[fi], 1.f);
@@ -738,8 +775,16 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
 
 #pragma unroll
   for (int fi = 0; fi < FPT; ++fi) {
-    const int t = a + fi * NP;
-    if (!lane || t >= NFK) continue;
+    int fle, t;
+    if constexpr (BMAP) {
+      int fe;
+      face_of(fi, fle, t, fe);
+      if (t >= NFK) continue;
+    } else {
+      t = a + fi * NP;
+      if (!lane || t >= NFK) continue;
+      fle = le;
+    }
     const int f = t / NK, kk = t % NK;
     const bool wall = e2_[fi] < 0;
     const bool xf = f < 2;
@@ -851,10 +896,10 @@ __device__ __forceinline__ void surf32_body(const Params &prm, const ParamsF &pf
       const float tup = tpx * Tp[T_U] + tpy * Tp[T_V];
       S[RE] += wf * (0.5f * (tup - tum) + eta * mua * (kp - km));
     }
-    s_surf[0][le][t] = make_float4(S[0], S[1], S[2], S[3]);
-    s_surf[1][le][t] = make_float4(S[4], S[5], S[6], 0.f);
-    s_lift0[le][t] = make_float4(lift[0], lift[1], lift[2], lift[3]);
-    s_lift1[le][t] = make_float2(lift[4], lift[5]);
+    s_surf[0][fle][t] = make_float4(S[0], S[1], S[2], S[3]);
+    s_surf[1][fle][t] = make_float4(S[4], S[5], S[6], 0.f);
+    s_lift0[fle][t] = make_float4(lift[0], lift[1], lift[2], lift[3]);
+    s_lift1[fle][t] = make_float2(lift[4], lift[5]);
   }
   __syncthreads();
 
