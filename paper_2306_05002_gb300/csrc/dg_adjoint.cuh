@@ -463,23 +463,29 @@ k_adj_volume(const Params prm, const double *__restrict__ w, const double *__res
     }
   }
   // closure: c (face nodes), k, B, P, u, v, rho
+  // (one reciprocal of the mixture denominator: this kernel is bound by the FP64 pipe, where each
+  // division is several operations)
   double bCm = 0.0, bden = 0.0, bir = 0.0;
+  const double iden = 1.0 / den;
   if (bc != 0.0) {
-    const double X = Pr + (Pr + Cm) / den;
+    const double PC = Pr + Cm;
+    const double X = Pr + PC * iden;
     const double c = sqrt(X * ir);
-    const double bX = bc * ir / (2.0 * c);
-    bir += bc * X / (2.0 * c);
-    bP += bX * (1.0 + 1.0 / den);
-    bCm += bX / den;
-    bden -= bX * (Pr + Cm) / (den * den);
+    const double h = 0.5 / c;  // 1 / (2 c)
+    const double bX = bc * ir * h;
+    bir += bc * X * h;
+    bP += bX * (1.0 + iden);
+    bCm += bX * iden;
+    bden -= bX * PC * iden * iden;
   }
   bu += u * bk;
   bv += v * bk;
   bP += prm.Bp * bB;
   // P = (rhoE - rhok - Cm) / den, rhok = (ru^2 + rv^2) / (2 rho)
-  const double brhoe = bP / den;
-  bCm -= bP / den;
-  bden -= bP * Pr / den;
+  const double bPd = bP * iden;
+  const double brhoe = bPd;
+  bCm -= bPd;
+  bden -= bPd * Pr;
   bw[RE] += brhoe;
   const double brhok = -brhoe;
   bw[RU] += brhok * q[RU] * ir;
