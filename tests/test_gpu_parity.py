@@ -309,14 +309,15 @@ def test_stream_handle_is_torch_current_stream(dg):
 
 @pytest.mark.parametrize("precision,pinned,maker", [
     ("fp64", False, "drop"), ("fp64", True, "drop"), ("fp32bulk", False, "drop"), ("fp32bulk", True, "drop"),
-    ("fp32bulk", True, "rt")])
+    ("fp32bulk", True, "rt"), ("fp32bulk", True, "drop64")])
 def test_step_host_buffer_round_trip(orc, dg, precision, pinned, maker):
     """dg_step_host (a CPU tensor, pageable or pinned) gives exactly dg_step on a device copy, and
     the FP64 result matches the oracle.  Single-step calls come first: on a pinned state the
     FP32-bulk single step reads the state over the host link once, keeps a device copy and adds its
     last increment to that copy (the same FP64 arithmetic as on a device state)."""
     import torch
-    wl = W.drop_2d(n=5, p=3, seed=2) if maker == "drop" else W.rayleigh_taylor(n=6, p=4)
+    wl = {"drop": lambda: W.drop_2d(n=5, p=3, seed=2), "rt": lambda: W.rayleigh_taylor(n=6, p=4),
+          "drop64": lambda: W.drop_2d(n=64, p=3, seed=2)}[maker]()  # drop64: the end-to-end workload
     s = dg.Solver(wl, precision=precision)
     h = torch.from_numpy(wl.w.copy())
     if pinned:
