@@ -33,11 +33,11 @@ enum KinMode { KIN_RHS = 0, KIN_K1 = 1, KIN_K2 = 2, KIN_K3 = 3, KIN_K4 = 4 };
 
 // Constants of one triangle type of the split-rectangle mesh (dg_tri.cuh): det = d(x,y)/d(r,s),
 // its inverse, the inverse-map derivatives, and per edge f the outward unit normal m, half the
-// edge length, the penalty eta_tri / h_e and the reference components of grad l . m
-// (gr = rx m0 + ry m1, gs = sx m0 + sy m1).
+// edge length and its reciprocal, the penalty eta_tri / h_e and the reference components of
+// grad l . m (gr = rx m0 + ry m1, gs = sx m0 + sy m1).
 struct TriConst {
   double det, idet, rx, ry, sx, sy;
-  double m0[3], m1[3], hl[3], eta[3], gr[3], gs[3];
+  double m0[3], m1[3], hl[3], ihl[3], eta[3], gr[3], gs[3];
 };
 
 struct KinParams {

@@ -40,6 +40,7 @@ void tri_constants(double hx, double hy, double eta_tri, TriConst tc[2]) {
       g.m0[f] = dy / len;
       g.m1[f] = -dx / len;
       g.hl[f] = 0.5 * len;
+      g.ihl[f] = 2.0 / len;
       g.eta[f] = eta_tri / (2.0 * (2.0 * g.det) / len);  // h_e = 2 |T| / |e|, |T| = 2 det
       g.gr[f] = g.rx * g.m0[f] + g.ry * g.m1[f];
       g.gs[f] = g.sx * g.m0[f] + g.sy * g.m1[f];

@@ -180,14 +180,15 @@ __device__ __forceinline__ void tri_eval_point(const KinParams &kp, const TriCon
 
 // phi, psi, d(phi)/dm and n . m at one edge point, m = sgn x the outward normal of the
 // triangle's edge f (sgn = -1: a neighbour's trace, seen along the normal of the triangle being
-// updated).  hl: half the edge length (d/dt = hl d/dtau along the edge).
+// updated).  ihl: the reciprocal of half the edge length (d/dtau = hl d/dt along the edge; a
+// product, not a division, on the FP64 pipe that bounds the kernel).
 struct TriEdgeTrace {
   double phi, psi, dphi_m, n_m;
 };
 
 template <int P>
 __device__ __forceinline__ void tri_edge_trace(const double *s_t, const TriLayout &L, int type, int f, int fk,
-                                               const double *fphi, const double *fpsi, double hl, double sgn,
+                                               const double *fphi, const double *fpsi, double ihl, double sgn,
                                                TriEdgeTrace *o) {
   constexpr int P1 = P + 1, NP = (P + 1) * (P + 2) / 2;
   const double *bev = s_t + L.bev() + fk * P1, *bet = s_t + L.bet() + fk * P1;
@@ -205,7 +206,7 @@ __device__ __forceinline__ void tri_edge_trace(const double *s_t, const TriLayou
     gp = fma(bn[n], fphi[n], gp);
     gs = fma(bn[n], fpsi[n], gs);
   }
-  const double st = pt / hl;  // tangential derivative of psi
+  const double st = pt * ihl;  // tangential derivative of psi
   const double g2 = gs * gs + st * st;
   o->phi = ph;
   o->psi = ps;
@@ -293,8 +294,8 @@ k_tri_stage(const KinParams kp, int mode, int kstep, double frac, const double *
         const int fk2 = f2 * NQ1 + (NQ1 - 1 - k);  // the same physical point, seen from the neighbour
         const TriConst &g = kp.tc[e & 1], &g2 = kp.tc[e2 & 1];
         TriEdgeTrace om, op;
-        tri_edge_trace<P>(s_t, L, e & 1, f, fk, s_w[le][0], s_w[le][1], g.hl[f], 1.0, &om);
-        tri_edge_trace<P>(s_t, L, e2 & 1, f2, fk2, s_nb[le][f][0], s_nb[le][f][1], g2.hl[f2], -1.0, &op);
+        tri_edge_trace<P>(s_t, L, e & 1, f, fk, s_w[le][0], s_w[le][1], g.ihl[f], 1.0, &om);
+        tri_edge_trace<P>(s_t, L, e2 & 1, f2, fk2, s_nb[le][f][0], s_nb[le][f][1], g2.ihl[f2], -1.0, &op);
         const double2 *vt = reinterpret_cast<const double2 *>(kp.vel_tab);
         const long vm = (long)e * NPT + NQV + fk, vp = (long)e2 * NPT + NQV + fk2;
         const long long nt = (long long)kp.E * NPT;
