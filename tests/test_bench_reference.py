@@ -37,3 +37,13 @@ def test_summary_digest_of_a_line():
     assert s["config4"]["acc_200_max"][1] != s["config4"]["acc_200_max"][1]  # a NaN stays a NaN
     assert "config3" not in s and "config1" not in s
     assert len(json.dumps(s)) < 1000
+
+
+def test_batch_roofline_units():
+    """The batched step's roofline: 168 B per node and stage, three stages a step, over the step time,
+    against the measured HBM copy rate."""
+    import bench
+    r = bench.batch_roofline(nodes=1_000_000, ms_step=1.0)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 168 * 3 * 1_000_000 / 1e-3 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
